@@ -1,0 +1,298 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled LB-EHD step (MLUPS) and the HBM roofline fraction of its
+dominant kernel on B300.
+
+One benchmark step = ``--lb-steps`` coupled lattice Boltzmann time steps (phase moments
+and wetting ghosts, Poisson solve, forces, fused collide + stream of all populations,
+observable reductions) of the workload, whose state (~350 MB for the 128x64x64 lattice)
+is larger than L2, so no L2 flush is needed between steps.
+
+Arms:
+  default            the CUDA library through its C ABI, inputs resident in HBM;
+  --impl reference   the FP64 CPU oracle on the host cores (a deliberately slow program;
+                     reported as a baseline, not a target).
+Multi-GPU (torchrun): independent replicas, one per GPU; no collective on the data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Coupled LB-EHD MLUPS, % of HBM roofline; batched/adjoint vs plain on 1 B300"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6400.0
+
+# Algorithmic bytes per fluid-site update of the fused collide kernel (FP32): every
+# population read once and written once (3D: 19 + 3*19 + 7 = 83 floats each way), plus the
+# site's own fields: Phi_i and Phi_i^{n-1} (24), rho_e and rho_e^{n-1} (8), u read+write (24),
+# conduction source read+write (8), potential (4), node class (1).
+COLLIDE_BYTES = {3: 83 * 4 * 2 + 24 + 8 + 24 + 8 + 4 + 1, 2: 41 * 4 * 2 + 24 + 8 + 24 + 8 + 4 + 1}
+# Whole-step model of the hot path per site update: populations read + written once
+# (664 B in 3D), macroscopic fields ~92 B, and ~16 B per Poisson sweep.
+STEP_BYTES = {3: (756, 16), 2: (388, 12)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(workload, steps, budget_s=None):
+    """Time the FP64 oracle as it stands on the host cores: (MLUPS, steps run, cores)."""
+    from oracle import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    w = workload
+    sim = O.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        sim.step(1)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return w.sites * done / dt / 1e6, done, O.get_threads(), dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2608_12868_b300 import workloads as W
+    w = W.WORKLOADS[args.workload]()
+    total = args.steps + args.warmup
+    budget = float(os.environ.get("LBEHD_REF_BUDGET_S", "150"))
+    mlups, done, cores, dt = cpu_oracle_rate(w, total, budget_s=budget)
+    sample = (f"{done} coupled steps of the full {'x'.join(map(str, w.shape[::-1]))} lattice "
+              f"(of {total} requested; capped at {budget:.0f} s), FP64, {cores} threads")
+    line = {
+        "metric": METRIC, "value": mlups, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / done * 1e3 * args.lb_steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "sites": w.sites, "lb_steps_per_step": args.lb_steps},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2608_12868_b300 import lbehd
+    from paper_2608_12868_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]()
+    stream = torch.cuda.Stream(dev)
+    mode = lbehd.POISSON_FIXED if args.poisson == "fixed" else lbehd.POISSON_HOST
+    sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=mode,
+                           poisson_fixed_sweeps=args.fixed_sweeps,
+                           poisson_check_every=args.check_every)
+    L = args.lb_steps
+    fluid = int((w.solid == 0).sum())
+    for _ in range(args.warmup):
+        sim.step(L)
+    warm_obs = sim.observe()
+
+    # ---------------- timed region: device time, inputs resident in HBM
+    sim.profile(True)
+    n0 = sim.launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.step(L)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = sim.launch_count() - n0
+    ms = ev0.elapsed_time(ev1)
+    prof = sim.profile_read()
+    sim.profile(False)
+    obs = sim.observe()
+    ms_max = max_over_ranks(world, ms, dev)
+    value = w.sites * L * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # ---------------- end to end through the C ABI with host buffers
+    Vh = np.ascontiguousarray(w.params.get("V", []), dtype=np.float64)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_electrodes(Vh)      # per-step input: electrode potentials (host -> device)
+        sim.step(L)
+        sim.observe()               # per-step result: droplet observables (device -> host)
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e = w.sites * L * args.steps * world / e2e_s / 1e6
+
+    # ---------------- roofline of the dominant kernel (fused collide + stream)
+    peak, peak_kind = measured_peaks()
+    coll_ms, coll_n = prof["collide"]
+    coll_avg_s = coll_ms / max(coll_n, 1) / 1e3
+    coll_bytes = fluid * COLLIDE_BYTES[w.dim] + w.sites
+    achieved = coll_bytes / coll_avg_s / 1e9
+    sweeps_per_step = prof["sor"][1] / max(L * args.steps, 1)
+    sb, sp = STEP_BYTES[w.dim]
+    step_bytes = w.sites * (sb + sp * sweeps_per_step)
+    step_gbs = step_bytes / (ms / 1e3 / (L * args.steps)) / 1e9
+    share = {k: round(v[0] / ms, 4) for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, done, cores, dt = cpu_oracle_rate(w, args.cpu_steps)
+        cpu = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {done} coupled steps of the same lattice, FP64, {dt:.1f} s"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": w.name, "sites": w.sites, "fluid_sites": fluid,
+                "lb_steps_per_step": L, "parallelism": f"replicas{world}",
+                "poisson": args.poisson, "poisson_sweeps_per_lb_step": sweeps_per_step,
+                "l2": "state (~350 MB) larger than the 126 MB L2; no flush",
+                "step_bytes_model_per_site": sb + sp * sweeps_per_step,
+                "step_gbs_model": step_gbs,
+                "kernel_time_share": share,
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_collide<3>", "peak_source": peak_kind,
+                         "bytes_per_launch": coll_bytes},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * len(Vh),
+                    "d2h_bytes_per_step": 2 * 16 * 8 + 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "obs_status": obs["status"],
+            "mass_drift": float(np.abs(obs["mass"] / warm_obs["mass"] - 1).max()),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="droplet_3d_128x64x64")
+    ap.add_argument("--lb-steps", type=int, default=20)
+    ap.add_argument("--poisson", choices=["host", "fixed"], default="host")
+    ap.add_argument("--fixed-sweeps", type=int, default=8)
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * lbehd.h -- C ABI of the B300 (sm_103a) coupled lattice Boltzmann electrohydrodynamics
+ * step: ternary conservative phase field (droplet, lubricant, ambient), incompressible
+ * momentum, leaky-dielectric charge transport and Gauss law, on micropillar geometry.
+ *
+ * Method: "Controlling the dynamics of an electric-field-driven droplet on a
+ * lubricant-infused micropillar surface", Methods:
+ *   conservative Allen-Cahn (Eq. 8), Navier-Stokes with capillary and electric forces
+ *   (Eq. 9), ternary chemical potential (Eqs. 10-11), electric force (Eq. 12),
+ *   Gauss law (Eq. 13), charge transport (Eq. 14), raw-moment MRT collision of the phase
+ *   field (Eqs. 15-19), wetting condition (Eq. 20a), momentum and charge collisions
+ *   (Eq. 20b), and the inner Poisson iterations that precede each hydrodynamic step.
+ *
+ * Conventions for every entry point:
+ *  - Return value 0 (LBEHD_OK) on success, a negative LBEHD_ERR_* code otherwise.
+ *    No C++ exception crosses this boundary. lbehd_last_error() gives a message.
+ *  - Host pointers passed in are borrowed for the duration of the call only.
+ *  - Device memory is owned by the handle until lbehd_destroy(); it is obtained from
+ *    cfg->alloc/cfg->free when given (e.g. PyTorch's caching allocator), else cudaMalloc.
+ *  - All GPU work is enqueued on cfg->stream (a cudaStream_t; NULL = legacy stream).
+ *    lbehd_step() returns after enqueueing, except for the host round trips of the
+ *    Poisson convergence test (see lbehd_config.poisson_mode). lbehd_observe(),
+ *    lbehd_copy_out() and lbehd_destroy() synchronise the stream.
+ *  - Lattice: site index i = x + nx * (y + ny * z), x fastest. 2D runs use nz = 1 and the
+ *    vertical axis is y; 3D runs use z. All axes are periodic; walls are solid nodes.
+ *  - Velocity order (shared with the parity tests): rest first, then each moving
+ *    velocity followed by its opposite.
+ *      D2Q9 : (0,0) (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)
+ *      D3Q19: (0,0,0) +-x +-y +-z (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *             (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *      D2Q5 / D3Q7 (charge): rest, +-x, +-y (, +-z)
+ */
+#ifndef LBEHD_H
+#define LBEHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBEHD_ABI_VERSION 1
+
+#define LBEHD_OK 0
+#define LBEHD_ERR_INVALID_ARG (-1)
+#define LBEHD_ERR_OOM (-2)
+#define LBEHD_ERR_POISSON_NOCONV (-3) /* step completed, Poisson hit its iteration cap */
+#define LBEHD_ERR_NONFINITE (-4)      /* a NaN/Inf appeared in the state */
+#define LBEHD_ERR_CUDA (-5)
+#define LBEHD_ERR_STATE (-6)          /* call not valid in the handle's current state */
+
+#define LBEHD_MAX_ELECTRODES 64
+
+/* Poisson convergence control. */
+#define LBEHD_POISSON_HOST 0   /* host checks the FP64 residual every poisson_check_every sweeps */
+#define LBEHD_POISSON_FIXED 1  /* exactly poisson_fixed_sweeps sweeps per step, residual recorded */
+
+/* Solid classes (cfg->solid): 0 fluid, 1 substrate (wetting angles theta_ij apply),
+ * 2 neutral wall (all angles 90 degrees). Electrode ids (cfg->electrode_id), meaningful
+ * on solid nodes only: -1 zero-flux wall, -2 grounded (phi = 0), k >= 0 electrode k held
+ * at electrode_V[k]. */
+typedef struct lbehd_config {
+    int dim;                 /* 2 (D2Q9 + D2Q5) or 3 (D3Q19 + D3Q7) */
+    int nx, ny, nz;          /* lattice extents; nz = 1 in 2D; nx (and ny in 3D) even */
+    const uint8_t *solid;    /* host, N solid classes */
+    const int16_t *electrode_id; /* host, N ids */
+    const double *phi_init;  /* host, 3*N initial Phi_1..3 (droplet, lubricant, ambient) */
+    double nu[3];            /* kinematic viscosity per phase; nu = sum Phi_i nu_i */
+    double eps[3];           /* permittivity per phase; eps = sum Phi_i eps_i */
+    double sigma[3];         /* conductivity per phase; sigma = sum Phi_i sigma_i */
+    double gamma12, gamma13, gamma23; /* pairwise surface tensions (Eq. 11) */
+    double theta12, theta13, theta23; /* contact angles on class-1 solid, degrees (Eq. 20a) */
+    double mobility;         /* M of Eq. 8 (0.0025); tau_Phi = 1/2 + M / c_s^2 */
+    double W;                /* interface width (5) */
+    double alpha;            /* charge diffusivity of Eq. 14 */
+    double body_force[3];    /* uniform body force density added to F */
+    double s_bulk;           /* relaxation rate of the trace of the momentum flux (1) */
+    double poisson_tol;      /* relative residual ||b - A phi||_2 / ||b||_2 to stop at */
+    int poisson_max_iter;    /* red-black sweep cap per step */
+    int poisson_check_every; /* sweeps between residual checks (LBEHD_POISSON_HOST) */
+    int poisson_mode;        /* LBEHD_POISSON_HOST or LBEHD_POISSON_FIXED */
+    int poisson_fixed_sweeps;/* sweeps per step in LBEHD_POISSON_FIXED */
+    double poisson_omega;    /* SOR factor; <= 0 picks 2 / (1 + sin(pi / H_vertical)) */
+    int n_electrodes;
+    const double *electrode_V; /* host, n_electrodes initial potentials */
+    void *(*alloc)(size_t bytes, void *ctx); /* optional device allocator */
+    void (*free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+    void *stream;            /* cudaStream_t */
+} lbehd_config;
+
+/* Droplet observables of the last completed step (FP64 sums over fluid nodes of the
+ * fields computed in that step). */
+typedef struct lbehd_obs {
+    long long step;          /* index of the step the fields belong to */
+    double M1;               /* sum Phi_1 (droplet volume) */
+    double centroid[3];      /* sum Phi_1 x / M1 */
+    double velocity[3];      /* sum Phi_1 u / M1 */
+    double f_ele[3];         /* electric force on the droplet, sum Phi_1 F_e */
+    double f_ele_total[3];   /* sum F_e over the fluid */
+    double f_drag[3];        /* f_ele - M1 (V^n - V^{n-1}): drag from the force balance */
+    double mass[3];          /* sum Phi_i, per component */
+    double charge;           /* sum rho_e */
+    int poisson_iters;       /* sweeps used by the last step's Poisson solve */
+    double poisson_resid;    /* its final relative residual */
+    int status;              /* LBEHD_OK or the first error code recorded */
+} lbehd_obs;
+
+typedef struct lbehd_handle lbehd_handle;
+
+/* Arrays that lbehd_copy_out / lbehd_device_ptr can reach. Populations are the
+ * pre-collision state at the current time; fields are those computed in the last step.
+ * FP32 throughout. Layouts (N = nx*ny*nz, Q = 9/19, QS = 5/7):
+ *   LBEHD_G     Q*N     momentum populations stored SHIFTED: g_n - w_n
+ *   LBEHD_FPHI  3*Q*N   phase-field populations [component][velocity][site]
+ *   LBEHD_FRHO  QS*N    charge populations
+ *   LBEHD_PHI   3*N     Phi_1..3 (boundary solid nodes hold the wetting ghosts)
+ *   LBEHD_RHO   N       rho_e
+ *   LBEHD_POT   N       electric potential (Dirichlet nodes hold their value)
+ *   LBEHD_U     3*N     velocity u = j + F/2
+ *   LBEHD_QSRC  N       conduction source div(sigma grad phi)
+ *   LBEHD_EPS   N       permittivity */
+enum lbehd_array {
+    LBEHD_G = 0, LBEHD_FPHI, LBEHD_FRHO, LBEHD_PHI, LBEHD_RHO, LBEHD_POT, LBEHD_U,
+    LBEHD_QSRC, LBEHD_EPS, LBEHD_NARRAYS
+};
+
+/* ABI version and sizeof(lbehd_config), for binding checks. */
+int lbehd_abi_version(void);
+size_t lbehd_config_size(void);
+
+/* Validate cfg, build the geometry tables (node classes, wetting normals), allocate the
+ * state and set the populations to equilibrium with u = 0, p = 1, rho_e = 0 and
+ * Phi = cfg->phi_init. Writes the new handle to *out. */
+int lbehd_init(const lbehd_config *cfg, lbehd_handle **out);
+
+/* Advance n >= 0 coupled steps: phase moments and wetting ghosts, Poisson solve, forces,
+ * fused collide + push-stream of the momentum, three phase-field and charge populations,
+ * observable reductions. Returns LBEHD_ERR_POISSON_NOCONV if any solve hit the cap
+ * (the steps are still completed). */
+int lbehd_step(lbehd_handle *h, int n);
+
+/* Set the electrode potentials used from the next step on (Dirichlet values of the
+ * Gauss law; the programmable switching of the Results). n must equal cfg->n_electrodes. */
+int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n);
+
+/* Synchronise the stream and fill *out with the last step's observables. Returns
+ * LBEHD_ERR_NONFINITE if a non-finite value was detected. */
+int lbehd_observe(lbehd_handle *h, lbehd_obs *out);
+
+/* Copy one array (enum lbehd_array) to host memory dst of at least *bytes; synchronises. */
+int lbehd_copy_out(lbehd_handle *h, int which, void *dst, size_t bytes);
+
+/* Device pointer and size in bytes of one array (valid until the next lbehd_step). */
+int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
+
+/* Number of kernels launched by this handle since init (for launch accounting). */
+long long lbehd_launch_count(lbehd_handle *h);
+
+/* Per-kernel device time, for roofline accounting: while profiling is enabled every
+ * launch of the handle is bracketed by CUDA events recorded on cfg->stream. Kernel
+ * classes: */
+#define LBEHD_KC_FIELDS 0   /* moments + wetting ghosts */
+#define LBEHD_KC_SOR 1      /* red-black Poisson sweeps */
+#define LBEHD_KC_RESIDUAL 2 /* residual norm and its final reduction */
+#define LBEHD_KC_COLLIDE 3  /* fused forces + collide + stream of all populations */
+#define LBEHD_KC_OBS 4      /* observable reduction */
+#define LBEHD_NKC 5
+
+/* Start (enable != 0) or stop recording. Enabling clears earlier records. */
+int lbehd_profile_enable(lbehd_handle *h, int enable);
+
+/* Synchronise and return, per kernel class, the summed device time in ms (ms[LBEHD_NKC])
+ * and the number of launches (count[LBEHD_NKC]) recorded since profiling was enabled. */
+int lbehd_profile_read(lbehd_handle *h, double *ms, long long *count);
+
+/* Message of the last error on this handle (or of the last failed init when h is NULL). */
+const char *lbehd_last_error(lbehd_handle *h);
+
+/* Free every device buffer (through cfg->free when given) and the handle. */
+void lbehd_destroy(lbehd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBEHD_H */

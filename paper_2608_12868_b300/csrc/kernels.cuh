@@ -1,0 +1,662 @@
+// kernels.cuh -- device kernels of the coupled LB-EHD step (sm_103a, FP32 state).
+//
+// One step n -> n+1 runs:
+//   k_fields    Phi_i = sum_n f_Phi_i,n (Eq. 19), rho_e = sum f_rho, permittivity, wetting
+//               ghosts on boundary solid nodes (Eq. 20a), Dirichlet potentials;
+//   k_sor / k_residual   red-black SOR on div(eps grad phi) = -rho_e (Eq. 13) with an FP64
+//               residual norm;
+//   k_collide   per fluid site, everything else fused: isotropic stencils of Phi_i and phi,
+//               chemical potential (Eqs. 10-11), capillary and electric forces (Eq. 12),
+//               sharpening flux (Eq. 18), conduction source of Eq. 14, then collide and
+//               push-stream the momentum, three phase-field (Eqs. 15-17) and charge
+//               populations with halfway bounce-back, and block partial sums (FP64) of the
+//               droplet observables;
+//   k_obs_final the deterministic FP64 sum of those partials.
+//
+// The raw-moment MRT collisions are evaluated in closed form. With every moment of order
+// >= 3 relaxing at rate 1 (and the trace of the momentum flux at s_bulk), M^-1 m* reduces
+// to  f* = f_eq + C/2 + sum_k (1 - s_k) delta_k col_k,  where delta_k is moment k of
+// f - f_eq + C/2 and col_k is column k of M^-1 (only the moments with s_k != 1 appear).
+// The columns used, for the raw monomial basis with a trace / deviatoric second-order
+// block:
+//   first order e_a          : +1/2 on +a, -1/2 on -a
+//   3D  ex^2 - ey^2          : 1/6 on +-x, -1/3 on +-y, 1/6 on +-z
+//   3D  ex^2 - ez^2          : 1/6 on +-x, 1/6 on +-y, -1/3 on +-z
+//   3D  trace e^2            : 1/6 on every axis velocity, -1 on rest
+//   2D  ex^2 - ey^2          : 1/4 on +-x, -1/4 on +-y;  trace: 1/4 on axes, -1 on rest
+//   ea eb (a != b)           : ea eb / 4 on the four diagonals of the (a, b) plane
+// Momentum populations are stored shifted, g_n - w_n, so FP32 keeps the small pressure
+// and velocity deviations.
+#pragma once
+
+#include <cstdint>
+
+#include "lattice.cuh"
+
+namespace lbehd {
+
+constexpr int NOBS = 16;      // observable accumulators per block
+constexpr int BX = 128;       // threads per block along x
+
+// info byte: bits 0-1 potential type, bits 2-3 wetting class.
+enum : uint8_t { PT_FLUID = 0, PT_DIRICHLET = 1, PT_NEUMANN = 2 };
+
+struct Params {
+    int nx, ny, nz;
+    long long N;
+    float nu[3], eps[3], sig[3];
+    float Y[3], YT;
+    float cos12, cos13, cos23;
+    float W;
+    float inv_tau_phi, inv_tau_rho;
+    float s_bulk;
+    float body[3];
+};
+
+struct State {
+    const float *g, *fphi, *frho;     // pre-collision populations at time n
+    float *g_out, *fphi_out, *frho_out;
+    const float *phi, *phi_prev;      // [3][N] Phi at n and n-1
+    const float *rho, *rho_prev;      // rho_e at n and n-1
+    float *u, *q;                     // u and conduction source: read as n-1, written as n
+    const float *pot;
+    const uint8_t *info;
+    double *obs_partials;             // [NOBS][nblocks]
+    int *flag;                        // bit 0: non-finite value seen
+};
+
+template <class L>
+__device__ __forceinline__ size_t nbr_index(int n, int x, int y, int z, int xp, int xm, int yp,
+                                            int ym, int zp, int zm, int nx, int ny)
+{
+    const int X = L::ex(n) > 0 ? xp : (L::ex(n) < 0 ? xm : x);
+    const int Y = L::ey(n) > 0 ? yp : (L::ey(n) < 0 ? ym : y);
+    const int Z = L::ez(n) > 0 ? zp : (L::ez(n) < 0 ? zm : z);
+    return (size_t)X + (size_t)nx * ((size_t)Y + (size_t)ny * (size_t)Z);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- initial state
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_init(Params P, const float *__restrict__ phi0,
+                                             float *__restrict__ g, float *__restrict__ fphi,
+                                             float *__restrict__ frho,
+                                             const uint8_t *__restrict__ info)
+{
+    using L = Lat<D>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx)
+        return;
+    const size_t N = P.N, i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    const bool fluid = (info[i] & 3) == PT_FLUID;
+#pragma unroll
+    for (int n = 0; n < L::Q; n++) {
+        g[n * N + i] = 0.0f;   // shifted: g_n - w_n with p* = 1, u = 0
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            fphi[(c * L::Q + n) * N + i] = fluid ? phi0[c * N + i] * L::w(n) : 0.0f;
+    }
+#pragma unroll
+    for (int n = 0; n < L::QS; n++)
+        frho[n * N + i] = 0.0f;
+}
+
+// ---------------------------------------------------------------- moments + ghosts
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict__ fphi,
+                                               const float *__restrict__ frho,
+                                               float *__restrict__ phi_out,
+                                               float *__restrict__ rho_out,
+                                               float *__restrict__ eps_out, float *__restrict__ pot,
+                                               const uint8_t *__restrict__ info,
+                                               const uint8_t *__restrict__ normal,
+                                               const int16_t *__restrict__ elec,
+                                               const float *__restrict__ V)
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx)
+        return;
+    const size_t N = P.N, i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    const uint8_t inf = info[i];
+    float Ph[3] = {0.0f, 0.0f, 0.0f};
+    if ((inf & 3) == PT_FLUID) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int n = 0; n < Q; n++)
+                acc += fphi[(c * Q + n) * N + i];
+            Ph[c] = acc;
+        }
+        float r = 0.0f;
+#pragma unroll
+        for (int n = 0; n < L::QS; n++)
+            r += frho[n * N + i];
+        rho_out[i] = r;
+    } else {
+        rho_out[i] = 0.0f;
+        const int k = normal[i];
+        if (k > 0) {
+            // Eq. 20a, explicit in the fluid node f = s + e_k along the lattice normal.
+            const int kx = L::ex(k), ky = L::ey(k), kz = L::ez(k);
+            const int X = (x + kx + P.nx) % P.nx, Y = (y + ky + P.ny) % P.ny,
+                      Z = (z + kz + P.nz) % P.nz;
+            const size_t f = X + (size_t)P.nx * (Y + (size_t)P.ny * Z);
+            float Pf[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int n = 0; n < Q; n++)
+                    acc += fphi[(c * Q + n) * N + f];
+                Pf[c] = acc;
+            }
+            float c12 = 0.0f, c13 = 0.0f, c23 = 0.0f;
+            if (((inf >> 2) & 3) == 1) {
+                c12 = P.cos12;
+                c13 = P.cos13;
+                c23 = P.cos23;
+            }
+            const float len = (kx * kx + ky * ky + kz * kz) == 2 ? 1.41421356237f : 1.0f;
+            const float s = 4.0f / P.W;
+            const float H1 = s * (-c13 * Pf[0] * Pf[2] - c12 * Pf[0] * Pf[1]);
+            const float H2 = s * (c12 * Pf[0] * Pf[1] - c23 * Pf[1] * Pf[2]);
+            const float H3 = s * (c23 * Pf[1] * Pf[2] + c13 * Pf[0] * Pf[2]);
+            Ph[0] = Pf[0] - len * H1;
+            Ph[1] = Pf[1] - len * H2;
+            Ph[2] = Pf[2] - len * H3;
+        }
+        if ((inf & 3) == PT_DIRICHLET) {
+            const int id = elec[i];
+            pot[i] = id >= 0 ? V[id] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        phi_out[c * N + i] = Ph[c];
+    eps_out[i] = Ph[0] * P.eps[0] + Ph[1] * P.eps[1] + Ph[2] * P.eps[2];
+}
+
+// ---------------------------------------------------------------- Poisson (Eq. 13)
+
+// One red-black SOR half sweep: thread t of a row updates x = 2t + parity.
+template <int D>
+__global__ void __launch_bounds__(BX) k_sor(Params P, float *__restrict__ pot,
+                                            const float *__restrict__ eps,
+                                            const float *__restrict__ rho,
+                                            const uint8_t *__restrict__ info, int color,
+                                            float omega)
+{
+    using L = Lat<D>;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + z + color) & 1);
+    if (x >= P.nx)
+        return;
+    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    if ((info[i] & 3) != PT_FLUID)
+        return;
+    const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
+    const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
+    const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
+    const float ei = eps[i];
+    float num = rho[i], den = 0.0f;
+#pragma unroll
+    for (int n = 1; n <= 2 * D; n++) {
+        const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
+        const int pt = info[j] & 3;
+        if (pt == PT_FLUID) {
+            const float k = 0.5f * (ei + eps[j]);
+            num += k * pot[j];
+            den += k;
+        } else if (pt == PT_DIRICHLET) {
+            num += ei * pot[j];
+            den += ei;
+        }
+    }
+    if (den > 0.0f)
+        pot[i] += omega * (num / den - pot[i]);
+}
+
+// Residual r = b - A phi per fluid node; block partials of sum r^2 and sum b^2 (FP64).
+template <int D>
+__global__ void __launch_bounds__(BX) k_residual(Params P, const float *__restrict__ pot,
+                                                 const float *__restrict__ eps,
+                                                 const float *__restrict__ rho,
+                                                 const uint8_t *__restrict__ info,
+                                                 double *__restrict__ partials)
+{
+    using L = Lat<D>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    float rr = 0.0f, bb = 0.0f;
+    if (x < P.nx) {
+        const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+        if ((info[i] & 3) == PT_FLUID) {
+            const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
+            const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
+            const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
+            const float ei = eps[i], pi = pot[i];
+            float b = rho[i], Ap = 0.0f;
+#pragma unroll
+            for (int n = 1; n <= 2 * D; n++) {
+                const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
+                const int pt = info[j] & 3;
+                if (pt == PT_FLUID) {
+                    Ap += 0.5f * (ei + eps[j]) * (pi - pot[j]);
+                } else if (pt == PT_DIRICHLET) {
+                    b += ei * pot[j];
+                    Ap += ei * pi;
+                }
+            }
+            const float r = b - Ap;
+            rr = r * r;
+            bb = b * b;
+        }
+    }
+    rr = warp_sum(rr);
+    bb = warp_sum(bb);
+    __shared__ double sm[2][BX / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm[0][wid] = rr;
+        sm[1][wid] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double acc = 0.0;
+        for (int k = 0; k < BX / 32; k++)
+            acc += sm[threadIdx.x][k];
+        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+        partials[2 * blk + threadIdx.x] = acc;
+    }
+}
+
+// Sum the residual partials in a fixed order: out[0] = sum r^2, out[1] = sum b^2.
+__global__ void __launch_bounds__(256) k_residual_final(const double *__restrict__ partials,
+                                                        long long nblocks, double *__restrict__ out)
+{
+    __shared__ double sm[2][256];
+    double a = 0.0, b = 0.0;
+    for (long long k = threadIdx.x; k < nblocks; k += 256) {
+        a += partials[2 * k];
+        b += partials[2 * k + 1];
+    }
+    sm[0][threadIdx.x] = a;
+    sm[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sm[0][0];
+        out[1] = sm[1][0];
+    }
+}
+
+// ---------------------------------------------------------------- fused collide + stream
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q, QS = L::QS;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const size_t N = P.N;
+    float ob[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; k++)
+        ob[k] = 0.0f;
+
+    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
+        const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
+        const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
+        const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
+
+        // ---- stencils of Phi_i and phi over the flow lattice
+        const float Pc[3] = {S.phi[i], S.phi[N + i], S.phi[2 * N + i]};
+        const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
+        const float pot_i = S.pot[i];
+        float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        float lP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
+        float qsrc = 0.0f;
+        unsigned fluid_nb = 1u;   // bit n: x + e_n is fluid (bit 0: the site itself)
+#pragma unroll
+        for (int n = 1; n < Q; n++) {
+            const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
+            const int pt = S.info[j] & 3;
+            const float wn = L::w(n);
+            const float ea[3] = {(float)L::ex(n), (float)L::ey(n), (float)L::ez(n)};
+            float Pn[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                Pn[c] = S.phi[c * N + j];
+                lP[c] += wn * (Pn[c] - Pc[c]);
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    gP[c][a] += wn * ea[a] * Pn[c];
+            }
+            const float potj = S.pot[j];
+            const float ph = pt == PT_NEUMANN ? pot_i : potj;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                gpot[a] += wn * ea[a] * ph;
+            if (pt == PT_FLUID) {
+                fluid_nb |= 1u << n;
+                if (n <= 2 * D) {
+                    const float sig_j = Pn[0] * P.sig[0] + Pn[1] * P.sig[1] + Pn[2] * P.sig[2];
+                    qsrc += 0.5f * (sig_i + sig_j) * (potj - pot_i);
+                }
+            }
+        }
+        const float inv_cs2 = 3.0f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            lP[c] *= 2.0f * inv_cs2;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                gP[c][a] *= inv_cs2;
+        }
+
+        // ---- chemical potential (Eqs. 10-11), capillary and electric forces (Eq. 12)
+        const float W = P.W;
+        const float tri = 24.0f * P.YT / W * Pc[0] * Pc[1] * Pc[2];
+        float Fs[3] = {0.f, 0.f, 0.f}, geps[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float mu = 24.0f * P.Y[c] / W * Pc[c] * (Pc[c] - 1.0f) * (Pc[c] - 0.5f) - tri -
+                             0.75f * P.Y[c] * W * lP[c];
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                Fs[a] += mu * gP[c][a];
+        }
+        float E[3], E2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            geps[a] = P.eps[0] * gP[0][a] + P.eps[1] * gP[1][a] + P.eps[2] * gP[2][a];
+            E[a] = -inv_cs2 * gpot[a];
+            E2 += E[a] * E[a];
+        }
+        const float rho = S.rho[i];
+        float Fe[3], F[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            Fe[a] = rho * E[a] - 0.5f * E2 * geps[a];
+            F[a] = Fs[a] + Fe[a] + P.body[a];
+        }
+
+        // ---- sharpening flux F_Phi,i (Eq. 18)
+        float FPhi[3][3];
+        {
+            float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
+                                       gP[c][2] * gP[c][2]) + 1e-12f;
+                const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    ln[c][a] = lam * gP[c][a];
+                    J[a] += ln[c][a];
+                }
+                sumsq += Pc[c] * Pc[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float r = Pc[c] * Pc[c] / sumsq;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    FPhi[c][a] = ln[c][a] - r * J[a];
+            }
+        }
+
+        // ---- momentum moments, velocity, previous-step values
+        float gs[Q];
+        float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int n = 0; n < Q; n++) {
+            gs[n] = S.g[n * N + i];
+            dp += gs[n];
+            jm[0] += L::ex(n) * gs[n];
+            jm[1] += L::ey(n) * gs[n];
+            jm[2] += L::ez(n) * gs[n];
+        }
+        float u[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            u[a] = jm[a] + 0.5f * F[a];
+        float uo[3], Po[3], rho_o, q_o;
+        if (first) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                uo[a] = u[a];
+                Po[a] = Pc[a];
+            }
+            rho_o = rho;
+            q_o = qsrc;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                uo[a] = S.u[a * N + i];
+                Po[a] = S.phi_prev[a * N + i];
+            }
+            rho_o = S.rho_prev[i];
+            q_o = S.q[i];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            S.u[a * N + i] = u[a];
+        S.q[i] = qsrc;
+
+        auto push = [&](float *out, int n, float v) {
+            if ((fluid_nb >> n) & 1u)
+                out[n * N + nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny)] = v;
+            else
+                out[opposite(n) * N + i] = v;
+        };
+
+        // ---- momentum collision (incompressible equilibrium, Guo forcing, MRT)
+        {
+            const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+            const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
+            const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
+            const float c_b = 1.0f - P.s_bulk;
+            float base[Q];
+            float d1 = 0.f, d2 = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f, dT = 0.f;
+#pragma unroll
+            for (int n = 0; n < Q; n++) {
+                const float cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+                const float eF = cx * F[0] + cy * F[1] + cz * F[2];
+                const float wn = L::w(n);
+                const float geq = wn * (dp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+                const float hR = wn * (1.5f * (eF - uF) + 4.5f * eu * eF);   // R_n / 2
+                base[n] = geq + hR;
+                const float A = gs[n] - geq + hR;
+                d1 += (cx * cx - cy * cy) * A;
+                d2 += (cx * cx - cz * cz) * A;
+                dxy += cx * cy * A;
+                dxz += cx * cz * A;
+                dyz += cy * cz * A;
+                dT += (cx * cx + cy * cy + cz * cz) * A;
+            }
+#pragma unroll
+            for (int n = 0; n < Q; n++) {
+                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+                const int e2 = cx * cx + cy * cy + cz * cz;
+                float corr = 0.0f, corrT = 0.0f;
+                if (D == 3) {
+                    if (e2 == 1) {
+                        corr = cx ? (d1 + d2) * (1.0f / 6.0f)
+                                  : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
+                                        : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
+                        corrT = dT * (1.0f / 6.0f);
+                    } else if (e2 == 2) {
+                        corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
+                    } else {
+                        corrT = -dT;
+                    }
+                } else {
+                    if (e2 == 1) {
+                        corr = cx ? 0.25f * d1 : -0.25f * d1;
+                        corrT = 0.25f * dT;
+                    } else if (e2 == 2) {
+                        corr = 0.25f * cx * cy * dxy;
+                    } else {
+                        corrT = -dT;
+                    }
+                }
+                push(S.g_out, n, base[n] + c_nu * corr + c_b * corrT);
+            }
+            if (!isfinite(dp + u[0] + u[1] + u[2]))
+                atomicOr(S.flag, 1);
+        }
+
+        // ---- phase-field collisions (Eqs. 15-17), one component at a time
+        const float c_phi = 1.0f - P.inv_tau_phi;
+#pragma unroll 1
+        for (int c = 0; c < 3; c++) {
+            float f[Q];
+            float jf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int n = 0; n < Q; n++) {
+                f[n] = S.fphi[(c * Q + n) * N + i];
+                jf[0] += L::ex(n) * f[n];
+                jf[1] += L::ey(n) * f[n];
+                jf[2] += L::ez(n) * f[n];
+            }
+            const float Pp = Pc[c];
+            float A[3], del[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                A[a] = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
+                del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A[a]);
+            }
+#pragma unroll
+            for (int n = 0; n < Q; n++) {
+                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+                const float eA = cx * A[0] + cy * A[1] + cz * A[2];
+                float v = L::w(n) * (Pp * (1.0f + inv_cs2 * eu) + 0.5f * inv_cs2 * eA);
+                if (cx * cx + cy * cy + cz * cz == 1)
+                    v += cx * del[0] + cy * del[1] + cz * del[2];
+                push(S.fphi_out + (size_t)c * Q * N, n, v);
+            }
+        }
+
+        // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
+        {
+            constexpr float inv_cs2s = 1.0f / L::cs2s;
+            float jr[3] = {0.f, 0.f, 0.f};
+            float fr[QS];
+#pragma unroll
+            for (int n = 0; n < QS; n++) {
+                fr[n] = S.frho[n * N + i];
+                jr[0] += L::ex(n) * fr[n];
+                jr[1] += L::ey(n) * fr[n];
+                jr[2] += L::ez(n) * fr[n];
+            }
+            const float c_rho = 1.0f - P.inv_tau_rho;
+            const float Qt = qsrc + 0.5f * (qsrc - q_o);
+            float Dm[3], del[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                Dm[a] = rho * u[a] - rho_o * uo[a];
+                del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm[a]);
+            }
+#pragma unroll
+            for (int n = 0; n < QS; n++) {
+                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+                const float eD = cx * Dm[0] + cy * Dm[1] + cz * Dm[2];
+                float v = L::ws(n) * (rho * (1.0f + inv_cs2s * eu) + 0.5f * inv_cs2s * eD + Qt);
+                if (n > 0)
+                    v += cx * del[0] + cy * del[1] + cz * del[2];
+                push(S.frho_out, n, v);
+            }
+        }
+
+        // ---- observable contributions
+        ob[0] = Pc[0];
+        ob[1] = Pc[0] * (float)x;
+        ob[2] = Pc[0] * (float)y;
+        ob[3] = Pc[0] * (float)z;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            ob[4 + a] = Pc[0] * u[a];
+            ob[7 + a] = Pc[0] * Fe[a];
+            ob[10 + a] = Fe[a];
+        }
+        ob[13] = Pc[1];
+        ob[14] = Pc[2];
+        ob[15] = rho;
+        if (!isfinite(Pc[0] + Pc[1] + Pc[2] + rho + qsrc))
+            atomicOr(S.flag, 1);
+    }
+
+    // ---- block partial sums: FP32 within a warp, FP64 across warps
+    __shared__ double sm[NOBS][BX / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NOBS; k++) {
+        const float v = warp_sum(ob[k]);
+        if (lane == 0)
+            sm[k][wid] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NOBS) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < BX / 32; w++)
+            acc += sm[threadIdx.x][w];
+        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
+        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+        S.obs_partials[threadIdx.x * nblk + blk] = acc;
+    }
+}
+
+// Fixed-order FP64 sum of the observable partials. obs[0..NOBS) receives this step's sums
+// and obs[NOBS..2 NOBS) the previous step's (for the drag force balance).
+__global__ void __launch_bounds__(256) k_obs_final(const double *__restrict__ partials,
+                                                   long long nblocks, double *__restrict__ obs)
+{
+    __shared__ double sm[256];
+    __shared__ double prev[NOBS];
+    if (threadIdx.x < NOBS)
+        prev[threadIdx.x] = obs[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < NOBS)
+        obs[NOBS + threadIdx.x] = prev[threadIdx.x];
+    for (int k = 0; k < NOBS; k++) {
+        double a = 0.0;
+        for (long long b = threadIdx.x; b < nblocks; b += 256)
+            a += partials[k * nblocks + b];
+        sm[threadIdx.x] = a;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
+                sm[threadIdx.x] += sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            obs[k] = sm[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace lbehd

@@ -1,0 +1,669 @@
+// lbehd.cu -- host side of the C ABI in include/lbehd.h: configuration checks, geometry
+// tables, device state, the per-step launch sequence and the Poisson convergence loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbehd.h"
+#include "kernels.cuh"
+
+namespace lbehd {
+
+static thread_local std::string g_init_error;
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace lbehd
+
+using namespace lbehd;
+
+struct lbehd_handle {
+    lbehd_config cfg;              // copy; host array pointers cleared after init
+    int dim = 0, nx = 0, ny = 0, nz = 0;
+    size_t N = 0;
+    int Q = 0, QS = 0;
+    Params P{};
+    cudaStream_t stream = nullptr;
+    std::vector<DevBuf> bufs;
+    // device state
+    float *g[2] = {}, *fphi[2] = {}, *frho[2] = {};
+    float *phi[2] = {}, *rho[2] = {};
+    float *u = nullptr, *q = nullptr, *pot = nullptr, *eps = nullptr, *V = nullptr;
+    uint8_t *info = nullptr, *normal = nullptr;
+    int16_t *elec = nullptr;
+    double *obs_partials = nullptr, *obs = nullptr, *res_partials = nullptr, *res = nullptr;
+    int *flag = nullptr;
+    double *h_res = nullptr;       // pinned: residual sums
+    int cur = 0;                   // population buffer holding the state at time n
+    int pcur = 0;                  // phi / rho buffer holding the last step's fields
+    bool first = true;
+    long long step = 0;
+    long long launches = 0;
+    float omega = 1.0f;
+    int last_iters = 0;
+    double last_resid = 0.0;
+    int status = LBEHD_OK;
+    std::string err;
+    dim3 grid, block, grid_sor;
+    size_t nblocks = 0;
+    // profiling: event pairs recorded around launches, per kernel class
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[LBEHD_NKC];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+};
+
+namespace {
+
+int fail(lbehd_handle *h, int code, const std::string &msg)
+{
+    if (h)
+        h->err = msg;
+    else
+        g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(lbehd_handle *h, cudaError_t e, const char *what)
+{
+    return fail(h, LBEHD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess)                        \
+            return cuda_fail((h), e_, #call);         \
+    } while (0)
+
+void *dev_alloc(lbehd_handle *h, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0)
+        bytes = 16;
+    if (h->cfg.alloc) {
+        p = h->cfg.alloc(bytes, h->cfg.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p)
+        h->bufs.push_back({p, bytes});
+    return p;
+}
+
+// Lattice normal of a boundary solid node: the fluid neighbour direction maximising
+// e_k . v / |e_k| with v = sum_n w_n e_n [fluid neighbour n]; integer weights (x36),
+// ties to the lowest index. 0 when the node has no fluid neighbour.
+template <int D>
+void build_normals(const lbehd_handle *h, const uint8_t *solid, std::vector<uint8_t> &normal)
+{
+    using L = Lat<D>;
+    const int nx = h->nx, ny = h->ny, nz = h->nz;
+    normal.assign(h->N, 0);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                const size_t i = x + (size_t)nx * (y + (size_t)ny * z);
+                if (!solid[i])
+                    continue;
+                long v[3] = {0, 0, 0};
+                bool fl[L::Q] = {};
+                bool any = false;
+                for (int n = 1; n < L::Q; n++) {
+                    const int X = (x + L::ex(n) + nx) % nx, Y = (y + L::ey(n) + ny) % ny,
+                              Z = (z + L::ez(n) + nz) % nz;
+                    fl[n] = solid[X + (size_t)nx * (Y + (size_t)ny * Z)] == 0;
+                    if (fl[n]) {
+                        const long iw = std::lround(36.0 * L::w(n));
+                        v[0] += iw * L::ex(n);
+                        v[1] += iw * L::ey(n);
+                        v[2] += iw * L::ez(n);
+                        any = true;
+                    }
+                }
+                if (!any)
+                    continue;
+                int best = 0;
+                long bdot = 0, blen2 = 1;
+                for (int n = 1; n < L::Q; n++) {
+                    if (!fl[n])
+                        continue;
+                    const long dot = L::ex(n) * v[0] + L::ey(n) * v[1] + L::ez(n) * v[2];
+                    const long len2 = L::ex(n) * L::ex(n) + L::ey(n) * L::ey(n) + L::ez(n) * L::ez(n);
+                    // dot/sqrt(len2) > bdot/sqrt(blen2), compared through signed squares
+                    const long a = dot * std::labs(dot) * blen2, b = bdot * std::labs(bdot) * len2;
+                    if (best == 0 || a > b) {
+                        best = n;
+                        bdot = dot;
+                        blen2 = len2;
+                    }
+                }
+                normal[i] = (uint8_t)best;
+            }
+}
+
+// Launch through here: counts launches and, while profiling, brackets them with events.
+template <class F>
+void launch(lbehd_handle *h, int kc, int nlaunch, F &&fn)
+{
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (h->prof) {
+        if (!h->ev_pool.empty()) {
+            ev = h->ev_pool.back();
+            h->ev_pool.pop_back();
+        } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
+                   cudaEventCreate(&ev.second) != cudaSuccess) {
+            ev = {nullptr, nullptr};
+        }
+        if (ev.first)
+            cudaEventRecord(ev.first, h->stream);
+    }
+    fn();
+    h->launches += nlaunch;
+    if (ev.first) {
+        cudaEventRecord(ev.second, h->stream);
+        h->ev_pending[kc].push_back(ev);
+    }
+}
+
+template <int D>
+int launch_fields(lbehd_handle *h)
+{
+    launch(h, LBEHD_KC_FIELDS, 1, [&] {
+        k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->fphi[h->cur], h->frho[h->cur],
+                                                          h->phi[h->pcur], h->rho[h->pcur], h->eps,
+                                                          h->pot, h->info, h->normal, h->elec, h->V);
+    });
+    return LBEHD_OK;
+}
+
+template <int D>
+int residual(lbehd_handle *h, double *rr, double *bb)
+{
+    launch(h, LBEHD_KC_RESIDUAL, 2, [&] {
+        k_residual<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->eps, h->rho[h->pcur],
+                                                            h->info, h->res_partials);
+        k_residual_final<<<1, 256, 0, h->stream>>>(h->res_partials, (long long)h->nblocks, h->res);
+    });
+    CK(h, cudaMemcpyAsync(h->h_res, h->res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *rr = h->h_res[0];
+    *bb = h->h_res[1];
+    return LBEHD_OK;
+}
+
+template <int D>
+void sweep(lbehd_handle *h)
+{
+    launch(h, LBEHD_KC_SOR, 2, [&] {
+        for (int color = 0; color < 2; color++)
+            k_sor<D><<<h->grid_sor, h->block, 0, h->stream>>>(h->P, h->pot, h->eps,
+                                                              h->rho[h->pcur], h->info, color,
+                                                              h->omega);
+    });
+}
+
+// Gauss law (Eq. 13): red-black SOR from the previous step's potential.
+template <int D>
+int poisson(lbehd_handle *h)
+{
+    const lbehd_config &c = h->cfg;
+    int iters = 0;
+    if (c.poisson_mode == LBEHD_POISSON_FIXED) {
+        for (; iters < c.poisson_fixed_sweeps; iters++)
+            sweep<D>(h);
+        h->last_iters = iters;
+        h->last_resid = -1.0;   // not measured in this mode
+        return LBEHD_OK;
+    }
+    double rr = 0.0, bb = 0.0;
+    int rc = residual<D>(h, &rr, &bb);
+    if (rc)
+        return rc;
+    if (bb == 0.0) {
+        // no charge and every Dirichlet value zero: phi = 0
+        CK(h, cudaMemsetAsync(h->pot, 0, h->N * sizeof(float), h->stream));
+        h->last_iters = 0;
+        h->last_resid = 0.0;
+        return LBEHD_OK;
+    }
+    const double tol2 = c.poisson_tol * c.poisson_tol * bb;
+    while (rr > tol2 && iters < c.poisson_max_iter) {
+        const int k = std::min(std::max(c.poisson_check_every, 1), c.poisson_max_iter - iters);
+        for (int s = 0; s < k; s++)
+            sweep<D>(h);
+        iters += k;
+        rc = residual<D>(h, &rr, &bb);
+        if (rc)
+            return rc;
+    }
+    h->last_iters = iters;
+    h->last_resid = std::sqrt(rr / bb);
+    if (rr > tol2) {
+        h->status = h->status ? h->status : LBEHD_ERR_POISSON_NOCONV;
+        return LBEHD_ERR_POISSON_NOCONV;
+    }
+    return LBEHD_OK;
+}
+
+template <int D>
+int do_step(lbehd_handle *h)
+{
+    int rc = launch_fields<D>(h);
+    if (rc)
+        return rc;
+    const int prc = poisson<D>(h);
+    if (prc && prc != LBEHD_ERR_POISSON_NOCONV)
+        return prc;
+    State S;
+    S.g = h->g[h->cur];
+    S.fphi = h->fphi[h->cur];
+    S.frho = h->frho[h->cur];
+    S.g_out = h->g[h->cur ^ 1];
+    S.fphi_out = h->fphi[h->cur ^ 1];
+    S.frho_out = h->frho[h->cur ^ 1];
+    S.phi = h->phi[h->pcur];
+    S.phi_prev = h->phi[h->pcur ^ 1];
+    S.rho = h->rho[h->pcur];
+    S.rho_prev = h->rho[h->pcur ^ 1];
+    S.u = h->u;
+    S.q = h->q;
+    S.pot = h->pot;
+    S.info = h->info;
+    S.obs_partials = h->obs_partials;
+    S.flag = h->flag;
+    launch(h, LBEHD_KC_COLLIDE, 1,
+           [&] { k_collide<D><<<h->grid, h->block, 0, h->stream>>>(h->P, S, h->first ? 1 : 0); });
+    launch(h, LBEHD_KC_OBS, 1, [&] {
+        k_obs_final<<<1, 256, 0, h->stream>>>(h->obs_partials, (long long)h->nblocks, h->obs);
+    });
+    CK(h, cudaGetLastError());
+    h->cur ^= 1;
+    h->pcur ^= 1;
+    h->first = false;
+    h->step++;
+    return prc;
+}
+
+int set_params(lbehd_handle *h)
+{
+    const lbehd_config &c = h->cfg;
+    Params &P = h->P;
+    P.nx = h->nx;
+    P.ny = h->ny;
+    P.nz = h->nz;
+    P.N = (long long)h->N;
+    for (int k = 0; k < 3; k++) {
+        P.nu[k] = (float)c.nu[k];
+        P.eps[k] = (float)c.eps[k];
+        P.sig[k] = (float)c.sigma[k];
+        P.body[k] = (float)c.body_force[k];
+    }
+    // Eq. 11
+    const double Y1 = c.gamma12 + c.gamma13 - c.gamma23;
+    const double Y2 = c.gamma12 + c.gamma23 - c.gamma13;
+    const double Y3 = c.gamma13 + c.gamma23 - c.gamma12;
+    if (Y1 == 0.0 || Y2 == 0.0 || Y3 == 0.0)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "surface tensions give a zero Upsilon (Eq. 11)");
+    P.Y[0] = (float)Y1;
+    P.Y[1] = (float)Y2;
+    P.Y[2] = (float)Y3;
+    P.YT = (float)(3.0 / (1.0 / Y1 + 1.0 / Y2 + 1.0 / Y3));
+    const double d2r = 3.14159265358979323846 / 180.0;
+    P.cos12 = (float)std::cos(c.theta12 * d2r);
+    P.cos13 = (float)std::cos(c.theta13 * d2r);
+    P.cos23 = (float)std::cos(c.theta23 * d2r);
+    P.W = (float)c.W;
+    const double cs2 = 1.0 / 3.0, cs2s = h->dim == 3 ? 0.25 : 1.0 / 3.0;
+    P.inv_tau_phi = (float)(1.0 / (0.5 + c.mobility / cs2));
+    P.inv_tau_rho = (float)(1.0 / (0.5 + c.alpha / cs2s));
+    P.s_bulk = (float)c.s_bulk;
+    const int hv = h->dim == 3 ? h->nz : h->ny;
+    h->omega = c.poisson_omega > 0.0 ? (float)c.poisson_omega
+                                     : (float)(2.0 / (1.0 + std::sin(3.14159265358979 / std::max(hv, 2))));
+    return LBEHD_OK;
+}
+
+template <int D>
+int init_impl(lbehd_handle *h)
+{
+    const lbehd_config &c = h->cfg;
+    const size_t N = h->N;
+    h->Q = Lat<D>::Q;
+    h->QS = Lat<D>::QS;
+    // geometry tables
+    std::vector<uint8_t> info(N), normal;
+    std::vector<int16_t> elec(N, -1);
+    for (size_t i = 0; i < N; i++) {
+        const uint8_t s = c.solid[i];
+        if (s > 2)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "solid class must be 0, 1 or 2");
+        const int id = c.electrode_id ? c.electrode_id[i] : -1;
+        if (id < -2 || id >= c.n_electrodes)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "electrode id out of range");
+        uint8_t pt = PT_FLUID;
+        if (s)
+            pt = (id >= 0 || id == -2) ? PT_DIRICHLET : PT_NEUMANN;
+        info[i] = (uint8_t)(pt | (s << 2));
+        elec[i] = (int16_t)(s ? id : -1);
+    }
+    build_normals<D>(h, c.solid, normal);
+    // device buffers
+    const size_t fb = sizeof(float);
+    for (int b = 0; b < 2; b++) {
+        h->g[b] = (float *)dev_alloc(h, h->Q * N * fb);
+        h->fphi[b] = (float *)dev_alloc(h, 3 * h->Q * N * fb);
+        h->frho[b] = (float *)dev_alloc(h, h->QS * N * fb);
+        h->phi[b] = (float *)dev_alloc(h, 3 * N * fb);
+        h->rho[b] = (float *)dev_alloc(h, N * fb);
+        if (!h->g[b] || !h->fphi[b] || !h->frho[b] || !h->phi[b] || !h->rho[b])
+            return fail(h, LBEHD_ERR_OOM, "device allocation failed (populations)");
+    }
+    h->u = (float *)dev_alloc(h, 3 * N * fb);
+    h->q = (float *)dev_alloc(h, N * fb);
+    h->pot = (float *)dev_alloc(h, N * fb);
+    h->eps = (float *)dev_alloc(h, N * fb);
+    h->V = (float *)dev_alloc(h, LBEHD_MAX_ELECTRODES * fb);
+    h->info = (uint8_t *)dev_alloc(h, N);
+    h->normal = (uint8_t *)dev_alloc(h, N);
+    h->elec = (int16_t *)dev_alloc(h, N * sizeof(int16_t));
+    h->block = dim3(BX, 1, 1);
+    h->grid = dim3((h->nx + BX - 1) / BX, h->ny, h->nz);
+    h->grid_sor = dim3((h->nx / 2 + BX - 1) / BX, h->ny, h->nz);
+    h->nblocks = (size_t)h->grid.x * h->grid.y * h->grid.z;
+    h->obs_partials = (double *)dev_alloc(h, NOBS * h->nblocks * sizeof(double));
+    h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
+    h->res_partials = (double *)dev_alloc(h, 2 * h->nblocks * sizeof(double));
+    h->res = (double *)dev_alloc(h, 2 * sizeof(double));
+    h->flag = (int *)dev_alloc(h, sizeof(int));
+    if (!h->u || !h->q || !h->pot || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
+        !h->obs_partials || !h->obs || !h->res_partials || !h->res || !h->flag)
+        return fail(h, LBEHD_ERR_OOM, "device allocation failed (fields)");
+    CK(h, cudaMallocHost(&h->h_res, 2 * sizeof(double)));
+    std::vector<float> phi0(3 * N), V(LBEHD_MAX_ELECTRODES, 0.0f);
+    for (size_t k = 0; k < 3 * N; k++)
+        phi0[k] = (float)c.phi_init[k];
+    for (int k = 0; k < c.n_electrodes; k++)
+        V[k] = (float)c.electrode_V[k];
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemcpyAsync(h->info, info.data(), N, cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->normal, normal.data(), N, cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->elec, elec.data(), N * sizeof(int16_t), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->V, V.data(), V.size() * fb, cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->phi[1], phi0.data(), 3 * N * fb, cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < 2; b++) {
+        CK(h, cudaMemsetAsync(h->g[b], 0, h->Q * N * fb, s));
+        CK(h, cudaMemsetAsync(h->fphi[b], 0, 3 * h->Q * N * fb, s));
+        CK(h, cudaMemsetAsync(h->frho[b], 0, h->QS * N * fb, s));
+        CK(h, cudaMemsetAsync(h->rho[b], 0, N * fb, s));
+    }
+    CK(h, cudaMemsetAsync(h->phi[0], 0, 3 * N * fb, s));
+    CK(h, cudaMemsetAsync(h->u, 0, 3 * N * fb, s));
+    CK(h, cudaMemsetAsync(h->q, 0, N * fb, s));
+    CK(h, cudaMemsetAsync(h->pot, 0, N * fb, s));
+    CK(h, cudaMemsetAsync(h->eps, 0, N * fb, s));
+    CK(h, cudaMemsetAsync(h->obs, 0, 2 * NOBS * sizeof(double), s));
+    CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    k_init<D><<<h->grid, h->block, 0, s>>>(h->P, h->phi[1], h->g[0], h->fphi[0], h->frho[0], h->info);
+    h->launches++;
+    CK(h, cudaGetLastError());
+    // host staging vectors die here: wait for the copies
+    CK(h, cudaStreamSynchronize(s));
+    h->cur = 0;
+    h->pcur = 0;
+    return LBEHD_OK;
+}
+
+void drop_events(lbehd_handle *h)
+{
+    for (auto &v : h->ev_pending) {
+        for (auto &e : v)
+            h->ev_pool.push_back(e);
+        v.clear();
+    }
+}
+
+void release(lbehd_handle *h)
+{
+    if (!h)
+        return;
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    drop_events(h);
+    for (auto &e : h->ev_pool) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    h->ev_pool.clear();
+    for (auto &b : h->bufs) {
+        if (h->cfg.free)
+            h->cfg.free(b.ptr, h->cfg.alloc_ctx);
+        else
+            cudaFree(b.ptr);
+    }
+    h->bufs.clear();
+    if (h->h_res)
+        cudaFreeHost(h->h_res);
+    h->h_res = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbehd_abi_version(void) { return LBEHD_ABI_VERSION; }
+
+size_t lbehd_config_size(void) { return sizeof(lbehd_config); }
+
+int lbehd_init(const lbehd_config *cfg, lbehd_handle **out)
+{
+    if (!cfg || !out)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null config or output pointer");
+    *out = nullptr;
+    if (cfg->dim != 2 && cfg->dim != 3)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (cfg->nx < 2 || cfg->ny < 2 || cfg->nz < 1 || (cfg->dim == 2 && cfg->nz != 1) ||
+        (cfg->dim == 3 && cfg->nz < 2))
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "bad lattice extents");
+    if (cfg->nx % 2 || (cfg->dim == 3 && cfg->ny % 2))
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG,
+                    "periodic extents must be even (red-black ordering of the Poisson sweep)");
+    if (cfg->ny > 65535 || cfg->nz > 65535)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "ny and nz must be <= 65535");
+    if (!cfg->solid || !cfg->phi_init)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "solid and phi_init are required");
+    if (cfg->n_electrodes < 0 || cfg->n_electrodes > LBEHD_MAX_ELECTRODES ||
+        (cfg->n_electrodes > 0 && !cfg->electrode_V))
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "bad electrode table");
+    if (!(cfg->W > 0.0) || !(cfg->mobility > 0.0) || !(cfg->alpha >= 0.0) ||
+        !(cfg->poisson_tol > 0.0) || cfg->poisson_max_iter < 1)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "W, mobility, poisson_tol must be > 0");
+    for (int k = 0; k < 3; k++)
+        if (!(cfg->nu[k] > 0.0) || !(cfg->eps[k] > 0.0) || !(cfg->sigma[k] >= 0.0))
+            return fail(nullptr, LBEHD_ERR_INVALID_ARG, "nu, eps > 0 and sigma >= 0 required");
+    lbehd_handle *h = new (std::nothrow) lbehd_handle();
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_OOM, "host allocation failed");
+    h->cfg = *cfg;
+    h->dim = cfg->dim;
+    h->nx = cfg->nx;
+    h->ny = cfg->ny;
+    h->nz = cfg->nz;
+    h->N = (size_t)cfg->nx * cfg->ny * cfg->nz;
+    h->stream = (cudaStream_t)cfg->stream;
+    int rc = set_params(h);
+    if (!rc)
+        rc = h->dim == 2 ? init_impl<2>(h) : init_impl<3>(h);
+    h->cfg.solid = nullptr;
+    h->cfg.electrode_id = nullptr;
+    h->cfg.phi_init = nullptr;
+    h->cfg.electrode_V = nullptr;
+    if (rc) {
+        g_init_error = h->err;
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBEHD_OK;
+}
+
+int lbehd_step(lbehd_handle *h, int n)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (n < 0)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "n must be >= 0");
+    int worst = LBEHD_OK;
+    for (int s = 0; s < n; s++) {
+        const int rc = h->dim == 2 ? do_step<2>(h) : do_step<3>(h);
+        if (rc == LBEHD_ERR_POISSON_NOCONV)
+            worst = rc;
+        else if (rc)
+            return rc;
+    }
+    if (worst)
+        h->err = "Poisson solve reached poisson_max_iter";
+    return worst;
+}
+
+int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (n != h->cfg.n_electrodes || (n > 0 && !V))
+        return fail(h, LBEHD_ERR_INVALID_ARG, "electrode count differs from the configuration");
+    float tmp[LBEHD_MAX_ELECTRODES];
+    for (int k = 0; k < n; k++)
+        tmp[k] = (float)V[k];
+    // pageable source: the copy is staged before this call returns
+    CK(h, cudaMemcpyAsync(h->V, tmp, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEHD_OK;
+}
+
+int lbehd_observe(lbehd_handle *h, lbehd_obs *out)
+{
+    if (!h || !out)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or output");
+    double o[2 * NOBS];
+    int flag = 0;
+    CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->step = h->step - 1;
+    const double M1 = o[0], M1p = o[NOBS];
+    out->M1 = M1;
+    for (int a = 0; a < 3; a++) {
+        out->centroid[a] = M1 != 0.0 ? o[1 + a] / M1 : 0.0;
+        out->velocity[a] = M1 != 0.0 ? o[4 + a] / M1 : 0.0;
+        out->f_ele[a] = o[7 + a];
+        out->f_ele_total[a] = o[10 + a];
+        const double Vp = M1p != 0.0 ? o[NOBS + 4 + a] / M1p : 0.0;
+        out->f_drag[a] = h->step >= 2 ? o[7 + a] - M1 * (out->velocity[a] - Vp) : 0.0;
+    }
+    out->mass[0] = M1;
+    out->mass[1] = o[13];
+    out->mass[2] = o[14];
+    out->charge = o[15];
+    out->poisson_iters = h->last_iters;
+    out->poisson_resid = h->last_resid;
+    out->status = flag ? LBEHD_ERR_NONFINITE : h->status;
+    if (flag)
+        return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
+    return LBEHD_OK;
+}
+
+static int array_info(lbehd_handle *h, int which, void **ptr, size_t *bytes)
+{
+    const size_t N = h->N, fb = sizeof(float);
+    switch (which) {
+    case LBEHD_G: *ptr = h->g[h->cur]; *bytes = h->Q * N * fb; break;
+    case LBEHD_FPHI: *ptr = h->fphi[h->cur]; *bytes = 3 * h->Q * N * fb; break;
+    case LBEHD_FRHO: *ptr = h->frho[h->cur]; *bytes = h->QS * N * fb; break;
+    case LBEHD_PHI: *ptr = h->phi[h->pcur ^ 1]; *bytes = 3 * N * fb; break;
+    case LBEHD_RHO: *ptr = h->rho[h->pcur ^ 1]; *bytes = N * fb; break;
+    case LBEHD_POT: *ptr = h->pot; *bytes = N * fb; break;
+    case LBEHD_U: *ptr = h->u; *bytes = 3 * N * fb; break;
+    case LBEHD_QSRC: *ptr = h->q; *bytes = N * fb; break;
+    case LBEHD_EPS: *ptr = h->eps; *bytes = N * fb; break;
+    default: return fail(h, LBEHD_ERR_INVALID_ARG, "unknown array id");
+    }
+    return LBEHD_OK;
+}
+
+int lbehd_copy_out(lbehd_handle *h, int which, void *dst, size_t bytes)
+{
+    if (!h || !dst)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or destination");
+    void *p = nullptr;
+    size_t nb = 0;
+    int rc = array_info(h, which, &p, &nb);
+    if (rc)
+        return rc;
+    if (bytes < nb)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "destination too small");
+    CK(h, cudaMemcpyAsync(dst, p, nb, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEHD_OK;
+}
+
+int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes)
+{
+    if (!h || !ptr || !bytes)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null argument");
+    return array_info(h, which, ptr, bytes);
+}
+
+long long lbehd_launch_count(lbehd_handle *h) { return h ? h->launches : 0; }
+
+int lbehd_profile_enable(lbehd_handle *h, int enable)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_events(h);
+    h->prof = enable != 0;
+    return LBEHD_OK;
+}
+
+int lbehd_profile_read(lbehd_handle *h, double *ms, long long *count)
+{
+    if (!h || !ms || !count)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null argument");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < LBEHD_NKC; k++) {
+        double acc = 0.0;
+        for (auto &e : h->ev_pending[k]) {
+            float t = 0.0f;
+            CK(h, cudaEventElapsedTime(&t, e.first, e.second));
+            acc += t;
+        }
+        ms[k] = acc;
+        count[k] = (long long)h->ev_pending[k].size();
+    }
+    return LBEHD_OK;
+}
+
+const char *lbehd_last_error(lbehd_handle *h)
+{
+    return h ? h->err.c_str() : g_init_error.c_str();
+}
+
+void lbehd_destroy(lbehd_handle *h)
+{
+    release(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+"""Python binding of the C ABI in include/lbehd.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``liblbehd.so`` built next to this file
+for sm_103a. There is no CPU fallback: if the library is missing, loading it raises.
+PyTorch supplies device memory (its caching allocator, through the ABI's allocator hooks)
+and the CUDA stream the library enqueues on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbehd.so")
+
+# enum lbehd_array
+G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS = range(9)
+ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot": POT,
+               "u": U, "qsrc": QSRC, "eps": EPS}
+POISSON_HOST, POISSON_FIXED = 0, 1
+
+# Storage convention of LBEHD_G: the library keeps g_n - w_n (lattice weights in the
+# documented velocity order).
+STORAGE_SHIFT = {
+    2: np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4),
+    3: np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12),
+}
+
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "POISSON_NOCONV", -4: "NONFINITE", -5: "CUDA",
+          -6: "STATE"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_D3 = ctypes.c_double * 3
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int),
+                ("solid", ctypes.POINTER(ctypes.c_uint8)),
+                ("electrode_id", ctypes.POINTER(ctypes.c_int16)),
+                ("phi_init", ctypes.POINTER(ctypes.c_double)),
+                ("nu", _D3), ("eps", _D3), ("sigma", _D3),
+                ("gamma12", ctypes.c_double), ("gamma13", ctypes.c_double),
+                ("gamma23", ctypes.c_double),
+                ("theta12", ctypes.c_double), ("theta13", ctypes.c_double),
+                ("theta23", ctypes.c_double),
+                ("mobility", ctypes.c_double), ("W", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("body_force", _D3), ("s_bulk", ctypes.c_double),
+                ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
+                ("poisson_check_every", ctypes.c_int), ("poisson_mode", ctypes.c_int),
+                ("poisson_fixed_sweeps", ctypes.c_int), ("poisson_omega", ctypes.c_double),
+                ("n_electrodes", ctypes.c_int),
+                ("electrode_V", ctypes.POINTER(ctypes.c_double)),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("M1", ctypes.c_double), ("centroid", _D3),
+                ("velocity", _D3), ("f_ele", _D3), ("f_ele_total", _D3), ("f_drag", _D3),
+                ("mass", _D3), ("charge", ctypes.c_double), ("poisson_iters", ctypes.c_int),
+                ("poisson_resid", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class LBEHDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbehd error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
+           "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
+           "lbehd_launch_count", "lbehd_profile_enable", "lbehd_profile_read",
+           "lbehd_last_error", "lbehd_destroy")
+KERNEL_CLASSES = ("fields", "sor", "residual", "collide", "obs")
+
+
+def load():
+    """Load liblbehd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                           "`python -m paper_2608_12868_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.lbehd_abi_version.restype = ctypes.c_int
+    lib.lbehd_config_size.restype = ctypes.c_size_t
+    lib.lbehd_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(P)]
+    lib.lbehd_step.argtypes = [P, ctypes.c_int]
+    lib.lbehd_set_electrodes.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.lbehd_observe.argtypes = [P, ctypes.POINTER(Obs)]
+    lib.lbehd_copy_out.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t]
+    lib.lbehd_device_ptr.argtypes = [P, ctypes.c_int, ctypes.POINTER(P),
+                                     ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbehd_launch_count.argtypes = [P]
+    lib.lbehd_launch_count.restype = ctypes.c_longlong
+    lib.lbehd_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.lbehd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbehd_last_error.argtypes = [P]
+    lib.lbehd_last_error.restype = ctypes.c_char_p
+    lib.lbehd_destroy.argtypes = [P]
+    lib.lbehd_destroy.restype = None
+    if lib.lbehd_config_size() != ctypes.sizeof(Config):
+        raise RuntimeError("lbehd_config layout mismatch between the binding and the library")
+    _lib = lib
+    return lib
+
+
+def _dptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Simulation:
+    """One coupled LB-EHD run on the GPU.
+
+    ``workload``: a ``workloads.Workload`` (geometry, initial Phi, parameters).
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream).
+    ``torch_alloc``: take device memory from PyTorch's caching allocator.
+    """
+
+    def __init__(self, workload, *, stream=None, torch_alloc=True, poisson_mode=POISSON_HOST,
+                 poisson_check_every=8, poisson_fixed_sweeps=8, poisson_omega=0.0, device=0):
+        import torch
+        self._torch = torch
+        lib = load()
+        self.workload = w = workload
+        self.dim, self.shape = w.dim, tuple(w.shape)
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.Q, self.QS = (9, 5) if w.dim == 2 else (19, 7)
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = w.params
+        solid = np.ascontiguousarray(w.solid, dtype=np.uint8).reshape(-1)
+        elec = np.ascontiguousarray(w.elec, dtype=np.int16).reshape(-1)
+        phi = np.ascontiguousarray(w.phi_init, dtype=np.float64).reshape(-1)
+        V = np.ascontiguousarray(p.get("V", []), dtype=np.float64)
+        c = Config()
+        c.dim, c.nx, c.ny, c.nz = w.dim, nx, ny, nz
+        c.solid, c.electrode_id, c.phi_init = (_dptr(solid, ctypes.c_uint8),
+                                               _dptr(elec, ctypes.c_int16),
+                                               _dptr(phi, ctypes.c_double))
+        for k in range(3):
+            c.nu[k], c.eps[k], c.sigma[k] = p["nu"][k], p["eps"][k], p["sig"][k]
+            c.body_force[k] = p.get("body", (0.0, 0.0, 0.0))[k]
+        c.gamma12, c.gamma13, c.gamma23 = p["gamma12"], p["gamma13"], p["gamma23"]
+        c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
+        c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
+        c.s_bulk = p.get("s_bulk", 1.0)
+        c.poisson_tol = p.get("poisson_tol", 1e-6)
+        c.poisson_max_iter = int(p.get("poisson_max_iter", 20000))
+        c.poisson_check_every = int(poisson_check_every)
+        c.poisson_mode = int(poisson_mode)
+        c.poisson_fixed_sweeps = int(poisson_fixed_sweeps)
+        c.poisson_omega = float(poisson_omega)
+        c.n_electrodes = len(V)
+        c.electrode_V = _dptr(V, ctypes.c_double) if len(V) else None
+        if torch_alloc:
+            dev, st = self.device, self.stream
+
+            def _alloc(nbytes, ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=st)
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+            c.alloc, c.free = self._alloc_cb, self._free_cb
+        c.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self._cfg = c
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lbehd_init(ctypes.byref(c), ctypes.byref(h))
+        if rc != 0:
+            raise LBEHDError(rc, lib.lbehd_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.n_electrodes = len(V)
+
+    # ----------------------------------------------------------------- calls
+
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            raise LBEHDError(rc, self._lib.lbehd_last_error(self._h).decode())
+        return rc
+
+    def step(self, n=1):
+        """Advance n steps; returns 0 or -3 (a Poisson solve hit its cap)."""
+        return self._check(self._lib.lbehd_step(self._h, int(n)), allow=(-3,))
+
+    def set_electrodes(self, V):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        self._check(self._lib.lbehd_set_electrodes(self._h, _dptr(V, ctypes.c_double), len(V)))
+
+    def observe(self):
+        o = Obs()
+        self._check(self._lib.lbehd_observe(self._h, ctypes.byref(o)))
+        return {
+            "step": o.step, "M1": o.M1, "centroid": np.array(o.centroid[:]),
+            "velocity": np.array(o.velocity[:]), "f_ele": np.array(o.f_ele[:]),
+            "f_ele_total": np.array(o.f_ele_total[:]), "f_drag": np.array(o.f_drag[:]),
+            "mass": np.array(o.mass[:]), "charge": o.charge, "poisson_iters": o.poisson_iters,
+            "poisson_resid": o.poisson_resid, "status": o.status,
+        }
+
+    def _shape_of(self, which):
+        nz, ny, nx = self.shape
+        return {G: (self.Q,), FPHI: (3, self.Q), FRHO: (self.QS,), PHI: (3,), RHO: (), POT: (),
+                U: (3,), QSRC: (), EPS: ()}[which] + (nz, ny, nx)
+
+    def array(self, which):
+        """Host copy (float32 numpy) of one array; ``which`` is a name or an enum value."""
+        which = ARRAY_NAMES.get(which, which)
+        out = np.empty(self._shape_of(which), dtype=np.float32)
+        self._check(self._lib.lbehd_copy_out(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
+                                             out.nbytes))
+        return out
+
+    def populations_g(self):
+        """Momentum populations g_n in float64 (the library stores g_n - w_n)."""
+        return self.array(G).astype(np.float64) + STORAGE_SHIFT[self.dim].reshape((-1, 1, 1, 1))
+
+    def tensor(self, which):
+        """Zero-copy torch view of one device array (valid until the next step)."""
+        which = ARRAY_NAMES.get(which, which)
+        ptr, nb = ctypes.c_void_p(), ctypes.c_size_t()
+        self._check(self._lib.lbehd_device_ptr(self._h, which, ctypes.byref(ptr), ctypes.byref(nb)))
+        shape = self._shape_of(which)
+
+        class _View:
+            __cuda_array_interface__ = {"shape": shape, "typestr": "<f4",
+                                        "data": (ptr.value, False), "version": 3,
+                                        "stream": None}
+        return self._torch.as_tensor(_View(), device=self.device)
+
+    def profile(self, enable=True):
+        """Record per-kernel device time with CUDA events on the library's stream."""
+        self._check(self._lib.lbehd_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} since profiling was enabled."""
+        n = len(KERNEL_CLASSES)
+        ms, cnt = (ctypes.c_double * n)(), (ctypes.c_longlong * n)()
+        self._check(self._lib.lbehd_profile_read(self._h, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def launch_count(self):
+        return int(self._lib.lbehd_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbehd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/lbehd.h declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(lbehd_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_12868_b300 import build
+    build.build()
+    from paper_2608_12868_b300 import lbehd
+    return lbehd.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "lbehd_init" in names and "lbehd_step" in names and "lbehd_observe" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2608_12868_b300",
+                                                                     "liblbehd.so")],
+                         capture_output=True, text=True, check=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+def test_binding_layout_matches_library(lib):
+    from paper_2608_12868_b300 import lbehd
+    assert lib.lbehd_abi_version() == 1
+    assert lib.lbehd_config_size() == ctypes.sizeof(lbehd.Config)
+    assert set(lbehd.EXPORTS) <= set(_declared())
+
+
+def test_library_is_built_for_sm_103a(lib):
+    from paper_2608_12868_b300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_init_rejects_bad_configs_before_touching_the_gpu(lib):
+    from paper_2608_12868_b300 import lbehd
+    c = lbehd.Config()
+    h = ctypes.c_void_p()
+    c.dim = 4
+    assert lib.lbehd_init(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"dim" in lib.lbehd_last_error(None)
+    c.dim, c.nx, c.ny, c.nz = 3, 15, 8, 8
+    assert lib.lbehd_init(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"even" in lib.lbehd_last_error(None)

@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded
+inputs.
+
+Bars (written here, derived from the target tolerances of the method):
+* populations: relative L-infinity max|f_gpu - f_oracle| / max|f_oracle| <= 1e-5 per
+  population set after up to 100 steps (FP32 state against FP64);
+* fields Phi_i: absolute L-infinity <= 1e-5 (they are O(1));
+* droplet observables (centroid velocity, electric force, drag): 0.5 % of their magnitude;
+* per-component mass: conserved to 1e-6 relative on the GPU.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_12868_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+OBS_TOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_12868_b300 import build, lbehd
+    build.build()
+    return lbehd
+
+
+def rel_linf(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def make_pair(gpu, oracle_mod, w, **kw):
+    sim = gpu.Simulation(w, **kw)
+    orc = oracle_mod.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    return sim, orc
+
+
+def compare_populations(sim, orc, tol=POP_TOL):
+    errs = {
+        "g": rel_linf(sim.populations_g(), orc.g),
+        "fphi": rel_linf(sim.array("fphi"), orc.fphi),
+        "frho": rel_linf(sim.array("frho"), orc.frho) if np.abs(orc.frho).max() > 0 else 0.0,
+    }
+    for k, v in errs.items():
+        assert v <= tol, (k, errs)
+    return errs
+
+
+def compare_fields(sim, orc, phi_tol=1e-5):
+    fluid = orc.solid == 0
+    phi = sim.array("phi")
+    assert np.abs(phi[:, fluid] - orc.Phi[:, fluid]).max() <= phi_tol
+    bnd = orc.normal > 0
+    if bnd.any():   # wetting ghosts (Eq. 20a)
+        assert np.abs(phi[:, bnd] - orc.Phi[:, bnd]).max() <= phi_tol
+    pot = sim.array("pot")
+    if np.abs(orc.pot).max() > 0:
+        assert rel_linf(pot[fluid], orc.pot[fluid]) <= 1e-4
+
+
+def compare_obs(sim, orc, keys=("velocity", "f_ele", "f_ele_total"), tol=OBS_TOL):
+    og, oo = sim.observe(), orc.observables()
+    for k in keys:
+        a, b = np.asarray(og[k]), np.asarray(oo[k])
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= tol * scale, (k, a, b)
+    assert np.abs(og["centroid"] - oo["centroid"]).max() <= 1e-3
+    assert np.abs(og["mass"] / oo["mass"] - 1).max() <= 1e-5
+
+
+@pytest.mark.parametrize("steps", [1, 10, 100])
+def test_small_2d_populations(gpu, oracle_mod, steps):
+    w = W.small_2d()
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(steps)
+    orc.step(steps)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+
+
+@pytest.mark.parametrize("steps", [1, 100])
+def test_small_3d_populations(gpu, oracle_mod, steps):
+    w = W.small_3d()
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(steps)
+    orc.step(steps)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+
+
+def test_small_3d_observables(gpu, oracle_mod):
+    w = W.small_3d()
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    for _ in range(4):
+        sim.step(25)
+        orc.step(25)
+        compare_obs(sim, orc)
+
+
+def test_droplet_2d_128x64(gpu, oracle_mod):
+    """The 2D 128x64 pillar-row workload: populations after 100 steps, observables every
+    100 steps up to 600."""
+    w = W.droplet_2d_128x64()
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(100)
+    orc.step(100)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+    compare_obs(sim, orc)
+    for _ in range(5):
+        sim.step(100)
+        orc.step(100)
+        compare_obs(sim, orc)
+
+
+def test_droplet_3d_128x64x64_full_size(gpu, oracle_mod):
+    """The 3D 128x64x64 workload at full size, in the launch configuration the benchmark
+    times: every population after 2 steps."""
+    w = W.droplet_3d_128x64x64()
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(2)
+    orc.step(2)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+    compare_obs(sim, orc, keys=("f_ele", "f_ele_total"))
+
+
+def test_electrode_switching_parity(gpu, oracle_mod):
+    """lbehd_set_electrodes mid-run matches the oracle switching at the same step."""
+    w = W.droplet_3d(32, 16, 16, R=5.0, pillar_h=3,
+                     electrodes=[(4, 10, 4, 12), (20, 28, 4, 12)], V=[0.05, 0.0], seed=11)
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(20)
+    orc.step(20)
+    sim.set_electrodes([0.0, 0.06])
+    orc.set_electrodes([0.0, 0.06])
+    sim.step(30)
+    orc.step(30)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+
+
+def test_ragged_and_periodic_edge_cases(gpu, oracle_mod):
+    """nx not a multiple of the block width; an all-fluid periodic box with no electrode
+    (the Poisson right-hand side is zero: phi = 0)."""
+    w = W.small_2d(nx=50, ny=30)
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.step(30)
+    orc.step(30)
+    compare_populations(sim, orc)
+
+    n = 20
+    shape = (1, n, n)
+    _, yy, xx = np.meshgrid(np.arange(1), np.arange(n), np.arange(n), indexing="ij")
+    pd = 0.5 * (1 - np.tanh(2 * (np.sqrt((xx - 10) ** 2 + (yy - 10) ** 2) - 5) / 5))
+    phi = np.stack([pd, 0 * pd, 1 - pd])
+    wp = W.Workload("periodic", 2, shape, np.zeros(shape, np.uint8), np.full(shape, -1, np.int16),
+                    phi, W.make_params(V=()))
+    sim, orc = make_pair(gpu, oracle_mod, wp)
+    sim.step(40)
+    orc.step(40)
+    compare_populations(sim, orc)
+    assert np.abs(sim.array("pot")).max() == 0.0
+
+
+def test_mass_conservation_long_run(gpu):
+    """Per-component mass over 1000 steps of the 3D 128x64x64 workload, FP32 state."""
+    w = W.droplet_3d_128x64x64()
+    sim = gpu.Simulation(w)
+    sim.step(1)
+    m0 = sim.observe()["mass"]
+    sim.step(1000)
+    o = sim.observe()
+    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6
+    assert o["status"] == 0
+
+
+def test_largest_workload_runs(gpu):
+    """384x128x96 long-transport lattice: allocates, steps, stays finite and conserving."""
+    w = W.transport_3d_384x128x96()
+    sim = gpu.Simulation(w)
+    sim.step(2)
+    m0 = sim.observe()["mass"]
+    sim.step(20)
+    o = sim.observe()
+    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6
+
+
+def test_error_paths(gpu):
+    """Non-finite state is reported (not a fault); a Poisson cap of one sweep is reported."""
+    w = W.small_2d()
+    w.phi_init = w.phi_init.copy()
+    w.phi_init[0, 0, 10, 10] = np.nan
+    sim = gpu.Simulation(w)
+    sim.step(2)
+    with pytest.raises(gpu.LBEHDError) as e:
+        sim.observe()
+    assert e.value.code == -4
+
+    w = W.small_2d()
+    w.params = dict(w.params, poisson_max_iter=1, poisson_tol=1e-12)
+    sim = gpu.Simulation(w, poisson_check_every=1)
+    assert sim.step(3) == -3
+
+
+def test_zero_copy_views(gpu):
+    w = W.small_3d()
+    sim = gpu.Simulation(w)
+    sim.step(3)
+    t = sim.tensor("phi").cpu().numpy()
+    assert np.array_equal(t, sim.array("phi"))
+    assert sim.launch_count() > 0
