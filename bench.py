@@ -178,7 +178,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(dev)
     mode = lbehd.POISSON_FIXED if args.poisson == "fixed" else lbehd.POISSON_HOST
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=mode,
-                           poisson_fixed_sweeps=args.fixed_sweeps,
+                           poisson_fixed_iters=args.fixed_iters,
                            poisson_check_every=args.check_every)
     L = args.lb_steps
     fluid = int((w.solid == 0).sum())
@@ -226,9 +226,10 @@ def run_ours(args, world, rank, local):
     coll_avg_s = coll_ms / max(coll_n, 1) / 1e3
     coll_bytes = fluid * COLLIDE_BYTES[w.dim] + w.sites
     achieved = coll_bytes / coll_avg_s / 1e9
-    sweeps_per_step = prof["sor"][1] / max(L * args.steps, 1)
+    solves = max(prof["fields"][1], 1)
+    iters_per_step = (prof["mg"][1] - solves) / solves   # one V-cycle record per iteration
     sb, sp = STEP_BYTES[w.dim]
-    step_bytes = w.sites * (sb + sp * sweeps_per_step)
+    step_bytes = w.sites * (sb + sp * iters_per_step)
     step_gbs = step_bytes / (ms / 1e3 / (L * args.steps)) / 1e9
     share = {k: round(v[0] / ms, 4) for k, v in prof.items()}
 
@@ -248,9 +249,10 @@ def run_ours(args, world, rank, local):
             "config": {
                 "workload": w.name, "sites": w.sites, "fluid_sites": fluid,
                 "lb_steps_per_step": L, "parallelism": f"replicas{world}",
-                "poisson": args.poisson, "poisson_sweeps_per_lb_step": sweeps_per_step,
+                "poisson": f"MG-preconditioned CG on the increment, {args.poisson} convergence",
+                "poisson_iters_per_lb_step": iters_per_step,
                 "l2": "state (~350 MB) larger than the 126 MB L2; no flush",
-                "step_bytes_model_per_site": sb + sp * sweeps_per_step,
+                "step_bytes_model_per_site": sb + sp * iters_per_step,
                 "step_gbs_model": step_gbs,
                 "kernel_time_share": share,
             },
@@ -278,8 +280,8 @@ def main():
     ap.add_argument("--workload", default="droplet_3d_128x64x64")
     ap.add_argument("--lb-steps", type=int, default=20)
     ap.add_argument("--poisson", choices=["host", "fixed"], default="host")
-    ap.add_argument("--fixed-sweeps", type=int, default=8)
-    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--fixed-iters", type=int, default=2)
+    ap.add_argument("--check-every", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

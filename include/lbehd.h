@@ -19,7 +19,7 @@
  *    cfg->alloc/cfg->free when given (e.g. PyTorch's caching allocator), else cudaMalloc.
  *  - All GPU work is enqueued on cfg->stream (a cudaStream_t; NULL = legacy stream).
  *    lbehd_step() returns after enqueueing, except for the host round trips of the
- *    Poisson convergence test (see lbehd_config.poisson_mode). lbehd_observe(),
+ *    Poisson convergence test in LBEHD_POISSON_HOST mode. lbehd_observe(),
  *    lbehd_copy_out() and lbehd_destroy() synchronise the stream.
  *  - Lattice: site index i = x + nx * (y + ny * z), x fastest. 2D runs use nz = 1 and the
  *    vertical axis is y; 3D runs use z. All axes are periodic; walls are solid nodes.
@@ -52,9 +52,10 @@ extern "C" {
 
 #define LBEHD_MAX_ELECTRODES 64
 
-/* Poisson convergence control. */
-#define LBEHD_POISSON_HOST 0   /* host checks the FP64 residual every poisson_check_every sweeps */
-#define LBEHD_POISSON_FIXED 1  /* exactly poisson_fixed_sweeps sweeps per step, residual recorded */
+/* Poisson (Eq. 13) solve per step: preconditioned CG on the potential increment, one
+ * multigrid V-cycle as preconditioner. Convergence control: */
+#define LBEHD_POISSON_HOST 0   /* host reads the FP64 residual every poisson_check_every iterations */
+#define LBEHD_POISSON_FIXED 1  /* exactly poisson_fixed_iters iterations, no host round trip */
 
 /* Solid classes (cfg->solid): 0 fluid, 1 substrate (wetting angles theta_ij apply),
  * 2 neutral wall (all angles 90 degrees). Electrode ids (cfg->electrode_id), meaningful
@@ -77,11 +78,14 @@ typedef struct lbehd_config {
     double body_force[3];    /* uniform body force density added to F */
     double s_bulk;           /* relaxation rate of the trace of the momentum flux (1) */
     double poisson_tol;      /* relative residual ||b - A phi||_2 / ||b||_2 to stop at */
-    int poisson_max_iter;    /* red-black sweep cap per step */
-    int poisson_check_every; /* sweeps between residual checks (LBEHD_POISSON_HOST) */
+    int poisson_max_iter;    /* cap on preconditioned-CG iterations per step */
     int poisson_mode;        /* LBEHD_POISSON_HOST or LBEHD_POISSON_FIXED */
-    int poisson_fixed_sweeps;/* sweeps per step in LBEHD_POISSON_FIXED */
-    double poisson_omega;    /* SOR factor; <= 0 picks 2 / (1 + sin(pi / H_vertical)) */
+    int poisson_check_every; /* iterations between host convergence checks (HOST mode) */
+    int poisson_fixed_iters; /* iterations per step in LBEHD_POISSON_FIXED */
+    int mg_nu;               /* red-black pre/post smoothing sweeps per level (0 -> 2) */
+    int mg_coarse_sweeps;    /* symmetric sweep pairs on the coarsest level (0 -> 8) */
+    int mg_max_levels;       /* multigrid levels (0 -> as many as the extents allow) */
+    double mg_scale;         /* scale of the Galerkin coarse operators (0 -> 0.6) */
     int n_electrodes;
     const double *electrode_V; /* host, n_electrodes initial potentials */
     void *(*alloc)(size_t bytes, void *ctx); /* optional device allocator */
@@ -102,7 +106,7 @@ typedef struct lbehd_obs {
     double f_drag[3];        /* f_ele - M1 (V^n - V^{n-1}): drag from the force balance */
     double mass[3];          /* sum Phi_i, per component */
     double charge;           /* sum rho_e */
-    int poisson_iters;       /* sweeps used by the last step's Poisson solve */
+    int poisson_iters;       /* CG iterations of the last step's Poisson solve */
     double poisson_resid;    /* its final relative residual */
     int status;              /* LBEHD_OK or the first error code recorded */
 } lbehd_obs;
@@ -162,8 +166,8 @@ long long lbehd_launch_count(lbehd_handle *h);
  * launch of the handle is bracketed by CUDA events recorded on cfg->stream. Kernel
  * classes: */
 #define LBEHD_KC_FIELDS 0   /* moments + wetting ghosts */
-#define LBEHD_KC_SOR 1      /* red-black Poisson sweeps */
-#define LBEHD_KC_RESIDUAL 2 /* residual norm and its final reduction */
+#define LBEHD_KC_MG 1       /* multigrid setup, smoothing and transfers */
+#define LBEHD_KC_CG 2       /* CG vector kernels, reductions and the increment update */
 #define LBEHD_KC_COLLIDE 3  /* fused forces + collide + stream of all populations */
 #define LBEHD_KC_OBS 4      /* observable reduction */
 #define LBEHD_NKC 5

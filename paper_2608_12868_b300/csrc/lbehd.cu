@@ -13,6 +13,7 @@
 
 #include "../../include/lbehd.h"
 #include "kernels.cuh"
+#include "poisson.cuh"
 
 namespace lbehd {
 
@@ -41,20 +42,35 @@ struct lbehd_handle {
     float *u = nullptr, *q = nullptr, *pot = nullptr, *eps = nullptr, *V = nullptr;
     uint8_t *info = nullptr, *normal = nullptr;
     int16_t *elec = nullptr;
-    double *obs_partials = nullptr, *obs = nullptr, *res_partials = nullptr, *res = nullptr;
+    double *obs_partials = nullptr, *obs = nullptr;
     int *flag = nullptr;
-    double *h_res = nullptr;       // pinned: residual sums
+    // Poisson: multigrid hierarchy (level 0 = the lattice) and CG vectors on level 0
+    struct Level {
+        MgDims d;
+        size_t n = 0;
+        int cz2 = 0;               // coarsening to the next level halves z too
+        float *D = nullptr, *kx = nullptr, *ky = nullptr, *kz = nullptr, *x = nullptr, *b = nullptr;
+        dim3 grid, grid_half;
+    };
+    std::vector<Level> mg;
+    float *delta = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
+    double *cg_partials = nullptr;
+    CgScalars *cg_s = nullptr;
+    CgScalars *h_cg = nullptr;     // pinned copy for the host convergence check
+    dim3 grid1d;
+    size_t nblocks1d = 0;
+    int mg_nu = 2, mg_coarse = 8;
+    float mg_scale = 0.6f;
     int cur = 0;                   // population buffer holding the state at time n
     int pcur = 0;                  // phi / rho buffer holding the last step's fields
     bool first = true;
     long long step = 0;
     long long launches = 0;
-    float omega = 1.0f;
     int last_iters = 0;
     double last_resid = 0.0;
     int status = LBEHD_OK;
     std::string err;
-    dim3 grid, block, grid_sor;
+    dim3 grid, block;
     size_t nblocks = 0;
     // profiling: event pairs recorded around launches, per kernel class
     bool prof = false;
@@ -186,69 +202,128 @@ int launch_fields(lbehd_handle *h)
     return LBEHD_OK;
 }
 
-template <int D>
-int residual(lbehd_handle *h, double *rr, double *bb)
+void mg_gs(lbehd_handle *h, const lbehd_handle::Level &L, int color)
 {
-    launch(h, LBEHD_KC_RESIDUAL, 2, [&] {
-        k_residual<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->eps, h->rho[h->pcur],
-                                                            h->info, h->res_partials);
-        k_residual_final<<<1, 256, 0, h->stream>>>(h->res_partials, (long long)h->nblocks, h->res);
+    k_mg_gs<<<L.grid_half, h->block, 0, h->stream>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, color);
+}
+
+// One symmetric V-cycle: x_l ~= A_l^-1 b_l, starting from x_l = 0.
+void vcycle(lbehd_handle *h, size_t l)
+{
+    const auto &L = h->mg[l];
+    cudaMemsetAsync(L.x, 0, L.n * sizeof(float), h->stream);
+    if (l + 1 == h->mg.size()) {
+        for (int s = 0; s < h->mg_coarse; s++) {
+            mg_gs(h, L, 0);
+            mg_gs(h, L, 1);
+            mg_gs(h, L, 1);
+            mg_gs(h, L, 0);
+        }
+        return;
+    }
+    for (int s = 0; s < h->mg_nu; s++) {
+        mg_gs(h, L, 0);
+        mg_gs(h, L, 1);
+    }
+    const auto &C = h->mg[l + 1];
+    k_mg_restrict<<<C.grid, h->block, 0, h->stream>>>(L.d, C.d, L.cz2, L.D, L.kx, L.ky, L.kz, L.b,
+                                                       L.x, C.b);
+    vcycle(h, l + 1);
+    k_mg_prolong<<<L.grid, h->block, 0, h->stream>>>(L.d, C.d, L.cz2, L.D, C.x, L.x);
+    for (int s = 0; s < h->mg_nu; s++) {
+        mg_gs(h, L, 1);
+        mg_gs(h, L, 0);
+    }
+}
+
+int vcycle_launches(const lbehd_handle *h)
+{
+    const int levels = (int)h->mg.size();
+    return (levels - 1) * (4 * h->mg_nu + 2) + 4 * h->mg_coarse;   // memsets not counted
+}
+
+void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
+{
+    k_pcg_scalar<<<1, 256, 0, h->stream>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s);
+}
+
+// One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x).
+void pcg_iteration(lbehd_handle *h)
+{
+    auto &L0 = h->mg[0];
+    launch(h, LBEHD_KC_MG, vcycle_launches(h), [&] { vcycle(h, 0); });
+    launch(h, LBEHD_KC_CG, 8, [&] {
+        k_pcg_dot<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_r, L0.x, h->cg_partials);
+        cg_scalar(h, 1, 1, h->nblocks1d);
+        k_pcg_p<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.x, h->cg_p, h->cg_s);
+        k_pcg_Ap<<<L0.grid, h->block, 0, h->stream>>>(L0.d, L0.D, L0.kx, L0.ky, L0.kz, h->cg_p,
+                                                       h->cg_q, h->cg_partials);
+        cg_scalar(h, 1, 2, h->nblocks);
+        k_pcg_update<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_p, h->cg_q, h->delta,
+                                                             h->cg_r, h->cg_s, h->cg_partials);
+        cg_scalar(h, 1, 3, h->nblocks1d);
     });
-    CK(h, cudaMemcpyAsync(h->h_res, h->res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+}
+
+int read_cg(lbehd_handle *h)
+{
+    CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    *rr = h->h_res[0];
-    *bb = h->h_res[1];
     return LBEHD_OK;
 }
 
-template <int D>
-void sweep(lbehd_handle *h)
-{
-    launch(h, LBEHD_KC_SOR, 2, [&] {
-        for (int color = 0; color < 2; color++)
-            k_sor<D><<<h->grid_sor, h->block, 0, h->stream>>>(h->P, h->pot, h->eps,
-                                                              h->rho[h->pcur], h->info, color,
-                                                              h->omega);
-    });
-}
-
-// Gauss law (Eq. 13): red-black SOR from the previous step's potential.
+// Gauss law (Eq. 13) for this step: operator set-up, FP64 defect of the warm start,
+// preconditioned CG on the increment, phi += delta.
 template <int D>
 int poisson(lbehd_handle *h)
 {
     const lbehd_config &c = h->cfg;
+    auto &L0 = h->mg[0];
+    launch(h, LBEHD_KC_MG, (int)h->mg.size(), [&] {
+        k_mg_setup0<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->eps, h->info, L0.D, L0.kx,
+                                                             L0.ky, L0.kz);
+        for (size_t l = 0; l + 1 < h->mg.size(); l++) {
+            const auto &F = h->mg[l];
+            const auto &C = h->mg[l + 1];
+            k_mg_coarsen<<<C.grid, h->block, 0, h->stream>>>(F.d, C.d, F.cz2, h->mg_scale, F.D,
+                                                             F.kx, F.ky, F.kz, C.D, C.kx, C.ky,
+                                                             C.kz);
+        }
+    });
+    launch(h, LBEHD_KC_CG, 2, [&] {
+        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->delta, h->eps,
+                                                            h->rho[h->pcur], h->info, L0.D,
+                                                            h->cg_r, h->cg_partials);
+        cg_scalar(h, 2, 0, h->nblocks);
+    });
     int iters = 0;
+    bool converged = true;
     if (c.poisson_mode == LBEHD_POISSON_FIXED) {
-        for (; iters < c.poisson_fixed_sweeps; iters++)
-            sweep<D>(h);
+        for (; iters < c.poisson_fixed_iters; iters++)
+            pcg_iteration(h);
         h->last_iters = iters;
-        h->last_resid = -1.0;   // not measured in this mode
-        return LBEHD_OK;
-    }
-    double rr = 0.0, bb = 0.0;
-    int rc = residual<D>(h, &rr, &bb);
-    if (rc)
-        return rc;
-    if (bb == 0.0) {
-        // no charge and every Dirichlet value zero: phi = 0
-        CK(h, cudaMemsetAsync(h->pot, 0, h->N * sizeof(float), h->stream));
-        h->last_iters = 0;
-        h->last_resid = 0.0;
-        return LBEHD_OK;
-    }
-    const double tol2 = c.poisson_tol * c.poisson_tol * bb;
-    while (rr > tol2 && iters < c.poisson_max_iter) {
-        const int k = std::min(std::max(c.poisson_check_every, 1), c.poisson_max_iter - iters);
-        for (int s = 0; s < k; s++)
-            sweep<D>(h);
-        iters += k;
-        rc = residual<D>(h, &rr, &bb);
+        h->last_resid = -1.0;   // read back by lbehd_observe
+    } else {
+        int rc = read_cg(h);
         if (rc)
             return rc;
+        const int every = std::max(c.poisson_check_every, 1);
+        while (!h->h_cg->done) {
+            for (int k = 0; k < every; k++)
+                pcg_iteration(h);
+            rc = read_cg(h);
+            if (rc)
+                return rc;
+        }
+        iters = h->h_cg->iters;
+        converged = h->h_cg->converged != 0;
+        h->last_iters = iters;
+        h->last_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
     }
-    h->last_iters = iters;
-    h->last_resid = std::sqrt(rr / bb);
-    if (rr > tol2) {
+    launch(h, LBEHD_KC_CG, 1, [&] {
+        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.D, h->delta, h->pot);
+    });
+    if (!converged) {
         h->status = h->status ? h->status : LBEHD_ERR_POISSON_NOCONV;
         return LBEHD_ERR_POISSON_NOCONV;
     }
@@ -327,9 +402,9 @@ int set_params(lbehd_handle *h)
     P.inv_tau_phi = (float)(1.0 / (0.5 + c.mobility / cs2));
     P.inv_tau_rho = (float)(1.0 / (0.5 + c.alpha / cs2s));
     P.s_bulk = (float)c.s_bulk;
-    const int hv = h->dim == 3 ? h->nz : h->ny;
-    h->omega = c.poisson_omega > 0.0 ? (float)c.poisson_omega
-                                     : (float)(2.0 / (1.0 + std::sin(3.14159265358979 / std::max(hv, 2))));
+    h->mg_nu = c.mg_nu > 0 ? c.mg_nu : 2;
+    h->mg_coarse = c.mg_coarse_sweeps > 0 ? c.mg_coarse_sweeps : 8;
+    h->mg_scale = c.mg_scale > 0.0 ? (float)c.mg_scale : 0.6f;
     return LBEHD_OK;
 }
 
@@ -357,6 +432,13 @@ int init_impl(lbehd_handle *h)
         elec[i] = (int16_t)(s ? id : -1);
     }
     build_normals<D>(h, c.solid, normal);
+    if (D == 3 && h->nz % 2) {
+        const size_t plane = (size_t)h->nx * h->ny;
+        for (size_t k = 0; k < plane; k++)
+            if (!c.solid[k] && !c.solid[(h->nz - 1) * plane + k])
+                return fail(h, LBEHD_ERR_INVALID_ARG,
+                            "odd nz needs a solid bottom or top layer (red-black colouring)");
+    }
     // device buffers
     const size_t fb = sizeof(float);
     for (int b = 0; b < 2; b++) {
@@ -378,17 +460,61 @@ int init_impl(lbehd_handle *h)
     h->elec = (int16_t *)dev_alloc(h, N * sizeof(int16_t));
     h->block = dim3(BX, 1, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, h->ny, h->nz);
-    h->grid_sor = dim3((h->nx / 2 + BX - 1) / BX, h->ny, h->nz);
     h->nblocks = (size_t)h->grid.x * h->grid.y * h->grid.z;
     h->obs_partials = (double *)dev_alloc(h, NOBS * h->nblocks * sizeof(double));
     h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
-    h->res_partials = (double *)dev_alloc(h, 2 * h->nblocks * sizeof(double));
-    h->res = (double *)dev_alloc(h, 2 * sizeof(double));
     h->flag = (int *)dev_alloc(h, sizeof(int));
     if (!h->u || !h->q || !h->pot || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
-        !h->obs_partials || !h->obs || !h->res_partials || !h->res || !h->flag)
+        !h->obs_partials || !h->obs || !h->flag)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (fields)");
-    CK(h, cudaMallocHost(&h->h_res, 2 * sizeof(double)));
+    // Poisson: CG vectors, reductions, multigrid hierarchy
+    h->grid1d = dim3((unsigned)((N + BX - 1) / BX), 1, 1);
+    h->nblocks1d = h->grid1d.x;
+    h->delta = (float *)dev_alloc(h, N * fb);
+    h->cg_r = (float *)dev_alloc(h, N * fb);
+    h->cg_p = (float *)dev_alloc(h, N * fb);
+    h->cg_q = (float *)dev_alloc(h, N * fb);
+    h->cg_partials = (double *)dev_alloc(h, 2 * std::max(h->nblocks, h->nblocks1d) * sizeof(double));
+    h->cg_s = (CgScalars *)dev_alloc(h, sizeof(CgScalars));
+    if (!h->delta || !h->cg_r || !h->cg_p || !h->cg_q || !h->cg_partials || !h->cg_s)
+        return fail(h, LBEHD_ERR_OOM, "device allocation failed (Poisson)");
+    {
+        MgDims d{h->nx, h->ny, h->nz};
+        const int maxl = c.mg_max_levels > 0 ? c.mg_max_levels : 16;
+        while ((int)h->mg.size() < maxl) {
+            lbehd_handle::Level L;
+            L.d = d;
+            L.n = (size_t)d.nx * d.ny * d.nz;
+            L.grid = dim3((d.nx + BX - 1) / BX, d.ny, d.nz);
+            L.grid_half = dim3((d.nx / 2 + 1 + BX - 1) / BX, d.ny, d.nz);
+            L.D = (float *)dev_alloc(h, L.n * fb);
+            L.kx = (float *)dev_alloc(h, L.n * fb);
+            L.ky = (float *)dev_alloc(h, L.n * fb);
+            L.kz = (float *)dev_alloc(h, L.n * fb);
+            L.x = (float *)dev_alloc(h, L.n * fb);
+            L.b = h->mg.empty() ? h->cg_r : (float *)dev_alloc(h, L.n * fb);
+            if (!L.D || !L.kx || !L.ky || !L.kz || !L.x || !L.b)
+                return fail(h, LBEHD_ERR_OOM, "device allocation failed (multigrid)");
+            // keep x and y even on every level (red-black colouring across the periodic wrap)
+            const bool more = d.nx % 4 == 0 && d.ny % 4 == 0 && (h->dim == 2 || d.nz >= 4);
+            L.cz2 = (more && h->dim == 3) ? 1 : 0;
+            h->mg.push_back(L);
+            if (!more)
+                break;
+            d = MgDims{d.nx / 2, d.ny / 2, h->dim == 3 ? (d.nz + 1) / 2 : 1};
+        }
+        h->mg.back().cz2 = 0;
+    }
+    CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
+    {
+        CgScalars s0{};
+        s0.tol2 = c.poisson_tol * c.poisson_tol;
+        s0.max_iter = c.poisson_max_iter;
+        CK(h, cudaMemcpyAsync(h->cg_s, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        CK(h, cudaMemsetAsync(h->delta, 0, N * fb, h->stream));
+        CK(h, cudaMemsetAsync(h->cg_p, 0, N * fb, h->stream));
+    }
     std::vector<float> phi0(3 * N), V(LBEHD_MAX_ELECTRODES, 0.0f);
     for (size_t k = 0; k < 3 * N; k++)
         phi0[k] = (float)c.phi_init[k];
@@ -451,9 +577,9 @@ void release(lbehd_handle *h)
             cudaFree(b.ptr);
     }
     h->bufs.clear();
-    if (h->h_res)
-        cudaFreeHost(h->h_res);
-    h->h_res = nullptr;
+    if (h->h_cg)
+        cudaFreeHost(h->h_cg);
+    h->h_cg = nullptr;
 }
 
 }  // namespace
@@ -476,7 +602,7 @@ int lbehd_init(const lbehd_config *cfg, lbehd_handle **out)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "bad lattice extents");
     if (cfg->nx % 2 || (cfg->dim == 3 && cfg->ny % 2))
         return fail(nullptr, LBEHD_ERR_INVALID_ARG,
-                    "periodic extents must be even (red-black ordering of the Poisson sweep)");
+                    "periodic extents must be even (red-black ordering of the Poisson smoother)");
     if (cfg->ny > 65535 || cfg->nz > 65535)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "ny and nz must be <= 65535");
     if (!cfg->solid || !cfg->phi_init)

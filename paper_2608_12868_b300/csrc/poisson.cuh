@@ -1,0 +1,414 @@
+// poisson.cuh -- Gauss law (Eq. 13) on the GPU: multigrid-preconditioned conjugate
+// gradients on the per-step increment of the potential.
+//
+// Each step solves A delta = r0 with r0 = b - A phi^{n-1}, where A is the 7/5-point
+// finite-volume operator of div(eps grad .) (face eps = (eps_i + eps_j)/2, Dirichlet value
+// on the solid node with face eps = eps_fluid, zero flux elsewhere) and b = rho_e + Dirichlet
+// terms. r0 is formed in FP64 from the FP32 state (phi^{n-1} + delta_warm, eps, rho_e are
+// exact in double), so the FP32 iteration on the small increment is not limited by the
+// rounding of phi itself. The warm start is the previous step's increment.
+//
+// Preconditioner: one symmetric V-cycle of cell-centred geometric multigrid. Coarse cells
+// aggregate 2x2(x2) fine cells; coarse face coefficients are the sums of the fine faces
+// they cover and the coarse diagonal is the sum of the children's diagonals minus twice
+// their internal faces (Galerkin operator for piecewise-constant prolongation), both scaled
+// by mg_scale (< 1 over-corrects, which compensates the weak constant interpolation).
+// Smoother: red-black Gauss-Seidel, (red, black)^nu before and (black, red)^nu after the
+// coarse correction; the coarsest level runs symmetric sweeps. A cell is active when its
+// diagonal is positive.
+//
+// CG scalars (alpha, beta, r.z, ...) stay in device memory, so an iteration needs no host
+// round trip; reductions are FP32 within a warp and FP64 across warps and blocks.
+#pragma once
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace lbehd {
+
+struct MgDims {
+    int nx, ny, nz;
+};
+
+struct CgScalars {
+    double rz;        // r . z of the current iteration
+    double rz_old;
+    double pq;        // p . A p
+    double rr;        // ||r||^2 (current residual)
+    double bb;        // ||b||^2
+    double alpha, beta;
+    double tol2;      // tol^2 (set by the host)
+    int iters;
+    int max_iter;
+    int done;         // 1 once rr <= tol2 * bb or iters >= max_iter
+    int converged;
+};
+
+__device__ __forceinline__ size_t cell(const MgDims &d, int x, int y, int z)
+{
+    return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
+}
+
+__device__ __forceinline__ int wrapp(int v, int n) { return v + 1 == n ? 0 : v + 1; }
+__device__ __forceinline__ int wrapm(int v, int n) { return v == 0 ? n - 1 : v - 1; }
+
+// Block reduction of up to 4 FP32 values into FP64 partials[k * nblk + blk].
+template <int NV>
+__device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
+{
+    __shared__ double sm[NV][BX / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const float s = warp_sum(v[k]);
+        if (lane == 0)
+            sm[k][wid] = (double)s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < BX / 32; w++)
+            acc += sm[threadIdx.x][w];
+        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
+        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+        partials[threadIdx.x * nblk + blk] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- level-0 operator
+
+// Face coefficients to the +x/+y/+z neighbours and the diagonal (all faces, Dirichlet
+// faces included) from eps and the node classes.
+template <int D>
+__global__ void __launch_bounds__(BX) k_mg_setup0(Params P, const float *__restrict__ eps,
+                                                  const uint8_t *__restrict__ info,
+                                                  float *__restrict__ Dg, float *__restrict__ kx,
+                                                  float *__restrict__ ky, float *__restrict__ kz)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx)
+        return;
+    const MgDims d{P.nx, P.ny, P.nz};
+    const size_t i = cell(d, x, y, z);
+    float kp[3] = {0.f, 0.f, 0.f}, diag = 0.0f;
+    if ((info[i] & 3) == PT_FLUID) {
+        const float ei = eps[i];
+        const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
+                              cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
+                              cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
+#pragma unroll
+        for (int f = 0; f < 2 * D; f++) {
+            const int pt = info[nb[f]] & 3;
+            float k = 0.0f;
+            if (pt == PT_FLUID)
+                k = 0.5f * (ei + eps[nb[f]]);
+            else if (pt == PT_DIRICHLET)
+                k = ei;
+            diag += k;
+            if ((f & 1) == 0)
+                kp[f >> 1] = pt == PT_FLUID ? k : 0.0f;
+        }
+    }
+    Dg[i] = diag;
+    kx[i] = kp[0];
+    ky[i] = kp[1];
+    kz[i] = kp[2];
+}
+
+// Galerkin coarsening (scaled) of one level.
+__global__ void __launch_bounds__(BX) k_mg_coarsen(MgDims f, MgDims c, int cz2, float scale,
+                                                   const float *__restrict__ Df,
+                                                   const float *__restrict__ kxf,
+                                                   const float *__restrict__ kyf,
+                                                   const float *__restrict__ kzf,
+                                                   float *__restrict__ Dc, float *__restrict__ kxc,
+                                                   float *__restrict__ kyc, float *__restrict__ kzc)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
+    if (X >= c.nx)
+        return;
+    const int nzc = cz2 ? 2 : 1;
+    float dsum = 0.f, internal = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int g = 0; g < nzc; g++) {
+                const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
+                if (x >= f.nx || y >= f.ny || z >= f.nz)
+                    continue;
+                const size_t i = cell(f, x, y, z);
+                dsum += Df[i];
+                // +x face: internal if the +x child exists in this coarse cell
+                if (a == 0 && x + 1 < f.nx)
+                    internal += kxf[i];
+                else
+                    fx += kxf[i];
+                if (b == 0 && y + 1 < f.ny)
+                    internal += kyf[i];
+                else
+                    fy += kyf[i];
+                if (cz2) {
+                    if (g == 0 && z + 1 < f.nz)
+                        internal += kzf[i];
+                    else
+                        fz += kzf[i];
+                }
+            }
+    const size_t I = cell(c, X, Y, Z);
+    const float dc = dsum - 2.0f * internal;
+    Dc[I] = dc > 0.0f ? scale * dc : 0.0f;
+    kxc[I] = scale * fx;
+    kyc[I] = scale * fy;
+    kzc[I] = scale * fz;
+}
+
+// ---------------------------------------------------------------- smoother / transfers
+
+__device__ __forceinline__ float offdiag_sum(const MgDims &d, size_t i, int x, int y, int z,
+                                             const float *__restrict__ kx,
+                                             const float *__restrict__ ky,
+                                             const float *__restrict__ kz,
+                                             const float *__restrict__ v)
+{
+    const int xp = wrapp(x, d.nx), xm = wrapm(x, d.nx);
+    const int yp = wrapp(y, d.ny), ym = wrapm(y, d.ny);
+    float s = kx[i] * v[cell(d, xp, y, z)] + kx[cell(d, xm, y, z)] * v[cell(d, xm, y, z)] +
+              ky[i] * v[cell(d, x, yp, z)] + ky[cell(d, x, ym, z)] * v[cell(d, x, ym, z)];
+    if (d.nz > 1) {
+        const int zp = wrapp(z, d.nz), zm = wrapm(z, d.nz);
+        s += kz[i] * v[cell(d, x, y, zp)] + kz[cell(d, x, y, zm)] * v[cell(d, x, y, zm)];
+    }
+    return s;
+}
+
+// One red-black Gauss-Seidel half sweep of A x = b on one level.
+__global__ void __launch_bounds__(BX) k_mg_gs(MgDims d, const float *__restrict__ Dg,
+                                              const float *__restrict__ kx,
+                                              const float *__restrict__ ky,
+                                              const float *__restrict__ kz,
+                                              const float *__restrict__ b, float *__restrict__ xv,
+                                              int color)
+{
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + z + color) & 1);
+    if (x >= d.nx)
+        return;
+    const size_t i = cell(d, x, y, z);
+    const float di = Dg[i];
+    if (di <= 0.0f)
+        return;
+    xv[i] = (b[i] + offdiag_sum(d, i, x, y, z, kx, ky, kz, xv)) / di;
+}
+
+// b_c = restriction (sum over children) of the fine residual b_f - A_f x_f.
+__global__ void __launch_bounds__(BX) k_mg_restrict(MgDims f, MgDims c, int cz2,
+                                                    const float *__restrict__ Df,
+                                                    const float *__restrict__ kx,
+                                                    const float *__restrict__ ky,
+                                                    const float *__restrict__ kz,
+                                                    const float *__restrict__ bf,
+                                                    const float *__restrict__ xf,
+                                                    float *__restrict__ bc)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
+    if (X >= c.nx)
+        return;
+    const int nzc = cz2 ? 2 : 1;
+    float acc = 0.0f;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int g = 0; g < nzc; g++) {
+                const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
+                if (x >= f.nx || y >= f.ny || z >= f.nz)
+                    continue;
+                const size_t i = cell(f, x, y, z);
+                const float di = Df[i];
+                if (di <= 0.0f)
+                    continue;
+                acc += bf[i] - (di * xf[i] - offdiag_sum(f, i, x, y, z, kx, ky, kz, xf));
+            }
+    bc[cell(c, X, Y, Z)] = acc;
+}
+
+// x_f += x_c(parent) on active fine cells.
+__global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
+                                                   const float *__restrict__ Df,
+                                                   const float *__restrict__ xc,
+                                                   float *__restrict__ xf)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= f.nx)
+        return;
+    const size_t i = cell(f, x, y, z);
+    if (Df[i] <= 0.0f)
+        return;
+    xf[i] += xc[cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
+}
+
+// ---------------------------------------------------------------- CG on level 0
+
+// r = b - A (phi + delta) in FP64 from the FP32 state; partials of ||r||^2 and ||b||^2.
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restrict__ pot,
+                                                 const float *__restrict__ delta,
+                                                 const float *__restrict__ eps,
+                                                 const float *__restrict__ rho,
+                                                 const uint8_t *__restrict__ info,
+                                                 const float *__restrict__ Dg,
+                                                 float *__restrict__ r, double *__restrict__ partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    float v[2] = {0.f, 0.f};
+    if (x < P.nx) {
+        const MgDims d{P.nx, P.ny, P.nz};
+        const size_t i = cell(d, x, y, z);
+        double ri = 0.0;
+        if (Dg[i] > 0.0f) {
+            const double ei = eps[i];
+            const double pi = (double)pot[i] + (double)delta[i];
+            double b = rho[i], Ax = 0.0;
+            const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
+                                  cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
+                                  cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
+#pragma unroll
+            for (int f = 0; f < 2 * D; f++) {
+                const int pt = info[nb[f]] & 3;
+                if (pt == PT_FLUID) {
+                    const double k = 0.5 * (ei + (double)eps[nb[f]]);
+                    Ax += k * (pi - ((double)pot[nb[f]] + (double)delta[nb[f]]));
+                } else if (pt == PT_DIRICHLET) {
+                    b += ei * (double)pot[nb[f]];
+                    Ax += ei * pi;
+                }
+            }
+            ri = b - Ax;
+            v[0] = (float)(ri * ri);
+            v[1] = (float)(b * b);
+        }
+        r[i] = (float)ri;
+    }
+    block_partials<2>(v, partials);
+}
+
+// p = z + beta p (beta = 0 on the first iteration).
+__global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict__ zv,
+                                              float *__restrict__ p, const CgScalars *__restrict__ s)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float beta = s->iters == 0 ? 0.0f : (float)s->beta;
+    p[i] = zv[i] + (beta != 0.0f ? beta * p[i] : 0.0f);
+}
+
+// q = A p on level 0 and partials of p . q.
+__global__ void __launch_bounds__(BX) k_pcg_Ap(MgDims d, const float *__restrict__ Dg,
+                                               const float *__restrict__ kx,
+                                               const float *__restrict__ ky,
+                                               const float *__restrict__ kz,
+                                               const float *__restrict__ p, float *__restrict__ q,
+                                               double *__restrict__ partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    float v[1] = {0.f};
+    if (x < d.nx) {
+        const size_t i = cell(d, x, y, z);
+        const float di = Dg[i];
+        float qi = 0.0f;
+        if (di > 0.0f) {
+            qi = di * p[i] - offdiag_sum(d, i, x, y, z, kx, ky, kz, p);
+            v[0] = p[i] * qi;
+        }
+        q[i] = qi;
+    }
+    block_partials<1>(v, partials);
+}
+
+// delta += alpha p, r -= alpha q, partials of ||r||^2.
+__global__ void __launch_bounds__(BX) k_pcg_update(size_t n, const float *__restrict__ p,
+                                                   const float *__restrict__ q,
+                                                   float *__restrict__ delta, float *__restrict__ r,
+                                                   const CgScalars *__restrict__ s,
+                                                   double *__restrict__ partials)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    float v[1] = {0.f};
+    if (i < n) {
+        const float a = (float)s->alpha;
+        delta[i] += a * p[i];
+        const float ri = r[i] - a * q[i];
+        r[i] = ri;
+        v[0] = ri * ri;
+    }
+    // 1D grid: reuse the generic block reduction (gridDim.y = gridDim.z = 1)
+    block_partials<1>(v, partials);
+}
+
+// partials of r . z
+__global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restrict__ a,
+                                                const float *__restrict__ b,
+                                                double *__restrict__ partials)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    float v[1] = {i < n ? a[i] * b[i] : 0.0f};
+    block_partials<1>(v, partials);
+}
+
+// Fixed-order FP64 sum of nv partial arrays and the CG scalar update that follows.
+//   op 0: init      rr, bb            -> done if rr <= tol2 bb
+//   op 1: r.z       rz                -> beta = rz / rz_old, rz_old = rz
+//   op 2: p.Ap      pq                -> alpha = rz / pq
+//   op 3: ||r||^2   rr                -> iters++, done / converged
+__global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ partials,
+                                                    long long nblocks, int nv, int op,
+                                                    CgScalars *__restrict__ s)
+{
+    __shared__ double sm[2][256];
+    for (int k = 0; k < nv; k++) {
+        double a = 0.0;
+        for (long long b = threadIdx.x; b < nblocks; b += 256)
+            a += partials[k * nblocks + b];
+        sm[k][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < nv; k++)
+                sm[k][threadIdx.x] += sm[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0)
+        return;
+    if (op == 0) {
+        s->rr = sm[0][0];
+        s->bb = sm[1][0];
+        s->iters = 0;
+        s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
+        s->done = s->converged || s->max_iter <= 0;
+    } else if (op == 1) {
+        s->rz = sm[0][0];
+        s->beta = s->iters == 0 || s->rz_old == 0.0 ? 0.0 : s->rz / s->rz_old;
+        s->rz_old = s->rz;
+    } else if (op == 2) {
+        s->pq = sm[0][0];
+        s->alpha = (!s->done && s->pq > 0.0) ? s->rz / s->pq : 0.0;
+    } else if (!s->done) {
+        s->rr = sm[0][0];
+        s->iters += 1;
+        s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
+        s->done = s->converged || s->iters >= s->max_iter;
+    }
+}
+
+// phi += delta on active cells.
+__global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
+                                                  const float *__restrict__ delta,
+                                                  float *__restrict__ pot)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n && Dg[i] > 0.0f)
+        pot[i] += delta[i];
+}
+
+}  // namespace lbehd

@@ -50,8 +50,10 @@ class Config(ctypes.Structure):
                 ("mobility", ctypes.c_double), ("W", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("body_force", _D3), ("s_bulk", ctypes.c_double),
                 ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
-                ("poisson_check_every", ctypes.c_int), ("poisson_mode", ctypes.c_int),
-                ("poisson_fixed_sweeps", ctypes.c_int), ("poisson_omega", ctypes.c_double),
+                ("poisson_mode", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
+                ("poisson_fixed_iters", ctypes.c_int), ("mg_nu", ctypes.c_int),
+                ("mg_coarse_sweeps", ctypes.c_int), ("mg_max_levels", ctypes.c_int),
+                ("mg_scale", ctypes.c_double),
                 ("n_electrodes", ctypes.c_int),
                 ("electrode_V", ctypes.POINTER(ctypes.c_double)),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
@@ -77,7 +79,7 @@ EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
            "lbehd_launch_count", "lbehd_profile_enable", "lbehd_profile_read",
            "lbehd_last_error", "lbehd_destroy")
-KERNEL_CLASSES = ("fields", "sor", "residual", "collide", "obs")
+KERNEL_CLASSES = ("fields", "mg", "cg", "collide", "obs")
 
 
 def load():
@@ -127,7 +129,8 @@ class Simulation:
     """
 
     def __init__(self, workload, *, stream=None, torch_alloc=True, poisson_mode=POISSON_HOST,
-                 poisson_check_every=8, poisson_fixed_sweeps=8, poisson_omega=0.0, device=0):
+                 poisson_check_every=1, poisson_fixed_iters=2, mg_nu=0, mg_coarse_sweeps=0,
+                 mg_max_levels=0, mg_scale=0.0, device=0):
         import torch
         self._torch = torch
         lib = load()
@@ -155,12 +158,13 @@ class Simulation:
         c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
         c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
         c.s_bulk = p.get("s_bulk", 1.0)
-        c.poisson_tol = p.get("poisson_tol", 1e-6)
-        c.poisson_max_iter = int(p.get("poisson_max_iter", 20000))
+        c.poisson_tol = p.get("poisson_tol", 1e-7)
+        c.poisson_max_iter = int(p.get("poisson_max_iter", 100))
         c.poisson_check_every = int(poisson_check_every)
         c.poisson_mode = int(poisson_mode)
-        c.poisson_fixed_sweeps = int(poisson_fixed_sweeps)
-        c.poisson_omega = float(poisson_omega)
+        c.poisson_fixed_iters = int(poisson_fixed_iters)
+        c.mg_nu, c.mg_coarse_sweeps = int(mg_nu), int(mg_coarse_sweeps)
+        c.mg_max_levels, c.mg_scale = int(mg_max_levels), float(mg_scale)
         c.n_electrodes = len(V)
         c.electrode_V = _dptr(V, ctypes.c_double) if len(V) else None
         if torch_alloc:

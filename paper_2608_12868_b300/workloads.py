@@ -63,7 +63,7 @@ def theta13_from_young(theta12, theta23=THETA23, g=SURFACE_TENSION):
 
 
 def make_params(*, visc_ratio=1.0, theta12=120.0, V=(0.05,), R=16.0, height=64, alpha=None,
-                body=(0.0, 0.0, 0.0), poisson_tol=1e-6, poisson_max_iter=20000):
+                body=(0.0, 0.0, 0.0), poisson_tol=1e-7, poisson_max_iter=100):
     """Lattice-unit parameters. alpha follows alpha* = alpha mu_w / (eps_w R0^2 E0^2) = 1e-4
     with E0 = phi0 / (fluid height)."""
     nu = (NU_DROPLET, NU_DROPLET * visc_ratio, NU_AMBIENT)
