@@ -121,13 +121,14 @@ typedef struct lbehd_handle lbehd_handle;
  *   LBEHD_FRHO  QS*N    charge populations
  *   LBEHD_PHI   3*N     Phi_1..3 (boundary solid nodes hold the wetting ghosts)
  *   LBEHD_RHO   N       rho_e
- *   LBEHD_POT   N       electric potential (Dirichlet nodes hold their value)
+ *   LBEHD_POT   N       electric potential, high part (Dirichlet nodes hold their value)
  *   LBEHD_U     3*N     velocity u = j + F/2
  *   LBEHD_QSRC  N       conduction source div(sigma grad phi)
- *   LBEHD_EPS   N       permittivity */
+ *   LBEHD_EPS   N       permittivity
+ *   LBEHD_POT_LO N      low part of the potential: phi = POT + POT_LO (compensated pair) */
 enum lbehd_array {
     LBEHD_G = 0, LBEHD_FPHI, LBEHD_FRHO, LBEHD_PHI, LBEHD_RHO, LBEHD_POT, LBEHD_U,
-    LBEHD_QSRC, LBEHD_EPS, LBEHD_NARRAYS
+    LBEHD_QSRC, LBEHD_EPS, LBEHD_POT_LO, LBEHD_NARRAYS
 };
 
 /* ABI version and sizeof(lbehd_config), for binding checks. */

@@ -3,8 +3,7 @@
 // One step n -> n+1 runs:
 //   k_fields    Phi_i = sum_n f_Phi_i,n (Eq. 19), rho_e = sum f_rho, permittivity, wetting
 //               ghosts on boundary solid nodes (Eq. 20a), Dirichlet potentials;
-//   k_sor / k_residual   red-black SOR on div(eps grad phi) = -rho_e (Eq. 13) with an FP64
-//               residual norm;
+//   (poisson.cuh) the Gauss law solve, div(eps grad phi) = -rho_e (Eq. 13);
 //   k_collide   per fluid site, everything else fused: isotropic stencils of Phi_i and phi,
 //               chemical potential (Eqs. 10-11), capillary and electric forces (Eq. 12),
 //               sharpening flux (Eq. 18), conduction source of Eq. 14, then collide and
@@ -59,7 +58,7 @@ struct State {
     const float *phi, *phi_prev;      // [3][N] Phi at n and n-1
     const float *rho, *rho_prev;      // rho_e at n and n-1
     float *u, *q;                     // u and conduction source: read as n-1, written as n
-    const float *pot;
+    const float *pot, *pot_lo;        // potential as a compensated pair hi + lo
     const uint8_t *info;
     double *obs_partials;             // [NOBS][nblocks]
     int *flag;                        // bit 0: non-finite value seen
@@ -117,10 +116,11 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict
                                                float *__restrict__ phi_out,
                                                float *__restrict__ rho_out,
                                                float *__restrict__ eps_out, float *__restrict__ pot,
+                                               float *__restrict__ pot_lo,
                                                const uint8_t *__restrict__ info,
                                                const uint8_t *__restrict__ normal,
                                                const int16_t *__restrict__ elec,
-                                               const float *__restrict__ V)
+                                               const double *__restrict__ V)
 {
     using L = Lat<D>;
     constexpr int Q = L::Q;
@@ -179,132 +179,16 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict
         }
         if ((inf & 3) == PT_DIRICHLET) {
             const int id = elec[i];
-            pot[i] = id >= 0 ? V[id] : 0.0f;
+            const double v = id >= 0 ? V[id] : 0.0;
+            const float hi = (float)v;
+            pot[i] = hi;
+            pot_lo[i] = (float)(v - (double)hi);
         }
     }
 #pragma unroll
     for (int c = 0; c < 3; c++)
         phi_out[c * N + i] = Ph[c];
     eps_out[i] = Ph[0] * P.eps[0] + Ph[1] * P.eps[1] + Ph[2] * P.eps[2];
-}
-
-// ---------------------------------------------------------------- Poisson (Eq. 13)
-
-// One red-black SOR half sweep: thread t of a row updates x = 2t + parity.
-template <int D>
-__global__ void __launch_bounds__(BX) k_sor(Params P, float *__restrict__ pot,
-                                            const float *__restrict__ eps,
-                                            const float *__restrict__ rho,
-                                            const uint8_t *__restrict__ info, int color,
-                                            float omega)
-{
-    using L = Lat<D>;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + z + color) & 1);
-    if (x >= P.nx)
-        return;
-    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
-    if ((info[i] & 3) != PT_FLUID)
-        return;
-    const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
-    const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
-    const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
-    const float ei = eps[i];
-    float num = rho[i], den = 0.0f;
-#pragma unroll
-    for (int n = 1; n <= 2 * D; n++) {
-        const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
-        const int pt = info[j] & 3;
-        if (pt == PT_FLUID) {
-            const float k = 0.5f * (ei + eps[j]);
-            num += k * pot[j];
-            den += k;
-        } else if (pt == PT_DIRICHLET) {
-            num += ei * pot[j];
-            den += ei;
-        }
-    }
-    if (den > 0.0f)
-        pot[i] += omega * (num / den - pot[i]);
-}
-
-// Residual r = b - A phi per fluid node; block partials of sum r^2 and sum b^2 (FP64).
-template <int D>
-__global__ void __launch_bounds__(BX) k_residual(Params P, const float *__restrict__ pot,
-                                                 const float *__restrict__ eps,
-                                                 const float *__restrict__ rho,
-                                                 const uint8_t *__restrict__ info,
-                                                 double *__restrict__ partials)
-{
-    using L = Lat<D>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    float rr = 0.0f, bb = 0.0f;
-    if (x < P.nx) {
-        const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
-        if ((info[i] & 3) == PT_FLUID) {
-            const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
-            const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
-            const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
-            const float ei = eps[i], pi = pot[i];
-            float b = rho[i], Ap = 0.0f;
-#pragma unroll
-            for (int n = 1; n <= 2 * D; n++) {
-                const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
-                const int pt = info[j] & 3;
-                if (pt == PT_FLUID) {
-                    Ap += 0.5f * (ei + eps[j]) * (pi - pot[j]);
-                } else if (pt == PT_DIRICHLET) {
-                    b += ei * pot[j];
-                    Ap += ei * pi;
-                }
-            }
-            const float r = b - Ap;
-            rr = r * r;
-            bb = b * b;
-        }
-    }
-    rr = warp_sum(rr);
-    bb = warp_sum(bb);
-    __shared__ double sm[2][BX / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        sm[0][wid] = rr;
-        sm[1][wid] = bb;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double acc = 0.0;
-        for (int k = 0; k < BX / 32; k++)
-            acc += sm[threadIdx.x][k];
-        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-        partials[2 * blk + threadIdx.x] = acc;
-    }
-}
-
-// Sum the residual partials in a fixed order: out[0] = sum r^2, out[1] = sum b^2.
-__global__ void __launch_bounds__(256) k_residual_final(const double *__restrict__ partials,
-                                                        long long nblocks, double *__restrict__ out)
-{
-    __shared__ double sm[2][256];
-    double a = 0.0, b = 0.0;
-    for (long long k = threadIdx.x; k < nblocks; k += 256) {
-        a += partials[2 * k];
-        b += partials[2 * k + 1];
-    }
-    sm[0][threadIdx.x] = a;
-    sm[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
-            sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        out[0] = sm[0][0];
-        out[1] = sm[1][0];
-    }
 }
 
 // ---------------------------------------------------------------- fused collide + stream
@@ -330,7 +214,7 @@ __global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
         // ---- stencils of Phi_i and phi over the flow lattice
         const float Pc[3] = {S.phi[i], S.phi[N + i], S.phi[2 * N + i]};
         const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
-        const float pot_i = S.pot[i];
+        const float pot_i = S.pot[i], lo_i = S.pot_lo[i];
         float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         float lP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
         float qsrc = 0.0f;
@@ -350,16 +234,17 @@ __global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
                 for (int a = 0; a < 3; a++)
                     gP[c][a] += wn * ea[a] * Pn[c];
             }
-            const float potj = S.pot[j];
-            const float ph = pt == PT_NEUMANN ? pot_i : potj;
+            // phi(x + e_n) - phi(x) from the compensated pairs (zero-flux solid: mirror)
+            const float dph =
+                pt == PT_NEUMANN ? 0.0f : (S.pot[j] - pot_i) + (S.pot_lo[j] - lo_i);
 #pragma unroll
             for (int a = 0; a < 3; a++)
-                gpot[a] += wn * ea[a] * ph;
+                gpot[a] += wn * ea[a] * dph;
             if (pt == PT_FLUID) {
                 fluid_nb |= 1u << n;
                 if (n <= 2 * D) {
                     const float sig_j = Pn[0] * P.sig[0] + Pn[1] * P.sig[1] + Pn[2] * P.sig[2];
-                    qsrc += 0.5f * (sig_i + sig_j) * (potj - pot_i);
+                    qsrc += 0.5f * (sig_i + sig_j) * dph;
                 }
             }
         }

@@ -39,7 +39,8 @@ struct lbehd_handle {
     // device state
     float *g[2] = {}, *fphi[2] = {}, *frho[2] = {};
     float *phi[2] = {}, *rho[2] = {};
-    float *u = nullptr, *q = nullptr, *pot = nullptr, *eps = nullptr, *V = nullptr;
+    float *u = nullptr, *q = nullptr, *pot = nullptr, *pot_lo = nullptr, *eps = nullptr;
+    double *V = nullptr;           // electrode potentials (device, FP64)
     uint8_t *info = nullptr, *normal = nullptr;
     int16_t *elec = nullptr;
     double *obs_partials = nullptr, *obs = nullptr;
@@ -197,7 +198,8 @@ int launch_fields(lbehd_handle *h)
     launch(h, LBEHD_KC_FIELDS, 1, [&] {
         k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->fphi[h->cur], h->frho[h->cur],
                                                           h->phi[h->pcur], h->rho[h->pcur], h->eps,
-                                                          h->pot, h->info, h->normal, h->elec, h->V);
+                                                          h->pot, h->pot_lo, h->info, h->normal,
+                                                          h->elec, h->V);
     });
     return LBEHD_OK;
 }
@@ -291,7 +293,7 @@ int poisson(lbehd_handle *h)
         }
     });
     launch(h, LBEHD_KC_CG, 2, [&] {
-        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->delta, h->eps,
+        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->pot_lo, h->delta, h->eps,
                                                             h->rho[h->pcur], h->info, L0.D,
                                                             h->cg_r, h->cg_partials);
         cg_scalar(h, 2, 0, h->nblocks);
@@ -321,7 +323,8 @@ int poisson(lbehd_handle *h)
         h->last_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
     }
     launch(h, LBEHD_KC_CG, 1, [&] {
-        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.D, h->delta, h->pot);
+        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.D, h->delta, h->pot,
+                                                            h->pot_lo);
     });
     if (!converged) {
         h->status = h->status ? h->status : LBEHD_ERR_POISSON_NOCONV;
@@ -353,6 +356,7 @@ int do_step(lbehd_handle *h)
     S.u = h->u;
     S.q = h->q;
     S.pot = h->pot;
+    S.pot_lo = h->pot_lo;
     S.info = h->info;
     S.obs_partials = h->obs_partials;
     S.flag = h->flag;
@@ -453,8 +457,9 @@ int init_impl(lbehd_handle *h)
     h->u = (float *)dev_alloc(h, 3 * N * fb);
     h->q = (float *)dev_alloc(h, N * fb);
     h->pot = (float *)dev_alloc(h, N * fb);
+    h->pot_lo = (float *)dev_alloc(h, N * fb);
     h->eps = (float *)dev_alloc(h, N * fb);
-    h->V = (float *)dev_alloc(h, LBEHD_MAX_ELECTRODES * fb);
+    h->V = (double *)dev_alloc(h, LBEHD_MAX_ELECTRODES * sizeof(double));
     h->info = (uint8_t *)dev_alloc(h, N);
     h->normal = (uint8_t *)dev_alloc(h, N);
     h->elec = (int16_t *)dev_alloc(h, N * sizeof(int16_t));
@@ -464,7 +469,7 @@ int init_impl(lbehd_handle *h)
     h->obs_partials = (double *)dev_alloc(h, NOBS * h->nblocks * sizeof(double));
     h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
     h->flag = (int *)dev_alloc(h, sizeof(int));
-    if (!h->u || !h->q || !h->pot || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
+    if (!h->u || !h->q || !h->pot || !h->pot_lo || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
         !h->obs_partials || !h->obs || !h->flag)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (fields)");
     // Poisson: CG vectors, reductions, multigrid hierarchy
@@ -515,16 +520,17 @@ int init_impl(lbehd_handle *h)
         CK(h, cudaMemsetAsync(h->delta, 0, N * fb, h->stream));
         CK(h, cudaMemsetAsync(h->cg_p, 0, N * fb, h->stream));
     }
-    std::vector<float> phi0(3 * N), V(LBEHD_MAX_ELECTRODES, 0.0f);
+    std::vector<float> phi0(3 * N);
+    std::vector<double> V(LBEHD_MAX_ELECTRODES, 0.0);
     for (size_t k = 0; k < 3 * N; k++)
         phi0[k] = (float)c.phi_init[k];
     for (int k = 0; k < c.n_electrodes; k++)
-        V[k] = (float)c.electrode_V[k];
+        V[k] = c.electrode_V[k];
     cudaStream_t s = h->stream;
     CK(h, cudaMemcpyAsync(h->info, info.data(), N, cudaMemcpyHostToDevice, s));
     CK(h, cudaMemcpyAsync(h->normal, normal.data(), N, cudaMemcpyHostToDevice, s));
     CK(h, cudaMemcpyAsync(h->elec, elec.data(), N * sizeof(int16_t), cudaMemcpyHostToDevice, s));
-    CK(h, cudaMemcpyAsync(h->V, V.data(), V.size() * fb, cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(h, cudaMemcpyAsync(h->phi[1], phi0.data(), 3 * N * fb, cudaMemcpyHostToDevice, s));
     for (int b = 0; b < 2; b++) {
         CK(h, cudaMemsetAsync(h->g[b], 0, h->Q * N * fb, s));
@@ -536,6 +542,7 @@ int init_impl(lbehd_handle *h)
     CK(h, cudaMemsetAsync(h->u, 0, 3 * N * fb, s));
     CK(h, cudaMemsetAsync(h->q, 0, N * fb, s));
     CK(h, cudaMemsetAsync(h->pot, 0, N * fb, s));
+    CK(h, cudaMemsetAsync(h->pot_lo, 0, N * fb, s));
     CK(h, cudaMemsetAsync(h->eps, 0, N * fb, s));
     CK(h, cudaMemsetAsync(h->obs, 0, 2 * NOBS * sizeof(double), s));
     CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), s));
@@ -668,11 +675,8 @@ int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
     if (n != h->cfg.n_electrodes || (n > 0 && !V))
         return fail(h, LBEHD_ERR_INVALID_ARG, "electrode count differs from the configuration");
-    float tmp[LBEHD_MAX_ELECTRODES];
-    for (int k = 0; k < n; k++)
-        tmp[k] = (float)V[k];
     // pageable source: the copy is staged before this call returns
-    CK(h, cudaMemcpyAsync(h->V, tmp, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->V, V, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBEHD_OK;
 }
@@ -723,6 +727,7 @@ static int array_info(lbehd_handle *h, int which, void **ptr, size_t *bytes)
     case LBEHD_U: *ptr = h->u; *bytes = 3 * N * fb; break;
     case LBEHD_QSRC: *ptr = h->q; *bytes = N * fb; break;
     case LBEHD_EPS: *ptr = h->eps; *bytes = N * fb; break;
+    case LBEHD_POT_LO: *ptr = h->pot_lo; *bytes = N * fb; break;
     default: return fail(h, LBEHD_ERR_INVALID_ARG, "unknown array id");
     }
     return LBEHD_OK;

@@ -4,9 +4,11 @@
 // Each step solves A delta = r0 with r0 = b - A phi^{n-1}, where A is the 7/5-point
 // finite-volume operator of div(eps grad .) (face eps = (eps_i + eps_j)/2, Dirichlet value
 // on the solid node with face eps = eps_fluid, zero flux elsewhere) and b = rho_e + Dirichlet
-// terms. r0 is formed in FP64 from the FP32 state (phi^{n-1} + delta_warm, eps, rho_e are
-// exact in double), so the FP32 iteration on the small increment is not limited by the
-// rounding of phi itself. The warm start is the previous step's increment.
+// terms. The potential is stored as a compensated pair of floats (hi + lo); r0 is formed in
+// FP64 from the FP32 state (hi + lo + delta_warm, eps, rho_e are exact in double), so the
+// FP32 iteration on the small increment is not limited by the rounding of phi itself, and
+// differences of phi (E, the conduction source of Eq. 14) keep ~FP64 accuracy. The warm
+// start is the previous step's increment.
 //
 // Preconditioner: one symmetric V-cycle of cell-centred geometric multigrid. Coarse cells
 // aggregate 2x2(x2) fine cells; coarse face coefficients are the sums of the fine faces
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
 // r = b - A (phi + delta) in FP64 from the FP32 state; partials of ||r||^2 and ||b||^2.
 template <int D>
 __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restrict__ pot,
+                                                 const float *__restrict__ pot_lo,
                                                  const float *__restrict__ delta,
                                                  const float *__restrict__ eps,
                                                  const float *__restrict__ rho,
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restri
         double ri = 0.0;
         if (Dg[i] > 0.0f) {
             const double ei = eps[i];
-            const double pi = (double)pot[i] + (double)delta[i];
+            const double pi = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
             double b = rho[i], Ax = 0.0;
             const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
                                   cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
@@ -276,9 +279,10 @@ __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restri
                 const int pt = info[nb[f]] & 3;
                 if (pt == PT_FLUID) {
                     const double k = 0.5 * (ei + (double)eps[nb[f]]);
-                    Ax += k * (pi - ((double)pot[nb[f]] + (double)delta[nb[f]]));
+                    Ax += k * (pi - ((double)pot[nb[f]] + (double)pot_lo[nb[f]] +
+                                     (double)delta[nb[f]]));
                 } else if (pt == PT_DIRICHLET) {
-                    b += ei * (double)pot[nb[f]];
+                    b += ei * ((double)pot[nb[f]] + (double)pot_lo[nb[f]]);
                     Ax += ei * pi;
                 }
             }
@@ -401,14 +405,19 @@ __global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ p
     }
 }
 
-// phi += delta on active cells.
+// phi += delta on active cells, phi kept as the compensated pair hi + lo.
 __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
                                                   const float *__restrict__ delta,
-                                                  float *__restrict__ pot)
+                                                  float *__restrict__ pot,
+                                                  float *__restrict__ pot_lo)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n && Dg[i] > 0.0f)
-        pot[i] += delta[i];
+    if (i < n && Dg[i] > 0.0f) {
+        const double t = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
+        const float hi = (float)t;
+        pot[i] = hi;
+        pot_lo[i] = (float)(t - (double)hi);
+    }
 }
 
 }  // namespace lbehd

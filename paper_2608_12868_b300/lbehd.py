@@ -16,9 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbehd.so")
 
 # enum lbehd_array
-G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS = range(9)
+G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS, POT_LO = range(10)
 ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot": POT,
-               "u": U, "qsrc": QSRC, "eps": EPS}
+               "u": U, "qsrc": QSRC, "eps": EPS, "pot_lo": POT_LO}
 POISSON_HOST, POISSON_FIXED = 0, 1
 
 # Storage convention of LBEHD_G: the library keeps g_n - w_n (lattice weights in the
@@ -218,7 +218,7 @@ class Simulation:
     def _shape_of(self, which):
         nz, ny, nx = self.shape
         return {G: (self.Q,), FPHI: (3, self.Q), FRHO: (self.QS,), PHI: (3,), RHO: (), POT: (),
-                U: (3,), QSRC: (), EPS: ()}[which] + (nz, ny, nx)
+                U: (3,), QSRC: (), EPS: (), POT_LO: ()}[which] + (nz, ny, nx)
 
     def array(self, which):
         """Host copy (float32 numpy) of one array; ``which`` is a name or an enum value."""
@@ -227,6 +227,10 @@ class Simulation:
         self._check(self._lib.lbehd_copy_out(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
                                              out.nbytes))
         return out
+
+    def potential(self):
+        """Electric potential in float64 from its compensated pair (hi + lo)."""
+        return self.array(POT).astype(np.float64) + self.array(POT_LO).astype(np.float64)
 
     def populations_g(self):
         """Momentum populations g_n in float64 (the library stores g_n - w_n)."""

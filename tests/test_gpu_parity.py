@@ -60,9 +60,9 @@ def compare_fields(sim, orc, phi_tol=1e-5):
     bnd = orc.normal > 0
     if bnd.any():   # wetting ghosts (Eq. 20a)
         assert np.abs(phi[:, bnd] - orc.Phi[:, bnd]).max() <= phi_tol
-    pot = sim.array("pot")
+    pot = sim.potential()
     if np.abs(orc.pot).max() > 0:
-        assert rel_linf(pot[fluid], orc.pot[fluid]) <= 1e-4
+        assert rel_linf(pot[fluid], orc.pot[fluid]) <= 1e-5
 
 
 def compare_obs(sim, orc, keys=("velocity", "f_ele", "f_ele_total"), tol=OBS_TOL):
