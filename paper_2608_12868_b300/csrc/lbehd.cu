@@ -54,7 +54,11 @@ struct lbehd_handle {
         dim3 grid, grid_half;
     };
     std::vector<Level> mg;
-    float *delta = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
+    // inc[s & 1] holds the potential increment of step s; the warm start of step s is the
+    // increment of step s-2 (the charge collision with tau_rho ~ 1/2 makes consecutive
+    // increments alternate). delta2: correction of a refinement pass.
+    float *inc[2] = {}, *delta2 = nullptr;
+    float *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
     double *cg_partials = nullptr;
     CgScalars *cg_s = nullptr;
     CgScalars *h_cg = nullptr;     // pinned copy for the host convergence check
@@ -249,8 +253,9 @@ void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
     k_pcg_scalar<<<1, 256, 0, h->stream>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s);
 }
 
-// One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x).
-void pcg_iteration(lbehd_handle *h)
+// One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x), updating
+// the increment x.
+void pcg_iteration(lbehd_handle *h, float *x)
 {
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_MG, vcycle_launches(h), [&] { vcycle(h, 0); });
@@ -261,8 +266,8 @@ void pcg_iteration(lbehd_handle *h)
         k_pcg_Ap<<<L0.grid, h->block, 0, h->stream>>>(L0.d, L0.D, L0.kx, L0.ky, L0.kz, h->cg_p,
                                                        h->cg_q, h->cg_partials);
         cg_scalar(h, 1, 2, h->nblocks);
-        k_pcg_update<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_p, h->cg_q, h->delta,
-                                                             h->cg_r, h->cg_s, h->cg_partials);
+        k_pcg_update<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_p, h->cg_q, x, h->cg_r,
+                                                             h->cg_s, h->cg_partials);
         cg_scalar(h, 1, 3, h->nblocks1d);
     });
 }
@@ -274,8 +279,50 @@ int read_cg(lbehd_handle *h)
     return LBEHD_OK;
 }
 
-// Gauss law (Eq. 13) for this step: operator set-up, FP64 defect of the warm start,
-// preconditioned CG on the increment, phi += delta.
+// r = b - A (phi + x) in FP64 and the CG start (op 0).
+template <int D>
+void pcg_start(lbehd_handle *h, const float *x)
+{
+    auto &L0 = h->mg[0];
+    launch(h, LBEHD_KC_CG, 2, [&] {
+        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->pot_lo, x, h->eps,
+                                                            h->rho[h->pcur], h->info, L0.D,
+                                                            h->cg_r, h->cg_partials);
+        cg_scalar(h, 2, 0, h->nblocks);
+    });
+}
+
+// phi += x (compensated); acc += x when acc is given.
+void pcg_apply(lbehd_handle *h, const float *x, float *acc)
+{
+    launch(h, LBEHD_KC_CG, 1, [&] {
+        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->mg[0].D, x, acc, h->pot,
+                                                            h->pot_lo);
+    });
+}
+
+// Run CG iterations on x until the device flag says done (host reads it back).
+int pcg_host_loop(lbehd_handle *h, float *x)
+{
+    int rc = read_cg(h);
+    if (rc)
+        return rc;
+    const int every = std::max(h->cfg.poisson_check_every, 1);
+    while (!h->h_cg->done) {
+        for (int k = 0; k < every; k++)
+            pcg_iteration(h, x);
+        rc = read_cg(h);
+        if (rc)
+            return rc;
+    }
+    return LBEHD_OK;
+}
+
+// Gauss law (Eq. 13) for this step: operator set-up; FP64 defect of the warm start;
+// preconditioned CG on the increment; phi += increment. In LBEHD_POISSON_HOST mode the
+// true FP64 residual is then re-checked and, if the FP32 iteration stopped short of the
+// tolerance (a large increment, e.g. the first solve from phi = 0), up to three
+// refinement passes solve for a further correction.
 template <int D>
 int poisson(lbehd_handle *h)
 {
@@ -292,40 +339,36 @@ int poisson(lbehd_handle *h)
                                                              C.kz);
         }
     });
-    launch(h, LBEHD_KC_CG, 2, [&] {
-        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->pot_lo, h->delta, h->eps,
-                                                            h->rho[h->pcur], h->info, L0.D,
-                                                            h->cg_r, h->cg_partials);
-        cg_scalar(h, 2, 0, h->nblocks);
-    });
-    int iters = 0;
+    float *x = h->inc[h->step & 1];   // holds the increment of step - 2: the warm start
+    pcg_start<D>(h, x);
     bool converged = true;
     if (c.poisson_mode == LBEHD_POISSON_FIXED) {
-        for (; iters < c.poisson_fixed_iters; iters++)
-            pcg_iteration(h);
-        h->last_iters = iters;
-        h->last_resid = -1.0;   // read back by lbehd_observe
-    } else {
-        int rc = read_cg(h);
+        for (int k = 0; k < c.poisson_fixed_iters; k++)
+            pcg_iteration(h, x);
+        pcg_apply(h, x, nullptr);
+        h->last_iters = c.poisson_fixed_iters;
+        h->last_resid = -1.0;
+        return LBEHD_OK;
+    }
+    int rc = pcg_host_loop(h, x);
+    if (rc)
+        return rc;
+    int iters = h->h_cg->iters;
+    pcg_apply(h, x, nullptr);
+    for (int pass = 0; pass < 3; pass++) {
+        CK(h, cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->stream));
+        pcg_start<D>(h, h->delta2);   // true residual of the updated potential
+        rc = pcg_host_loop(h, h->delta2);
         if (rc)
             return rc;
-        const int every = std::max(c.poisson_check_every, 1);
-        while (!h->h_cg->done) {
-            for (int k = 0; k < every; k++)
-                pcg_iteration(h);
-            rc = read_cg(h);
-            if (rc)
-                return rc;
-        }
-        iters = h->h_cg->iters;
-        converged = h->h_cg->converged != 0;
-        h->last_iters = iters;
-        h->last_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
+        if (h->h_cg->iters == 0)
+            break;
+        iters += h->h_cg->iters;
+        pcg_apply(h, h->delta2, x);
     }
-    launch(h, LBEHD_KC_CG, 1, [&] {
-        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.D, h->delta, h->pot,
-                                                            h->pot_lo);
-    });
+    converged = h->h_cg->converged != 0;
+    h->last_iters = iters;
+    h->last_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
     if (!converged) {
         h->status = h->status ? h->status : LBEHD_ERR_POISSON_NOCONV;
         return LBEHD_ERR_POISSON_NOCONV;
@@ -475,13 +518,15 @@ int init_impl(lbehd_handle *h)
     // Poisson: CG vectors, reductions, multigrid hierarchy
     h->grid1d = dim3((unsigned)((N + BX - 1) / BX), 1, 1);
     h->nblocks1d = h->grid1d.x;
-    h->delta = (float *)dev_alloc(h, N * fb);
+    h->inc[0] = (float *)dev_alloc(h, N * fb);
+    h->inc[1] = (float *)dev_alloc(h, N * fb);
+    h->delta2 = (float *)dev_alloc(h, N * fb);
     h->cg_r = (float *)dev_alloc(h, N * fb);
     h->cg_p = (float *)dev_alloc(h, N * fb);
     h->cg_q = (float *)dev_alloc(h, N * fb);
     h->cg_partials = (double *)dev_alloc(h, 2 * std::max(h->nblocks, h->nblocks1d) * sizeof(double));
     h->cg_s = (CgScalars *)dev_alloc(h, sizeof(CgScalars));
-    if (!h->delta || !h->cg_r || !h->cg_p || !h->cg_q || !h->cg_partials || !h->cg_s)
+    if (!h->inc[0] || !h->inc[1] || !h->delta2 || !h->cg_r || !h->cg_p || !h->cg_q || !h->cg_partials || !h->cg_s)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (Poisson)");
     {
         MgDims d{h->nx, h->ny, h->nz};
@@ -517,7 +562,8 @@ int init_impl(lbehd_handle *h)
         s0.max_iter = c.poisson_max_iter;
         CK(h, cudaMemcpyAsync(h->cg_s, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
-        CK(h, cudaMemsetAsync(h->delta, 0, N * fb, h->stream));
+        CK(h, cudaMemsetAsync(h->inc[0], 0, N * fb, h->stream));
+        CK(h, cudaMemsetAsync(h->inc[1], 0, N * fb, h->stream));
         CK(h, cudaMemsetAsync(h->cg_p, 0, N * fb, h->stream));
     }
     std::vector<float> phi0(3 * N);

@@ -8,7 +8,8 @@
 // FP64 from the FP32 state (hi + lo + delta_warm, eps, rho_e are exact in double), so the
 // FP32 iteration on the small increment is not limited by the rounding of phi itself, and
 // differences of phi (E, the conduction source of Eq. 14) keep ~FP64 accuracy. The warm
-// start is the previous step's increment.
+// start is the increment of two steps back (consecutive increments alternate in sign
+// because the charge collision relaxes its first moments with 1 - 1/tau_rho ~ -1).
 //
 // Preconditioner: one symmetric V-cycle of cell-centred geometric multigrid. Coarse cells
 // aggregate 2x2(x2) fine cells; coarse face coefficients are the sums of the fine faces
@@ -405,14 +406,18 @@ __global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ p
     }
 }
 
-// phi += delta on active cells, phi kept as the compensated pair hi + lo.
+// phi += delta on active cells, phi kept as the compensated pair hi + lo; acc += delta
+// when acc is given (accumulates a refinement correction into the step's increment).
 __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
                                                   const float *__restrict__ delta,
+                                                  float *__restrict__ acc,
                                                   float *__restrict__ pot,
                                                   float *__restrict__ pot_lo)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n && Dg[i] > 0.0f) {
+        if (acc)
+            acc[i] += delta[i];
         const double t = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
         const float hi = (float)t;
         pot[i] = hi;
