@@ -20,6 +20,8 @@
  *    deviatoric parts; all moments of order >= 3 relax at rate 1.
  *  - AC source (Eq. 17): first moment = c_s^2 F_Phi + d(Phi u)/dt so that the
  *    recovered equation is Eq. 8 with M = c_s^2 (tau_Phi - 1/2).
+ *  - Normal of Eq. 18: n = grad Phi / sqrt(|grad Phi|^2 + 1e-10) (continuous where
+ *    grad Phi = 0).
  *  - Time derivatives are backward differences, zero on the first step.
  *  - Wetting (Eq. 20a): ghost Phi on boundary solid nodes from the fluid node along
  *    the lattice normal, normal pointing into the fluid.
@@ -461,7 +463,9 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
             s->Fs[i] += mu * gx;
             s->Fs[N + i] += mu * gy;
             s->Fs[2 * N + i] += mu * gz;
-            double gn = sqrt(gx * gx + gy * gy + gz * gz) + 1e-12;
+            /* n = grad Phi / |grad Phi|, regularised as grad / sqrt(|grad|^2 + 1e-10) so
+             * that it stays continuous where grad Phi vanishes (critical points of Phi) */
+            double gn = sqrt(gx * gx + gy * gy + gz * gz + 1e-10);
             double lam = 4.0 / W * fabs(P[c] * (1.0 - P[c]));
             lam_n[c][0] = lam * gx / gn;
             lam_n[c][1] = lam * gy / gn;

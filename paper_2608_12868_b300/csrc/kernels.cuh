@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
             float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
+                // n = grad / sqrt(|grad|^2 + 1e-10): continuous where grad Phi vanishes
                 const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
-                                       gP[c][2] * gP[c][2]) + 1e-12f;
+                                       gP[c][2] * gP[c][2] + 1e-10f);
                 const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
