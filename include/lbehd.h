@@ -56,6 +56,9 @@ extern "C" {
  * multigrid V-cycle as preconditioner. Convergence control: */
 #define LBEHD_POISSON_HOST 0   /* host reads the FP64 residual every poisson_check_every iterations */
 #define LBEHD_POISSON_FIXED 1  /* exactly poisson_fixed_iters iterations, no host round trip */
+#define LBEHD_POISSON_GRAPH 2  /* each step after the first replays a CUDA graph whose CG loop
+                                * (and one refinement check) runs as device-side conditional
+                                * while nodes: no host round trip, convergence to poisson_tol */
 
 /* Solid classes (cfg->solid): 0 fluid, 1 substrate (wetting angles theta_ij apply),
  * 2 neutral wall (all angles 90 degrees). Electrode ids (cfg->electrode_id), meaningful
@@ -160,7 +163,17 @@ int lbehd_copy_out(lbehd_handle *h, int which, void *dst, size_t bytes);
 /* Device pointer and size in bytes of one array (valid until the next lbehd_step). */
 int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
 
-/* Number of kernels launched by this handle since init (for launch accounting). */
+/* Counters since init (synchronises: reads the device-side iteration counter). */
+typedef struct lbehd_stats {
+    long long steps;          /* coupled steps taken */
+    long long poisson_iters;  /* preconditioned-CG iterations, all steps and passes */
+    long long graph_launches; /* step graphs replayed (LBEHD_POISSON_GRAPH) */
+    long long kernels;        /* kernels launched, as lbehd_launch_count() */
+} lbehd_stats;
+int lbehd_get_stats(lbehd_handle *h, lbehd_stats *out);
+
+/* Number of kernels launched by this handle since init (for launch accounting; kernels run
+ * inside graph replays are counted from the device-side iteration counter; synchronises). */
 long long lbehd_launch_count(lbehd_handle *h);
 
 /* Per-kernel device time, for roofline accounting: while profiling is enabled every
@@ -173,7 +186,8 @@ long long lbehd_launch_count(lbehd_handle *h);
 #define LBEHD_KC_OBS 4      /* observable reduction */
 #define LBEHD_NKC 5
 
-/* Start (enable != 0) or stop recording. Enabling clears earlier records. */
+/* Start (enable != 0) or stop recording. Enabling clears earlier records. While profiling,
+ * steps run as eager launches even in LBEHD_POISSON_GRAPH mode. */
 int lbehd_profile_enable(lbehd_handle *h, int enable);
 
 /* Synchronise and return, per kernel class, the summed device time in ms (ms[LBEHD_NKC])

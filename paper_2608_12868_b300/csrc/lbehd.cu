@@ -35,6 +35,8 @@ struct lbehd_handle {
     int Q = 0, QS = 0;
     Params P{};
     cudaStream_t stream = nullptr;
+    cudaStream_t ls = nullptr;     // stream the launch helpers enqueue on (stream, or aux
+    cudaStream_t aux = nullptr;    //   while a conditional-loop body is being captured)
     std::vector<DevBuf> bufs;
     // device state
     float *g[2] = {}, *fphi[2] = {}, *frho[2] = {};
@@ -64,6 +66,13 @@ struct lbehd_handle {
     CgScalars *h_cg = nullptr;     // pinned copy for the host convergence check
     dim3 grid1d;
     size_t nblocks1d = 0;
+    // CUDA graphs of one step per step parity (LBEHD_POISSON_GRAPH)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphConditionalHandle cond = 0;
+    int use_cond = 0;
+    long long graph_launches = 0, graph_static_kernels[2] = {0, 0}, iter_kernels = 0;
+    long long graph_iters0 = 0;    // device iteration counter when graphs took over
+    bool graph_launches_started = false;
     int mg_nu = 2, mg_coarse = 8;
     float mg_scale = 0.6f;
     int cur = 0;                   // population buffer holding the state at time n
@@ -186,12 +195,12 @@ void launch(lbehd_handle *h, int kc, int nlaunch, F &&fn)
             ev = {nullptr, nullptr};
         }
         if (ev.first)
-            cudaEventRecord(ev.first, h->stream);
+            cudaEventRecord(ev.first, h->ls);
     }
     fn();
     h->launches += nlaunch;
     if (ev.first) {
-        cudaEventRecord(ev.second, h->stream);
+        cudaEventRecord(ev.second, h->ls);
         h->ev_pending[kc].push_back(ev);
     }
 }
@@ -200,7 +209,7 @@ template <int D>
 int launch_fields(lbehd_handle *h)
 {
     launch(h, LBEHD_KC_FIELDS, 1, [&] {
-        k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->fphi[h->cur], h->frho[h->cur],
+        k_fields<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->fphi[h->cur], h->frho[h->cur],
                                                           h->phi[h->pcur], h->rho[h->pcur], h->eps,
                                                           h->pot, h->pot_lo, h->info, h->normal,
                                                           h->elec, h->V);
@@ -210,14 +219,14 @@ int launch_fields(lbehd_handle *h)
 
 void mg_gs(lbehd_handle *h, const lbehd_handle::Level &L, int color)
 {
-    k_mg_gs<<<L.grid_half, h->block, 0, h->stream>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, color);
+    k_mg_gs<<<L.grid_half, h->block, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, color);
 }
 
 // One symmetric V-cycle: x_l ~= A_l^-1 b_l, starting from x_l = 0.
 void vcycle(lbehd_handle *h, size_t l)
 {
     const auto &L = h->mg[l];
-    cudaMemsetAsync(L.x, 0, L.n * sizeof(float), h->stream);
+    cudaMemsetAsync(L.x, 0, L.n * sizeof(float), h->ls);
     if (l + 1 == h->mg.size()) {
         for (int s = 0; s < h->mg_coarse; s++) {
             mg_gs(h, L, 0);
@@ -232,10 +241,10 @@ void vcycle(lbehd_handle *h, size_t l)
         mg_gs(h, L, 1);
     }
     const auto &C = h->mg[l + 1];
-    k_mg_restrict<<<C.grid, h->block, 0, h->stream>>>(L.d, C.d, L.cz2, L.D, L.kx, L.ky, L.kz, L.b,
+    k_mg_restrict<<<C.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.D, L.kx, L.ky, L.kz, L.b,
                                                        L.x, C.b);
     vcycle(h, l + 1);
-    k_mg_prolong<<<L.grid, h->block, 0, h->stream>>>(L.d, C.d, L.cz2, L.D, C.x, L.x);
+    k_mg_prolong<<<L.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.D, C.x, L.x);
     for (int s = 0; s < h->mg_nu; s++) {
         mg_gs(h, L, 1);
         mg_gs(h, L, 0);
@@ -250,7 +259,8 @@ int vcycle_launches(const lbehd_handle *h)
 
 void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
 {
-    k_pcg_scalar<<<1, 256, 0, h->stream>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s);
+    k_pcg_scalar<<<1, 256, 0, h->ls>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s, h->cond,
+                                        h->use_cond);
 }
 
 // One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x), updating
@@ -260,13 +270,13 @@ void pcg_iteration(lbehd_handle *h, float *x)
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_MG, vcycle_launches(h), [&] { vcycle(h, 0); });
     launch(h, LBEHD_KC_CG, 8, [&] {
-        k_pcg_dot<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_r, L0.x, h->cg_partials);
+        k_pcg_dot<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_r, L0.x, h->cg_partials);
         cg_scalar(h, 1, 1, h->nblocks1d);
-        k_pcg_p<<<h->grid1d, h->block, 0, h->stream>>>(h->N, L0.x, h->cg_p, h->cg_s);
-        k_pcg_Ap<<<L0.grid, h->block, 0, h->stream>>>(L0.d, L0.D, L0.kx, L0.ky, L0.kz, h->cg_p,
+        k_pcg_p<<<h->grid1d, h->block, 0, h->ls>>>(h->N, L0.x, h->cg_p, h->cg_s);
+        k_pcg_Ap<<<L0.grid, h->block, 0, h->ls>>>(L0.d, L0.D, L0.kx, L0.ky, L0.kz, h->cg_p,
                                                        h->cg_q, h->cg_partials);
         cg_scalar(h, 1, 2, h->nblocks);
-        k_pcg_update<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->cg_p, h->cg_q, x, h->cg_r,
+        k_pcg_update<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_p, h->cg_q, x, h->cg_r,
                                                              h->cg_s, h->cg_partials);
         cg_scalar(h, 1, 3, h->nblocks1d);
     });
@@ -279,16 +289,16 @@ int read_cg(lbehd_handle *h)
     return LBEHD_OK;
 }
 
-// r = b - A (phi + x) in FP64 and the CG start (op 0).
+// r = b - A (phi + x) in FP64 and the CG start (op 0: first pass of a step, 4: refinement).
 template <int D>
-void pcg_start(lbehd_handle *h, const float *x)
+void pcg_start(lbehd_handle *h, const float *x, int op = 0)
 {
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_CG, 2, [&] {
-        k_pcg_init<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->pot, h->pot_lo, x, h->eps,
+        k_pcg_init<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->pot, h->pot_lo, x, h->eps,
                                                             h->rho[h->pcur], h->info, L0.D,
                                                             h->cg_r, h->cg_partials);
-        cg_scalar(h, 2, 0, h->nblocks);
+        cg_scalar(h, 2, op, h->nblocks);
     });
 }
 
@@ -296,7 +306,7 @@ void pcg_start(lbehd_handle *h, const float *x)
 void pcg_apply(lbehd_handle *h, const float *x, float *acc)
 {
     launch(h, LBEHD_KC_CG, 1, [&] {
-        k_pcg_apply<<<h->grid1d, h->block, 0, h->stream>>>(h->N, h->mg[0].D, x, acc, h->pot,
+        k_pcg_apply<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->mg[0].D, x, acc, h->pot,
                                                             h->pot_lo);
     });
 }
@@ -324,21 +334,27 @@ int pcg_host_loop(lbehd_handle *h, float *x)
 // tolerance (a large increment, e.g. the first solve from phi = 0), up to three
 // refinement passes solve for a further correction.
 template <int D>
-int poisson(lbehd_handle *h)
+void mg_setup(lbehd_handle *h)
 {
-    const lbehd_config &c = h->cfg;
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_MG, (int)h->mg.size(), [&] {
-        k_mg_setup0<D><<<h->grid, h->block, 0, h->stream>>>(h->P, h->eps, h->info, L0.D, L0.kx,
+        k_mg_setup0<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->eps, h->info, L0.D, L0.kx,
                                                              L0.ky, L0.kz);
         for (size_t l = 0; l + 1 < h->mg.size(); l++) {
             const auto &F = h->mg[l];
             const auto &C = h->mg[l + 1];
-            k_mg_coarsen<<<C.grid, h->block, 0, h->stream>>>(F.d, C.d, F.cz2, h->mg_scale, F.D,
+            k_mg_coarsen<<<C.grid, h->block, 0, h->ls>>>(F.d, C.d, F.cz2, h->mg_scale, F.D,
                                                              F.kx, F.ky, F.kz, C.D, C.kx, C.ky,
                                                              C.kz);
         }
     });
+}
+
+template <int D>
+int poisson(lbehd_handle *h)
+{
+    const lbehd_config &c = h->cfg;
+    mg_setup<D>(h);
     float *x = h->inc[h->step & 1];   // holds the increment of step - 2: the warm start
     pcg_start<D>(h, x);
     bool converged = true;
@@ -356,8 +372,8 @@ int poisson(lbehd_handle *h)
     int iters = h->h_cg->iters;
     pcg_apply(h, x, nullptr);
     for (int pass = 0; pass < 3; pass++) {
-        CK(h, cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->stream));
-        pcg_start<D>(h, h->delta2);   // true residual of the updated potential
+        CK(h, cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->ls));
+        pcg_start<D>(h, h->delta2, 4);   // true residual of the updated potential
         rc = pcg_host_loop(h, h->delta2);
         if (rc)
             return rc;
@@ -377,14 +393,8 @@ int poisson(lbehd_handle *h)
 }
 
 template <int D>
-int do_step(lbehd_handle *h)
+void collide(lbehd_handle *h)
 {
-    int rc = launch_fields<D>(h);
-    if (rc)
-        return rc;
-    const int prc = poisson<D>(h);
-    if (prc && prc != LBEHD_ERR_POISSON_NOCONV)
-        return prc;
     State S;
     S.g = h->g[h->cur];
     S.fphi = h->fphi[h->cur];
@@ -404,10 +414,146 @@ int do_step(lbehd_handle *h)
     S.obs_partials = h->obs_partials;
     S.flag = h->flag;
     launch(h, LBEHD_KC_COLLIDE, 1,
-           [&] { k_collide<D><<<h->grid, h->block, 0, h->stream>>>(h->P, S, h->first ? 1 : 0); });
+           [&] { k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0); });
     launch(h, LBEHD_KC_OBS, 1, [&] {
-        k_obs_final<<<1, 256, 0, h->stream>>>(h->obs_partials, (long long)h->nblocks, h->obs);
+        k_obs_final<<<1, 256, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks, h->obs);
     });
+}
+
+// Capture the body of a device-side while loop (condition h->cond) into a conditional
+// node appended to the stream's ongoing capture.
+template <class F>
+int add_while(lbehd_handle *h, F &&body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(h, cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h->cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(h, cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    CK(h, cudaStreamBeginCaptureToGraph(h->aux, bodyg, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed));
+    h->ls = h->aux;
+    const long long k0 = h->launches;
+    body();
+    h->iter_kernels = h->launches - k0;
+    h->launches = k0;
+    h->ls = h->stream;
+    cudaGraph_t out = nullptr;
+    CK(h, cudaStreamEndCapture(h->aux, &out));
+    CK(h, cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies));
+    return LBEHD_OK;
+}
+
+// One whole coupled step as a CUDA graph for the given step parity: moments, Poisson
+// (device-side CG loop, then one refinement check with its own loop), collide + stream.
+template <int D>
+int capture_step(lbehd_handle *h, int parity)
+{
+    const int cur = h->cur, pcur = h->pcur;
+    const long long step = h->step, launches = h->launches;
+    const bool prof = h->prof;
+    h->cur = h->pcur = parity;
+    h->step = parity;
+    h->prof = false;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle c1 = 0, c2 = 0;
+    int rc = LBEHD_OK;
+    auto body = [&]() -> int {
+        CK(h, cudaGraphCreate(&g, 0));
+        CK(h, cudaGraphConditionalHandleCreate(&c1, g, 0, 0));
+        CK(h, cudaGraphConditionalHandleCreate(&c2, g, 0, 0));
+        CK(h, cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeRelaxed));
+        h->ls = h->stream;
+        h->use_cond = 1;
+        launch_fields<D>(h);
+        mg_setup<D>(h);
+        float *x = h->inc[parity];
+        h->cond = c1;
+        pcg_start<D>(h, x, 0);
+        int r = add_while(h, [&] { pcg_iteration(h, x); });
+        if (r)
+            return r;
+        pcg_apply(h, x, nullptr);
+        cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->stream);
+        h->cond = c2;
+        pcg_start<D>(h, h->delta2, 4);
+        r = add_while(h, [&] { pcg_iteration(h, h->delta2); });
+        if (r)
+            return r;
+        pcg_apply(h, h->delta2, x);
+        collide<D>(h);
+        cudaGraph_t out = nullptr;
+        CK(h, cudaStreamEndCapture(h->stream, &out));
+        CK(h, cudaGraphInstantiate(&h->gexec[parity], g, 0));
+        return LBEHD_OK;
+    };
+    rc = body();
+    h->graph_static_kernels[parity] = h->launches - launches;
+    h->use_cond = 0;
+    h->cond = 0;
+    if (g)
+        cudaGraphDestroy(g);
+    h->cur = cur;
+    h->pcur = pcur;
+    h->step = step;
+    h->launches = launches;
+    h->prof = prof;
+    if (rc) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(h->stream, &junk);
+            if (junk)
+                cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+    }
+    return rc;
+}
+
+template <int D>
+int do_step(lbehd_handle *h)
+{
+    // graph replay (profiling brackets eager launches with events, so it runs eagerly)
+    if (h->cfg.poisson_mode == LBEHD_POISSON_GRAPH && !h->first && !h->prof) {
+        const int parity = (int)(h->step & 1);
+        if (!h->gexec[parity]) {
+            const int rc = capture_step<D>(h, parity);
+            if (rc)
+                return rc;
+        }
+        if (!h->graph_launches && !h->graph_launches_started) {
+            h->graph_launches_started = true;
+            CgScalars s0;
+            CK(h, cudaMemcpyAsync(&s0, h->cg_s, sizeof(s0), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            h->graph_iters0 = s0.total_iters;
+        }
+        CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
+        h->graph_launches++;
+        h->launches += h->graph_static_kernels[parity];
+        h->cur ^= 1;
+        h->pcur ^= 1;
+        h->step++;
+        return LBEHD_OK;
+    }
+    int rc = launch_fields<D>(h);
+    if (rc)
+        return rc;
+    const int prc = poisson<D>(h);
+    if (prc && prc != LBEHD_ERR_POISSON_NOCONV)
+        return prc;
+    collide<D>(h);
     CK(h, cudaGetLastError());
     h->cur ^= 1;
     h->pcur ^= 1;
@@ -556,6 +702,7 @@ int init_impl(lbehd_handle *h)
         h->mg.back().cz2 = 0;
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
+    CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     {
         CgScalars s0{};
         s0.tol2 = c.poisson_tol * c.poisson_tol;
@@ -633,6 +780,12 @@ void release(lbehd_handle *h)
     if (h->h_cg)
         cudaFreeHost(h->h_cg);
     h->h_cg = nullptr;
+    for (auto &e : h->gexec)
+        if (e)
+            cudaGraphExecDestroy(e);
+    if (h->aux)
+        cudaStreamDestroy(h->aux);
+    h->aux = nullptr;
 }
 
 }  // namespace
@@ -679,6 +832,7 @@ int lbehd_init(const lbehd_config *cfg, lbehd_handle **out)
     h->nz = cfg->nz;
     h->N = (size_t)cfg->nx * cfg->ny * cfg->nz;
     h->stream = (cudaStream_t)cfg->stream;
+    h->ls = h->stream;
     int rc = set_params(h);
     if (!rc)
         rc = h->dim == 2 ? init_impl<2>(h) : init_impl<3>(h);
@@ -735,6 +889,7 @@ int lbehd_observe(lbehd_handle *h, lbehd_obs *out)
     int flag = 0;
     CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     std::memset(out, 0, sizeof(*out));
     out->step = h->step - 1;
@@ -752,9 +907,10 @@ int lbehd_observe(lbehd_handle *h, lbehd_obs *out)
     out->mass[1] = o[13];
     out->mass[2] = o[14];
     out->charge = o[15];
-    out->poisson_iters = h->last_iters;
-    out->poisson_resid = h->last_resid;
-    out->status = flag ? LBEHD_ERR_NONFINITE : h->status;
+    out->poisson_iters = h->h_cg->step_iters;
+    out->poisson_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
+    out->status = flag ? LBEHD_ERR_NONFINITE
+                       : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
     if (flag)
         return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
     return LBEHD_OK;
@@ -802,7 +958,36 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes)
     return array_info(h, which, ptr, bytes);
 }
 
-long long lbehd_launch_count(lbehd_handle *h) { return h ? h->launches : 0; }
+long long lbehd_launch_count(lbehd_handle *h)
+{
+    if (!h)
+        return 0;
+    long long n = h->launches;
+    if (h->graph_launches_started) {
+        // kernels inside the graphs' while loops: iterations since graphs took over
+        CgScalars s0;
+        if (cudaMemcpyAsync(&s0, h->cg_s, sizeof(s0), cudaMemcpyDeviceToHost, h->stream) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(h->stream) == cudaSuccess)
+            n += (s0.total_iters - h->graph_iters0) * h->iter_kernels;
+    }
+    return n;
+}
+
+int lbehd_get_stats(lbehd_handle *h, lbehd_stats *out)
+{
+    if (!h || !out)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null argument");
+    CgScalars s0;
+    CK(h, cudaMemcpyAsync(&s0, h->cg_s, sizeof(s0), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    out->steps = h->step;
+    out->poisson_iters = s0.total_iters;
+    out->graph_launches = h->graph_launches;
+    out->kernels = h->launches +
+                   (h->graph_launches_started ? (s0.total_iters - h->graph_iters0) * h->iter_kernels : 0);
+    return LBEHD_OK;
+}
 
 int lbehd_profile_enable(lbehd_handle *h, int enable)
 {

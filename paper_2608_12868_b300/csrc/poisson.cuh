@@ -42,10 +42,13 @@ struct CgScalars {
     double bb;        // ||b||^2
     double alpha, beta;
     double tol2;      // tol^2 (set by the host)
-    int iters;
+    int iters;        // iterations of the current pass
     int max_iter;
     int done;         // 1 once rr <= tol2 * bb or iters >= max_iter
     int converged;
+    int step_iters;   // iterations of the current step, all passes
+    int nonconv;      // sticky: some pass stopped at max_iter without converging
+    long long total_iters;
 };
 
 __device__ __forceinline__ size_t cell(const MgDims &d, int x, int y, int z)
@@ -361,13 +364,16 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 }
 
 // Fixed-order FP64 sum of nv partial arrays and the CG scalar update that follows.
-//   op 0: init      rr, bb            -> done if rr <= tol2 bb
+//   op 0: start     rr, bb            -> done if rr <= tol2 bb (resets the step counter)
+//   op 4: restart   as op 0 for a refinement pass (keeps the step counter)
 //   op 1: r.z       rz                -> beta = rz / rz_old, rz_old = rz
 //   op 2: p.Ap      pq                -> alpha = rz / pq
 //   op 3: ||r||^2   rr                -> iters++, done / converged
+// With use_cond, ops 0, 4 and 3 also set the graph's while-loop condition to !done.
 __global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ partials,
                                                     long long nblocks, int nv, int op,
-                                                    CgScalars *__restrict__ s)
+                                                    CgScalars *__restrict__ s,
+                                                    cudaGraphConditionalHandle cond, int use_cond)
 {
     __shared__ double sm[2][256];
     for (int k = 0; k < nv; k++) {
@@ -385,10 +391,12 @@ __global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ p
     }
     if (threadIdx.x != 0)
         return;
-    if (op == 0) {
+    if (op == 0 || op == 4) {
         s->rr = sm[0][0];
         s->bb = sm[1][0];
         s->iters = 0;
+        if (op == 0)
+            s->step_iters = 0;
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->max_iter <= 0;
     } else if (op == 1) {
@@ -401,9 +409,15 @@ __global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ p
     } else if (!s->done) {
         s->rr = sm[0][0];
         s->iters += 1;
+        s->step_iters += 1;
+        s->total_iters += 1;
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->iters >= s->max_iter;
+        if (s->done && !s->converged)
+            s->nonconv = 1;
     }
+    if (use_cond && op != 1 && op != 2)
+        cudaGraphSetConditional(cond, s->done ? 0u : 1u);
 }
 
 // phi += delta on active cells, phi kept as the compensated pair hi + lo; acc += delta

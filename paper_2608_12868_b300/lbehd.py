@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "liblbehd.so")
 G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS, POT_LO = range(10)
 ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot": POT,
                "u": U, "qsrc": QSRC, "eps": EPS, "pot_lo": POT_LO}
-POISSON_HOST, POISSON_FIXED = 0, 1
+POISSON_HOST, POISSON_FIXED, POISSON_GRAPH = 0, 1, 2
 
 # Storage convention of LBEHD_G: the library keeps g_n - w_n (lattice weights in the
 # documented velocity order).
@@ -67,6 +67,11 @@ class Obs(ctypes.Structure):
                 ("poisson_resid", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("poisson_iters", ctypes.c_longlong),
+                ("graph_launches", ctypes.c_longlong), ("kernels", ctypes.c_longlong)]
+
+
 class LBEHDError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"lbehd error {code} ({ERRORS.get(code, '?')}): {msg}")
@@ -77,7 +82,7 @@ _lib = None
 
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
-           "lbehd_launch_count", "lbehd_profile_enable", "lbehd_profile_read",
+           "lbehd_launch_count", "lbehd_get_stats", "lbehd_profile_enable", "lbehd_profile_read",
            "lbehd_last_error", "lbehd_destroy")
 KERNEL_CLASSES = ("fields", "mg", "cg", "collide", "obs")
 
@@ -103,6 +108,7 @@ def load():
                                      ctypes.POINTER(ctypes.c_size_t)]
     lib.lbehd_launch_count.argtypes = [P]
     lib.lbehd_launch_count.restype = ctypes.c_longlong
+    lib.lbehd_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.lbehd_profile_enable.argtypes = [P, ctypes.c_int]
     lib.lbehd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
@@ -259,6 +265,12 @@ class Simulation:
         ms, cnt = (ctypes.c_double * n)(), (ctypes.c_longlong * n)()
         self._check(self._lib.lbehd_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def stats(self):
+        """Counters since init: steps, Poisson CG iterations, graph replays, kernels."""
+        st = Stats()
+        self._check(self._lib.lbehd_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
 
     def launch_count(self):
         return int(self._lib.lbehd_launch_count(self._h))

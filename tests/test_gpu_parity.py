@@ -122,21 +122,42 @@ def test_droplet_2d_128x64(gpu, oracle_mod):
 
 def test_droplet_3d_128x64x64_full_size(gpu, oracle_mod):
     """The 3D 128x64x64 workload at full size, in the launch configuration the benchmark
-    times: every population after 2 steps."""
+    times (graph replay with the device-side Poisson loop): every population after 3 steps."""
     w = W.droplet_3d_128x64x64()
-    sim, orc = make_pair(gpu, oracle_mod, w)
-    sim.step(2)
-    orc.step(2)
+    sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.step(3)
+    orc.step(3)
+    assert sim.stats()["graph_launches"] == 2
     compare_populations(sim, orc)
     compare_fields(sim, orc)
     compare_obs(sim, orc, keys=("f_ele", "f_ele_total"))
 
 
+@pytest.mark.parametrize("case", ["small_2d", "small_3d"])
+def test_graph_mode_parity(gpu, oracle_mod, case):
+    """Graph replay (CG loop as device-side conditional nodes) against the oracle, and
+    against eager launches with host convergence checks."""
+    w = getattr(W, case)()
+    sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
+    host = gpu.Simulation(w, poisson_mode=gpu.POISSON_HOST)
+    sim.step(100)
+    orc.step(100)
+    host.step(100)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+    assert sim.stats()["graph_launches"] == 99
+    assert rel_linf(sim.array("fphi"), host.array("fphi").astype(np.float64)) <= 1e-6
+    assert rel_linf(sim.potential(), host.potential()) <= 1e-6
+    o = sim.observe()
+    assert o["status"] == 0 and o["poisson_iters"] >= 0
+
+
 def test_electrode_switching_parity(gpu, oracle_mod):
-    """lbehd_set_electrodes mid-run matches the oracle switching at the same step."""
+    """lbehd_set_electrodes mid-run (graph replay) matches the oracle switching at the same
+    step."""
     w = W.droplet_3d(32, 16, 16, R=5.0, pillar_h=3,
                      electrodes=[(4, 10, 4, 12), (20, 28, 4, 12)], V=[0.05, 0.0], seed=11)
-    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
     sim.step(20)
     orc.step(20)
     sim.set_electrodes([0.0, 0.06])
@@ -173,7 +194,7 @@ def test_ragged_and_periodic_edge_cases(gpu, oracle_mod):
 def test_mass_conservation_long_run(gpu):
     """Per-component mass over 1000 steps of the 3D 128x64x64 workload, FP32 state."""
     w = W.droplet_3d_128x64x64()
-    sim = gpu.Simulation(w)
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     sim.step(1)
     m0 = sim.observe()["mass"]
     sim.step(1000)
