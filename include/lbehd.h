@@ -17,7 +17,9 @@
  *  - Host pointers passed in are borrowed for the duration of the call only.
  *  - Device memory is owned by the handle until lbehd_destroy(); it is obtained from
  *    cfg->alloc/cfg->free when given (e.g. PyTorch's caching allocator), else cudaMalloc.
- *  - All GPU work is enqueued on cfg->stream (a cudaStream_t; NULL = legacy stream).
+ *  - All GPU work is enqueued on cfg->stream (a cudaStream_t). For NULL the library creates
+ *    its own blocking stream (ordered with the legacy default stream), because graph
+ *    capture is not possible on the legacy stream.
  *    lbehd_step() returns after enqueueing, except for the host round trips of the
  *    Poisson convergence test in LBEHD_POISSON_HOST mode. lbehd_observe(),
  *    lbehd_copy_out() and lbehd_destroy() synchronise the stream.

@@ -516,32 +516,22 @@ __global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
     }
 }
 
-// Fixed-order FP64 sum of the observable partials. obs[0..NOBS) receives this step's sums
-// and obs[NOBS..2 NOBS) the previous step's (for the drag force balance).
-__global__ void __launch_bounds__(256) k_obs_final(const double *__restrict__ partials,
-                                                   long long nblocks, double *__restrict__ obs)
+// Fixed-order FP64 sum of the observable partials: warp k reduces observable k (NOBS
+// warps). obs[0..NOBS) receives this step's sums and obs[NOBS..2 NOBS) the previous step's
+// (for the drag force balance).
+__global__ void __launch_bounds__(NOBS * 32) k_obs_final(const double *__restrict__ partials,
+                                                        long long nblocks, double *__restrict__ obs)
 {
-    __shared__ double sm[256];
-    __shared__ double prev[NOBS];
-    if (threadIdx.x < NOBS)
-        prev[threadIdx.x] = obs[threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < NOBS)
-        obs[NOBS + threadIdx.x] = prev[threadIdx.x];
-    for (int k = 0; k < NOBS; k++) {
-        double a = 0.0;
-        for (long long b = threadIdx.x; b < nblocks; b += 256)
-            a += partials[k * nblocks + b];
-        sm[threadIdx.x] = a;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if (threadIdx.x < s)
-                sm[threadIdx.x] += sm[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0)
-            obs[k] = sm[0];
-        __syncthreads();
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (long long b = lane; b < nblocks; b += 32)
+        a += partials[k * nblocks + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+        obs[NOBS + k] = obs[k];
+        obs[k] = a;
     }
 }
 

@@ -37,6 +37,7 @@ struct lbehd_handle {
     cudaStream_t stream = nullptr;
     cudaStream_t ls = nullptr;     // stream the launch helpers enqueue on (stream, or aux
     cudaStream_t aux = nullptr;    //   while a conditional-loop body is being captured)
+    cudaStream_t own_stream = nullptr;  // created when cfg->stream is the legacy stream
     std::vector<DevBuf> bufs;
     // device state
     float *g[2] = {}, *fphi[2] = {}, *frho[2] = {};
@@ -416,7 +417,7 @@ void collide(lbehd_handle *h)
     launch(h, LBEHD_KC_COLLIDE, 1,
            [&] { k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0); });
     launch(h, LBEHD_KC_OBS, 1, [&] {
-        k_obs_final<<<1, 256, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks, h->obs);
+        k_obs_final<<<1, NOBS * 32, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks, h->obs);
     });
 }
 
@@ -786,6 +787,9 @@ void release(lbehd_handle *h)
     if (h->aux)
         cudaStreamDestroy(h->aux);
     h->aux = nullptr;
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    h->own_stream = nullptr;
 }
 
 }  // namespace
@@ -832,6 +836,15 @@ int lbehd_init(const lbehd_config *cfg, lbehd_handle **out)
     h->nz = cfg->nz;
     h->N = (size_t)cfg->nx * cfg->ny * cfg->nz;
     h->stream = (cudaStream_t)cfg->stream;
+    if (!h->stream) {
+        // the legacy default stream cannot be captured into a graph: use an own blocking
+        // stream, which stays ordered with the legacy stream
+        if (cudaStreamCreate(&h->own_stream) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, LBEHD_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        h->stream = h->own_stream;
+    }
     h->ls = h->stream;
     int rc = set_params(h);
     if (!rc)
