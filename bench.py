@@ -286,6 +286,26 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_profile_window(args, local):
+    """Warm up, then bracket --profile-steps eager coupled steps with cudaProfilerStart /
+    Stop (for `ncu --profile-from-start off`). Prints one line, no timing."""
+    import torch
+    from paper_2608_12868_b300 import lbehd
+    from paper_2608_12868_b300 import workloads as W
+    torch.cuda.set_device(local)
+    w = W.WORKLOADS[args.workload]()
+    stream = torch.cuda.Stream()
+    sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=lbehd.POISSON_HOST)
+    sim.step(args.warmup * args.lb_steps)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    sim.step(args.profile_steps)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile_window": args.profile_steps, "workload": w.name,
+                      "stats": sim.stats()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,8 +319,13 @@ def main():
     ap.add_argument("--check-every", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only run a profiler window of this many eager steps (for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    if args.profile_steps:
+        run_profile_window(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

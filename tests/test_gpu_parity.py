@@ -170,17 +170,21 @@ def test_electrode_switching_parity(gpu, oracle_mod):
 
 def test_ragged_and_periodic_edge_cases(gpu, oracle_mod):
     """nx not a multiple of the block width; an all-fluid periodic box with no electrode
-    (the Poisson right-hand side is zero: phi = 0)."""
+    (the Poisson right-hand side is zero: phi = 0). The drop sits off the lattice symmetry
+    lines: in an exactly mirror-symmetric box the sharpening flux of Eq. 18 amplifies
+    rounding-level symmetry breaking at the saddle points between periodic images, so FP32
+    and FP64 runs part there by construction."""
     w = W.small_2d(nx=50, ny=30)
     sim, orc = make_pair(gpu, oracle_mod, w)
     sim.step(30)
     orc.step(30)
     compare_populations(sim, orc)
 
-    n = 20
+    n = 32
     shape = (1, n, n)
     _, yy, xx = np.meshgrid(np.arange(1), np.arange(n), np.arange(n), indexing="ij")
-    pd = 0.5 * (1 - np.tanh(2 * (np.sqrt((xx - 10) ** 2 + (yy - 10) ** 2) - 5) / 5))
+    r = np.sqrt((xx - 16.3) ** 2 + (yy - 16.15) ** 2)
+    pd = 0.5 * (1 - np.tanh(2 * (r - 8) / 5))
     phi = np.stack([pd, 0 * pd, 1 - pd])
     wp = W.Workload("periodic", 2, shape, np.zeros(shape, np.uint8), np.full(shape, -1, np.int16),
                     phi, W.make_params(V=()))
