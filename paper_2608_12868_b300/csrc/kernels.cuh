@@ -193,8 +193,10 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict
 
 // ---------------------------------------------------------------- fused collide + stream
 
+// 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
+// the kernel is memory-latency bound and needs the warps.
 template <int D>
-__global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
+__global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
 {
     using L = Lat<D>;
     constexpr int Q = L::Q, QS = L::QS;
@@ -516,22 +518,40 @@ __global__ void __launch_bounds__(BX) k_collide(Params P, State S, int first)
     }
 }
 
-// Fixed-order FP64 sum of the observable partials: warp k reduces observable k (NOBS
-// warps). obs[0..NOBS) receives this step's sums and obs[NOBS..2 NOBS) the previous step's
-// (for the drag force balance).
-__global__ void __launch_bounds__(NOBS * 32) k_obs_final(const double *__restrict__ partials,
-                                                        long long nblocks, double *__restrict__ obs)
+// Fixed-order FP64 sum of the observable partials: block k reduces observable k.
+// obs[0..NOBS) receives this step's sums and obs[NOBS..2 NOBS) the previous step's (for the
+// drag force balance).
+constexpr int OBS_THREADS = 256;
+__global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restrict__ partials,
+                                                          long long nblocks,
+                                                          double *__restrict__ obs)
 {
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a = 0.0;
-    for (long long b = lane; b < nblocks; b += 32)
-        a += partials[k * nblocks + b];
+    const int k = blockIdx.x;
+    const double *p = partials + k * nblocks;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long b = threadIdx.x;
+    for (; b + 3 * OBS_THREADS < nblocks; b += 4 * OBS_THREADS) {
+        a0 += p[b];
+        a1 += p[b + OBS_THREADS];
+        a2 += p[b + 2 * OBS_THREADS];
+        a3 += p[b + 3 * OBS_THREADS];
+    }
+    for (; b < nblocks; b += OBS_THREADS)
+        a0 += p[b];
+    double a = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) {
+    __shared__ double sm[OBS_THREADS / 32];
+    if ((threadIdx.x & 31) == 0)
+        sm[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < OBS_THREADS / 32; w++)
+            t += sm[w];
         obs[NOBS + k] = obs[k];
-        obs[k] = a;
+        obs[k] = t;
     }
 }
 

@@ -75,6 +75,9 @@ struct lbehd_handle {
     long long graph_iters0 = 0;    // device iteration counter when graphs took over
     bool graph_launches_started = false;
     int mg_nu = 2, mg_coarse = 8;
+    int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
+    TailLevels tail{};
+    size_t tail_smem = 0;
     float mg_scale = 0.6f;
     int cur = 0;                   // population buffer holding the state at time n
     int pcur = 0;                  // phi / rho buffer holding the last step's fields
@@ -223,10 +226,18 @@ void mg_gs(lbehd_handle *h, const lbehd_handle::Level &L, int color)
     k_mg_gs<<<L.grid_half, h->block, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, color);
 }
 
-// One symmetric V-cycle: x_l ~= A_l^-1 b_l, starting from x_l = 0.
+// One symmetric V-cycle: x_l ~= A_l^-1 b_l, starting from x_l = 0. Levels from
+// h->tail_level down run in one shared-memory kernel.
 void vcycle(lbehd_handle *h, size_t l)
 {
     const auto &L = h->mg[l];
+    if ((int)l == h->tail_level) {
+        TailLevels T = h->tail;
+        T.b0 = L.b;
+        T.x0 = L.x;
+        k_mg_tail<<<1, TAIL_THREADS, h->tail_smem, h->ls>>>(T);
+        return;
+    }
     cudaMemsetAsync(L.x, 0, L.n * sizeof(float), h->ls);
     if (l + 1 == h->mg.size()) {
         for (int s = 0; s < h->mg_coarse; s++) {
@@ -255,13 +266,15 @@ void vcycle(lbehd_handle *h, size_t l)
 int vcycle_launches(const lbehd_handle *h)
 {
     const int levels = (int)h->mg.size();
-    return (levels - 1) * (4 * h->mg_nu + 2) + 4 * h->mg_coarse;   // memsets not counted
+    if (h->tail_level >= 0)
+        return h->tail_level * (4 * h->mg_nu + 2) + 1;   // memsets not counted
+    return (levels - 1) * (4 * h->mg_nu + 2) + 4 * h->mg_coarse;
 }
 
 void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
 {
-    k_pcg_scalar<<<1, 256, 0, h->ls>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s, h->cond,
-                                        h->use_cond);
+    k_pcg_scalar<<<1, SCALAR_THREADS, 0, h->ls>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s,
+                                                   h->cond, h->use_cond);
 }
 
 // One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x), updating
@@ -417,7 +430,8 @@ void collide(lbehd_handle *h)
     launch(h, LBEHD_KC_COLLIDE, 1,
            [&] { k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0); });
     launch(h, LBEHD_KC_OBS, 1, [&] {
-        k_obs_final<<<1, NOBS * 32, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks, h->obs);
+        k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks,
+                                                     h->obs);
     });
 }
 
@@ -663,7 +677,13 @@ int init_impl(lbehd_handle *h)
         !h->obs_partials || !h->obs || !h->flag)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (fields)");
     // Poisson: CG vectors, reductions, multigrid hierarchy
-    h->grid1d = dim3((unsigned)((N + BX - 1) / BX), 1, 1);
+    {
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const size_t want = (N + BX - 1) / BX, cap = (size_t)nsm * 8;
+        h->grid1d = dim3((unsigned)std::min(want, cap), 1, 1);
+    }
     h->nblocks1d = h->grid1d.x;
     h->inc[0] = (float *)dev_alloc(h, N * fb);
     h->inc[1] = (float *)dev_alloc(h, N * fb);
@@ -701,6 +721,35 @@ int init_impl(lbehd_handle *h)
             d = MgDims{d.nx / 2, d.ny / 2, h->dim == 3 ? (d.nz + 1) / 2 : 1};
         }
         h->mg.back().cz2 = 0;
+        // shared-memory tail: the first level with <= TAIL_MAX_CELLS cells and all below
+        for (size_t l = 0; l < h->mg.size(); l++) {
+            const size_t nl = h->mg.size() - l;
+            if (h->mg[l].n <= (size_t)TAIL_MAX_CELLS && nl <= (size_t)TAIL_MAX_LEVELS) {
+                TailLevels &T = h->tail;
+                T.nl = (int)nl;
+                T.nu = h->mg_nu;
+                T.coarse = h->mg_coarse;
+                int off = 0;
+                for (size_t k = 0; k < nl; k++) {
+                    const auto &L = h->mg[l + k];
+                    T.d[k] = L.d;
+                    T.cz2[k] = L.cz2;
+                    T.off[k] = off;
+                    T.D[k] = L.D;
+                    T.kx[k] = L.kx;
+                    T.ky[k] = L.ky;
+                    T.kz[k] = L.kz;
+                    off += (int)L.n;
+                }
+                T.total = off;
+                h->tail_smem = 6 * (size_t)off * sizeof(float);
+                h->tail_level = (int)l;
+                if (h->tail_smem > 48 * 1024)
+                    CK(h, cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)h->tail_smem));
+                break;
+            }
+        }
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
     CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));

@@ -4,10 +4,10 @@
 // Each step solves A delta = r0 with r0 = b - A phi^{n-1}, where A is the 7/5-point
 // finite-volume operator of div(eps grad .) (face eps = (eps_i + eps_j)/2, Dirichlet value
 // on the solid node with face eps = eps_fluid, zero flux elsewhere) and b = rho_e + Dirichlet
-// terms. The potential is stored as a compensated pair of floats (hi + lo); r0 is formed in
-// FP64 from the FP32 state (hi + lo + delta_warm, eps, rho_e are exact in double), so the
-// FP32 iteration on the small increment is not limited by the rounding of phi itself, and
-// differences of phi (E, the conduction source of Eq. 14) keep ~FP64 accuracy. The warm
+// terms. The potential is stored as a compensated pair of floats (hi + lo); r0 is formed
+// from compensated differences of it, so the FP32 iteration on the small increment is not
+// limited by the rounding of phi itself, and differences of phi (E, the conduction source
+// of Eq. 14) keep ~FP64 accuracy. The warm
 // start is the increment of two steps back (consecutive increments alternate in sign
 // because the charge collision relaxes its first moments with 1 - 1/tau_rho ~ -1).
 //
@@ -252,9 +252,131 @@ __global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
     xf[i] += xc[cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
 }
 
+// ---------------------------------------------------------------- small-level tail
+
+constexpr int TAIL_MAX_LEVELS = 8;
+constexpr int TAIL_MAX_CELLS = 1024;   // cells of the finest tail level
+constexpr int TAIL_THREADS = 1024;
+
+struct TailLevels {
+    int nl;                            // levels in the tail (the last is the coarsest)
+    int nu, coarse;
+    MgDims d[TAIL_MAX_LEVELS];
+    int cz2[TAIL_MAX_LEVELS];
+    int off[TAIL_MAX_LEVELS];          // offset of each level in the shared arrays
+    const float *D[TAIL_MAX_LEVELS], *kx[TAIL_MAX_LEVELS], *ky[TAIL_MAX_LEVELS],
+        *kz[TAIL_MAX_LEVELS];
+    const float *b0;                   // right-hand side of the finest tail level (global)
+    float *x0;                         // its solution (global)
+    int total;                         // cells of all tail levels
+};
+
+__device__ __forceinline__ void tail_gs(const TailLevels &T, int l, int color, const float *sD,
+                                        const float *sx_, const float *sy_, const float *sz_,
+                                        const float *sb, float *sxv)
+{
+    const MgDims d = T.d[l];
+    const int o = T.off[l], n = d.nx * d.ny * d.nz;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int x = c % d.nx, y = (c / d.nx) % d.ny, z = c / (d.nx * d.ny);
+        if (((x + y + z) & 1) != color)
+            continue;
+        const float di = sD[o + c];
+        if (di <= 0.0f)
+            continue;
+        sxv[o + c] = (sb[o + c] + offdiag_sum(d, c, x, y, z, sx_ + o, sy_ + o, sz_ + o, sxv + o)) / di;
+    }
+}
+
+// The V-cycle on every level from the tail's finest down, in shared memory, one CTA.
+// Same arithmetic, cell by cell, as the multi-launch levels above it.
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
+{
+    extern __shared__ float sm[];
+    const int tot = T.total;
+    float *sD = sm, *skx = sm + tot, *sky = sm + 2 * tot, *skz = sm + 3 * tot, *sx = sm + 4 * tot,
+          *sb = sm + 5 * tot;
+    for (int l = 0; l < T.nl; l++) {
+        const int n = T.d[l].nx * T.d[l].ny * T.d[l].nz, o = T.off[l];
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            sD[o + c] = T.D[l][c];
+            skx[o + c] = T.kx[l][c];
+            sky[o + c] = T.ky[l][c];
+            skz[o + c] = T.kz[l][c];
+            sx[o + c] = 0.0f;
+            if (l == 0)
+                sb[c] = T.b0[c];
+        }
+    }
+    __syncthreads();
+    // down: smooth, restrict
+    for (int l = 0; l + 1 < T.nl; l++) {
+        for (int s = 0; s < T.nu; s++) {
+            tail_gs(T, l, 0, sD, skx, sky, skz, sb, sx);
+            __syncthreads();
+            tail_gs(T, l, 1, sD, skx, sky, skz, sb, sx);
+            __syncthreads();
+        }
+        const MgDims f = T.d[l], c = T.d[l + 1];
+        const int fo = T.off[l], co = T.off[l + 1], nc = c.nx * c.ny * c.nz, nzc = T.cz2[l] ? 2 : 1;
+        for (int C = threadIdx.x; C < nc; C += blockDim.x) {
+            const int X = C % c.nx, Y = (C / c.nx) % c.ny, Z = C / (c.nx * c.ny);
+            float acc = 0.0f;
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++)
+                    for (int g = 0; g < nzc; g++) {
+                        const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
+                        if (x >= f.nx || y >= f.ny || z >= f.nz)
+                            continue;
+                        const int i = (int)cell(f, x, y, z);
+                        const float di = sD[fo + i];
+                        if (di <= 0.0f)
+                            continue;
+                        acc += sb[fo + i] - (di * sx[fo + i] - offdiag_sum(f, i, x, y, z, skx + fo,
+                                                                           sky + fo, skz + fo, sx + fo));
+                    }
+            sb[co + C] = acc;
+        }
+        __syncthreads();
+    }
+    // coarsest: symmetric sweeps
+    const int lc = T.nl - 1;
+    for (int s = 0; s < T.coarse; s++) {
+        const int order[4] = {0, 1, 1, 0};
+        for (int k = 0; k < 4; k++) {
+            tail_gs(T, lc, order[k], sD, skx, sky, skz, sb, sx);
+            __syncthreads();
+        }
+    }
+    // up: prolong, smooth
+    for (int l = T.nl - 2; l >= 0; l--) {
+        const MgDims f = T.d[l], c = T.d[l + 1];
+        const int fo = T.off[l], co = T.off[l + 1], n = f.nx * f.ny * f.nz, cz2 = T.cz2[l];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int x = i % f.nx, y = (i / f.nx) % f.ny, z = i / (f.nx * f.ny);
+            if (sD[fo + i] > 0.0f)
+                sx[fo + i] += sx[co + (int)cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
+        }
+        __syncthreads();
+        for (int s = 0; s < T.nu; s++) {
+            tail_gs(T, l, 1, sD, skx, sky, skz, sb, sx);
+            __syncthreads();
+            tail_gs(T, l, 0, sD, skx, sky, skz, sb, sx);
+            __syncthreads();
+        }
+    }
+    const int n0 = T.d[0].nx * T.d[0].ny * T.d[0].nz;
+    for (int c = threadIdx.x; c < n0; c += blockDim.x)
+        T.x0[c] = sx[c];
+}
+
 // ---------------------------------------------------------------- CG on level 0
 
-// r = b - A (phi + delta) in FP64 from the FP32 state; partials of ||r||^2 and ||b||^2.
+// r = b - A (phi + delta) from the compensated potential; partials of ||r||^2 and ||b||^2.
+// Only differences of the potential enter: r_i = rho_i + sum_faces k_f (phi_j - phi_i), with
+// phi_j - phi_i = (hi_j - hi_i) + (lo_j - lo_i) + (delta_j - delta_i). Neighbouring hi parts
+// are close, so their difference is exact in FP32, and r keeps the accuracy an FP64
+// evaluation of b - A phi would have, in FP32 arithmetic.
 template <int D>
 __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restrict__ pot,
                                                  const float *__restrict__ pot_lo,
@@ -270,31 +392,31 @@ __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restri
     if (x < P.nx) {
         const MgDims d{P.nx, P.ny, P.nz};
         const size_t i = cell(d, x, y, z);
-        double ri = 0.0;
+        float ri = 0.0f;
         if (Dg[i] > 0.0f) {
-            const double ei = eps[i];
-            const double pi = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
-            double b = rho[i], Ax = 0.0;
+            const float ei = eps[i], hi = pot[i], lo = pot_lo[i], di = delta[i];
+            float b = rho[i];
+            ri = b;
             const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
                                   cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
                                   cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
 #pragma unroll
             for (int f = 0; f < 2 * D; f++) {
-                const int pt = info[nb[f]] & 3;
+                const size_t j = nb[f];
+                const int pt = info[j] & 3;
                 if (pt == PT_FLUID) {
-                    const double k = 0.5 * (ei + (double)eps[nb[f]]);
-                    Ax += k * (pi - ((double)pot[nb[f]] + (double)pot_lo[nb[f]] +
-                                     (double)delta[nb[f]]));
+                    const float dphi = (pot[j] - hi) + (pot_lo[j] - lo) + (delta[j] - di);
+                    ri += 0.5f * (ei + eps[j]) * dphi;
                 } else if (pt == PT_DIRICHLET) {
-                    b += ei * ((double)pot[nb[f]] + (double)pot_lo[nb[f]]);
-                    Ax += ei * pi;
+                    const float dphi = (pot[j] - hi) + (pot_lo[j] - lo) - di;
+                    ri += ei * dphi;
+                    b += ei * (pot[j] + pot_lo[j]);
                 }
             }
-            ri = b - Ax;
-            v[0] = (float)(ri * ri);
-            v[1] = (float)(b * b);
+            v[0] = ri * ri;
+            v[1] = b * b;
         }
-        r[i] = (float)ri;
+        r[i] = ri;
     }
     block_partials<2>(v, partials);
 }
@@ -303,11 +425,10 @@ __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restri
 __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict__ zv,
                                               float *__restrict__ p, const CgScalars *__restrict__ s)
 {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
     const float beta = s->iters == 0 ? 0.0f : (float)s->beta;
-    p[i] = zv[i] + (beta != 0.0f ? beta * p[i] : 0.0f);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = zv[i] + (beta != 0.0f ? beta * p[i] : 0.0f);
 }
 
 // q = A p on level 0 and partials of p . q.
@@ -340,14 +461,14 @@ __global__ void __launch_bounds__(BX) k_pcg_update(size_t n, const float *__rest
                                                    const CgScalars *__restrict__ s,
                                                    double *__restrict__ partials)
 {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const float a = (float)s->alpha;
     float v[1] = {0.f};
-    if (i < n) {
-        const float a = (float)s->alpha;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
         delta[i] += a * p[i];
         const float ri = r[i] - a * q[i];
         r[i] = ri;
-        v[0] = ri * ri;
+        v[0] += ri * ri;
     }
     // 1D grid: reuse the generic block reduction (gridDim.y = gridDim.z = 1)
     block_partials<1>(v, partials);
@@ -358,8 +479,10 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
                                                 const float *__restrict__ b,
                                                 double *__restrict__ partials)
 {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    float v[1] = {i < n ? a[i] * b[i] : 0.0f};
+    float v[1] = {0.0f};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        v[0] += a[i] * b[i];
     block_partials<1>(v, partials);
 }
 
@@ -370,44 +493,61 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 //   op 2: p.Ap      pq                -> alpha = rz / pq
 //   op 3: ||r||^2   rr                -> iters++, done / converged
 // With use_cond, ops 0, 4 and 3 also set the graph's while-loop condition to !done.
-__global__ void __launch_bounds__(256) k_pcg_scalar(const double *__restrict__ partials,
-                                                    long long nblocks, int nv, int op,
-                                                    CgScalars *__restrict__ s,
-                                                    cudaGraphConditionalHandle cond, int use_cond)
+constexpr int SCALAR_THREADS = 1024;
+__global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__restrict__ partials,
+                                                               long long nblocks, int nv, int op,
+                                                               CgScalars *__restrict__ s,
+                                                               cudaGraphConditionalHandle cond,
+                                                               int use_cond)
 {
-    __shared__ double sm[2][256];
+    __shared__ double sm[2][SCALAR_THREADS / 32];
+    double tot[2] = {0.0, 0.0};
     for (int k = 0; k < nv; k++) {
-        double a = 0.0;
-        for (long long b = threadIdx.x; b < nblocks; b += 256)
-            a += partials[k * nblocks + b];
-        sm[k][threadIdx.x] = a;
+        const double *p = partials + k * nblocks;
+        double a0 = 0.0, a1 = 0.0;
+        long long b = threadIdx.x;
+        for (; b + SCALAR_THREADS < nblocks; b += 2 * SCALAR_THREADS) {
+            a0 += p[b];
+            a1 += p[b + SCALAR_THREADS];
+        }
+        if (b < nblocks)
+            a0 += p[b];
+        double a = a0 + a1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0)
+            sm[k][threadIdx.x >> 5] = a;
     }
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < nv; k++)
-                sm[k][threadIdx.x] += sm[k][threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < nv; k++) {
+            double a = sm[k][threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+            tot[k] = a;
+        }
     }
     if (threadIdx.x != 0)
         return;
     if (op == 0 || op == 4) {
-        s->rr = sm[0][0];
-        s->bb = sm[1][0];
+        s->rr = tot[0];
+        s->bb = tot[1];
         s->iters = 0;
         if (op == 0)
             s->step_iters = 0;
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->max_iter <= 0;
     } else if (op == 1) {
-        s->rz = sm[0][0];
+        s->rz = tot[0];
         s->beta = s->iters == 0 || s->rz_old == 0.0 ? 0.0 : s->rz / s->rz_old;
         s->rz_old = s->rz;
     } else if (op == 2) {
-        s->pq = sm[0][0];
+        s->pq = tot[0];
         s->alpha = (!s->done && s->pq > 0.0) ? s->rz / s->pq : 0.0;
     } else if (!s->done) {
-        s->rr = sm[0][0];
+        s->rr = tot[0];
         s->iters += 1;
         s->step_iters += 1;
         s->total_iters += 1;
@@ -428,8 +568,10 @@ __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restr
                                                   float *__restrict__ pot,
                                                   float *__restrict__ pot_lo)
 {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n && Dg[i] > 0.0f) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (Dg[i] <= 0.0f)
+            continue;
         if (acc)
             acc[i] += delta[i];
         const double t = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
