@@ -383,8 +383,12 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
                 dyz += cy * cz * A;
                 dT += (cx * cx + cy * cy + cz * cz) * A;
             }
+            // moving populations first; the rest population takes the exact remainder of
+            // the conserved zeroth moment (the FP32 weights do not sum to 1 exactly, which
+            // would otherwise create mass at ~1e-8 per step)
+            float sum = 0.0f;
 #pragma unroll
-            for (int n = 0; n < Q; n++) {
+            for (int n = 1; n < Q; n++) {
                 const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
                 const int e2 = cx * cx + cy * cy + cz * cz;
                 float corr = 0.0f, corrT = 0.0f;
@@ -409,8 +413,11 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
                         corrT = -dT;
                     }
                 }
-                push(S.g_out, n, base[n] + c_nu * corr + c_b * corrT);
+                const float v = base[n] + c_nu * corr + c_b * corrT;
+                sum += v;
+                push(S.g_out, n, v);
             }
+            push(S.g_out, 0, dp - sum);
             if (!isfinite(dp + u[0] + u[1] + u[2]))
                 atomicOr(S.flag, 1);
         }
@@ -435,16 +442,19 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
                 A[a] = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
                 del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A[a]);
             }
+            float sum = 0.0f;
 #pragma unroll
-            for (int n = 0; n < Q; n++) {
+            for (int n = 1; n < Q; n++) {
                 const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
                 const float eu = cx * u[0] + cy * u[1] + cz * u[2];
                 const float eA = cx * A[0] + cy * A[1] + cz * A[2];
                 float v = L::w(n) * (Pp * (1.0f + inv_cs2 * eu) + 0.5f * inv_cs2 * eA);
                 if (cx * cx + cy * cy + cz * cz == 1)
                     v += cx * del[0] + cy * del[1] + cz * del[2];
+                sum += v;
                 push(S.fphi_out + (size_t)c * Q * N, n, v);
             }
+            push(S.fphi_out + (size_t)c * Q * N, 0, Pp - sum);   // Phi is conserved
         }
 
         // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
@@ -467,16 +477,18 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
                 Dm[a] = rho * u[a] - rho_o * uo[a];
                 del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm[a]);
             }
+            float sum = 0.0f;
 #pragma unroll
-            for (int n = 0; n < QS; n++) {
+            for (int n = 1; n < QS; n++) {
                 const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
                 const float eu = cx * u[0] + cy * u[1] + cz * u[2];
                 const float eD = cx * Dm[0] + cy * Dm[1] + cz * Dm[2];
                 float v = L::ws(n) * (rho * (1.0f + inv_cs2s * eu) + 0.5f * inv_cs2s * eD + Qt);
-                if (n > 0)
-                    v += cx * del[0] + cy * del[1] + cz * del[2];
+                v += cx * del[0] + cy * del[1] + cz * del[2];
+                sum += v;
                 push(S.frho_out, n, v);
             }
+            push(S.frho_out, 0, (rho + Qt) - sum);   // zeroth moment: rho_e + source
         }
 
         // ---- observable contributions

@@ -271,61 +271,66 @@ struct TailLevels {
     int total;                         // cells of all tail levels
 };
 
-__device__ __forceinline__ void tail_gs(const TailLevels &T, int l, int color, const float *sD,
-                                        const float *sx_, const float *sy_, const float *sz_,
-                                        const float *sb, float *sxv)
-{
-    const MgDims d = T.d[l];
-    const int o = T.off[l], n = d.nx * d.ny * d.nz;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const int x = c % d.nx, y = (c / d.nx) % d.ny, z = c / (d.nx * d.ny);
-        if (((x + y + z) & 1) != color)
-            continue;
-        const float di = sD[o + c];
-        if (di <= 0.0f)
-            continue;
-        sxv[o + c] = (sb[o + c] + offdiag_sum(d, c, x, y, z, sx_ + o, sy_ + o, sz_ + o, sxv + o)) / di;
-    }
-}
-
-// The V-cycle on every level from the tail's finest down, in shared memory, one CTA.
-// Same arithmetic, cell by cell, as the multi-launch levels above it.
+// The V-cycle on every level from the tail's finest down, in shared memory, one CTA. Thread t
+// owns cell t of every tail level (levels have <= TAIL_THREADS cells), so its coordinates are
+// computed once. Same arithmetic, cell by cell, as the multi-launch levels above it.
 __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
 {
     extern __shared__ float sm[];
-    const int tot = T.total;
+    const int tot = T.total, t = threadIdx.x;
     float *sD = sm, *skx = sm + tot, *sky = sm + 2 * tot, *skz = sm + 3 * tot, *sx = sm + 4 * tot,
           *sb = sm + 5 * tot;
-    for (int l = 0; l < T.nl; l++) {
-        const int n = T.d[l].nx * T.d[l].ny * T.d[l].nz, o = T.off[l];
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            sD[o + c] = T.D[l][c];
-            skx[o + c] = T.kx[l][c];
-            sky[o + c] = T.ky[l][c];
-            skz[o + c] = T.kz[l][c];
-            sx[o + c] = 0.0f;
-            if (l == 0)
-                sb[c] = T.b0[c];
+    int cx[TAIL_MAX_LEVELS], cy[TAIL_MAX_LEVELS], cz[TAIL_MAX_LEVELS];
+    bool own[TAIL_MAX_LEVELS];
+#pragma unroll
+    for (int l = 0; l < TAIL_MAX_LEVELS; l++) {
+        own[l] = false;
+        cx[l] = cy[l] = cz[l] = 0;
+        if (l < T.nl) {
+            const MgDims d = T.d[l];
+            const int n = d.nx * d.ny * d.nz, o = T.off[l];
+            own[l] = t < n;
+            if (own[l]) {
+                cx[l] = t % d.nx;
+                cy[l] = (t / d.nx) % d.ny;
+                cz[l] = t / (d.nx * d.ny);
+                sD[o + t] = T.D[l][t];
+                skx[o + t] = T.kx[l][t];
+                sky[o + t] = T.ky[l][t];
+                skz[o + t] = T.kz[l][t];
+                sx[o + t] = 0.0f;
+                if (l == 0)
+                    sb[t] = T.b0[t];
+            }
         }
     }
     __syncthreads();
+    auto gs = [&](int l, int color) {
+        if (own[l] && ((cx[l] + cy[l] + cz[l]) & 1) == color) {
+            const int o = T.off[l];
+            const float di = sD[o + t];
+            if (di > 0.0f)
+                sx[o + t] = (sb[o + t] + offdiag_sum(T.d[l], t, cx[l], cy[l], cz[l], skx + o, sky + o,
+                                                     skz + o, sx + o)) / di;
+        }
+        __syncthreads();
+    };
     // down: smooth, restrict
+#pragma unroll 1
     for (int l = 0; l + 1 < T.nl; l++) {
         for (int s = 0; s < T.nu; s++) {
-            tail_gs(T, l, 0, sD, skx, sky, skz, sb, sx);
-            __syncthreads();
-            tail_gs(T, l, 1, sD, skx, sky, skz, sb, sx);
-            __syncthreads();
+            gs(l, 0);
+            gs(l, 1);
         }
-        const MgDims f = T.d[l], c = T.d[l + 1];
-        const int fo = T.off[l], co = T.off[l + 1], nc = c.nx * c.ny * c.nz, nzc = T.cz2[l] ? 2 : 1;
-        for (int C = threadIdx.x; C < nc; C += blockDim.x) {
-            const int X = C % c.nx, Y = (C / c.nx) % c.ny, Z = C / (c.nx * c.ny);
+        if (own[l + 1]) {
+            const MgDims f = T.d[l];
+            const int fo = T.off[l], nzc = T.cz2[l] ? 2 : 1;
             float acc = 0.0f;
             for (int a = 0; a < 2; a++)
                 for (int b = 0; b < 2; b++)
                     for (int g = 0; g < nzc; g++) {
-                        const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
+                        const int x = 2 * cx[l + 1] + a, y = 2 * cy[l + 1] + b,
+                                  z = nzc * cz[l + 1] + g;
                         if (x >= f.nx || y >= f.ny || z >= f.nz)
                             continue;
                         const int i = (int)cell(f, x, y, z);
@@ -335,39 +340,36 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
                         acc += sb[fo + i] - (di * sx[fo + i] - offdiag_sum(f, i, x, y, z, skx + fo,
                                                                            sky + fo, skz + fo, sx + fo));
                     }
-            sb[co + C] = acc;
+            sb[T.off[l + 1] + t] = acc;
         }
         __syncthreads();
     }
     // coarsest: symmetric sweeps
     const int lc = T.nl - 1;
+#pragma unroll 1
     for (int s = 0; s < T.coarse; s++) {
-        const int order[4] = {0, 1, 1, 0};
-        for (int k = 0; k < 4; k++) {
-            tail_gs(T, lc, order[k], sD, skx, sky, skz, sb, sx);
-            __syncthreads();
-        }
+        gs(lc, 0);
+        gs(lc, 1);
+        gs(lc, 1);
+        gs(lc, 0);
     }
     // up: prolong, smooth
+#pragma unroll 1
     for (int l = T.nl - 2; l >= 0; l--) {
-        const MgDims f = T.d[l], c = T.d[l + 1];
-        const int fo = T.off[l], co = T.off[l + 1], n = f.nx * f.ny * f.nz, cz2 = T.cz2[l];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int x = i % f.nx, y = (i / f.nx) % f.ny, z = i / (f.nx * f.ny);
-            if (sD[fo + i] > 0.0f)
-                sx[fo + i] += sx[co + (int)cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
+        if (own[l]) {
+            const int fo = T.off[l];
+            if (sD[fo + t] > 0.0f)
+                sx[fo + t] += sx[T.off[l + 1] + (int)cell(T.d[l + 1], cx[l] >> 1, cy[l] >> 1,
+                                                           T.cz2[l] ? (cz[l] >> 1) : cz[l])];
         }
         __syncthreads();
         for (int s = 0; s < T.nu; s++) {
-            tail_gs(T, l, 1, sD, skx, sky, skz, sb, sx);
-            __syncthreads();
-            tail_gs(T, l, 0, sD, skx, sky, skz, sb, sx);
-            __syncthreads();
+            gs(l, 1);
+            gs(l, 0);
         }
     }
-    const int n0 = T.d[0].nx * T.d[0].ny * T.d[0].nz;
-    for (int c = threadIdx.x; c < n0; c += blockDim.x)
-        T.x0[c] = sx[c];
+    if (own[0])
+        T.x0[t] = sx[t];
 }
 
 // ---------------------------------------------------------------- CG on level 0
