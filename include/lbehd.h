@@ -196,6 +196,29 @@ int lbehd_profile_enable(lbehd_handle *h, int enable);
  * and the number of launches (count[LBEHD_NKC]) recorded since profiling was enabled. */
 int lbehd_profile_read(lbehd_handle *h, double *ms, long long *count);
 
+/* Droplet phase moments of caller-owned device fields, computed without allocating any
+ * device memory. The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate, such as a host program that hands out all device memory
+ * from its own pre-sized pool (an allocation behind its back could fail or fragment the
+ * pool) or a framework that calls foreign kernels where it forbids allocation.
+ * Inputs (device, FP32, site index i = x + nx (y + ny z)): phi = 3*N values Phi_1..3,
+ * u = 3*N velocity components, solid = N solid classes (0 = fluid; only fluid sites count).
+ * Output (device, written asynchronously on `stream`): out[10] = M1 = sum Phi_1,
+ * centroid[3] = sum Phi_1 x / M1, velocity[3] = sum Phi_1 u / M1, mass[3] = sum Phi_i,
+ * the quantities lbehd_observe reports for the droplet.
+ * Scratch: the per-block partial sums live in one file-scope __device__ array of
+ * 2048 x 10 doubles (160 KB), which every GPU that loads the library holds until the
+ * process exits. This caps the lattice at 2048 x 8192 = 16 777 216 sites; larger lattices
+ * are rejected with LBEHD_ERR_INVALID_ARG. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call overwrites the partials it reads, so nothing needs
+ * clearing, but all calls share the array: calls whose kernels overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors: LBEHD_ERR_INVALID_ARG (bad extents, null pointer, too large), LBEHD_ERR_CUDA;
+ * the message is in lbehd_last_error(NULL). */
+int lbehd_phase_moments_noalloc(int dim, int nx, int ny, int nz, const float *phi,
+                                const float *u, const uint8_t *solid, double *out, void *stream);
+
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
 const char *lbehd_last_error(lbehd_handle *h);
 

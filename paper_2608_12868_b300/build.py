@@ -4,7 +4,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = [os.path.join(HERE, "csrc", "lbehd.cu")]
+SRC = [os.path.join(HERE, "csrc", "lbehd.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "lattice.cuh")] + [
     os.path.join(os.path.dirname(HERE), "include", "lbehd.h")]
 LIB = os.path.join(HERE, "liblbehd.so")

@@ -19,6 +19,8 @@ namespace lbehd {
 
 static thread_local std::string g_init_error;
 
+void set_global_error(const std::string &msg) { g_init_error = msg; }
+
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
