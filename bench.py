@@ -181,6 +181,8 @@ def run_ours(args, world, rank, local):
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=mode,
                            poisson_fixed_iters=args.fixed_iters,
                            poisson_check_every=args.check_every)
+    sim.set_option(lbehd.OPT_COLLIDE, {"auto": lbehd.COLLIDE_AUTO, "global": lbehd.COLLIDE_GLOBAL,
+                                       "staged": lbehd.COLLIDE_STAGED}[args.collide])
     L = args.lb_steps
     fluid = int((w.solid == 0).sum())
     for _ in range(args.warmup):
@@ -277,7 +279,7 @@ def run_ours(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_collide<3>", "peak_source": peak_kind,
+                         "kernel": "k_collide (" + args.collide + ")", "peak_source": peak_kind,
                          "timing": "CUDA events around each k_collide launch over a second "
                                    "timed region of the same length",
                          "bytes_per_launch": coll_bytes},
@@ -321,6 +323,7 @@ def main():
     ap.add_argument("--workload", default="droplet_3d_128x64x64")
     ap.add_argument("--lb-steps", type=int, default=20)
     ap.add_argument("--warmup-seconds", type=float, default=2.0)
+    ap.add_argument("--collide", choices=["auto", "global", "staged"], default="auto")
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)

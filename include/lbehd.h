@@ -48,7 +48,8 @@ extern "C" {
 #define LBEHD_ERR_INVALID_ARG (-1)
 #define LBEHD_ERR_OOM (-2)
 #define LBEHD_ERR_POISSON_NOCONV (-3) /* step completed, Poisson hit its iteration cap */
-#define LBEHD_ERR_NONFINITE (-4)      /* a NaN/Inf appeared in the state */
+#define LBEHD_ERR_NONFINITE (-4)      /* a NaN/Inf appeared in the state, or a bounded device
+                                       * wait (shared-memory staging) gave up */
 #define LBEHD_ERR_CUDA (-5)
 #define LBEHD_ERR_STATE (-6)          /* call not valid in the handle's current state */
 
@@ -164,6 +165,14 @@ int lbehd_copy_out(lbehd_handle *h, int which, void *dst, size_t bytes);
 
 /* Device pointer and size in bytes of one array (valid until the next lbehd_step). */
 int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
+
+/* Implementation options (synchronises; discards captured step graphs).
+ *   LBEHD_OPT_COLLIDE: which fused collide kernel runs: 0 automatic (staged when
+ *   nx % 4 == 0), 1 populations loaded straight from global memory, 2 population tile
+ *   staged into shared memory by bulk asynchronous copies (needs nx % 4 == 0). Both give
+ *   the same arithmetic. */
+#define LBEHD_OPT_COLLIDE 1
+int lbehd_set_option(lbehd_handle *h, int option, long long value);
 
 /* Counters since init (synchronises: reads the device-side iteration counter). */
 typedef struct lbehd_stats {

@@ -31,6 +31,7 @@
 #include <cstdint>
 
 #include "lattice.cuh"
+#include "tma.cuh"
 
 namespace lbehd {
 
@@ -61,7 +62,7 @@ struct State {
     const float *pot, *pot_lo;        // potential as a compensated pair hi + lo
     const uint8_t *info;
     double *obs_partials;             // [NOBS][nblocks]
-    int *flag;                        // bit 0: non-finite value seen
+    int *flag;                        // bit 0: non-finite value seen; bit 1: staging timed out
 };
 
 template <class L>
@@ -193,323 +194,338 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict
 
 // ---------------------------------------------------------------- fused collide + stream
 
-// 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
-// the kernel is memory-latency bound and needs the warps.
-template <int D>
-__global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
+// Population sources for collide_site: straight from global memory, or from a
+// shared-memory tile staged by bulk copies.
+struct GlobalPops {
+    const float *__restrict__ gp, *__restrict__ fp, *__restrict__ rp;
+    size_t N, i;
+    int Q;
+    __device__ __forceinline__ float g(int n) const { return gp[n * N + i]; }
+    __device__ __forceinline__ float phi(int c, int n) const { return fp[(c * Q + n) * N + i]; }
+    __device__ __forceinline__ float rho(int n) const { return rp[n * N + i]; }
+};
+
+struct SmemPops {
+    const float *s;   // [population array][tile x], row stride TW
+    int t, Q;
+    __device__ __forceinline__ float g(int n) const { return s[n * BX + t]; }
+    __device__ __forceinline__ float phi(int c, int n) const { return s[(Q + c * Q + n) * BX + t]; }
+    __device__ __forceinline__ float rho(int n) const { return s[(4 * Q + n) * BX + t]; }
+};
+
+// Everything the step does at one fluid site after the moments and the Poisson solve:
+// stencils, forces, the three collisions, push streaming, observable contributions.
+template <int D, class Pops>
+__device__ __forceinline__ void collide_site(const Params &P, const State &S, int x, int y, int z,
+                                             size_t i, int first, const Pops &pops,
+                                             float (&ob)[NOBS])
 {
     using L = Lat<D>;
     constexpr int Q = L::Q, QS = L::QS;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const size_t N = P.N;
-    float ob[NOBS];
-#pragma unroll
-    for (int k = 0; k < NOBS; k++)
-        ob[k] = 0.0f;
+    const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
+    const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
+    const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
 
-    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
-    if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
-        const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
-        const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
-        const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
-
-        // ---- stencils of Phi_i and phi over the flow lattice
-        const float Pc[3] = {S.phi[i], S.phi[N + i], S.phi[2 * N + i]};
-        const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
-        const float pot_i = S.pot[i], lo_i = S.pot_lo[i];
-        float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        float lP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
-        float qsrc = 0.0f;
-        unsigned fluid_nb = 1u;   // bit n: x + e_n is fluid (bit 0: the site itself)
+    // ---- stencils of Phi_i and phi over the flow lattice
+    const float Pc[3] = {S.phi[i], S.phi[N + i], S.phi[2 * N + i]};
+    const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
+    const float pot_i = S.pot[i], lo_i = S.pot_lo[i];
+    float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float lP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
+    float qsrc = 0.0f;
+    unsigned fluid_nb = 1u;   // bit n: x + e_n is fluid (bit 0: the site itself)
 #pragma unroll
-        for (int n = 1; n < Q; n++) {
-            const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
-            const int pt = S.info[j] & 3;
-            const float wn = L::w(n);
-            const float ea[3] = {(float)L::ex(n), (float)L::ey(n), (float)L::ez(n)};
-            float Pn[3];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                Pn[c] = S.phi[c * N + j];
-                lP[c] += wn * (Pn[c] - Pc[c]);
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-                    gP[c][a] += wn * ea[a] * Pn[c];
-            }
-            // phi(x + e_n) - phi(x) from the compensated pairs (zero-flux solid: mirror)
-            const float dph =
-                pt == PT_NEUMANN ? 0.0f : (S.pot[j] - pot_i) + (S.pot_lo[j] - lo_i);
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                gpot[a] += wn * ea[a] * dph;
-            if (pt == PT_FLUID) {
-                fluid_nb |= 1u << n;
-                if (n <= 2 * D) {
-                    const float sig_j = Pn[0] * P.sig[0] + Pn[1] * P.sig[1] + Pn[2] * P.sig[2];
-                    qsrc += 0.5f * (sig_i + sig_j) * dph;
-                }
-            }
-        }
-        const float inv_cs2 = 3.0f;
+    for (int n = 1; n < Q; n++) {
+        const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
+        const int pt = S.info[j] & 3;
+        const float wn = L::w(n);
+        const float ea[3] = {(float)L::ex(n), (float)L::ey(n), (float)L::ez(n)};
+        float Pn[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            lP[c] *= 2.0f * inv_cs2;
+            Pn[c] = S.phi[c * N + j];
+            lP[c] += wn * (Pn[c] - Pc[c]);
 #pragma unroll
             for (int a = 0; a < 3; a++)
-                gP[c][a] *= inv_cs2;
+                gP[c][a] += wn * ea[a] * Pn[c];
         }
+        // phi(x + e_n) - phi(x) from the compensated pairs (zero-flux solid: mirror)
+        const float dph =
+            pt == PT_NEUMANN ? 0.0f : (S.pot[j] - pot_i) + (S.pot_lo[j] - lo_i);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            gpot[a] += wn * ea[a] * dph;
+        if (pt == PT_FLUID) {
+            fluid_nb |= 1u << n;
+            if (n <= 2 * D) {
+                const float sig_j = Pn[0] * P.sig[0] + Pn[1] * P.sig[1] + Pn[2] * P.sig[2];
+                qsrc += 0.5f * (sig_i + sig_j) * dph;
+            }
+        }
+    }
+    const float inv_cs2 = 3.0f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        lP[c] *= 2.0f * inv_cs2;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            gP[c][a] *= inv_cs2;
+    }
 
-        // ---- chemical potential (Eqs. 10-11), capillary and electric forces (Eq. 12)
-        const float W = P.W;
-        const float tri = 24.0f * P.YT / W * Pc[0] * Pc[1] * Pc[2];
-        float Fs[3] = {0.f, 0.f, 0.f}, geps[3];
+    // ---- chemical potential (Eqs. 10-11), capillary and electric forces (Eq. 12)
+    const float W = P.W;
+    const float tri = 24.0f * P.YT / W * Pc[0] * Pc[1] * Pc[2];
+    float Fs[3] = {0.f, 0.f, 0.f}, geps[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float mu = 24.0f * P.Y[c] / W * Pc[c] * (Pc[c] - 1.0f) * (Pc[c] - 0.5f) - tri -
+                         0.75f * P.Y[c] * W * lP[c];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            Fs[a] += mu * gP[c][a];
+    }
+    float E[3], E2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        geps[a] = P.eps[0] * gP[0][a] + P.eps[1] * gP[1][a] + P.eps[2] * gP[2][a];
+        E[a] = -inv_cs2 * gpot[a];
+        E2 += E[a] * E[a];
+    }
+    const float rho = S.rho[i];
+    float Fe[3], F[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        Fe[a] = rho * E[a] - 0.5f * E2 * geps[a];
+        F[a] = Fs[a] + Fe[a] + P.body[a];
+    }
+
+    // ---- sharpening flux F_Phi,i (Eq. 18)
+    float FPhi[3][3];
+    {
+        float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const float mu = 24.0f * P.Y[c] / W * Pc[c] * (Pc[c] - 1.0f) * (Pc[c] - 0.5f) - tri -
-                             0.75f * P.Y[c] * W * lP[c];
+            // n = grad / sqrt(|grad|^2 + 1e-10): continuous where grad Phi vanishes
+            const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
+                                   gP[c][2] * gP[c][2] + 1e-10f);
+            const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                ln[c][a] = lam * gP[c][a];
+                J[a] += ln[c][a];
+            }
+            sumsq += Pc[c] * Pc[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float r = Pc[c] * Pc[c] / sumsq;
 #pragma unroll
             for (int a = 0; a < 3; a++)
-                Fs[a] += mu * gP[c][a];
+                FPhi[c][a] = ln[c][a] - r * J[a];
         }
-        float E[3], E2 = 0.0f;
+    }
+
+    // ---- momentum moments, velocity, previous-step values
+    float gs[Q];
+    float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int n = 0; n < Q; n++) {
+        gs[n] = pops.g(n);
+        dp += gs[n];
+        jm[0] += L::ex(n) * gs[n];
+        jm[1] += L::ey(n) * gs[n];
+        jm[2] += L::ez(n) * gs[n];
+    }
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        u[a] = jm[a] + 0.5f * F[a];
+    float uo[3], Po[3], rho_o, q_o;
+    if (first) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            geps[a] = P.eps[0] * gP[0][a] + P.eps[1] * gP[1][a] + P.eps[2] * gP[2][a];
-            E[a] = -inv_cs2 * gpot[a];
-            E2 += E[a] * E[a];
+            uo[a] = u[a];
+            Po[a] = Pc[a];
         }
-        const float rho = S.rho[i];
-        float Fe[3], F[3];
+        rho_o = rho;
+        q_o = qsrc;
+    } else {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            Fe[a] = rho * E[a] - 0.5f * E2 * geps[a];
-            F[a] = Fs[a] + Fe[a] + P.body[a];
+            uo[a] = S.u[a * N + i];
+            Po[a] = S.phi_prev[a * N + i];
         }
+        rho_o = S.rho_prev[i];
+        q_o = S.q[i];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        S.u[a * N + i] = u[a];
+    S.q[i] = qsrc;
 
-        // ---- sharpening flux F_Phi,i (Eq. 18)
-        float FPhi[3][3];
-        {
-            float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                // n = grad / sqrt(|grad|^2 + 1e-10): continuous where grad Phi vanishes
-                const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
-                                       gP[c][2] * gP[c][2] + 1e-10f);
-                const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    ln[c][a] = lam * gP[c][a];
-                    J[a] += ln[c][a];
-                }
-                sumsq += Pc[c] * Pc[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float r = Pc[c] * Pc[c] / sumsq;
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-                    FPhi[c][a] = ln[c][a] - r * J[a];
-            }
-        }
+    auto push = [&](float *out, int n, float v) {
+        if ((fluid_nb >> n) & 1u)
+            out[n * N + nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny)] = v;
+        else
+            out[opposite(n) * N + i] = v;
+    };
 
-        // ---- momentum moments, velocity, previous-step values
-        float gs[Q];
-        float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f};
+    // ---- momentum collision (incompressible equilibrium, Guo forcing, MRT)
+    {
+        const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
+        const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
+        const float c_b = 1.0f - P.s_bulk;
+        float base[Q];
+        float d1 = 0.f, d2 = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f, dT = 0.f;
 #pragma unroll
         for (int n = 0; n < Q; n++) {
-            gs[n] = S.g[n * N + i];
-            dp += gs[n];
-            jm[0] += L::ex(n) * gs[n];
-            jm[1] += L::ey(n) * gs[n];
-            jm[2] += L::ez(n) * gs[n];
+            const float cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+            const float eF = cx * F[0] + cy * F[1] + cz * F[2];
+            const float wn = L::w(n);
+            const float geq = wn * (dp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+            const float hR = wn * (1.5f * (eF - uF) + 4.5f * eu * eF);   // R_n / 2
+            base[n] = geq + hR;
+            const float A = gs[n] - geq + hR;
+            d1 += (cx * cx - cy * cy) * A;
+            d2 += (cx * cx - cz * cz) * A;
+            dxy += cx * cy * A;
+            dxz += cx * cz * A;
+            dyz += cy * cz * A;
+            dT += (cx * cx + cy * cy + cz * cz) * A;
         }
-        float u[3];
+        // moving populations first; the rest population takes the exact remainder of
+        // the conserved zeroth moment (the FP32 weights do not sum to 1 exactly, which
+        // would otherwise create mass at ~1e-8 per step)
+        float sum = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 3; a++)
-            u[a] = jm[a] + 0.5f * F[a];
-        float uo[3], Po[3], rho_o, q_o;
-        if (first) {
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                uo[a] = u[a];
-                Po[a] = Pc[a];
-            }
-            rho_o = rho;
-            q_o = qsrc;
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                uo[a] = S.u[a * N + i];
-                Po[a] = S.phi_prev[a * N + i];
-            }
-            rho_o = S.rho_prev[i];
-            q_o = S.q[i];
-        }
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            S.u[a * N + i] = u[a];
-        S.q[i] = qsrc;
-
-        auto push = [&](float *out, int n, float v) {
-            if ((fluid_nb >> n) & 1u)
-                out[n * N + nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny)] = v;
-            else
-                out[opposite(n) * N + i] = v;
-        };
-
-        // ---- momentum collision (incompressible equilibrium, Guo forcing, MRT)
-        {
-            const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-            const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
-            const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
-            const float c_b = 1.0f - P.s_bulk;
-            float base[Q];
-            float d1 = 0.f, d2 = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f, dT = 0.f;
-#pragma unroll
-            for (int n = 0; n < Q; n++) {
-                const float cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-                const float eF = cx * F[0] + cy * F[1] + cz * F[2];
-                const float wn = L::w(n);
-                const float geq = wn * (dp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-                const float hR = wn * (1.5f * (eF - uF) + 4.5f * eu * eF);   // R_n / 2
-                base[n] = geq + hR;
-                const float A = gs[n] - geq + hR;
-                d1 += (cx * cx - cy * cy) * A;
-                d2 += (cx * cx - cz * cz) * A;
-                dxy += cx * cy * A;
-                dxz += cx * cz * A;
-                dyz += cy * cz * A;
-                dT += (cx * cx + cy * cy + cz * cz) * A;
-            }
-            // moving populations first; the rest population takes the exact remainder of
-            // the conserved zeroth moment (the FP32 weights do not sum to 1 exactly, which
-            // would otherwise create mass at ~1e-8 per step)
-            float sum = 0.0f;
-#pragma unroll
-            for (int n = 1; n < Q; n++) {
-                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-                const int e2 = cx * cx + cy * cy + cz * cz;
-                float corr = 0.0f, corrT = 0.0f;
-                if (D == 3) {
-                    if (e2 == 1) {
-                        corr = cx ? (d1 + d2) * (1.0f / 6.0f)
-                                  : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
-                                        : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
-                        corrT = dT * (1.0f / 6.0f);
-                    } else if (e2 == 2) {
-                        corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
-                    } else {
-                        corrT = -dT;
-                    }
+        for (int n = 1; n < Q; n++) {
+            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+            const int e2 = cx * cx + cy * cy + cz * cz;
+            float corr = 0.0f, corrT = 0.0f;
+            if (D == 3) {
+                if (e2 == 1) {
+                    corr = cx ? (d1 + d2) * (1.0f / 6.0f)
+                              : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
+                                    : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
+                    corrT = dT * (1.0f / 6.0f);
+                } else if (e2 == 2) {
+                    corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
                 } else {
-                    if (e2 == 1) {
-                        corr = cx ? 0.25f * d1 : -0.25f * d1;
-                        corrT = 0.25f * dT;
-                    } else if (e2 == 2) {
-                        corr = 0.25f * cx * cy * dxy;
-                    } else {
-                        corrT = -dT;
-                    }
+                    corrT = -dT;
                 }
-                const float v = base[n] + c_nu * corr + c_b * corrT;
-                sum += v;
-                push(S.g_out, n, v);
+            } else {
+                if (e2 == 1) {
+                    corr = cx ? 0.25f * d1 : -0.25f * d1;
+                    corrT = 0.25f * dT;
+                } else if (e2 == 2) {
+                    corr = 0.25f * cx * cy * dxy;
+                } else {
+                    corrT = -dT;
+                }
             }
-            push(S.g_out, 0, dp - sum);
-            if (!isfinite(dp + u[0] + u[1] + u[2]))
-                atomicOr(S.flag, 1);
+            const float v = base[n] + c_nu * corr + c_b * corrT;
+            sum += v;
+            push(S.g_out, n, v);
         }
-
-        // ---- phase-field collisions (Eqs. 15-17), one component at a time
-        const float c_phi = 1.0f - P.inv_tau_phi;
-#pragma unroll 1
-        for (int c = 0; c < 3; c++) {
-            float f[Q];
-            float jf[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int n = 0; n < Q; n++) {
-                f[n] = S.fphi[(c * Q + n) * N + i];
-                jf[0] += L::ex(n) * f[n];
-                jf[1] += L::ey(n) * f[n];
-                jf[2] += L::ez(n) * f[n];
-            }
-            const float Pp = Pc[c];
-            float A[3], del[3];
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                A[a] = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
-                del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A[a]);
-            }
-            float sum = 0.0f;
-#pragma unroll
-            for (int n = 1; n < Q; n++) {
-                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-                const float eA = cx * A[0] + cy * A[1] + cz * A[2];
-                float v = L::w(n) * (Pp * (1.0f + inv_cs2 * eu) + 0.5f * inv_cs2 * eA);
-                if (cx * cx + cy * cy + cz * cz == 1)
-                    v += cx * del[0] + cy * del[1] + cz * del[2];
-                sum += v;
-                push(S.fphi_out + (size_t)c * Q * N, n, v);
-            }
-            push(S.fphi_out + (size_t)c * Q * N, 0, Pp - sum);   // Phi is conserved
-        }
-
-        // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
-        {
-            constexpr float inv_cs2s = 1.0f / L::cs2s;
-            float jr[3] = {0.f, 0.f, 0.f};
-            float fr[QS];
-#pragma unroll
-            for (int n = 0; n < QS; n++) {
-                fr[n] = S.frho[n * N + i];
-                jr[0] += L::ex(n) * fr[n];
-                jr[1] += L::ey(n) * fr[n];
-                jr[2] += L::ez(n) * fr[n];
-            }
-            const float c_rho = 1.0f - P.inv_tau_rho;
-            const float Qt = qsrc + 0.5f * (qsrc - q_o);
-            float Dm[3], del[3];
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                Dm[a] = rho * u[a] - rho_o * uo[a];
-                del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm[a]);
-            }
-            float sum = 0.0f;
-#pragma unroll
-            for (int n = 1; n < QS; n++) {
-                const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-                const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-                const float eD = cx * Dm[0] + cy * Dm[1] + cz * Dm[2];
-                float v = L::ws(n) * (rho * (1.0f + inv_cs2s * eu) + 0.5f * inv_cs2s * eD + Qt);
-                v += cx * del[0] + cy * del[1] + cz * del[2];
-                sum += v;
-                push(S.frho_out, n, v);
-            }
-            push(S.frho_out, 0, (rho + Qt) - sum);   // zeroth moment: rho_e + source
-        }
-
-        // ---- observable contributions
-        ob[0] = Pc[0];
-        ob[1] = Pc[0] * (float)x;
-        ob[2] = Pc[0] * (float)y;
-        ob[3] = Pc[0] * (float)z;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            ob[4 + a] = Pc[0] * u[a];
-            ob[7 + a] = Pc[0] * Fe[a];
-            ob[10 + a] = Fe[a];
-        }
-        ob[13] = Pc[1];
-        ob[14] = Pc[2];
-        ob[15] = rho;
-        if (!isfinite(Pc[0] + Pc[1] + Pc[2] + rho + qsrc))
+        push(S.g_out, 0, dp - sum);
+        if (!isfinite(dp + u[0] + u[1] + u[2]))
             atomicOr(S.flag, 1);
     }
 
-    // ---- block partial sums: FP32 within a warp, FP64 across warps
+    // ---- phase-field collisions (Eqs. 15-17), one component at a time
+    const float c_phi = 1.0f - P.inv_tau_phi;
+#pragma unroll 1
+    for (int c = 0; c < 3; c++) {
+        float f[Q];
+        float jf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int n = 0; n < Q; n++) {
+            f[n] = pops.phi(c, n);
+            jf[0] += L::ex(n) * f[n];
+            jf[1] += L::ey(n) * f[n];
+            jf[2] += L::ez(n) * f[n];
+        }
+        const float Pp = Pc[c];
+        float A[3], del[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            A[a] = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
+            del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A[a]);
+        }
+        float sum = 0.0f;
+#pragma unroll
+        for (int n = 1; n < Q; n++) {
+            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+            const float eA = cx * A[0] + cy * A[1] + cz * A[2];
+            float v = L::w(n) * (Pp * (1.0f + inv_cs2 * eu) + 0.5f * inv_cs2 * eA);
+            if (cx * cx + cy * cy + cz * cz == 1)
+                v += cx * del[0] + cy * del[1] + cz * del[2];
+            sum += v;
+            push(S.fphi_out + (size_t)c * Q * N, n, v);
+        }
+        push(S.fphi_out + (size_t)c * Q * N, 0, Pp - sum);   // Phi is conserved
+    }
+
+    // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
+    {
+        constexpr float inv_cs2s = 1.0f / L::cs2s;
+        float jr[3] = {0.f, 0.f, 0.f};
+        float fr[QS];
+#pragma unroll
+        for (int n = 0; n < QS; n++) {
+            fr[n] = pops.rho(n);
+            jr[0] += L::ex(n) * fr[n];
+            jr[1] += L::ey(n) * fr[n];
+            jr[2] += L::ez(n) * fr[n];
+        }
+        const float c_rho = 1.0f - P.inv_tau_rho;
+        const float Qt = qsrc + 0.5f * (qsrc - q_o);
+        float Dm[3], del[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            Dm[a] = rho * u[a] - rho_o * uo[a];
+            del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm[a]);
+        }
+        float sum = 0.0f;
+#pragma unroll
+        for (int n = 1; n < QS; n++) {
+            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
+            const float eD = cx * Dm[0] + cy * Dm[1] + cz * Dm[2];
+            float v = L::ws(n) * (rho * (1.0f + inv_cs2s * eu) + 0.5f * inv_cs2s * eD + Qt);
+            v += cx * del[0] + cy * del[1] + cz * del[2];
+            sum += v;
+            push(S.frho_out, n, v);
+        }
+        push(S.frho_out, 0, (rho + Qt) - sum);   // zeroth moment: rho_e + source
+    }
+
+    // ---- observable contributions
+    ob[0] = Pc[0];
+    ob[1] = Pc[0] * (float)x;
+    ob[2] = Pc[0] * (float)y;
+    ob[3] = Pc[0] * (float)z;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        ob[4 + a] = Pc[0] * u[a];
+        ob[7 + a] = Pc[0] * Fe[a];
+        ob[10 + a] = Fe[a];
+    }
+    ob[13] = Pc[1];
+    ob[14] = Pc[2];
+    ob[15] = rho;
+    if (!isfinite(Pc[0] + Pc[1] + Pc[2] + rho + qsrc))
+        atomicOr(S.flag, 1);
+}
+
+// Block partial sums of the observables: FP32 within a warp, FP64 across warps.
+__device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], double *partials)
+{
     __shared__ double sm[NOBS][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -526,8 +542,79 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
             acc += sm[threadIdx.x][w];
         const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
         const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-        S.obs_partials[threadIdx.x * nblk + blk] = acc;
+        partials[threadIdx.x * nblk + blk] = acc;
     }
+}
+
+// 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
+// the kernel is memory-latency bound and needs the warps.
+template <int D>
+__global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    float ob[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; k++)
+        ob[k] = 0.0f;
+    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
+        const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, i, Lat<D>::Q};
+        collide_site<D>(P, S, x, y, z, i, first, pops, ob);
+    }
+    block_obs_partials(ob, S.obs_partials);
+}
+
+// Same step with the block's population tile staged into shared memory by bulk copies:
+// thread 0 issues one cp.async.bulk per population array (the 128-site row segment of the
+// tile, 512 B), completing on one mbarrier; the copies of the resident blocks stay in
+// flight while other blocks compute, independent of registers. Needs nx % 4 == 0 (16-byte
+// aligned row segments). A wait that never completes sets flag bit 1, waits once more for
+// the copies in flight and leaves the block (its partials zeroed).
+constexpr int STAGE_MAX_POLLS = 1 << 22;
+template <int D>
+__global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first)
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q, NPOP = 4 * Q + L::QS;
+    extern __shared__ __align__(128) float spop[];   // NPOP x BX
+    __shared__ __align__(8) uint64_t bar;
+    const int x0 = blockIdx.x * BX, y = blockIdx.y, z = blockIdx.z;
+    const int tw = min(BX, P.nx - x0);
+    const size_t N = P.N, row = (size_t)P.nx * (y + (size_t)P.ny * z) + x0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)tw * 4u;
+        mbar_arrive_expect_tx(&bar, bytes * NPOP);
+        for (int a = 0; a < Q; a++)
+            bulk_copy_g2s(spop + a * BX, S.g + a * N + row, bytes, &bar);
+        for (int a = 0; a < 3 * Q; a++)
+            bulk_copy_g2s(spop + (Q + a) * BX, S.fphi + a * N + row, bytes, &bar);
+        for (int a = 0; a < L::QS; a++)
+            bulk_copy_g2s(spop + (4 * Q + a) * BX, S.frho + a * N + row, bytes, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
+    float ob[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; k++)
+        ob[k] = 0.0f;
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0)
+            atomicOr(S.flag, 2);
+        mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
+        block_obs_partials(ob, S.obs_partials);
+        return;
+    }
+    const int t = threadIdx.x, x = x0 + t;
+    const size_t i = row + t;
+    if (t < tw && (S.info[i] & 3) == PT_FLUID) {
+        const SmemPops pops{spop, t, Q};
+        collide_site<D>(P, S, x, y, z, i, first, pops, ob);
+    }
+    block_obs_partials(ob, S.obs_partials);
 }
 
 // Fixed-order FP64 sum of the observable partials: block k reduces observable k.

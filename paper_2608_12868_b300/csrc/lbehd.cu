@@ -76,6 +76,7 @@ struct lbehd_handle {
     long long graph_launches = 0, graph_static_kernels[2] = {0, 0}, iter_kernels = 0;
     long long graph_iters0 = 0;    // device iteration counter when graphs took over
     bool graph_launches_started = false;
+    int collide_variant = 0;       // LBEHD_OPT_COLLIDE: 0 auto, 1 global loads, 2 staged
     int mg_nu = 2, mg_coarse = 8;
     int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
     TailLevels tail{};
@@ -409,6 +410,12 @@ int poisson(lbehd_handle *h)
 }
 
 template <int D>
+constexpr size_t staged_smem()
+{
+    return (size_t)(4 * Lat<D>::Q + Lat<D>::QS) * BX * sizeof(float);
+}
+
+template <int D>
 void collide(lbehd_handle *h)
 {
     State S;
@@ -429,8 +436,14 @@ void collide(lbehd_handle *h)
     S.info = h->info;
     S.obs_partials = h->obs_partials;
     S.flag = h->flag;
-    launch(h, LBEHD_KC_COLLIDE, 1,
-           [&] { k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0); });
+    const bool staged = h->collide_variant == 2 || (h->collide_variant == 0 && h->nx % 4 == 0);
+    launch(h, LBEHD_KC_COLLIDE, 1, [&] {
+        if (staged)
+            k_collide_staged<D><<<h->grid, h->block, staged_smem<D>(), h->ls>>>(h->P, S,
+                                                                               h->first ? 1 : 0);
+        else
+            k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0);
+    });
     launch(h, LBEHD_KC_OBS, 1, [&] {
         k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks,
                                                      h->obs);
@@ -1036,6 +1049,27 @@ long long lbehd_launch_count(lbehd_handle *h)
             n += (s0.total_iters - h->graph_iters0) * h->iter_kernels;
     }
     return n;
+}
+
+int lbehd_set_option(lbehd_handle *h, int option, long long value)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (option == LBEHD_OPT_COLLIDE) {
+        if (value < 0 || value > 2)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_COLLIDE takes 0, 1 or 2");
+        if (value == 2 && h->nx % 4)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "the staged collide kernel needs nx % 4 == 0");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->collide_variant = (int)value;
+        for (auto &e : h->gexec)   // captured graphs hold the previous choice
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+        return LBEHD_OK;
+    }
+    return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
 }
 
 int lbehd_get_stats(lbehd_handle *h, lbehd_stats *out)

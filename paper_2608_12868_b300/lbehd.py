@@ -20,6 +20,8 @@ G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS, POT_LO = range(10)
 ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot": POT,
                "u": U, "qsrc": QSRC, "eps": EPS, "pot_lo": POT_LO}
 POISSON_HOST, POISSON_FIXED, POISSON_GRAPH = 0, 1, 2
+OPT_COLLIDE = 1
+COLLIDE_AUTO, COLLIDE_GLOBAL, COLLIDE_STAGED = 0, 1, 2
 
 # Storage convention of LBEHD_G: the library keeps g_n - w_n (lattice weights in the
 # documented velocity order).
@@ -82,7 +84,7 @@ _lib = None
 
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
-           "lbehd_launch_count", "lbehd_get_stats", "lbehd_profile_enable", "lbehd_profile_read",
+           "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable", "lbehd_profile_read",
            "lbehd_last_error", "lbehd_destroy")
 KERNEL_CLASSES = ("fields", "mg", "cg", "collide", "obs")
 
@@ -109,6 +111,7 @@ def load():
     lib.lbehd_launch_count.argtypes = [P]
     lib.lbehd_launch_count.restype = ctypes.c_longlong
     lib.lbehd_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lbehd_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
     lib.lbehd_profile_enable.argtypes = [P, ctypes.c_int]
     lib.lbehd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
@@ -265,6 +268,9 @@ class Simulation:
         ms, cnt = (ctypes.c_double * n)(), (ctypes.c_longlong * n)()
         self._check(self._lib.lbehd_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def set_option(self, option, value):
+        self._check(self._lib.lbehd_set_option(self._h, int(option), int(value)))
 
     def stats(self):
         """Counters since init: steps, Poisson CG iterations, graph replays, kernels."""

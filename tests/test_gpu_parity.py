@@ -95,6 +95,20 @@ def test_small_3d_populations(gpu, oracle_mod, steps):
     compare_fields(sim, orc)
 
 
+@pytest.mark.parametrize("variant", ["global", "staged"])
+def test_collide_kernel_variants(gpu, oracle_mod, variant):
+    """Both fused collide kernels (populations loaded from global memory, or staged into
+    shared memory by bulk copies) against the oracle, on a 3D case with a ragged x tile."""
+    w = W.droplet_3d(136, 16, 16, R=5.0, pillar_h=3, electrodes=[(90, 120, 4, 12)], seed=12)
+    sim, orc = make_pair(gpu, oracle_mod, w)
+    sim.set_option(gpu.OPT_COLLIDE, gpu.COLLIDE_GLOBAL if variant == "global" else gpu.COLLIDE_STAGED)
+    sim.step(30)
+    orc.step(30)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+    assert sim.observe()["status"] == 0
+
+
 def test_small_3d_observables(gpu, oracle_mod):
     w = W.small_3d()
     sim, orc = make_pair(gpu, oracle_mod, w)
