@@ -304,6 +304,8 @@ def run_profile_window(args, local):
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream()
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=lbehd.POISSON_HOST)
+    sim.set_option(lbehd.OPT_COLLIDE, {"auto": lbehd.COLLIDE_AUTO, "global": lbehd.COLLIDE_GLOBAL,
+                                       "staged": lbehd.COLLIDE_STAGED}[args.collide])
     sim.step(args.warmup * args.lb_steps)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()

@@ -215,47 +215,68 @@ struct SmemPops {
 
 // Everything the step does at one fluid site after the moments and the Poisson solve:
 // stencils, forces, the three collisions, push streaming, observable contributions.
+// Written for a low instruction count: 32-bit neighbour offsets computed once, the
+// equilibrium + half-source terms folded into one scalar and one vector per population set
+// (f*_n = w_n (C + e_n . B) + ...), and the non-equilibrium second moments of the momentum
+// populations formed from their raw moments and the closed-form moments of g_eq and R:
+//   Pi(g_eq) = c_s^2 p* I + u u,   Pi(R) = u F + F u.
 template <int D, class Pops>
 __device__ __forceinline__ void collide_site(const Params &P, const State &S, int x, int y, int z,
-                                             size_t i, int first, const Pops &pops,
+                                             int i, int first, const Pops &pops,
                                              float (&ob)[NOBS])
 {
     using L = Lat<D>;
     constexpr int Q = L::Q, QS = L::QS;
-    const size_t N = P.N;
-    const int xp = x + 1 == P.nx ? 0 : x + 1, xm = x == 0 ? P.nx - 1 : x - 1;
-    const int yp = y + 1 == P.ny ? 0 : y + 1, ym = y == 0 ? P.ny - 1 : y - 1;
-    const int zp = z + 1 == P.nz ? 0 : z + 1, zm = z == 0 ? P.nz - 1 : z - 1;
+    const int N = (int)P.N;
+    const int nx = P.nx, nxy = P.nx * P.ny;
+    // periodic neighbour offsets
+    const int oxp = x + 1 == P.nx ? 1 - P.nx : 1, oxm = x == 0 ? P.nx - 1 : -1;
+    const int oyp = (y + 1 == P.ny ? 1 - P.ny : 1) * nx, oym = (y == 0 ? P.ny - 1 : -1) * nx;
+    const int ozp = (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, ozm = (z == 0 ? P.nz - 1 : -1) * nxy;
+    auto off = [&](int n) -> int {
+        return (L::ex(n) > 0 ? oxp : (L::ex(n) < 0 ? oxm : 0)) +
+               (L::ey(n) > 0 ? oyp : (L::ey(n) < 0 ? oym : 0)) +
+               (L::ez(n) > 0 ? ozp : (L::ez(n) < 0 ? ozm : 0));
+    };
+    const float *__restrict__ phi0 = S.phi;
+    const float *__restrict__ phi1 = S.phi + N;
+    const float *__restrict__ phi2 = S.phi + 2 * (size_t)N;
+    const float *__restrict__ pot = S.pot;
+    const float *__restrict__ plo = S.pot_lo;
+    const uint8_t *__restrict__ info = S.info;
 
     // ---- stencils of Phi_i and phi over the flow lattice
-    const float Pc[3] = {S.phi[i], S.phi[N + i], S.phi[2 * N + i]};
+    const float Pc[3] = {phi0[i], phi1[i], phi2[i]};
     const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
-    const float pot_i = S.pot[i], lo_i = S.pot_lo[i];
+    const float pot_i = pot[i], lo_i = plo[i];
     float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float lP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
+    float sP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
     float qsrc = 0.0f;
     unsigned fluid_nb = 1u;   // bit n: x + e_n is fluid (bit 0: the site itself)
 #pragma unroll
     for (int n = 1; n < Q; n++) {
-        const size_t j = nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny);
-        const int pt = S.info[j] & 3;
+        const int j = i + off(n);
+        const int pt = info[j] & 3;
         const float wn = L::w(n);
-        const float ea[3] = {(float)L::ex(n), (float)L::ey(n), (float)L::ez(n)};
-        float Pn[3];
+        const float Pn[3] = {phi0[j], phi1[j], phi2[j]};
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            Pn[c] = S.phi[c * N + j];
-            lP[c] += wn * (Pn[c] - Pc[c]);
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                gP[c][a] += wn * ea[a] * Pn[c];
+            sP[c] += wn * Pn[c];
+            if (L::ex(n))
+                gP[c][0] += (L::ex(n) > 0 ? wn : -wn) * Pn[c];
+            if (L::ey(n))
+                gP[c][1] += (L::ey(n) > 0 ? wn : -wn) * Pn[c];
+            if (L::ez(n))
+                gP[c][2] += (L::ez(n) > 0 ? wn : -wn) * Pn[c];
         }
         // phi(x + e_n) - phi(x) from the compensated pairs (zero-flux solid: mirror)
-        const float dph =
-            pt == PT_NEUMANN ? 0.0f : (S.pot[j] - pot_i) + (S.pot_lo[j] - lo_i);
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            gpot[a] += wn * ea[a] * dph;
+        const float dph = pt == PT_NEUMANN ? 0.0f : (pot[j] - pot_i) + (plo[j] - lo_i);
+        if (L::ex(n))
+            gpot[0] += (L::ex(n) > 0 ? wn : -wn) * dph;
+        if (L::ey(n))
+            gpot[1] += (L::ey(n) > 0 ? wn : -wn) * dph;
+        if (L::ez(n))
+            gpot[2] += (L::ez(n) > 0 ? wn : -wn) * dph;
         if (pt == PT_FLUID) {
             fluid_nb |= 1u << n;
             if (n <= 2 * D) {
@@ -264,10 +285,12 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
             }
         }
     }
-    const float inv_cs2 = 3.0f;
+    constexpr float inv_cs2 = 3.0f;
+    constexpr float wmov = 1.0f - L::w(0);   // sum of the moving weights
+    float lP[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        lP[c] *= 2.0f * inv_cs2;
+        lP[c] = 2.0f * inv_cs2 * (sP[c] - wmov * Pc[c]);
 #pragma unroll
         for (int a = 0; a < 3; a++)
             gP[c][a] *= inv_cs2;
@@ -317,25 +340,44 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
             }
             sumsq += Pc[c] * Pc[c];
         }
+        const float inv_sumsq = 1.0f / sumsq;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const float r = Pc[c] * Pc[c] / sumsq;
+            const float r = Pc[c] * Pc[c] * inv_sumsq;
 #pragma unroll
             for (int a = 0; a < 3; a++)
                 FPhi[c][a] = ln[c][a] - r * J[a];
         }
     }
 
-    // ---- momentum moments, velocity, previous-step values
+    // ---- momentum moments (shifted populations gs = g - w), velocity
     float gs[Q];
-    float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f};
+    float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f}, m2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int n = 0; n < Q; n++) {
-        gs[n] = pops.g(n);
-        dp += gs[n];
-        jm[0] += L::ex(n) * gs[n];
-        jm[1] += L::ey(n) * gs[n];
-        jm[2] += L::ez(n) * gs[n];
+        const float v = pops.g(n);
+        gs[n] = v;
+        dp += v;
+        constexpr int dummy = 0;
+        (void)dummy;
+        if (L::ex(n))
+            jm[0] += L::ex(n) > 0 ? v : -v;
+        if (L::ey(n))
+            jm[1] += L::ey(n) > 0 ? v : -v;
+        if (L::ez(n))
+            jm[2] += L::ez(n) > 0 ? v : -v;
+        if (L::ex(n))
+            m2[0] += v;   // sum ex^2 gs
+        if (L::ey(n))
+            m2[1] += v;
+        if (L::ez(n))
+            m2[2] += v;
+        if (L::ex(n) && L::ey(n))
+            m2[3] += L::ex(n) * L::ey(n) > 0 ? v : -v;
+        if (L::ex(n) && L::ez(n))
+            m2[4] += L::ex(n) * L::ez(n) > 0 ? v : -v;
+        if (L::ey(n) && L::ez(n))
+            m2[5] += L::ey(n) * L::ez(n) > 0 ? v : -v;
     }
     float u[3];
 #pragma unroll
@@ -353,22 +395,23 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     } else {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            uo[a] = S.u[a * N + i];
-            Po[a] = S.phi_prev[a * N + i];
+            uo[a] = S.u[a * (size_t)N + i];
+            Po[a] = S.phi_prev[a * (size_t)N + i];
         }
         rho_o = S.rho_prev[i];
         q_o = S.q[i];
     }
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        S.u[a * N + i] = u[a];
+        S.u[a * (size_t)N + i] = u[a];
     S.q[i] = qsrc;
 
+    // push f*_n to x + e_n, or into the opposite slot at x when x + e_n is solid
     auto push = [&](float *out, int n, float v) {
-        if ((fluid_nb >> n) & 1u)
-            out[n * N + nbr_index<L>(n, x, y, z, xp, xm, yp, ym, zp, zm, P.nx, P.ny)] = v;
-        else
-            out[opposite(n) * N + i] = v;
+        const bool fl = (fluid_nb >> n) & 1u;
+        const int slot = fl ? n : opposite(n);
+        const int site = fl ? i + off(n) : i;
+        out[(size_t)slot * N + site] = v;
     };
 
     // ---- momentum collision (incompressible equilibrium, Guo forcing, MRT)
@@ -378,33 +421,30 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
         const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
         const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
         const float c_b = 1.0f - P.s_bulk;
-        float base[Q];
-        float d1 = 0.f, d2 = 0.f, dxy = 0.f, dxz = 0.f, dyz = 0.f, dT = 0.f;
-#pragma unroll
-        for (int n = 0; n < Q; n++) {
-            const float cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-            const float eF = cx * F[0] + cy * F[1] + cz * F[2];
-            const float wn = L::w(n);
-            const float geq = wn * (dp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-            const float hR = wn * (1.5f * (eF - uF) + 4.5f * eu * eF);   // R_n / 2
-            base[n] = geq + hR;
-            const float A = gs[n] - geq + hR;
-            d1 += (cx * cx - cy * cy) * A;
-            d2 += (cx * cx - cz * cz) * A;
-            dxy += cx * cy * A;
-            dxz += cx * cz * A;
-            dyz += cy * cz * A;
-            dT += (cx * cx + cy * cy + cz * cz) * A;
-        }
-        // moving populations first; the rest population takes the exact remainder of
-        // the conserved zeroth moment (the FP32 weights do not sum to 1 exactly, which
-        // would otherwise create mass at ~1e-8 per step)
+        // non-equilibrium moments of g - g_eq + R/2 (deviatoric / off-diagonal / trace)
+        const float uFd[3] = {u[0] * F[0], u[1] * F[1], u[2] * F[2]};
+        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) - (uFd[0] - uFd[1]);
+        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) - (uFd[0] - uFd[2]);
+        const float dxy = m2[3] - u[0] * u[1] - 0.5f * (u[0] * F[1] + u[1] * F[0]);
+        const float dxz = m2[4] - u[0] * u[2] - 0.5f * (u[0] * F[2] + u[2] * F[0]);
+        const float dyz = m2[5] - u[1] * u[2] - 0.5f * (u[1] * F[2] + u[2] * F[1]);
+        const float dT = (m2[0] + m2[1] + m2[2]) - (float)D * (1.0f / 3.0f) * dp - uu - uF;
+        // w_n [C0 + e.V + (e.u)(4.5 e.u + 4.5 e.F)] = g_eq,n - w_n + R_n / 2
+        const float C0 = dp - 1.5f * uu - 1.5f * uF;
+        const float V[3] = {3.0f * u[0] + 1.5f * F[0], 3.0f * u[1] + 1.5f * F[1],
+                            3.0f * u[2] + 1.5f * F[2]};
         float sum = 0.0f;
 #pragma unroll
         for (int n = 1; n < Q; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
             const int e2 = cx * cx + cy * cy + cz * cz;
+            const float eu = (cx ? (cx > 0 ? u[0] : -u[0]) : 0.f) + (cy ? (cy > 0 ? u[1] : -u[1]) : 0.f) +
+                             (cz ? (cz > 0 ? u[2] : -u[2]) : 0.f);
+            const float eF = (cx ? (cx > 0 ? F[0] : -F[0]) : 0.f) + (cy ? (cy > 0 ? F[1] : -F[1]) : 0.f) +
+                             (cz ? (cz > 0 ? F[2] : -F[2]) : 0.f);
+            const float eV = (cx ? (cx > 0 ? V[0] : -V[0]) : 0.f) + (cy ? (cy > 0 ? V[1] : -V[1]) : 0.f) +
+                             (cz ? (cz > 0 ? V[2] : -V[2]) : 0.f);
+            float v = L::w(n) * (C0 + eV + eu * (4.5f * eu + 4.5f * eF));
             float corr = 0.0f, corrT = 0.0f;
             if (D == 3) {
                 if (e2 == 1) {
@@ -412,97 +452,105 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
                               : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
                                     : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
                     corrT = dT * (1.0f / 6.0f);
-                } else if (e2 == 2) {
-                    corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
                 } else {
-                    corrT = -dT;
+                    corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
                 }
             } else {
                 if (e2 == 1) {
                     corr = cx ? 0.25f * d1 : -0.25f * d1;
                     corrT = 0.25f * dT;
-                } else if (e2 == 2) {
-                    corr = 0.25f * cx * cy * dxy;
                 } else {
-                    corrT = -dT;
+                    corr = 0.25f * cx * cy * dxy;
                 }
             }
-            const float v = base[n] + c_nu * corr + c_b * corrT;
+            v += c_nu * corr + c_b * corrT;
             sum += v;
             push(S.g_out, n, v);
         }
+        // rest population: exact remainder of the conserved zeroth moment (the FP32
+        // weights do not sum to 1 exactly, which would otherwise create mass every step)
         push(S.g_out, 0, dp - sum);
         if (!isfinite(dp + u[0] + u[1] + u[2]))
             atomicOr(S.flag, 1);
     }
 
-    // ---- phase-field collisions (Eqs. 15-17), one component at a time
+    // ---- phase-field collisions (Eqs. 15-17)
     const float c_phi = 1.0f - P.inv_tau_phi;
-#pragma unroll 1
+#pragma unroll
     for (int c = 0; c < 3; c++) {
-        float f[Q];
         float jf[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int n = 0; n < Q; n++) {
-            f[n] = pops.phi(c, n);
-            jf[0] += L::ex(n) * f[n];
-            jf[1] += L::ey(n) * f[n];
-            jf[2] += L::ez(n) * f[n];
+        for (int n = 1; n < Q; n++) {
+            const float v = pops.phi(c, n);
+            if (L::ex(n))
+                jf[0] += L::ex(n) > 0 ? v : -v;
+            if (L::ey(n))
+                jf[1] += L::ey(n) > 0 ? v : -v;
+            if (L::ez(n))
+                jf[2] += L::ez(n) > 0 ? v : -v;
         }
         const float Pp = Pc[c];
-        float A[3], del[3];
+        float B[3], del[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            A[a] = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
-            del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A[a]);
+            const float A = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
+            del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A);
+            B[a] = inv_cs2 * Pp * u[a] + 0.5f * inv_cs2 * A;   // w_n (P + e.B) = f_eq + C/2
         }
+        float *out = S.fphi_out + (size_t)c * Q * N;
         float sum = 0.0f;
 #pragma unroll
         for (int n = 1; n < Q; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-            const float eA = cx * A[0] + cy * A[1] + cz * A[2];
-            float v = L::w(n) * (Pp * (1.0f + inv_cs2 * eu) + 0.5f * inv_cs2 * eA);
+            const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
+                             (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
+            float v = L::w(n) * (Pp + eB);
             if (cx * cx + cy * cy + cz * cz == 1)
-                v += cx * del[0] + cy * del[1] + cz * del[2];
+                v += (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
+                     (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
             sum += v;
-            push(S.fphi_out + (size_t)c * Q * N, n, v);
+            push(out, n, v);
         }
-        push(S.fphi_out + (size_t)c * Q * N, 0, Pp - sum);   // Phi is conserved
+        push(out, 0, Pp - sum);   // Phi is conserved
     }
 
     // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
     {
         constexpr float inv_cs2s = 1.0f / L::cs2s;
         float jr[3] = {0.f, 0.f, 0.f};
-        float fr[QS];
 #pragma unroll
-        for (int n = 0; n < QS; n++) {
-            fr[n] = pops.rho(n);
-            jr[0] += L::ex(n) * fr[n];
-            jr[1] += L::ey(n) * fr[n];
-            jr[2] += L::ez(n) * fr[n];
+        for (int n = 1; n < QS; n++) {
+            const float v = pops.rho(n);
+            if (L::ex(n))
+                jr[0] += L::ex(n) > 0 ? v : -v;
+            if (L::ey(n))
+                jr[1] += L::ey(n) > 0 ? v : -v;
+            if (L::ez(n))
+                jr[2] += L::ez(n) > 0 ? v : -v;
         }
         const float c_rho = 1.0f - P.inv_tau_rho;
         const float Qt = qsrc + 0.5f * (qsrc - q_o);
-        float Dm[3], del[3];
+        float B[3], del[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            Dm[a] = rho * u[a] - rho_o * uo[a];
-            del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm[a]);
+            const float Dm = rho * u[a] - rho_o * uo[a];
+            del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm);
+            B[a] = inv_cs2s * (rho * u[a] + 0.5f * Dm);
         }
+        const float C0 = rho + Qt;
         float sum = 0.0f;
 #pragma unroll
         for (int n = 1; n < QS; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const float eu = cx * u[0] + cy * u[1] + cz * u[2];
-            const float eD = cx * Dm[0] + cy * Dm[1] + cz * Dm[2];
-            float v = L::ws(n) * (rho * (1.0f + inv_cs2s * eu) + 0.5f * inv_cs2s * eD + Qt);
-            v += cx * del[0] + cy * del[1] + cz * del[2];
+            const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
+                             (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
+            const float ed = (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
+                             (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
+            const float v = L::ws(n) * (C0 + eB) + ed;
             sum += v;
             push(S.frho_out, n, v);
         }
-        push(S.frho_out, 0, (rho + Qt) - sum);   // zeroth moment: rho_e + source
+        push(S.frho_out, 0, C0 - sum);   // zeroth moment: rho_e + source
     }
 
     // ---- observable contributions
@@ -556,9 +604,9 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
 #pragma unroll
     for (int k = 0; k < NOBS; k++)
         ob[k] = 0.0f;
-    const size_t i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    const int i = x + P.nx * (y + P.ny * z);
     if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
-        const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, i, Lat<D>::Q};
+        const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, (size_t)i, Lat<D>::Q};
         collide_site<D>(P, S, x, y, z, i, first, pops, ob);
     }
     block_obs_partials(ob, S.obs_partials);
@@ -609,7 +657,7 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int
         return;
     }
     const int t = threadIdx.x, x = x0 + t;
-    const size_t i = row + t;
+    const int i = (int)row + t;
     if (t < tw && (S.info[i] & 3) == PT_FLUID) {
         const SmemPops pops{spop, t, Q};
         collide_site<D>(P, S, x, y, z, i, first, pops, ob);

@@ -879,6 +879,9 @@ int lbehd_init(const lbehd_config *cfg, lbehd_handle **out)
                     "periodic extents must be even (red-black ordering of the Poisson smoother)");
     if (cfg->ny > 65535 || cfg->nz > 65535)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "ny and nz must be <= 65535");
+    if ((long long)cfg->nx * cfg->ny * cfg->nz * 19 >= (1LL << 31))
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG,
+                    "lattice too large: 32-bit site offsets need 19 * N < 2^31");
     if (!cfg->solid || !cfg->phi_init)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "solid and phi_init are required");
     if (cfg->n_electrodes < 0 || cfg->n_electrodes > LBEHD_MAX_ELECTRODES ||
