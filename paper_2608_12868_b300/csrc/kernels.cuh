@@ -28,6 +28,8 @@
 // and velocity deviations.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "lattice.cuh"
@@ -206,11 +208,67 @@ struct GlobalPops {
 };
 
 struct SmemPops {
-    const float *s;   // [population array][tile x], row stride TW
+    const float *s;   // [population array][tile site], stride BX = TX * TY
     int t, Q;
     __device__ __forceinline__ float g(int n) const { return s[n * BX + t]; }
     __device__ __forceinline__ float phi(int c, int n) const { return s[(Q + c * Q + n) * BX + t]; }
     __device__ __forceinline__ float rho(int n) const { return s[(4 * Q + n) * BX + t]; }
+};
+
+// Stencil-field sources for collide_site: Phi_1..3, the compensated potential and the node
+// class at the site and at its lattice neighbours, from global memory or from a halo tile
+// in shared memory.
+struct GlobalStencil {
+    const float *__restrict__ p0, *__restrict__ p1, *__restrict__ p2, *__restrict__ pot,
+        *__restrict__ plo;
+    const uint8_t *__restrict__ info;
+    int i;
+    int oxp, oxm, oyp, oym, ozp, ozm;
+    template <class L>
+    __device__ __forceinline__ int idx(int n) const
+    {
+        return i + (L::ex(n) > 0 ? oxp : (L::ex(n) < 0 ? oxm : 0)) +
+               (L::ey(n) > 0 ? oyp : (L::ey(n) < 0 ? oym : 0)) +
+               (L::ez(n) > 0 ? ozp : (L::ez(n) < 0 ? ozm : 0));
+    }
+    template <class L>
+    __device__ __forceinline__ void at(int n, float (&P)[3], float &ph, float &lo, int &pt) const
+    {
+        const int j = n ? idx<L>(n) : i;
+        P[0] = p0[j];
+        P[1] = p1[j];
+        P[2] = p2[j];
+        ph = pot[j];
+        lo = plo[j];
+        pt = info[j] & 3;
+    }
+};
+
+// Halo tile layout: HX x HY x HZ sites, fields [Phi_1, Phi_2, Phi_3, pot, pot_lo] then info.
+constexpr int TX = 32, TY = 4;
+template <int D>
+struct Halo {
+    static constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? 3 : 1;
+    static constexpr int N = HX * HY * HZ;
+};
+
+template <int D>
+struct SmemStencil {
+    const float *f;        // 5 * Halo<D>::N floats
+    const uint8_t *info;   // Halo<D>::N bytes
+    int h;                 // halo index of the site
+    template <class L>
+    __device__ __forceinline__ void at(int n, float (&P)[3], float &ph, float &lo, int &pt) const
+    {
+        constexpr int HX = Halo<D>::HX, HXY = Halo<D>::HX * Halo<D>::HY, HN = Halo<D>::N;
+        const int j = h + L::ex(n) + HX * L::ey(n) + HXY * L::ez(n);
+        P[0] = f[j];
+        P[1] = f[HN + j];
+        P[2] = f[2 * HN + j];
+        ph = f[3 * HN + j];
+        lo = f[4 * HN + j];
+        pt = info[j] & 3;
+    }
 };
 
 // Everything the step does at one fluid site after the moments and the Poisson solve:
@@ -220,10 +278,10 @@ struct SmemPops {
 // (f*_n = w_n (C + e_n . B) + ...), and the non-equilibrium second moments of the momentum
 // populations formed from their raw moments and the closed-form moments of g_eq and R:
 //   Pi(g_eq) = c_s^2 p* I + u u,   Pi(R) = u F + F u.
-template <int D, class Pops>
+template <int D, class Pops, class Stencil>
 __device__ __forceinline__ void collide_site(const Params &P, const State &S, int x, int y, int z,
                                              int i, int first, const Pops &pops,
-                                             float (&ob)[NOBS])
+                                             const Stencil &st, float (&ob)[NOBS])
 {
     using L = Lat<D>;
     constexpr int Q = L::Q, QS = L::QS;
@@ -238,27 +296,21 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
                (L::ey(n) > 0 ? oyp : (L::ey(n) < 0 ? oym : 0)) +
                (L::ez(n) > 0 ? ozp : (L::ez(n) < 0 ? ozm : 0));
     };
-    const float *__restrict__ phi0 = S.phi;
-    const float *__restrict__ phi1 = S.phi + N;
-    const float *__restrict__ phi2 = S.phi + 2 * (size_t)N;
-    const float *__restrict__ pot = S.pot;
-    const float *__restrict__ plo = S.pot_lo;
-    const uint8_t *__restrict__ info = S.info;
-
     // ---- stencils of Phi_i and phi over the flow lattice
-    const float Pc[3] = {phi0[i], phi1[i], phi2[i]};
+    float Pc[3], pot_i, lo_i;
+    int pt_i;
+    st.template at<L>(0, Pc, pot_i, lo_i, pt_i);
     const float sig_i = Pc[0] * P.sig[0] + Pc[1] * P.sig[1] + Pc[2] * P.sig[2];
-    const float pot_i = pot[i], lo_i = plo[i];
     float gP[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float sP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
     float qsrc = 0.0f;
     unsigned fluid_nb = 1u;   // bit n: x + e_n is fluid (bit 0: the site itself)
 #pragma unroll
     for (int n = 1; n < Q; n++) {
-        const int j = i + off(n);
-        const int pt = info[j] & 3;
+        float Pn[3], potj, loj;
+        int pt;
+        st.template at<L>(n, Pn, potj, loj, pt);
         const float wn = L::w(n);
-        const float Pn[3] = {phi0[j], phi1[j], phi2[j]};
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             sP[c] += wn * Pn[c];
@@ -270,7 +322,7 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
                 gP[c][2] += (L::ez(n) > 0 ? wn : -wn) * Pn[c];
         }
         // phi(x + e_n) - phi(x) from the compensated pairs (zero-flux solid: mirror)
-        const float dph = pt == PT_NEUMANN ? 0.0f : (pot[j] - pot_i) + (plo[j] - lo_i);
+        const float dph = pt == PT_NEUMANN ? 0.0f : (potj - pot_i) + (loj - lo_i);
         if (L::ex(n))
             gpot[0] += (L::ex(n) > 0 ? wn : -wn) * dph;
         if (L::ey(n))
@@ -607,60 +659,110 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
     const int i = x + P.nx * (y + P.ny * z);
     if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
         const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, (size_t)i, Lat<D>::Q};
-        collide_site<D>(P, S, x, y, z, i, first, pops, ob);
+        const int nx = P.nx, nxy = P.nx * P.ny;
+        const GlobalStencil st{S.phi, S.phi + P.N, S.phi + 2 * P.N, S.pot, S.pot_lo, S.info, i,
+                               x + 1 == P.nx ? 1 - P.nx : 1, x == 0 ? P.nx - 1 : -1,
+                               (y + 1 == P.ny ? 1 - P.ny : 1) * nx, (y == 0 ? P.ny - 1 : -1) * nx,
+                               (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, (z == 0 ? P.nz - 1 : -1) * nxy};
+        collide_site<D>(P, S, x, y, z, i, first, pops, st, ob);
     }
     block_obs_partials(ob, S.obs_partials);
 }
 
-// Same step with the block's population tile staged into shared memory by bulk copies:
-// thread 0 issues one cp.async.bulk per population array (the 128-site row segment of the
-// tile, 512 B), completing on one mbarrier; the copies of the resident blocks stay in
-// flight while other blocks compute, independent of registers. Needs nx % 4 == 0 (16-byte
-// aligned row segments). A wait that never completes sets flag bit 1, waits once more for
-// the copies in flight and leaves the block (its partials zeroed).
+// Tensor maps of the three population sets of one buffer, each a 4D tensor
+// (x, y, z, population array), box TX x TY x 1 x (all arrays of the set).
+struct PopMaps {
+    CUtensorMap g, fphi, frho;
+};
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <int D>
+constexpr int staged_pop_floats()
+{
+    return (4 * Lat<D>::Q + Lat<D>::QS) * TX * TY;
+}
+
+template <int D>
+constexpr size_t staged_smem_bytes()
+{
+    return (size_t)staged_pop_floats<D>() * 4 + (size_t)Halo<D>::N * (5 * 4 + 1);
+}
+
+// The step on a TX x TY tile with everything it reads staged in shared memory: thread 0
+// issues three 4D TMA tensor copies (all population arrays of the tile, completing on one
+// mbarrier) while the block loads the stencil fields of the tile and its one-site halo
+// (periodic wrap) cooperatively. Needs nx % 4 == 0 (16-byte row strides for the tensor
+// maps). A barrier wait that never completes sets flag bit 1, waits once more for the copies
+// in flight and leaves the block (its partials zeroed).
 constexpr int STAGE_MAX_POLLS = 1 << 22;
 template <int D>
-__global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first)
+__global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first,
+                                                          const __grid_constant__ PopMaps maps)
 {
     using L = Lat<D>;
-    constexpr int Q = L::Q, NPOP = 4 * Q + L::QS;
-    extern __shared__ __align__(128) float spop[];   // NPOP x BX
+    constexpr int Q = L::Q, HN = Halo<D>::N, HX = Halo<D>::HX, HY = Halo<D>::HY;
+    extern __shared__ __align__(128) float spop[];   // populations, then halo fields
+    float *shal = spop + staged_pop_floats<D>();
+    uint8_t *sinf = reinterpret_cast<uint8_t *>(shal + 5 * HN);
     __shared__ __align__(8) uint64_t bar;
-    const int x0 = blockIdx.x * BX, y = blockIdx.y, z = blockIdx.z;
-    const int tw = min(BX, P.nx - x0);
-    const size_t N = P.N, row = (size_t)P.nx * (y + (size_t)P.ny * z) + x0;
-    if (threadIdx.x == 0) {
+    const int t = threadIdx.x, tx = t & (TX - 1), ty = t / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z = blockIdx.z;
+    if (t == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)tw * 4u;
-        mbar_arrive_expect_tx(&bar, bytes * NPOP);
-        for (int a = 0; a < Q; a++)
-            bulk_copy_g2s(spop + a * BX, S.g + a * N + row, bytes, &bar);
-        for (int a = 0; a < 3 * Q; a++)
-            bulk_copy_g2s(spop + (Q + a) * BX, S.fphi + a * N + row, bytes, &bar);
-        for (int a = 0; a < L::QS; a++)
-            bulk_copy_g2s(spop + (4 * Q + a) * BX, S.frho + a * N + row, bytes, &bar);
+    if (t == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)staged_pop_floats<D>() * 4u);
+        tma_load_4d(spop, &maps.g, x0, y0, z, 0, &bar);
+        tma_load_4d(spop + Q * TX * TY, &maps.fphi, x0, y0, z, 0, &bar);
+        tma_load_4d(spop + 4 * Q * TX * TY, &maps.frho, x0, y0, z, 0, &bar);
     }
+    // stencil fields of the tile and its halo, periodic in every direction
+    const size_t N = P.N;
+    for (int e = t; e < HN; e += BX) {
+        const int hx = e % HX, hy = (e / HX) % HY, hz = e / (HX * HY);
+        int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = D == 3 ? z - 1 + hz : z;
+        gx += gx < 0 ? P.nx : (gx >= P.nx ? -P.nx : 0);
+        gy += gy < 0 ? P.ny : (gy >= P.ny ? -P.ny : 0);
+        gz += gz < 0 ? P.nz : (gz >= P.nz ? -P.nz : 0);
+        const size_t g = gx + (size_t)P.nx * (gy + (size_t)P.ny * gz);
+        shal[e] = S.phi[g];
+        shal[HN + e] = S.phi[N + g];
+        shal[2 * HN + e] = S.phi[2 * N + g];
+        shal[3 * HN + e] = S.pot[g];
+        shal[4 * HN + e] = S.pot_lo[g];
+        sinf[e] = S.info[g];
+    }
+    __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
     float ob[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; k++)
         ob[k] = 0.0f;
     if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0)
+        if (t == 0)
             atomicOr(S.flag, 2);
         mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
         block_obs_partials(ob, S.obs_partials);
         return;
     }
-    const int t = threadIdx.x, x = x0 + t;
-    const int i = (int)row + t;
-    if (t < tw && (S.info[i] & 3) == PT_FLUID) {
+    const int x = x0 + tx, y = y0 + ty;
+    const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
+    if (x < P.nx && y < P.ny && (sinf[h] & 3) == PT_FLUID) {
+        const int i = x + P.nx * (y + P.ny * z);
         const SmemPops pops{spop, t, Q};
-        collide_site<D>(P, S, x, y, z, i, first, pops, ob);
+        const SmemStencil<D> st{shal, sinf, h};
+        collide_site<D>(P, S, x, y, z, i, first, pops, st, ob);
     }
     block_obs_partials(ob, S.obs_partials);
 }

@@ -77,6 +77,10 @@ struct lbehd_handle {
     long long graph_iters0 = 0;    // device iteration counter when graphs took over
     bool graph_launches_started = false;
     int collide_variant = 0;       // LBEHD_OPT_COLLIDE: 0 auto, 1 global loads, 2 staged
+    bool maps_ok = false;          // tensor maps of both population buffers encoded
+    PopMaps maps[2];
+    dim3 grid_tile;                // TX x TY tiles of the staged collide kernel
+    size_t nblocks_tile = 0;
     int mg_nu = 2, mg_coarse = 8;
     int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
     TailLevels tail{};
@@ -410,12 +414,6 @@ int poisson(lbehd_handle *h)
 }
 
 template <int D>
-constexpr size_t staged_smem()
-{
-    return (size_t)(4 * Lat<D>::Q + Lat<D>::QS) * BX * sizeof(float);
-}
-
-template <int D>
 void collide(lbehd_handle *h)
 {
     State S;
@@ -436,17 +434,17 @@ void collide(lbehd_handle *h)
     S.info = h->info;
     S.obs_partials = h->obs_partials;
     S.flag = h->flag;
-    const bool staged = h->collide_variant == 2 || (h->collide_variant == 0 && h->nx % 4 == 0);
+    const bool staged = h->maps_ok && h->collide_variant != 1;
+    const size_t nblk = staged ? h->nblocks_tile : h->nblocks;
     launch(h, LBEHD_KC_COLLIDE, 1, [&] {
         if (staged)
-            k_collide_staged<D><<<h->grid, h->block, staged_smem<D>(), h->ls>>>(h->P, S,
-                                                                               h->first ? 1 : 0);
+            k_collide_staged<D><<<h->grid_tile, h->block, staged_smem_bytes<D>(), h->ls>>>(
+                h->P, S, h->first ? 1 : 0, h->maps[h->cur]);
         else
             k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0);
     });
     launch(h, LBEHD_KC_OBS, 1, [&] {
-        k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)h->nblocks,
-                                                     h->obs);
+        k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)nblk, h->obs);
     });
 }
 
@@ -631,6 +629,43 @@ int set_params(lbehd_handle *h)
     return LBEHD_OK;
 }
 
+// Tensor maps (x, y, z, array) of the population sets of both buffers, box TX x TY x 1 x
+// (all arrays), for the staged collide kernel. cuTensorMapEncodeTiled comes from the driver
+// through the runtime's entry-point query (no link-time dependency on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_pop_maps(lbehd_handle *h)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return fail(h, LBEHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    EncodeTiledFn encode = (EncodeTiledFn)fn;
+    const cuuint64_t N = h->N;
+    auto one = [&](CUtensorMap *m, float *base, int narr) -> bool {
+        const cuuint64_t dims[4] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz,
+                                    (cuuint64_t)narr};
+        const cuuint64_t strides[3] = {(cuuint64_t)h->nx * 4, (cuuint64_t)h->nx * h->ny * 4, N * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1u, (cuuint32_t)narr};
+        const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
+    };
+    for (int b = 0; b < 2; b++)
+        if (!one(&h->maps[b].g, h->g[b], h->Q) || !one(&h->maps[b].fphi, h->fphi[b], 3 * h->Q) ||
+            !one(&h->maps[b].frho, h->frho[b], h->QS))
+            return fail(h, LBEHD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    h->maps_ok = true;
+    return LBEHD_OK;
+}
+
 template <int D>
 int init_impl(lbehd_handle *h)
 {
@@ -685,7 +720,10 @@ int init_impl(lbehd_handle *h)
     h->block = dim3(BX, 1, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, h->ny, h->nz);
     h->nblocks = (size_t)h->grid.x * h->grid.y * h->grid.z;
-    h->obs_partials = (double *)dev_alloc(h, NOBS * h->nblocks * sizeof(double));
+    h->grid_tile = dim3((h->nx + TX - 1) / TX, (h->ny + TY - 1) / TY, h->nz);
+    h->nblocks_tile = (size_t)h->grid_tile.x * h->grid_tile.y * h->grid_tile.z;
+    h->obs_partials =
+        (double *)dev_alloc(h, NOBS * std::max(h->nblocks, h->nblocks_tile) * sizeof(double));
     h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
     h->flag = (int *)dev_alloc(h, sizeof(int));
     if (!h->u || !h->q || !h->pot || !h->pot_lo || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
@@ -768,6 +806,13 @@ int init_impl(lbehd_handle *h)
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
     CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    if (h->nx % 4 == 0) {
+        int rc = encode_pop_maps(h);
+        if (rc)
+            return rc;
+        CK(h, cudaFuncSetAttribute(k_collide_staged<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem_bytes<D>()));
+    }
     {
         CgScalars s0{};
         s0.tol2 = c.poisson_tol * c.poisson_tol;
@@ -1061,7 +1106,7 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
     if (option == LBEHD_OPT_COLLIDE) {
         if (value < 0 || value > 2)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_COLLIDE takes 0, 1 or 2");
-        if (value == 2 && h->nx % 4)
+        if (value == 2 && !h->maps_ok)
             return fail(h, LBEHD_ERR_INVALID_ARG, "the staged collide kernel needs nx % 4 == 0");
         CK(h, cudaStreamSynchronize(h->stream));
         h->collide_variant = (int)value;
