@@ -271,6 +271,26 @@ struct SmemStencil {
     }
 };
 
+// The site's own scalar fields read by collide_site (charge now and before, the previous
+// velocity, Phi and conduction source), loaded early so their latency overlaps other work.
+struct SitePre {
+    float rho, rho_o, q_o, uo[3], Po[3];
+};
+
+__device__ __forceinline__ SitePre load_site_pre(const State &S, size_t N, int i)
+{
+    SitePre p;
+    p.rho = S.rho[i];
+    p.rho_o = S.rho_prev[i];
+    p.q_o = S.q[i];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        p.uo[a] = S.u[a * N + i];
+        p.Po[a] = S.phi_prev[a * N + i];
+    }
+    return p;
+}
+
 // Everything the step does at one fluid site after the moments and the Poisson solve:
 // stencils, forces, the three collisions, push streaming, observable contributions.
 // Written for a low instruction count: 32-bit neighbour offsets computed once, the
@@ -281,7 +301,8 @@ struct SmemStencil {
 template <int D, class Pops, class Stencil>
 __device__ __forceinline__ void collide_site(const Params &P, const State &S, int x, int y, int z,
                                              int i, int first, const Pops &pops,
-                                             const Stencil &st, float (&ob)[NOBS])
+                                             const Stencil &st, const SitePre &pre,
+                                             float (&ob)[NOBS])
 {
     using L = Lat<D>;
     constexpr int Q = L::Q, QS = L::QS;
@@ -367,7 +388,7 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
         E[a] = -inv_cs2 * gpot[a];
         E2 += E[a] * E[a];
     }
-    const float rho = S.rho[i];
+    const float rho = pre.rho;
     float Fe[3], F[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -447,11 +468,11 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     } else {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            uo[a] = S.u[a * (size_t)N + i];
-            Po[a] = S.phi_prev[a * (size_t)N + i];
+            uo[a] = pre.uo[a];
+            Po[a] = pre.Po[a];
         }
-        rho_o = S.rho_prev[i];
-        q_o = S.q[i];
+        rho_o = pre.rho_o;
+        q_o = pre.q_o;
     }
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -664,7 +685,8 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
                                x + 1 == P.nx ? 1 - P.nx : 1, x == 0 ? P.nx - 1 : -1,
                                (y + 1 == P.ny ? 1 - P.ny : 1) * nx, (y == 0 ? P.ny - 1 : -1) * nx,
                                (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, (z == 0 ? P.nz - 1 : -1) * nxy};
-        collide_site<D>(P, S, x, y, z, i, first, pops, st, ob);
+        const SitePre pre = load_site_pre(S, (size_t)P.N, i);
+        collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
     block_obs_partials(ob, S.obs_partials);
 }
@@ -727,21 +749,43 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int
         tma_load_4d(spop + Q * TX * TY, &maps.fphi, x0, y0, z, 0, &bar);
         tma_load_4d(spop + 4 * Q * TX * TY, &maps.frho, x0, y0, z, 0, &bar);
     }
-    // stencil fields of the tile and its halo, periodic in every direction
     const size_t N = P.N;
-    for (int e = t; e < HN; e += BX) {
-        const int hx = e % HX, hy = (e / HX) % HY, hz = e / (HX * HY);
-        int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = D == 3 ? z - 1 + hz : z;
-        gx += gx < 0 ? P.nx : (gx >= P.nx ? -P.nx : 0);
-        gy += gy < 0 ? P.ny : (gy >= P.ny ? -P.ny : 0);
-        gz += gz < 0 ? P.nz : (gz >= P.nz ? -P.nz : 0);
-        const size_t g = gx + (size_t)P.nx * (gy + (size_t)P.ny * gz);
-        shal[e] = S.phi[g];
-        shal[HN + e] = S.phi[N + g];
-        shal[2 * HN + e] = S.phi[2 * N + g];
-        shal[3 * HN + e] = S.pot[g];
-        shal[4 * HN + e] = S.pot_lo[g];
-        sinf[e] = S.info[g];
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < P.nx && y < P.ny;
+    const int i = active ? x + P.nx * (y + P.ny * z) : 0;
+    const SitePre pre = load_site_pre(S, N, i);   // issued now, used after the staging
+    // stencil fields of the tile and its halo, periodic in every direction: every load of
+    // this thread is issued before the first shared-memory store
+    constexpr int HIT = (HN + BX - 1) / BX;
+    float hv[HIT][5];
+    uint8_t hinf[HIT];
+#pragma unroll
+    for (int k = 0; k < HIT; k++) {
+        const int e = t + k * BX;
+        if (e < HN) {
+            const int hx = e % HX, hy = (e / HX) % HY, hz = e / (HX * HY);
+            int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = D == 3 ? z - 1 + hz : z;
+            gx += gx < 0 ? P.nx : (gx >= P.nx ? -P.nx : 0);
+            gy += gy < 0 ? P.ny : (gy >= P.ny ? -P.ny : 0);
+            gz += gz < 0 ? P.nz : (gz >= P.nz ? -P.nz : 0);
+            const size_t g = gx + (size_t)P.nx * (gy + (size_t)P.ny * gz);
+            hv[k][0] = S.phi[g];
+            hv[k][1] = S.phi[N + g];
+            hv[k][2] = S.phi[2 * N + g];
+            hv[k][3] = S.pot[g];
+            hv[k][4] = S.pot_lo[g];
+            hinf[k] = S.info[g];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < HIT; k++) {
+        const int e = t + k * BX;
+        if (e < HN) {
+#pragma unroll
+            for (int f = 0; f < 5; f++)
+                shal[f * HN + e] = hv[k][f];
+            sinf[e] = hinf[k];
+        }
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
@@ -756,13 +800,11 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int
         block_obs_partials(ob, S.obs_partials);
         return;
     }
-    const int x = x0 + tx, y = y0 + ty;
     const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
-    if (x < P.nx && y < P.ny && (sinf[h] & 3) == PT_FLUID) {
-        const int i = x + P.nx * (y + P.ny * z);
+    if (active && (sinf[h] & 3) == PT_FLUID) {
         const SmemPops pops{spop, t, Q};
         const SmemStencil<D> st{shal, sinf, h};
-        collide_site<D>(P, S, x, y, z, i, first, pops, st, ob);
+        collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
     block_obs_partials(ob, S.obs_partials);
 }
