@@ -172,6 +172,10 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   staged into shared memory by bulk asynchronous copies (needs nx % 4 == 0). Both give
  *   the same arithmetic. */
 #define LBEHD_OPT_COLLIDE 1
+/*   LBEHD_OPT_MG_REFRESH: rebuild the multigrid hierarchy (the Poisson preconditioner)
+ *   every `value` steps (default 16). The CG operator itself is formed from this step's
+ *   permittivity every step, so the refresh period only affects convergence speed. */
+#define LBEHD_OPT_MG_REFRESH 2
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 
 /* Counters since init (synchronises: reads the device-side iteration counter). */

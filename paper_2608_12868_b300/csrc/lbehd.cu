@@ -38,7 +38,8 @@ struct lbehd_handle {
     Params P{};
     cudaStream_t stream = nullptr;
     cudaStream_t ls = nullptr;     // stream the launch helpers enqueue on (stream, or aux
-    cudaStream_t aux = nullptr;    //   while a conditional-loop body is being captured)
+    cudaStream_t aux = nullptr;    //   while a conditional-node body is being captured)
+    cudaStream_t aux2 = nullptr;   // body capture of a conditional node nested in another
     cudaStream_t own_stream = nullptr;  // created when cfg->stream is the legacy stream
     std::vector<DevBuf> bufs;
     // device state
@@ -70,10 +71,12 @@ struct lbehd_handle {
     dim3 grid1d;
     size_t nblocks1d = 0;
     // CUDA graphs of one step per step parity (LBEHD_POISSON_GRAPH)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphConditionalHandle cond = 0;
-    int use_cond = 0;
-    long long graph_launches = 0, graph_static_kernels[2] = {0, 0}, iter_kernels = 0;
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][refresh]
+    cudaGraphConditionalHandle cond = 0, cond_ref = 0;
+    int use_cond = 0, use_ref = 0;
+    int mg_refresh = 16;           // multigrid hierarchy rebuilt every mg_refresh steps
+    bool mg_valid = false;
+    long long graph_launches = 0, graph_static_kernels[2][2] = {{0, 0}, {0, 0}}, iter_kernels = 0;
     long long graph_iters0 = 0;    // device iteration counter when graphs took over
     bool graph_launches_started = false;
     int collide_variant = 0;       // LBEHD_OPT_COLLIDE: 0 auto, 1 global loads, 2 staged
@@ -281,11 +284,12 @@ int vcycle_launches(const lbehd_handle *h)
 void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
 {
     k_pcg_scalar<<<1, SCALAR_THREADS, 0, h->ls>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s,
-                                                   h->cond, h->use_cond);
+                                                   h->cond, h->use_cond, h->cond_ref, h->use_ref);
 }
 
 // One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x), updating
 // the increment x.
+template <int D>
 void pcg_iteration(lbehd_handle *h, float *x)
 {
     auto &L0 = h->mg[0];
@@ -294,8 +298,8 @@ void pcg_iteration(lbehd_handle *h, float *x)
         k_pcg_dot<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_r, L0.x, h->cg_partials);
         cg_scalar(h, 1, 1, h->nblocks1d);
         k_pcg_p<<<h->grid1d, h->block, 0, h->ls>>>(h->N, L0.x, h->cg_p, h->cg_s);
-        k_pcg_Ap<<<L0.grid, h->block, 0, h->ls>>>(L0.d, L0.D, L0.kx, L0.ky, L0.kz, h->cg_p,
-                                                       h->cg_q, h->cg_partials);
+        k_pcg_Ap<D><<<L0.grid, h->block, 0, h->ls>>>(h->P, h->eps, h->info, L0.D, h->cg_p,
+                                                      h->cg_q, h->cg_partials);
         cg_scalar(h, 1, 2, h->nblocks);
         k_pcg_update<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_p, h->cg_q, x, h->cg_r,
                                                              h->cg_s, h->cg_partials);
@@ -333,6 +337,7 @@ void pcg_apply(lbehd_handle *h, const float *x, float *acc)
 }
 
 // Run CG iterations on x until the device flag says done (host reads it back).
+template <int D>
 int pcg_host_loop(lbehd_handle *h, float *x)
 {
     int rc = read_cg(h);
@@ -341,7 +346,7 @@ int pcg_host_loop(lbehd_handle *h, float *x)
     const int every = std::max(h->cfg.poisson_check_every, 1);
     while (!h->h_cg->done) {
         for (int k = 0; k < every; k++)
-            pcg_iteration(h, x);
+            pcg_iteration<D>(h, x);
         rc = read_cg(h);
         if (rc)
             return rc;
@@ -369,33 +374,41 @@ void mg_setup(lbehd_handle *h)
                                                              C.kz);
         }
     });
+    h->mg_valid = true;
 }
+
+// The multigrid hierarchy only preconditions (the CG operator is formed from eps each step),
+// so it is rebuilt every mg_refresh steps; eps moves with the slowly moving interfaces.
+bool mg_due(const lbehd_handle *h) { return !h->mg_valid || h->step % h->mg_refresh == 0; }
 
 template <int D>
 int poisson(lbehd_handle *h)
 {
     const lbehd_config &c = h->cfg;
-    mg_setup<D>(h);
+    if (mg_due(h))
+        mg_setup<D>(h);
     float *x = h->inc[h->step & 1];   // holds the increment of step - 2: the warm start
     pcg_start<D>(h, x);
     bool converged = true;
     if (c.poisson_mode == LBEHD_POISSON_FIXED) {
         for (int k = 0; k < c.poisson_fixed_iters; k++)
-            pcg_iteration(h, x);
+            pcg_iteration<D>(h, x);
         pcg_apply(h, x, nullptr);
         h->last_iters = c.poisson_fixed_iters;
         h->last_resid = -1.0;
         return LBEHD_OK;
     }
-    int rc = pcg_host_loop(h, x);
+    int rc = pcg_host_loop<D>(h, x);
     if (rc)
         return rc;
     int iters = h->h_cg->iters;
     pcg_apply(h, x, nullptr);
-    for (int pass = 0; pass < 3; pass++) {
+    // refinement: only after a pass that iterated (with none, the start residual was the
+    // true residual and already within the tolerance)
+    for (int pass = 0; pass < 3 && h->h_cg->iters > 0; pass++) {
         CK(h, cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->ls));
         pcg_start<D>(h, h->delta2, 4);   // true residual of the updated potential
-        rc = pcg_host_loop(h, h->delta2);
+        rc = pcg_host_loop<D>(h, h->delta2);
         if (rc)
             return rc;
         if (h->h_cg->iters == 0)
@@ -448,43 +461,45 @@ void collide(lbehd_handle *h)
     });
 }
 
-// Capture the body of a device-side while loop (condition h->cond) into a conditional
-// node appended to the stream's ongoing capture.
+// Append a conditional node (while or if, on handle `cond`) to the ongoing capture of
+// stream `cap`; its body is captured from `body` on stream `bs`.
 template <class F>
-int add_while(lbehd_handle *h, F &&body)
+int add_cond(lbehd_handle *h, cudaStream_t cap, cudaStream_t bs, cudaGraphConditionalHandle cond,
+             cudaGraphConditionalNodeType type, F &&body)
 {
     cudaStreamCaptureStatus st;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     size_t nd = 0;
-    CK(h, cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &cg, &deps, nullptr, &nd));
+    CK(h, cudaStreamGetCaptureInfo(cap, &st, nullptr, &cg, &deps, nullptr, &nd));
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h->cond;
-    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.handle = cond;
+    np.conditional.type = type;
     np.conditional.size = 1;
     cudaGraphNode_t node;
     CK(h, cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
     cudaGraph_t bodyg = np.conditional.phGraph_out[0];
-    CK(h, cudaStreamBeginCaptureToGraph(h->aux, bodyg, nullptr, nullptr, 0,
+    CK(h, cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeRelaxed));
-    h->ls = h->aux;
-    const long long k0 = h->launches;
-    body();
-    h->iter_kernels = h->launches - k0;
-    h->launches = k0;
-    h->ls = h->stream;
+    const cudaStream_t prev = h->ls;
+    h->ls = bs;
+    const int rc = body();
+    h->ls = prev;
     cudaGraph_t out = nullptr;
-    CK(h, cudaStreamEndCapture(h->aux, &out));
-    CK(h, cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1,
+    CK(h, cudaStreamEndCapture(bs, &out));
+    if (rc)
+        return rc;
+    CK(h, cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1,
                                               cudaStreamSetCaptureDependencies));
     return LBEHD_OK;
 }
 
 // One whole coupled step as a CUDA graph for the given step parity: moments, Poisson
-// (device-side CG loop, then one refinement check with its own loop), collide + stream.
+// (multigrid rebuild when `refresh`, device-side CG loop, then, if that loop iterated, one
+// refinement check with its own loop), collide + stream.
 template <int D>
-int capture_step(lbehd_handle *h, int parity)
+int capture_step(lbehd_handle *h, int parity, int refresh)
 {
     const int cur = h->cur, pcur = h->pcur;
     const long long step = h->step, launches = h->launches;
@@ -493,42 +508,66 @@ int capture_step(lbehd_handle *h, int parity)
     h->step = parity;
     h->prof = false;
     cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle c1 = 0, c2 = 0;
-    int rc = LBEHD_OK;
+    cudaGraphConditionalHandle c1 = 0, c2 = 0, cr = 0;
+    long long ref_kernels = 0;
     auto body = [&]() -> int {
         CK(h, cudaGraphCreate(&g, 0));
         CK(h, cudaGraphConditionalHandleCreate(&c1, g, 0, 0));
         CK(h, cudaGraphConditionalHandleCreate(&c2, g, 0, 0));
+        CK(h, cudaGraphConditionalHandleCreate(&cr, g, 0, 0));
         CK(h, cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeRelaxed));
         h->ls = h->stream;
         h->use_cond = 1;
         launch_fields<D>(h);
-        mg_setup<D>(h);
+        if (refresh)
+            mg_setup<D>(h);
         float *x = h->inc[parity];
         h->cond = c1;
+        h->cond_ref = cr;
+        h->use_ref = 1;
         pcg_start<D>(h, x, 0);
-        int r = add_while(h, [&] { pcg_iteration(h, x); });
+        int r = add_cond(h, h->stream, h->aux, c1, cudaGraphCondTypeWhile, [&]() -> int {
+            const long long k0 = h->launches;
+            pcg_iteration<D>(h, x);
+            h->iter_kernels = h->launches - k0;
+            h->launches = k0;
+            return LBEHD_OK;
+        });
+        h->use_ref = 0;
         if (r)
             return r;
         pcg_apply(h, x, nullptr);
-        cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->stream);
-        h->cond = c2;
-        pcg_start<D>(h, h->delta2, 4);
-        r = add_while(h, [&] { pcg_iteration(h, h->delta2); });
+        r = add_cond(h, h->stream, h->aux, cr, cudaGraphCondTypeIf, [&]() -> int {
+            const long long k0 = h->launches;
+            cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->ls);
+            h->cond = c2;
+            pcg_start<D>(h, h->delta2, 4);
+            const int r2 = add_cond(h, h->aux, h->aux2, c2, cudaGraphCondTypeWhile, [&]() -> int {
+                const long long k1 = h->launches;
+                pcg_iteration<D>(h, h->delta2);
+                h->launches = k1;
+                return LBEHD_OK;
+            });
+            pcg_apply(h, h->delta2, x);
+            ref_kernels = h->launches - k0;
+            h->launches = k0;
+            return r2;
+        });
         if (r)
             return r;
-        pcg_apply(h, h->delta2, x);
         collide<D>(h);
         cudaGraph_t out = nullptr;
         CK(h, cudaStreamEndCapture(h->stream, &out));
-        CK(h, cudaGraphInstantiate(&h->gexec[parity], g, 0));
+        CK(h, cudaGraphInstantiate(&h->gexec[parity][refresh], g, 0));
         return LBEHD_OK;
     };
-    rc = body();
-    h->graph_static_kernels[parity] = h->launches - launches;
+    const int rc = body();
+    h->graph_static_kernels[parity][refresh] = h->launches - launches;
     h->use_cond = 0;
-    h->cond = 0;
+    h->use_ref = 0;
+    h->cond = h->cond_ref = 0;
+    h->ls = h->stream;
     if (g)
         cudaGraphDestroy(g);
     h->cur = cur;
@@ -538,14 +577,17 @@ int capture_step(lbehd_handle *h, int parity)
     h->prof = prof;
     if (rc) {
         cudaStreamCaptureStatus st;
-        if (cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(h->stream, &junk);
-            if (junk)
-                cudaGraphDestroy(junk);
-        }
+        for (cudaStream_t sx : {h->aux2, h->aux, h->stream})
+            if (sx && cudaStreamIsCapturing(sx, &st) == cudaSuccess &&
+                st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(sx, &junk);
+                if (junk)
+                    cudaGraphDestroy(junk);
+            }
         cudaGetLastError();
     }
+    (void)ref_kernels;
     return rc;
 }
 
@@ -554,9 +596,9 @@ int do_step(lbehd_handle *h)
 {
     // graph replay (profiling brackets eager launches with events, so it runs eagerly)
     if (h->cfg.poisson_mode == LBEHD_POISSON_GRAPH && !h->first && !h->prof) {
-        const int parity = (int)(h->step & 1);
-        if (!h->gexec[parity]) {
-            const int rc = capture_step<D>(h, parity);
+        const int parity = (int)(h->step & 1), refresh = mg_due(h) ? 1 : 0;
+        if (!h->gexec[parity][refresh]) {
+            const int rc = capture_step<D>(h, parity, refresh);
             if (rc)
                 return rc;
         }
@@ -567,9 +609,9 @@ int do_step(lbehd_handle *h)
             CK(h, cudaStreamSynchronize(h->stream));
             h->graph_iters0 = s0.total_iters;
         }
-        CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
+        CK(h, cudaGraphLaunch(h->gexec[parity][refresh], h->stream));
         h->graph_launches++;
-        h->launches += h->graph_static_kernels[parity];
+        h->launches += h->graph_static_kernels[parity][refresh];
         h->cur ^= 1;
         h->pcur ^= 1;
         h->step++;
@@ -806,6 +848,7 @@ int init_impl(lbehd_handle *h)
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
     CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    CK(h, cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
     if (h->nx % 4 == 0) {
         int rc = encode_pop_maps(h);
         if (rc)
@@ -890,12 +933,16 @@ void release(lbehd_handle *h)
     if (h->h_cg)
         cudaFreeHost(h->h_cg);
     h->h_cg = nullptr;
-    for (auto &e : h->gexec)
-        if (e)
-            cudaGraphExecDestroy(e);
+    for (auto &row : h->gexec)
+        for (auto &e : row)
+            if (e)
+                cudaGraphExecDestroy(e);
     if (h->aux)
         cudaStreamDestroy(h->aux);
     h->aux = nullptr;
+    if (h->aux2)
+        cudaStreamDestroy(h->aux2);
+    h->aux2 = nullptr;
     if (h->own_stream)
         cudaStreamDestroy(h->own_stream);
     h->own_stream = nullptr;
@@ -1110,11 +1157,26 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
             return fail(h, LBEHD_ERR_INVALID_ARG, "the staged collide kernel needs nx % 4 == 0");
         CK(h, cudaStreamSynchronize(h->stream));
         h->collide_variant = (int)value;
-        for (auto &e : h->gexec)   // captured graphs hold the previous choice
-            if (e) {
-                cudaGraphExecDestroy(e);
-                e = nullptr;
-            }
+        for (auto &row : h->gexec)   // captured graphs hold the previous choice
+            for (auto &e : row)
+                if (e) {
+                    cudaGraphExecDestroy(e);
+                    e = nullptr;
+                }
+        return LBEHD_OK;
+    }
+    if (option == LBEHD_OPT_MG_REFRESH) {
+        if (value < 1 || value > (1 << 20))
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_MG_REFRESH must be >= 1");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->mg_refresh = (int)value;
+        h->mg_valid = false;
+        for (auto &row : h->gexec)
+            for (auto &e : row)
+                if (e) {
+                    cudaGraphExecDestroy(e);
+                    e = nullptr;
+                }
         return LBEHD_OK;
     }
     return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");

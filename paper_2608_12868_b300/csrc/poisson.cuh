@@ -433,23 +433,37 @@ __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict_
         p[i] = zv[i] + (beta != 0.0f ? beta * p[i] : 0.0f);
 }
 
-// q = A p on level 0 and partials of p . q.
-__global__ void __launch_bounds__(BX) k_pcg_Ap(MgDims d, const float *__restrict__ Dg,
-                                               const float *__restrict__ kx,
-                                               const float *__restrict__ ky,
-                                               const float *__restrict__ kz,
+// q = A p with the operator of this step (from eps and the node classes; the multigrid
+// hierarchy may be a few steps old, which only changes the preconditioner) and partials of
+// p . q. Dirichlet neighbours hold no correction (p = 0 there).
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_Ap(Params P, const float *__restrict__ eps,
+                                               const uint8_t *__restrict__ info,
+                                               const float *__restrict__ Dg,
                                                const float *__restrict__ p, float *__restrict__ q,
                                                double *__restrict__ partials)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     float v[1] = {0.f};
-    if (x < d.nx) {
+    if (x < P.nx) {
+        const MgDims d{P.nx, P.ny, P.nz};
         const size_t i = cell(d, x, y, z);
-        const float di = Dg[i];
         float qi = 0.0f;
-        if (di > 0.0f) {
-            qi = di * p[i] - offdiag_sum(d, i, x, y, z, kx, ky, kz, p);
-            v[0] = p[i] * qi;
+        if (Dg[i] > 0.0f) {
+            const float ei = eps[i], pi = p[i];
+            const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
+                                  cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
+                                  cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
+#pragma unroll
+            for (int f = 0; f < 2 * D; f++) {
+                const size_t j = nb[f];
+                const int pt = info[j] & 3;
+                if (pt == PT_FLUID)
+                    qi += 0.5f * (ei + eps[j]) * (pi - p[j]);
+                else if (pt == PT_DIRICHLET)
+                    qi += ei * pi;
+            }
+            v[0] = pi * qi;
         }
         q[i] = qi;
     }
@@ -494,13 +508,16 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 //   op 1: r.z       rz                -> beta = rz / rz_old, rz_old = rz
 //   op 2: p.Ap      pq                -> alpha = rz / pq
 //   op 3: ||r||^2   rr                -> iters++, done / converged
-// With use_cond, ops 0, 4 and 3 also set the graph's while-loop condition to !done.
+// With use_cond, ops 0, 4 and 3 also set the graph's while-loop condition to !done; with
+// use_ref, op 0 clears and op 3 sets the condition of the refinement block.
 constexpr int SCALAR_THREADS = 1024;
 __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__restrict__ partials,
                                                                long long nblocks, int nv, int op,
                                                                CgScalars *__restrict__ s,
                                                                cudaGraphConditionalHandle cond,
-                                                               int use_cond)
+                                                               int use_cond,
+                                                               cudaGraphConditionalHandle cond_ref,
+                                                               int use_ref)
 {
     __shared__ double sm[2][SCALAR_THREADS / 32];
     double tot[2] = {0.0, 0.0};
@@ -560,10 +577,16 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
     }
     if (use_cond && op != 1 && op != 2)
         cudaGraphSetConditional(cond, s->done ? 0u : 1u);
+    // refinement check runs only when the main pass iterated
+    if (use_ref && op == 0)
+        cudaGraphSetConditional(cond_ref, 0u);
+    if (use_ref && op == 3)
+        cudaGraphSetConditional(cond_ref, 1u);
 }
 
-// phi += delta on active cells, phi kept as the compensated pair hi + lo; acc += delta
-// when acc is given (accumulates a refinement correction into the step's increment).
+// phi += delta on active cells, phi kept as the compensated pair hi + lo (two-sum in FP32:
+// the rounding error of hi + delta is carried into lo); acc += delta when acc is given
+// (accumulates a refinement correction into the step's increment).
 __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
                                                   const float *__restrict__ delta,
                                                   float *__restrict__ acc,
@@ -574,12 +597,17 @@ __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restr
          i += (size_t)gridDim.x * blockDim.x) {
         if (Dg[i] <= 0.0f)
             continue;
+        const float d = delta[i];
         if (acc)
-            acc[i] += delta[i];
-        const double t = (double)pot[i] + (double)pot_lo[i] + (double)delta[i];
-        const float hi = (float)t;
-        pot[i] = hi;
-        pot_lo[i] = (float)(t - (double)hi);
+            acc[i] += d;
+        const float hi = pot[i];
+        const float t = hi + d;                       // two-sum: t + err = hi + d exactly
+        const float bv = t - hi;
+        const float err = (hi - (t - bv)) + (d - bv);
+        const float lo = pot_lo[i] + err;
+        const float s = t + lo;                       // renormalise the pair
+        pot[i] = s;
+        pot_lo[i] = lo - (s - t);
     }
 }
 
