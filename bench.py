@@ -21,6 +21,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -36,6 +38,9 @@ COLLIDE_BYTES = {3: 83 * 4 * 2 + 24 + 8 + 24 + 8 + 4 + 1, 2: 41 * 4 * 2 + 24 + 8
 # Whole-step model of the hot path per site update: populations read + written once
 # (664 B in 3D), macroscopic fields ~92 B, and ~16 B per Poisson sweep.
 STEP_BYTES = {3: (756, 16), 2: (388, 12)}
+# LBEHD_OPT_COLLIDE values
+COLLIDE_CHOICES = {"auto": 0, "global": 1, "staged": 2, "staged64x2": 3, "staged16x8": 4}
+VARIANT_NAMES = {1: "global", 2: "staged32x4", 3: "staged64x2", 4: "staged16x8"}
 
 
 def measured_peaks():
@@ -167,7 +172,6 @@ def run_reference(args, world, rank):
 
 
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
     from paper_2608_12868_b300 import lbehd
     from paper_2608_12868_b300 import workloads as W
@@ -181,8 +185,14 @@ def run_ours(args, world, rank, local):
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=mode,
                            poisson_fixed_iters=args.fixed_iters,
                            poisson_check_every=args.check_every)
-    sim.set_option(lbehd.OPT_COLLIDE, {"auto": lbehd.COLLIDE_AUTO, "global": lbehd.COLLIDE_GLOBAL,
-                                       "staged": lbehd.COLLIDE_STAGED}[args.collide])
+    tuned = None
+    if args.collide == "tune":
+        sim.step(1)
+        variant, tune_ms = sim.autotune(reps=20)
+        tuned = {"variant": VARIANT_NAMES[variant],
+                 "ms_per_launch": {VARIANT_NAMES[v]: round(t, 5) for v, t in tune_ms.items()}}
+    else:
+        sim.set_option(lbehd.OPT_COLLIDE, COLLIDE_CHOICES[args.collide])
     L = args.lb_steps
     fluid = int((w.solid == 0).sum())
     for _ in range(args.warmup):
@@ -253,6 +263,10 @@ def run_ours(args, world, rank, local):
     step_gbs = step_bytes / (ms / 1e3 / (L * args.steps)) / 1e9
     share = {k: round(v[0] / prof_ms, 4) for k, v in prof.items()}
 
+    batched = None
+    if args.batched > 0:
+        batched = run_batched(args, dev, value / world, peak, peak_kind)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, done, cores, dt = cpu_oracle_rate(w, args.cpu_steps)
@@ -279,7 +293,8 @@ def run_ours(args, world, rank, local):
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_collide (" + args.collide + ")", "peak_source": peak_kind,
+                         "kernel": "k_collide (" + (tuned["variant"] if tuned else args.collide)
+                                   + ")", "peak_source": peak_kind,
                          "timing": "CUDA events around each k_collide launch over a second "
                                    "timed region of the same length",
                          "bytes_per_launch": coll_bytes},
@@ -288,10 +303,73 @@ def run_ours(args, world, rank, local):
                     "d2h_bytes_per_step": 2 * 16 * 8 + 4},
             "gpu_launches": launches,
             "clocks": clocks,
+            "autotune": tuned,
+            "batched": batched,
             "obs_status": obs["status"],
             "mass_drift": float(np.abs(obs["mass"] / warm_obs["mass"] - 1).max()),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_batched(args, dev, plain_mlups, peak, peak_kind):
+    """The 64-instance sweep (uneven 3D lattices from 48^3 to 128x64x64, viscosity ratio,
+    contact angle and electrode potential drawn per instance) as one batch: per-instance
+    collide kernels from the autotuner, one graph launch per coupled step for all
+    instances. Same timing rules as the plain arm (device events, inputs resident)."""
+    import collections
+    import torch
+    from paper_2608_12868_b300 import lbehd
+    from paper_2608_12868_b300 import workloads as W
+    ws = W.batched_sweep(n=args.batched)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    batch = lbehd.Batch(ws, stream=stream, device=dev.index)
+    batch.step(1)
+    variants, _ = batch.autotune(reps=10)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    L = args.lb_steps
+    for _ in range(args.warmup):
+        batch.step(L)
+    torch.cuda.synchronize(dev)
+    t_w = time.perf_counter()
+    while time.perf_counter() - t_w < args.warmup_seconds:
+        batch.step(L)
+        torch.cuda.synchronize(dev)
+    m0 = [o["mass"] for o in batch.observe()]
+    st0 = batch.stats()
+    steps = max(1, args.batched_steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        batch.step(L)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    st1 = batch.stats()
+    obs = batch.observe()
+    sites = sum(w.sites for w in ws)
+    mlups = sites * L * steps / (ms / 1e3) / 1e6
+    iters = (st1["poisson_iters"] - st0["poisson_iters"]) / (L * steps * len(ws))
+    sb, sp = STEP_BYTES[3]
+    gbs = sites * (sb + sp * iters) / (ms / 1e3 / (L * steps)) / 1e9
+    drift = max(float(np.abs(o["mass"] / m - 1).max()) for o, m in zip(obs, m0))
+    out = {
+        "workload": f"batched_sweep_{len(ws)}: {len(ws)} uneven 3D instances "
+                    "(48^3 .. 128x64x64), one graph launch per coupled step",
+        "instances": len(ws), "sites": sites, "value": mlups, "unit": UNIT,
+        "ms_per_lb_step": ms / (L * steps), "lb_steps_timed": L * steps,
+        "vs_plain": mlups / plain_mlups,
+        "gpu_launches": st1["kernels"] - st0["kernels"],
+        "graph_launches": st1["graph_launches"] - st0["graph_launches"],
+        "poisson_iters_per_instance_step": iters,
+        "step_gbs_model": gbs, "step_model_frac": gbs / peak, "peak_source": peak_kind,
+        "collide_variants": dict(collections.Counter(VARIANT_NAMES[v] for v in variants)),
+        "setup_s": setup_s, "status_all_ok": all(o["status"] == 0 for o in obs),
+        "mass_drift": drift,
+    }
+    batch.close()
+    return out
 
 
 def run_profile_window(args, local):
@@ -304,8 +382,11 @@ def run_profile_window(args, local):
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream()
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=lbehd.POISSON_HOST)
-    sim.set_option(lbehd.OPT_COLLIDE, {"auto": lbehd.COLLIDE_AUTO, "global": lbehd.COLLIDE_GLOBAL,
-                                       "staged": lbehd.COLLIDE_STAGED}[args.collide])
+    if args.collide == "tune":
+        sim.step(1)
+        sim.autotune(reps=20)
+    else:
+        sim.set_option(lbehd.OPT_COLLIDE, COLLIDE_CHOICES[args.collide])
     sim.step(args.warmup * args.lb_steps)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
@@ -325,7 +406,10 @@ def main():
     ap.add_argument("--workload", default="droplet_3d_128x64x64")
     ap.add_argument("--lb-steps", type=int, default=20)
     ap.add_argument("--warmup-seconds", type=float, default=2.0)
-    ap.add_argument("--collide", choices=["auto", "global", "staged"], default="auto")
+    ap.add_argument("--collide", choices=["tune"] + list(COLLIDE_CHOICES), default="tune")
+    ap.add_argument("--batched", type=int, default=64,
+                    help="instances of the batched sweep measured after the plain arm (0: skip)")
+    ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBEHD_ABI_VERSION 1
+#define LBEHD_ABI_VERSION 2
 
 #define LBEHD_OK 0
 #define LBEHD_ERR_INVALID_ARG (-1)
@@ -167,10 +167,11 @@ int lbehd_copy_out(lbehd_handle *h, int which, void *dst, size_t bytes);
 int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
 
 /* Implementation options (synchronises; discards captured step graphs).
- *   LBEHD_OPT_COLLIDE: which fused collide kernel runs: 0 automatic (staged when
- *   nx % 4 == 0), 1 populations loaded straight from global memory, 2 population tile
- *   staged into shared memory by bulk asynchronous copies (needs nx % 4 == 0). Both give
- *   the same arithmetic. */
+ *   LBEHD_OPT_COLLIDE: which fused collide kernel runs: 0 automatic (2 when nx % 4 == 0,
+ *   else 1), 1 populations and stencil fields loaded straight from global memory (128-site
+ *   row blocks), 2 / 3 / 4 tile staged into shared memory (populations by TMA tensor copies,
+ *   stencil halo by cooperative loads) on 32x4 / 64x2 / 16x8 tiles (needs nx % 4 == 0).
+ *   All give the same arithmetic. */
 #define LBEHD_OPT_COLLIDE 1
 /*   LBEHD_OPT_MG_REFRESH: rebuild the multigrid hierarchy (the Poisson preconditioner)
  *   every `value` steps (default 16). The CG operator itself is formed from this step's
@@ -232,11 +233,78 @@ int lbehd_profile_read(lbehd_handle *h, double *ms, long long *count);
 int lbehd_phase_moments_noalloc(int dim, int nx, int ny, int nz, const float *phi,
                                 const float *u, const uint8_t *solid, double *out, void *stream);
 
+/* Collide-kernel autotuner. Times each collide kernel the instance can run (1 global
+ * loads; 2, 3, 4 staged 32x4, 64x2, 16x8 tiles when nx % 4 == 0) on the current state,
+ * `reps` launches each after two untimed ones, keeps the fastest as LBEHD_OPT_COLLIDE and
+ * writes the mean time per launch in ms to ms[v - 1] (ms[4], -1 for a kernel that cannot
+ * run; may be NULL). The state is left as it was: the timed launches write only the
+ * buffers the next step overwrites first, and u, the conduction source and the error flag
+ * are saved and restored around them. Synchronises; discards captured step graphs. Returns
+ * the chosen variant (>= 1) or a negative error code. Must not be called on an instance
+ * owned by a batch (use lbehd_batch_autotune). */
+int lbehd_autotune(lbehd_handle *h, int reps, double *ms);
+
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
 const char *lbehd_last_error(lbehd_handle *h);
 
-/* Free every device buffer (through cfg->free when given) and the handle. */
+/* Free every device buffer (through cfg->free when given) and the handle. A handle owned
+ * by a batch is left alone (lbehd_batch_destroy frees it). */
 void lbehd_destroy(lbehd_handle *h);
+
+/* ---------------------------------------------------------------- batched form
+ * Many independent instances of the coupled step (a sweep over lubricant viscosity,
+ * wettability and field strength on lattices of different sizes) advanced together, one
+ * CUDA graph launch per step for the whole batch. In each step graph the moments kernel and
+ * the collide kernels are each one launch over all instances (an instance table in the
+ * kernel parameters; instances grouped by their collide kernel, up to 64 per launch), while
+ * every instance's Poisson solve runs as its own branch with its own device-side CG loop,
+ * so instances that converge in fewer iterations never wait for the others. Each instance
+ * computes exactly what lbehd_step computes for it alone in LBEHD_POISSON_GRAPH mode with
+ * the same LBEHD_OPT_COLLIDE and LBEHD_OPT_MG_REFRESH (bitwise on the state).
+ * All instances must have the same dim; they share one stream (cfgs[0].stream, or a
+ * stream the batch creates when that is NULL) and run in LBEHD_POISSON_GRAPH mode whatever
+ * cfgs[i].poisson_mode says. */
+typedef struct lbehd_batch lbehd_batch;
+
+/* Initialise n >= 1 instances from cfgs[0..n) (each as lbehd_init would; host arrays are
+ * borrowed for the call). On failure nothing is left allocated and the message is in
+ * lbehd_last_error(NULL). */
+int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out);
+
+/* Advance every instance by n steps (the first step of a fresh batch runs instance by
+ * instance; from then on one graph launch per step). Asynchronous; returns
+ * LBEHD_ERR_POISSON_NOCONV if a host-checked solve hit its cap. */
+int lbehd_batch_step(lbehd_batch *b, int n);
+
+/* Number of instances, and instance i (0 <= i < n; NULL otherwise). The instance handle is
+ * borrowed: lbehd_observe, lbehd_copy_out, lbehd_device_ptr, lbehd_set_electrodes,
+ * lbehd_get_stats and lbehd_last_error work on it; lbehd_step, lbehd_set_option,
+ * lbehd_autotune and lbehd_profile_enable are refused with LBEHD_ERR_INVALID_ARG. */
+int lbehd_batch_size(lbehd_batch *b);
+lbehd_handle *lbehd_batch_instance(lbehd_batch *b, int i);
+
+/* Observables of every instance (out[n]) with one synchronisation. Returns
+ * LBEHD_ERR_NONFINITE if any instance saw a non-finite value (its out[i].status says so). */
+int lbehd_batch_observe(lbehd_batch *b, lbehd_obs *out);
+
+/* Options for every instance (LBEHD_OPT_COLLIDE, LBEHD_OPT_MG_REFRESH as for one handle). */
+int lbehd_batch_set_option(lbehd_batch *b, int option, long long value);
+
+/* Run lbehd_autotune on every instance: each gets the collide kernel that is fastest for
+ * its own lattice (ragged tiles, solid fraction), and the batched collide launches are
+ * regrouped accordingly. variants[n] (may be NULL) receives the choices and ms[4 n] (may be
+ * NULL) the timings. Synchronises. */
+int lbehd_batch_autotune(lbehd_batch *b, int reps, int *variants, double *ms);
+
+/* Counters of the whole batch: steps (per instance), Poisson iterations and kernels summed
+ * over instances, graph_launches = batch step graphs launched. Synchronises. */
+int lbehd_batch_get_stats(lbehd_batch *b, lbehd_stats *out);
+
+/* Message of the batch's last error. */
+const char *lbehd_batch_last_error(lbehd_batch *b);
+
+/* Free every instance and the batch. */
+void lbehd_batch_destroy(lbehd_batch *b);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = [os.path.join(HERE, "csrc", "lbehd.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "lattice.cuh")] + [
-    os.path.join(os.path.dirname(HERE), "include", "lbehd.h")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(HERE, "csrc")))
+              if f.endswith(".cuh")] + [os.path.join(os.path.dirname(HERE), "include", "lbehd.h")]
 LIB = os.path.join(HERE, "liblbehd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",

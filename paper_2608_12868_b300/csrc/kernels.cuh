@@ -113,23 +113,30 @@ __global__ void __launch_bounds__(BX) k_init(Params P, const float *__restrict__
 
 // ---------------------------------------------------------------- moments + ghosts
 
+// Pointers one moments + ghosts pass reads and writes (buffers of the step's parity).
+struct FieldPtrs {
+    const float *fphi, *frho;
+    float *phi_out, *rho_out, *eps_out, *pot, *pot_lo;
+    const uint8_t *info, *normal;
+    const int16_t *elec;
+    const double *V;
+};
+
 template <int D>
-__global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict__ fphi,
-                                               const float *__restrict__ frho,
-                                               float *__restrict__ phi_out,
-                                               float *__restrict__ rho_out,
-                                               float *__restrict__ eps_out, float *__restrict__ pot,
-                                               float *__restrict__ pot_lo,
-                                               const uint8_t *__restrict__ info,
-                                               const uint8_t *__restrict__ normal,
-                                               const int16_t *__restrict__ elec,
-                                               const double *__restrict__ V)
+__device__ __forceinline__ void fields_site(const Params &P, const FieldPtrs &F, int x, int y, int z)
 {
     using L = Lat<D>;
     constexpr int Q = L::Q;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx)
-        return;
+    const float *__restrict__ fphi = F.fphi;
+    const float *__restrict__ frho = F.frho;
+    float *__restrict__ phi_out = F.phi_out;
+    float *__restrict__ rho_out = F.rho_out;
+    float *__restrict__ pot = F.pot;
+    float *__restrict__ pot_lo = F.pot_lo;
+    const uint8_t *__restrict__ info = F.info;
+    const uint8_t *__restrict__ normal = F.normal;
+    const int16_t *__restrict__ elec = F.elec;
+    const double *__restrict__ V = F.V;
     const size_t N = P.N, i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
     const uint8_t inf = info[i];
     float Ph[3] = {0.0f, 0.0f, 0.0f};
@@ -191,7 +198,15 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, const float *__restrict
 #pragma unroll
     for (int c = 0; c < 3; c++)
         phi_out[c * N + i] = Ph[c];
-    eps_out[i] = Ph[0] * P.eps[0] + Ph[1] * P.eps[1] + Ph[2] * P.eps[2];
+    F.eps_out[i] = Ph[0] * P.eps[0] + Ph[1] * P.eps[1] + Ph[2] * P.eps[2];
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_fields(Params P, FieldPtrs F)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x < P.nx)
+        fields_site<D>(P, F, x, y, z);
 }
 
 // ---------------------------------------------------------------- fused collide + stream
@@ -208,7 +223,7 @@ struct GlobalPops {
 };
 
 struct SmemPops {
-    const float *s;   // [population array][tile site], stride BX = TX * TY
+    const float *s;   // [population array][tile site], stride BX (sites per tile)
     int t, Q;
     __device__ __forceinline__ float g(int n) const { return s[n * BX + t]; }
     __device__ __forceinline__ float phi(int c, int n) const { return s[(Q + c * Q + n) * BX + t]; }
@@ -244,23 +259,25 @@ struct GlobalStencil {
     }
 };
 
+// Tiles of the staged collide kernel: TX x TY sites (TX * TY = BX), TY in {2, 4, 8}.
 // Halo tile layout: HX x HY x HZ sites, fields [Phi_1, Phi_2, Phi_3, pot, pot_lo] then info.
-constexpr int TX = 32, TY = 4;
-template <int D>
+template <int D, int TY>
 struct Halo {
+    static constexpr int TX = BX / TY;
     static constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? 3 : 1;
     static constexpr int N = HX * HY * HZ;
 };
 
-template <int D>
+template <int D, int TY>
 struct SmemStencil {
-    const float *f;        // 5 * Halo<D>::N floats
-    const uint8_t *info;   // Halo<D>::N bytes
+    const float *f;        // 5 * Halo::N floats
+    const uint8_t *info;   // Halo::N bytes
     int h;                 // halo index of the site
     template <class L>
     __device__ __forceinline__ void at(int n, float (&P)[3], float &ph, float &lo, int &pt) const
     {
-        constexpr int HX = Halo<D>::HX, HXY = Halo<D>::HX * Halo<D>::HY, HN = Halo<D>::N;
+        using H = Halo<D, TY>;
+        constexpr int HX = H::HX, HXY = H::HX * H::HY, HN = H::N;
         const int j = h + L::ex(n) + HX * L::ey(n) + HXY * L::ez(n);
         P[0] = f[j];
         P[1] = f[HN + j];
@@ -645,7 +662,8 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
 }
 
 // Block partial sums of the observables: FP32 within a warp, FP64 across warps.
-__device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], double *partials)
+__device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], double *partials,
+                                                   size_t blk, size_t nblk)
 {
     __shared__ double sm[NOBS][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -661,22 +679,15 @@ __device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], doub
 #pragma unroll
         for (int w = 0; w < BX / 32; w++)
             acc += sm[threadIdx.x][w];
-        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
-        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
         partials[threadIdx.x * nblk + blk] = acc;
     }
 }
 
-// 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
-// the kernel is memory-latency bound and needs the warps.
+// One site of the global-load variant (no-op for x >= nx or a non-fluid site).
 template <int D>
-__global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
+__device__ __forceinline__ void collide_global_site(const Params &P, const State &S, int first,
+                                                    int x, int y, int z, float (&ob)[NOBS])
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    float ob[NOBS];
-#pragma unroll
-    for (int k = 0; k < NOBS; k++)
-        ob[k] = 0.0f;
     const int i = x + P.nx * (y + P.ny * z);
     if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
         const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, (size_t)i, Lat<D>::Q};
@@ -688,7 +699,30 @@ __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
         const SitePre pre = load_site_pre(S, (size_t)P.N, i);
         collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
-    block_obs_partials(ob, S.obs_partials);
+}
+
+__device__ __forceinline__ size_t grid_block_index()
+{
+    return blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+}
+
+__device__ __forceinline__ size_t grid_block_count()
+{
+    return (size_t)gridDim.x * gridDim.y * gridDim.z;
+}
+
+// 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
+// the kernel is memory-latency bound and needs the warps.
+template <int D>
+__global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
+{
+    float ob[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; k++)
+        ob[k] = 0.0f;
+    collide_global_site<D>(P, S, first, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
+                           blockIdx.z, ob);
+    block_obs_partials(ob, S.obs_partials, grid_block_index(), grid_block_count());
 }
 
 // Tensor maps of the three population sets of one buffer, each a 4D tensor
@@ -710,13 +744,13 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 template <int D>
 constexpr int staged_pop_floats()
 {
-    return (4 * Lat<D>::Q + Lat<D>::QS) * TX * TY;
+    return (4 * Lat<D>::Q + Lat<D>::QS) * BX;
 }
 
-template <int D>
+template <int D, int TY>
 constexpr size_t staged_smem_bytes()
 {
-    return (size_t)staged_pop_floats<D>() * 4 + (size_t)Halo<D>::N * (5 * 4 + 1);
+    return (size_t)staged_pop_floats<D>() * 4 + (size_t)Halo<D, TY>::N * (5 * 4 + 1);
 }
 
 // The step on a TX x TY tile with everything it reads staged in shared memory: thread 0
@@ -726,18 +760,19 @@ constexpr size_t staged_smem_bytes()
 // maps). A barrier wait that never completes sets flag bit 1, waits once more for the copies
 // in flight and leaves the block (its partials zeroed).
 constexpr int STAGE_MAX_POLLS = 1 << 22;
-template <int D>
-__global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first,
-                                                          const __grid_constant__ PopMaps maps)
+template <int D, int TY>
+__device__ __forceinline__ void collide_staged_tile(const Params &P, const State &S, int first,
+                                                    const PopMaps *maps, int x0, int y0, int z,
+                                                    size_t blk, size_t nblk)
 {
     using L = Lat<D>;
-    constexpr int Q = L::Q, HN = Halo<D>::N, HX = Halo<D>::HX, HY = Halo<D>::HY;
+    using H = Halo<D, TY>;
+    constexpr int Q = L::Q, HN = H::N, HX = H::HX, HY = H::HY, TX = H::TX;
     extern __shared__ __align__(128) float spop[];   // populations, then halo fields
     float *shal = spop + staged_pop_floats<D>();
     uint8_t *sinf = reinterpret_cast<uint8_t *>(shal + 5 * HN);
     __shared__ __align__(8) uint64_t bar;
     const int t = threadIdx.x, tx = t & (TX - 1), ty = t / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z = blockIdx.z;
     if (t == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -745,9 +780,9 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int
     __syncthreads();
     if (t == 0) {
         mbar_arrive_expect_tx(&bar, (uint32_t)staged_pop_floats<D>() * 4u);
-        tma_load_4d(spop, &maps.g, x0, y0, z, 0, &bar);
-        tma_load_4d(spop + Q * TX * TY, &maps.fphi, x0, y0, z, 0, &bar);
-        tma_load_4d(spop + 4 * Q * TX * TY, &maps.frho, x0, y0, z, 0, &bar);
+        tma_load_4d(spop, &maps->g, x0, y0, z, 0, &bar);
+        tma_load_4d(spop + Q * BX, &maps->fphi, x0, y0, z, 0, &bar);
+        tma_load_4d(spop + 4 * Q * BX, &maps->frho, x0, y0, z, 0, &bar);
     }
     const size_t N = P.N;
     const int x = x0 + tx, y = y0 + ty;
@@ -797,27 +832,33 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int
         if (t == 0)
             atomicOr(S.flag, 2);
         mbar_wait_bounded(&bar, 0, STAGE_MAX_POLLS);
-        block_obs_partials(ob, S.obs_partials);
+        block_obs_partials(ob, S.obs_partials, blk, nblk);
         return;
     }
     const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
     if (active && (sinf[h] & 3) == PT_FLUID) {
         const SmemPops pops{spop, t, Q};
-        const SmemStencil<D> st{shal, sinf, h};
+        const SmemStencil<D, TY> st{shal, sinf, h};
         collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
-    block_obs_partials(ob, S.obs_partials);
+    block_obs_partials(ob, S.obs_partials, blk, nblk);
+}
+
+template <int D, int TY>
+__global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first,
+                                                          const __grid_constant__ PopMaps maps)
+{
+    collide_staged_tile<D, TY>(P, S, first, &maps, blockIdx.x * Halo<D, TY>::TX, blockIdx.y * TY,
+                               blockIdx.z, grid_block_index(), grid_block_count());
 }
 
 // Fixed-order FP64 sum of the observable partials: block k reduces observable k.
 // obs[0..NOBS) receives this step's sums and obs[NOBS..2 NOBS) the previous step's (for the
 // drag force balance).
 constexpr int OBS_THREADS = 256;
-__global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restrict__ partials,
-                                                          long long nblocks,
-                                                          double *__restrict__ obs)
+__device__ __forceinline__ void obs_final_block(const double *__restrict__ partials,
+                                                long long nblocks, double *__restrict__ obs, int k)
 {
-    const int k = blockIdx.x;
     const double *p = partials + k * nblocks;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     long long b = threadIdx.x;
@@ -844,6 +885,13 @@ __global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restr
         obs[NOBS + k] = obs[k];
         obs[k] = t;
     }
+}
+
+__global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restrict__ partials,
+                                                          long long nblocks,
+                                                          double *__restrict__ obs)
+{
+    obs_final_block(partials, nblocks, obs, blockIdx.x);
 }
 
 }  // namespace lbehd

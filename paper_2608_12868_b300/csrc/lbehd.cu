@@ -7,11 +7,13 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/lbehd.h"
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "poisson.cuh"
 
@@ -79,11 +81,12 @@ struct lbehd_handle {
     long long graph_launches = 0, graph_static_kernels[2][2] = {{0, 0}, {0, 0}}, iter_kernels = 0;
     long long graph_iters0 = 0;    // device iteration counter when graphs took over
     bool graph_launches_started = false;
-    int collide_variant = 0;       // LBEHD_OPT_COLLIDE: 0 auto, 1 global loads, 2 staged
+    int collide_variant = 0;       // LBEHD_OPT_COLLIDE: 0 auto, 1 global loads, 2-4 staged
+    bool batch_owned = false;      // instance of an lbehd_batch (stepped and freed by it)
     bool maps_ok = false;          // tensor maps of both population buffers encoded
-    PopMaps maps[2];
-    dim3 grid_tile;                // TX x TY tiles of the staged collide kernel
-    size_t nblocks_tile = 0;
+    PopMaps maps[3][2];            // [tile shape][buffer]; shapes TY = 4, 2, 8
+    dim3 grid_tile[3];             // TX x TY tiles of the staged collide kernel
+    size_t nblocks_tile[3] = {0, 0, 0};
     int mg_nu = 2, mg_coarse = 8;
     int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
     TailLevels tail{};
@@ -219,15 +222,17 @@ void launch(lbehd_handle *h, int kc, int nlaunch, F &&fn)
     }
 }
 
+FieldPtrs field_ptrs(const lbehd_handle *h, int cur, int pcur)
+{
+    return FieldPtrs{h->fphi[cur], h->frho[cur], h->phi[pcur], h->rho[pcur], h->eps, h->pot,
+                     h->pot_lo, h->info, h->normal, h->elec, h->V};
+}
+
 template <int D>
 int launch_fields(lbehd_handle *h)
 {
-    launch(h, LBEHD_KC_FIELDS, 1, [&] {
-        k_fields<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->fphi[h->cur], h->frho[h->cur],
-                                                          h->phi[h->pcur], h->rho[h->pcur], h->eps,
-                                                          h->pot, h->pot_lo, h->info, h->normal,
-                                                          h->elec, h->V);
-    });
+    const FieldPtrs F = field_ptrs(h, h->cur, h->pcur);
+    launch(h, LBEHD_KC_FIELDS, 1, [&] { k_fields<D><<<h->grid, h->block, 0, h->ls>>>(h->P, F); });
     return LBEHD_OK;
 }
 
@@ -426,20 +431,19 @@ int poisson(lbehd_handle *h)
     return LBEHD_OK;
 }
 
-template <int D>
-void collide(lbehd_handle *h)
+State collide_state(const lbehd_handle *h, int cur, int pcur)
 {
     State S;
-    S.g = h->g[h->cur];
-    S.fphi = h->fphi[h->cur];
-    S.frho = h->frho[h->cur];
-    S.g_out = h->g[h->cur ^ 1];
-    S.fphi_out = h->fphi[h->cur ^ 1];
-    S.frho_out = h->frho[h->cur ^ 1];
-    S.phi = h->phi[h->pcur];
-    S.phi_prev = h->phi[h->pcur ^ 1];
-    S.rho = h->rho[h->pcur];
-    S.rho_prev = h->rho[h->pcur ^ 1];
+    S.g = h->g[cur];
+    S.fphi = h->fphi[cur];
+    S.frho = h->frho[cur];
+    S.g_out = h->g[cur ^ 1];
+    S.fphi_out = h->fphi[cur ^ 1];
+    S.frho_out = h->frho[cur ^ 1];
+    S.phi = h->phi[pcur];
+    S.phi_prev = h->phi[pcur ^ 1];
+    S.rho = h->rho[pcur];
+    S.rho_prev = h->rho[pcur ^ 1];
     S.u = h->u;
     S.q = h->q;
     S.pot = h->pot;
@@ -447,18 +451,49 @@ void collide(lbehd_handle *h)
     S.info = h->info;
     S.obs_partials = h->obs_partials;
     S.flag = h->flag;
-    const bool staged = h->maps_ok && h->collide_variant != 1;
-    const size_t nblk = staged ? h->nblocks_tile : h->nblocks;
+    return S;
+}
+
+// Collide variant actually run: 0 (automatic) resolves to the 32x4 staged kernel when the
+// tensor maps exist, else to the global-load kernel.
+int resolved_variant(const lbehd_handle *h)
+{
+    const int v = h->collide_variant;
+    if (v == 1 || !h->maps_ok)
+        return 1;
+    return v == 0 ? 2 : v;
+}
+
+// tile shape index of a staged variant: 2 -> TY 4, 3 -> TY 2, 4 -> TY 8
+int tile_shape(int v) { return v == 3 ? 1 : (v == 4 ? 2 : 0); }
+
+template <int D>
+void collide(lbehd_handle *h, bool with_obs = true)
+{
+    const State S = collide_state(h, h->cur, h->pcur);
+    // variants: 1 global loads, 2/3/4 staged tiles with TY = 4 / 2 / 8
+    const int v = resolved_variant(h);
+    const int shape = tile_shape(v);
+    const bool staged = v != 1;
+    const size_t nblk = staged ? h->nblocks_tile[shape] : h->nblocks;
+    const int first = h->first ? 1 : 0;
     launch(h, LBEHD_KC_COLLIDE, 1, [&] {
-        if (staged)
-            k_collide_staged<D><<<h->grid_tile, h->block, staged_smem_bytes<D>(), h->ls>>>(
-                h->P, S, h->first ? 1 : 0, h->maps[h->cur]);
+        if (!staged)
+            k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, first);
+        else if (shape == 0)
+            k_collide_staged<D, 4><<<h->grid_tile[0], h->block, staged_smem_bytes<D, 4>(), h->ls>>>(
+                h->P, S, first, h->maps[0][h->cur]);
+        else if (shape == 1)
+            k_collide_staged<D, 2><<<h->grid_tile[1], h->block, staged_smem_bytes<D, 2>(), h->ls>>>(
+                h->P, S, first, h->maps[1][h->cur]);
         else
-            k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, h->first ? 1 : 0);
+            k_collide_staged<D, 8><<<h->grid_tile[2], h->block, staged_smem_bytes<D, 8>(), h->ls>>>(
+                h->P, S, first, h->maps[2][h->cur]);
     });
-    launch(h, LBEHD_KC_OBS, 1, [&] {
-        k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)nblk, h->obs);
-    });
+    if (with_obs)
+        launch(h, LBEHD_KC_OBS, 1, [&] {
+            k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)nblk, h->obs);
+        });
 }
 
 // Append a conditional node (while or if, on handle `cond`) to the ongoing capture of
@@ -495,11 +530,14 @@ int add_cond(lbehd_handle *h, cudaStream_t cap, cudaStream_t bs, cudaGraphCondit
     return LBEHD_OK;
 }
 
-// One whole coupled step as a CUDA graph for the given step parity: moments, Poisson
-// (multigrid rebuild when `refresh`, device-side CG loop, then, if that loop iterated, one
-// refinement check with its own loop), collide + stream.
+// Enqueue one coupled step on h->stream, which must be capturing into `g` (the
+// conditional handles are created in `g`): moments, Poisson (multigrid rebuild when
+// `refresh`, device-side CG loop, then, if that loop iterated, one refinement check with
+// its own loop), collide + stream. Buffers are those of a step with the given parity.
+// With full == false only the Poisson part is recorded (the batched step launches the
+// moments and collide kernels of all instances itself).
 template <int D>
-int capture_step(lbehd_handle *h, int parity, int refresh)
+int record_step(lbehd_handle *h, cudaGraph_t g, int parity, int refresh, bool full = true)
 {
     const int cur = h->cur, pcur = h->pcur;
     const long long step = h->step, launches = h->launches;
@@ -507,19 +545,15 @@ int capture_step(lbehd_handle *h, int parity, int refresh)
     h->cur = h->pcur = parity;
     h->step = parity;
     h->prof = false;
-    cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle c1 = 0, c2 = 0, cr = 0;
-    long long ref_kernels = 0;
     auto body = [&]() -> int {
-        CK(h, cudaGraphCreate(&g, 0));
         CK(h, cudaGraphConditionalHandleCreate(&c1, g, 0, 0));
         CK(h, cudaGraphConditionalHandleCreate(&c2, g, 0, 0));
         CK(h, cudaGraphConditionalHandleCreate(&cr, g, 0, 0));
-        CK(h, cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
-                                            cudaStreamCaptureModeRelaxed));
         h->ls = h->stream;
         h->use_cond = 1;
-        launch_fields<D>(h);
+        if (full)
+            launch_fields<D>(h);
         if (refresh)
             mg_setup<D>(h);
         float *x = h->inc[parity];
@@ -550,16 +584,13 @@ int capture_step(lbehd_handle *h, int parity, int refresh)
                 return LBEHD_OK;
             });
             pcg_apply(h, h->delta2, x);
-            ref_kernels = h->launches - k0;
-            h->launches = k0;
+            h->launches = k0;   // the refinement block rarely runs: not counted as static
             return r2;
         });
         if (r)
             return r;
-        collide<D>(h);
-        cudaGraph_t out = nullptr;
-        CK(h, cudaStreamEndCapture(h->stream, &out));
-        CK(h, cudaGraphInstantiate(&h->gexec[parity][refresh], g, 0));
+        if (full)
+            collide<D>(h);
         return LBEHD_OK;
     };
     const int rc = body();
@@ -568,26 +599,50 @@ int capture_step(lbehd_handle *h, int parity, int refresh)
     h->use_ref = 0;
     h->cond = h->cond_ref = 0;
     h->ls = h->stream;
-    if (g)
-        cudaGraphDestroy(g);
     h->cur = cur;
     h->pcur = pcur;
     h->step = step;
     h->launches = launches;
     h->prof = prof;
+    return rc;
+}
+
+void abort_capture(cudaStream_t sx)
+{
+    cudaStreamCaptureStatus st;
+    if (sx && cudaStreamIsCapturing(sx, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(sx, &junk);
+        if (junk)
+            cudaGraphDestroy(junk);
+    }
+}
+
+// One whole coupled step as a CUDA graph for the given step parity (see record_step).
+template <int D>
+int capture_step(lbehd_handle *h, int parity, int refresh)
+{
+    cudaGraph_t g = nullptr;
+    int rc = LBEHD_OK;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess)
+        return fail(h, LBEHD_ERR_CUDA, "cudaGraphCreate failed");
+    if (cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        rc = fail(h, LBEHD_ERR_CUDA, "cudaStreamBeginCaptureToGraph failed");
+    if (!rc)
+        rc = record_step<D>(h, g, parity, refresh);
+    if (!rc) {
+        cudaGraph_t out = nullptr;
+        if (cudaStreamEndCapture(h->stream, &out) != cudaSuccess ||
+            cudaGraphInstantiate(&h->gexec[parity][refresh], g, 0) != cudaSuccess)
+            rc = fail(h, LBEHD_ERR_CUDA, "step graph capture failed");
+    }
     if (rc) {
-        cudaStreamCaptureStatus st;
         for (cudaStream_t sx : {h->aux2, h->aux, h->stream})
-            if (sx && cudaStreamIsCapturing(sx, &st) == cudaSuccess &&
-                st != cudaStreamCaptureStatusNone) {
-                cudaGraph_t junk = nullptr;
-                cudaStreamEndCapture(sx, &junk);
-                if (junk)
-                    cudaGraphDestroy(junk);
-            }
+            abort_capture(sx);
         cudaGetLastError();
     }
-    (void)ref_kernels;
+    cudaGraphDestroy(g);
     return rc;
 }
 
@@ -689,21 +744,24 @@ int encode_pop_maps(lbehd_handle *h)
         return fail(h, LBEHD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     EncodeTiledFn encode = (EncodeTiledFn)fn;
     const cuuint64_t N = h->N;
-    auto one = [&](CUtensorMap *m, float *base, int narr) -> bool {
+    auto one = [&](CUtensorMap *m, float *base, int narr, int ty) -> bool {
         const cuuint64_t dims[4] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz,
                                     (cuuint64_t)narr};
         const cuuint64_t strides[3] = {(cuuint64_t)h->nx * 4, (cuuint64_t)h->nx * h->ny * 4, N * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1u, (cuuint32_t)narr};
+        const cuuint32_t box[4] = {(cuuint32_t)(BX / ty), (cuuint32_t)ty, 1u, (cuuint32_t)narr};
         const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
         return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
                CUDA_SUCCESS;
     };
-    for (int b = 0; b < 2; b++)
-        if (!one(&h->maps[b].g, h->g[b], h->Q) || !one(&h->maps[b].fphi, h->fphi[b], 3 * h->Q) ||
-            !one(&h->maps[b].frho, h->frho[b], h->QS))
-            return fail(h, LBEHD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    const int tys[3] = {4, 2, 8};
+    for (int k = 0; k < 3; k++)
+        for (int b = 0; b < 2; b++)
+            if (!one(&h->maps[k][b].g, h->g[b], h->Q, tys[k]) ||
+                !one(&h->maps[k][b].fphi, h->fphi[b], 3 * h->Q, tys[k]) ||
+                !one(&h->maps[k][b].frho, h->frho[b], h->QS, tys[k]))
+                return fail(h, LBEHD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     h->maps_ok = true;
     return LBEHD_OK;
 }
@@ -762,10 +820,17 @@ int init_impl(lbehd_handle *h)
     h->block = dim3(BX, 1, 1);
     h->grid = dim3((h->nx + BX - 1) / BX, h->ny, h->nz);
     h->nblocks = (size_t)h->grid.x * h->grid.y * h->grid.z;
-    h->grid_tile = dim3((h->nx + TX - 1) / TX, (h->ny + TY - 1) / TY, h->nz);
-    h->nblocks_tile = (size_t)h->grid_tile.x * h->grid_tile.y * h->grid_tile.z;
-    h->obs_partials =
-        (double *)dev_alloc(h, NOBS * std::max(h->nblocks, h->nblocks_tile) * sizeof(double));
+    size_t nblk_max = h->nblocks;
+    {
+        const int tys[3] = {4, 2, 8};
+        for (int k = 0; k < 3; k++) {
+            const int tx = BX / tys[k];
+            h->grid_tile[k] = dim3((h->nx + tx - 1) / tx, (h->ny + tys[k] - 1) / tys[k], h->nz);
+            h->nblocks_tile[k] = (size_t)h->grid_tile[k].x * h->grid_tile[k].y * h->grid_tile[k].z;
+            nblk_max = std::max(nblk_max, h->nblocks_tile[k]);
+        }
+    }
+    h->obs_partials = (double *)dev_alloc(h, NOBS * nblk_max * sizeof(double));
     h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
     h->flag = (int *)dev_alloc(h, sizeof(int));
     if (!h->u || !h->q || !h->pot || !h->pot_lo || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
@@ -853,8 +918,12 @@ int init_impl(lbehd_handle *h)
         int rc = encode_pop_maps(h);
         if (rc)
             return rc;
-        CK(h, cudaFuncSetAttribute(k_collide_staged<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)staged_smem_bytes<D>()));
+        CK(h, cudaFuncSetAttribute(k_collide_staged<D, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem_bytes<D, 4>()));
+        CK(h, cudaFuncSetAttribute(k_collide_staged<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem_bytes<D, 2>()));
+        CK(h, cudaFuncSetAttribute(k_collide_staged<D, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem_bytes<D, 8>()));
     }
     {
         CgScalars s0{};
@@ -948,6 +1017,463 @@ void release(lbehd_handle *h)
     h->own_stream = nullptr;
 }
 
+
+// ------------------------------------------------------------ collide autotuner
+
+// Time every collide kernel the instance can run on its current state (see lbehd_autotune)
+// and keep the fastest. The timed launches write the other population buffer and the
+// observable partials (both overwritten first by the next step) and u, q and the error
+// flag, which are saved in the CG work vectors (dead between steps) and restored.
+template <int D>
+int autotune_impl(lbehd_handle *h, int reps, double *ms_out)
+{
+    reps = std::max(1, std::min(reps, 1000));
+    const size_t N = h->N, fb = sizeof(float);
+    CK(h, cudaStreamSynchronize(h->stream));
+    float *save[4] = {h->cg_r, h->cg_p, h->cg_q, h->delta2};
+    for (int c = 0; c < 3; c++)
+        CK(h, cudaMemcpyAsync(save[c], h->u + c * N, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(save[3], h->q, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    int flag0 = 0;
+    CK(h, cudaMemcpyAsync(&flag0, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    const int v0 = h->collide_variant;
+    const bool prof = h->prof, first = h->first;
+    h->prof = false;
+    h->first = false;
+    h->ls = h->stream;
+    int best = 1;
+    float best_ms = 0.0f;
+    int rc = LBEHD_OK;
+    for (int v = 1; v <= 4 && !rc; v++) {
+        double ms = -1.0;
+        if (v == 1 || h->maps_ok) {
+            h->collide_variant = v;
+            collide<D>(h, false);
+            collide<D>(h, false);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps; r++)
+                collide<D>(h, false);
+            cudaEventRecord(e1, h->stream);
+            float t = 0.0f;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(h, e, "autotune timing");
+                break;
+            }
+            t /= (float)reps;
+            ms = t;
+            if (v == 1 || t < best_ms) {
+                best = v;
+                best_ms = t;
+            }
+        }
+        if (ms_out)
+            ms_out[v - 1] = ms;
+    }
+    h->prof = prof;
+    h->first = first;
+    h->collide_variant = rc ? v0 : best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int c = 0; c < 3; c++)
+        CK(h, cudaMemcpyAsync(h->u + c * N, save[c], N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->q, save[3], N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->flag, &flag0, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto &row : h->gexec)   // captured graphs hold the previous choice
+        for (auto &e : row)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    return rc ? rc : best;
+}
+
+int set_option_impl(lbehd_handle *h, int option, long long value)
+{
+    if (option == LBEHD_OPT_COLLIDE) {
+        if (value < 0 || value > 4)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_COLLIDE takes 0 to 4");
+        if (value >= 2 && !h->maps_ok)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "the staged collide kernel needs nx % 4 == 0");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->collide_variant = (int)value;
+    } else if (option == LBEHD_OPT_MG_REFRESH) {
+        if (value < 1 || value > (1 << 20))
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_MG_REFRESH must be >= 1");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->mg_refresh = (int)value;
+        h->mg_valid = false;
+    } else {
+        return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
+    }
+    for (auto &row : h->gexec)   // captured graphs hold the previous choice
+        for (auto &e : row)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    return LBEHD_OK;
+}
+
+// Observables: enqueue the copies (o[2 NOBS], flag, CG scalars into h->h_cg), then, after
+// the stream is synchronised, fill *out.
+int observe_enqueue(lbehd_handle *h, double *o, int *flag)
+{
+    CK(h, cudaMemcpyAsync(o, h->obs, 2 * NOBS * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
+    return LBEHD_OK;
+}
+
+int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    out->step = h->step - 1;
+    const double M1 = o[0], M1p = o[NOBS];
+    out->M1 = M1;
+    for (int a = 0; a < 3; a++) {
+        out->centroid[a] = M1 != 0.0 ? o[1 + a] / M1 : 0.0;
+        out->velocity[a] = M1 != 0.0 ? o[4 + a] / M1 : 0.0;
+        out->f_ele[a] = o[7 + a];
+        out->f_ele_total[a] = o[10 + a];
+        const double Vp = M1p != 0.0 ? o[NOBS + 4 + a] / M1p : 0.0;
+        out->f_drag[a] = h->step >= 2 ? o[7 + a] - M1 * (out->velocity[a] - Vp) : 0.0;
+    }
+    out->mass[0] = M1;
+    out->mass[1] = o[13];
+    out->mass[2] = o[14];
+    out->charge = o[15];
+    out->poisson_iters = h->h_cg->step_iters;
+    out->poisson_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
+    out->status = flag ? LBEHD_ERR_NONFINITE
+                       : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
+    if (flag)
+        return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
+    return LBEHD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ batched form
+
+struct lbehd_batch {
+    std::vector<lbehd_handle *> inst;
+    int dim = 0;
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    PopMaps *maps = nullptr;           // device: [2][n] tensor maps, per step parity
+    double *h_obs = nullptr;           // pinned: [n][2 NOBS] observables, then [n] flags
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][refresh]
+    long long static_kernels[2][2] = {{0, 0}, {0, 0}};
+    long long launches = 0, graph_launches = 0;
+    bool graphs_started = false;
+    std::string err;
+};
+
+namespace {
+
+int bfail(lbehd_batch *b, int code, const std::string &msg)
+{
+    b->err = msg;
+    return code;
+}
+
+#define BCK(b, call)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return bfail((b), LBEHD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_batch_graphs(lbehd_batch *b)
+{
+    for (auto &row : b->gexec)
+        for (auto &e : row)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+}
+
+// Current capture dependencies of a stream (copied: the returned array is only valid until
+// the next call on the stream).
+int capture_deps(lbehd_batch *b, std::vector<cudaGraphNode_t> &out)
+{
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    BCK(b, cudaStreamGetCaptureInfo(b->stream, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    out.assign(deps, deps + nd);
+    return LBEHD_OK;
+}
+
+int set_deps(lbehd_batch *b, const std::vector<cudaGraphNode_t> &deps)
+{
+    BCK(b, cudaStreamUpdateCaptureDependencies(b->stream, const_cast<cudaGraphNode_t *>(deps.data()),
+                                               nullptr, deps.size(),
+                                               cudaStreamSetCaptureDependencies));
+    return LBEHD_OK;
+}
+
+template <int D>
+void launch_collide_chunk(lbehd_batch *b, int v, const CollideBatch &A, int blocks)
+{
+    if (v == 1)
+        k_collide_batch<D><<<blocks, BX, 0, b->stream>>>(A);
+    else if (v == 2)
+        k_collide_staged_batch<D, 4><<<blocks, BX, staged_smem_bytes<D, 4>(), b->stream>>>(A);
+    else if (v == 3)
+        k_collide_staged_batch<D, 2><<<blocks, BX, staged_smem_bytes<D, 2>(), b->stream>>>(A);
+    else
+        k_collide_staged_batch<D, 8><<<blocks, BX, staged_smem_bytes<D, 8>(), b->stream>>>(A);
+}
+
+// Blocks of one instance in the batched collide launch of variant v.
+long long collide_blocks(const lbehd_handle *h, int v)
+{
+    return v == 1 ? (long long)((h->N + BX - 1) / BX) : (long long)h->nblocks_tile[tile_shape(v)];
+}
+
+// The whole batch's step for one parity as one graph: the moments of every instance (one
+// launch per 64 instances), then each instance's Poisson solve as its own branch, then
+// the collide kernels (one launch per group of instances running the same kernel, the
+// groups as parallel branches), then the observable sums of every instance.
+template <int D>
+int capture_batch(lbehd_batch *b, int parity, int refresh)
+{
+    const int n = (int)b->inst.size();
+    std::vector<int> order;   // instances grouped by collide kernel
+    for (int v = 1; v <= 4; v++)
+        for (int i = 0; i < n; i++)
+            if (resolved_variant(b->inst[i]) == v)
+                order.push_back(i);
+    std::vector<PopMaps> hm(n);
+    for (int k = 0; k < n; k++) {
+        const lbehd_handle *h = b->inst[order[k]];
+        const int v = resolved_variant(h);
+        if (v != 1)
+            hm[k] = h->maps[tile_shape(v)][parity];
+        else
+            std::memset(&hm[k], 0, sizeof(PopMaps));
+    }
+    PopMaps *dmaps = b->maps + (size_t)parity * n;
+    BCK(b, cudaMemcpyAsync(dmaps, hm.data(), n * sizeof(PopMaps), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaGraphCreate(&g, 0));
+    int rc = LBEHD_OK;
+    long long kernels = 0;
+    std::unique_ptr<FieldsBatch> FA(new FieldsBatch);
+    std::unique_ptr<CollideBatch> CA(new CollideBatch);
+    std::unique_ptr<ObsBatch> OA(new ObsBatch);
+    auto body = [&]() -> int {
+        BCK(b, cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+        // moments + ghosts
+        for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
+            const int m = std::min(BATCH_MAX, n - c0);
+            std::memset(FA.get(), 0, sizeof(FieldsBatch));
+            FA->n = m;
+            long long blocks = 0;
+            for (int k = 0; k < m; k++) {
+                const lbehd_handle *h = b->inst[c0 + k];
+                FA->start[k] = (int)blocks;
+                FA->P[k] = h->P;
+                FA->F[k] = field_ptrs(h, parity, parity);
+                blocks += (long long)((h->N + BX - 1) / BX);
+            }
+            FA->start[m] = (int)blocks;
+            k_fields_batch<D><<<(unsigned)blocks, BX, 0, b->stream>>>(*FA);
+            kernels++;
+        }
+        // Poisson, one branch per instance
+        std::vector<cudaGraphNode_t> fork, ends, tmp;
+        int r = capture_deps(b, fork);
+        if (r)
+            return r;
+        for (lbehd_handle *h : b->inst) {
+            if ((r = set_deps(b, fork)))
+                return r;
+            r = record_step<D>(h, g, parity, refresh, false);
+            if (r)
+                return bfail(b, r, "instance Poisson capture: " + h->err);
+            kernels += h->graph_static_kernels[parity][refresh];
+            if ((r = capture_deps(b, tmp)))
+                return r;
+            ends.insert(ends.end(), tmp.begin(), tmp.end());
+        }
+        // collide + stream: one launch per chunk of a kernel group, chunks in parallel
+        std::vector<cudaGraphNode_t> cends;
+        for (int k0 = 0; k0 < n;) {
+            const int v = resolved_variant(b->inst[order[k0]]);
+            int m = 0;
+            while (k0 + m < n && m < BATCH_MAX && resolved_variant(b->inst[order[k0 + m]]) == v)
+                m++;
+            std::memset(CA.get(), 0, sizeof(CollideBatch));
+            CA->n = m;
+            CA->first = 0;
+            CA->maps = dmaps + k0;
+            long long blocks = 0;
+            for (int k = 0; k < m; k++) {
+                const lbehd_handle *h = b->inst[order[k0 + k]];
+                CA->start[k] = (int)blocks;
+                if (v != 1) {
+                    CA->tiles_x[k] = (int)h->grid_tile[tile_shape(v)].x;
+                    CA->tiles_y[k] = (int)h->grid_tile[tile_shape(v)].y;
+                }
+                CA->P[k] = h->P;
+                CA->S[k] = collide_state(h, parity, parity);
+                blocks += collide_blocks(h, v);
+            }
+            CA->start[m] = (int)blocks;
+            if ((r = set_deps(b, ends)))
+                return r;
+            launch_collide_chunk<D>(b, v, *CA, (int)blocks);
+            kernels++;
+            if ((r = capture_deps(b, tmp)))
+                return r;
+            cends.insert(cends.end(), tmp.begin(), tmp.end());
+            k0 += m;
+        }
+        if ((r = set_deps(b, cends)))
+            return r;
+        // observable sums
+        for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
+            const int m = std::min(BATCH_MAX, n - c0);
+            std::memset(OA.get(), 0, sizeof(ObsBatch));
+            OA->n = m;
+            for (int k = 0; k < m; k++) {
+                const lbehd_handle *h = b->inst[c0 + k];
+                OA->partials[k] = h->obs_partials;
+                OA->nblocks[k] = collide_blocks(h, resolved_variant(h));
+                OA->obs[k] = h->obs;
+            }
+            k_obs_final_batch<<<dim3(NOBS, m), OBS_THREADS, 0, b->stream>>>(*OA);
+            kernels++;
+        }
+        BCK(b, cudaGetLastError());
+        cudaGraph_t out = nullptr;
+        BCK(b, cudaStreamEndCapture(b->stream, &out));
+        BCK(b, cudaGraphInstantiate(&b->gexec[parity][refresh], g, 0));
+        return LBEHD_OK;
+    };
+    rc = body();
+    if (rc) {
+        for (lbehd_handle *h : b->inst)
+            for (cudaStream_t sx : {h->aux2, h->aux})
+                abort_capture(sx);
+        abort_capture(b->stream);
+        cudaGetLastError();
+    }
+    cudaGraphDestroy(g);
+    b->static_kernels[parity][refresh] = kernels;
+    return rc;
+}
+
+template <int D>
+int batch_step_one(lbehd_batch *b)
+{
+    bool any_first = false;
+    for (lbehd_handle *h : b->inst)
+        any_first = any_first || h->first;
+    if (any_first) {
+        // the first step (initial fields, host-checked Poisson solve) runs per instance
+        int worst = LBEHD_OK;
+        for (lbehd_handle *h : b->inst) {
+            const int rc = do_step<D>(h);
+            if (rc == LBEHD_ERR_POISSON_NOCONV)
+                worst = rc;
+            else if (rc)
+                return bfail(b, rc, "first step: " + h->err);
+        }
+        return worst;
+    }
+    const lbehd_handle *h0 = b->inst[0];
+    const int parity = (int)(h0->step & 1);
+    int refresh = 0;
+    for (lbehd_handle *h : b->inst) {
+        if (h->step != h0->step || h->cur != parity || h->pcur != parity)
+            return bfail(b, LBEHD_ERR_INVALID_ARG, "batch instances are out of step");
+        refresh |= mg_due(h) ? 1 : 0;
+    }
+    if (!b->gexec[parity][refresh]) {
+        const int rc = capture_batch<D>(b, parity, refresh);
+        if (rc)
+            return rc;
+    }
+    if (!b->graphs_started) {
+        // kernels inside the Poisson while loops are counted from the device iteration
+        // counters: remember where they stood
+        for (lbehd_handle *h : b->inst)
+            BCK(b, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                   b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        for (lbehd_handle *h : b->inst) {
+            h->graph_iters0 = h->h_cg->total_iters;
+            h->graph_launches_started = true;
+        }
+        b->graphs_started = true;
+    }
+    BCK(b, cudaGraphLaunch(b->gexec[parity][refresh], b->stream));
+    b->graph_launches++;
+    b->launches += b->static_kernels[parity][refresh];
+    for (lbehd_handle *h : b->inst) {
+        h->cur ^= 1;
+        h->pcur ^= 1;
+        h->step++;
+        h->graph_launches++;
+    }
+    return LBEHD_OK;
+}
+
+void batch_release(lbehd_batch *b)
+{
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    drop_batch_graphs(b);
+    for (lbehd_handle *h : b->inst) {
+        release(h);
+        delete h;
+    }
+    b->inst.clear();
+    if (b->maps) {
+        if (b->free)
+            b->free(b->maps, b->alloc_ctx);
+        else
+            cudaFree(b->maps);
+    }
+    b->maps = nullptr;
+    if (b->h_obs)
+        cudaFreeHost(b->h_obs);
+    b->h_obs = nullptr;
+    if (b->own_stream)
+        cudaStreamDestroy(b->own_stream);
+    b->own_stream = nullptr;
+}
+
+template <int D>
+int batch_kernel_attributes()
+{
+    if (cudaFuncSetAttribute(k_collide_staged_batch<D, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)staged_smem_bytes<D, 4>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_collide_staged_batch<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)staged_smem_bytes<D, 2>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_collide_staged_batch<D, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)staged_smem_bytes<D, 8>()) != cudaSuccess)
+        return LBEHD_ERR_CUDA;
+    return LBEHD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1026,6 +1552,8 @@ int lbehd_step(lbehd_handle *h, int n)
 {
     if (!h)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_step");
     if (n < 0)
         return fail(h, LBEHD_ERR_INVALID_ARG, "n must be >= 0");
     int worst = LBEHD_OK;
@@ -1059,33 +1587,11 @@ int lbehd_observe(lbehd_handle *h, lbehd_obs *out)
         return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or output");
     double o[2 * NOBS];
     int flag = 0;
-    CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
+    const int rc = observe_enqueue(h, o, &flag);
+    if (rc)
+        return rc;
     CK(h, cudaStreamSynchronize(h->stream));
-    std::memset(out, 0, sizeof(*out));
-    out->step = h->step - 1;
-    const double M1 = o[0], M1p = o[NOBS];
-    out->M1 = M1;
-    for (int a = 0; a < 3; a++) {
-        out->centroid[a] = M1 != 0.0 ? o[1 + a] / M1 : 0.0;
-        out->velocity[a] = M1 != 0.0 ? o[4 + a] / M1 : 0.0;
-        out->f_ele[a] = o[7 + a];
-        out->f_ele_total[a] = o[10 + a];
-        const double Vp = M1p != 0.0 ? o[NOBS + 4 + a] / M1p : 0.0;
-        out->f_drag[a] = h->step >= 2 ? o[7 + a] - M1 * (out->velocity[a] - Vp) : 0.0;
-    }
-    out->mass[0] = M1;
-    out->mass[1] = o[13];
-    out->mass[2] = o[14];
-    out->charge = o[15];
-    out->poisson_iters = h->h_cg->step_iters;
-    out->poisson_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
-    out->status = flag ? LBEHD_ERR_NONFINITE
-                       : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
-    if (flag)
-        return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
-    return LBEHD_OK;
+    return observe_fill(h, o, flag, out);
 }
 
 static int array_info(lbehd_handle *h, int which, void **ptr, size_t *bytes)
@@ -1150,36 +1656,18 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
 {
     if (!h)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
-    if (option == LBEHD_OPT_COLLIDE) {
-        if (value < 0 || value > 2)
-            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_COLLIDE takes 0, 1 or 2");
-        if (value == 2 && !h->maps_ok)
-            return fail(h, LBEHD_ERR_INVALID_ARG, "the staged collide kernel needs nx % 4 == 0");
-        CK(h, cudaStreamSynchronize(h->stream));
-        h->collide_variant = (int)value;
-        for (auto &row : h->gexec)   // captured graphs hold the previous choice
-            for (auto &e : row)
-                if (e) {
-                    cudaGraphExecDestroy(e);
-                    e = nullptr;
-                }
-        return LBEHD_OK;
-    }
-    if (option == LBEHD_OPT_MG_REFRESH) {
-        if (value < 1 || value > (1 << 20))
-            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_MG_REFRESH must be >= 1");
-        CK(h, cudaStreamSynchronize(h->stream));
-        h->mg_refresh = (int)value;
-        h->mg_valid = false;
-        for (auto &row : h->gexec)
-            for (auto &e : row)
-                if (e) {
-                    cudaGraphExecDestroy(e);
-                    e = nullptr;
-                }
-        return LBEHD_OK;
-    }
-    return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_set_option");
+    return set_option_impl(h, option, value);
+}
+
+int lbehd_autotune(lbehd_handle *h, int reps, double *ms)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_autotune");
+    return h->dim == 2 ? autotune_impl<2>(h, reps, ms) : autotune_impl<3>(h, reps, ms);
 }
 
 int lbehd_get_stats(lbehd_handle *h, lbehd_stats *out)
@@ -1201,6 +1689,8 @@ int lbehd_profile_enable(lbehd_handle *h, int enable)
 {
     if (!h)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: profiling is per handle");
     CK(h, cudaStreamSynchronize(h->stream));
     drop_events(h);
     h->prof = enable != 0;
@@ -1232,8 +1722,180 @@ const char *lbehd_last_error(lbehd_handle *h)
 
 void lbehd_destroy(lbehd_handle *h)
 {
+    if (h && h->batch_owned)
+        return;
     release(h);
     delete h;
+}
+
+// ---------------------------------------------------------------- batched form
+
+int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
+{
+    if (!cfgs || !out || n < 1)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null configs or output, or n < 1");
+    *out = nullptr;
+    for (int i = 1; i < n; i++)
+        if (cfgs[i].dim != cfgs[0].dim)
+            return fail(nullptr, LBEHD_ERR_INVALID_ARG, "batch instances must share dim");
+    if (cfgs[0].dim != 2 && cfgs[0].dim != 3)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "dim must be 2 or 3");
+    lbehd_batch *b = new (std::nothrow) lbehd_batch();
+    if (!b)
+        return fail(nullptr, LBEHD_ERR_OOM, "host allocation failed");
+    b->dim = cfgs[0].dim;
+    b->alloc = cfgs[0].alloc;
+    b->free = cfgs[0].free;
+    b->alloc_ctx = cfgs[0].alloc_ctx;
+    b->stream = (cudaStream_t)cfgs[0].stream;
+    auto bail = [&](int code, const std::string &msg) {
+        batch_release(b);
+        delete b;
+        return fail(nullptr, code, msg);
+    };
+    if (!b->stream) {
+        if (cudaStreamCreate(&b->own_stream) != cudaSuccess)
+            return bail(LBEHD_ERR_CUDA, "cudaStreamCreate failed");
+        b->stream = b->own_stream;
+    }
+    if ((b->dim == 2 ? batch_kernel_attributes<2>() : batch_kernel_attributes<3>()) != LBEHD_OK)
+        return bail(LBEHD_ERR_CUDA, "cudaFuncSetAttribute failed for the batched kernels");
+    for (int i = 0; i < n; i++) {
+        lbehd_config c = cfgs[i];
+        c.stream = b->stream;
+        c.poisson_mode = LBEHD_POISSON_GRAPH;
+        lbehd_handle *h = nullptr;
+        const int rc = lbehd_init(&c, &h);
+        if (rc)
+            return bail(rc, "instance " + std::to_string(i) + ": " + g_init_error);
+        h->batch_owned = true;
+        b->inst.push_back(h);
+    }
+    const size_t mb = 2 * (size_t)n * sizeof(PopMaps);
+    if (b->alloc)
+        b->maps = (PopMaps *)b->alloc(mb, b->alloc_ctx);
+    else if (cudaMalloc((void **)&b->maps, mb) != cudaSuccess)
+        b->maps = nullptr;
+    if (!b->maps)
+        return bail(LBEHD_ERR_OOM, "device allocation of the batch tensor-map table failed");
+    if (cudaMallocHost((void **)&b->h_obs, (size_t)n * (2 * NOBS + 1) * sizeof(double)) != cudaSuccess)
+        return bail(LBEHD_ERR_OOM, "pinned host allocation failed");
+    *out = b;
+    return LBEHD_OK;
+}
+
+int lbehd_batch_step(lbehd_batch *b, int n)
+{
+    if (!b)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch");
+    if (n < 0)
+        return bfail(b, LBEHD_ERR_INVALID_ARG, "n must be >= 0");
+    int worst = LBEHD_OK;
+    for (int s = 0; s < n; s++) {
+        const int rc = b->dim == 2 ? batch_step_one<2>(b) : batch_step_one<3>(b);
+        if (rc == LBEHD_ERR_POISSON_NOCONV)
+            worst = rc;
+        else if (rc)
+            return rc;
+    }
+    if (worst)
+        b->err = "Poisson solve reached poisson_max_iter";
+    return worst;
+}
+
+int lbehd_batch_size(lbehd_batch *b) { return b ? (int)b->inst.size() : 0; }
+
+lbehd_handle *lbehd_batch_instance(lbehd_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->inst.size())
+        return nullptr;
+    return b->inst[i];
+}
+
+int lbehd_batch_observe(lbehd_batch *b, lbehd_obs *out)
+{
+    if (!b || !out)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch or output");
+    const int n = (int)b->inst.size();
+    int *flags = reinterpret_cast<int *>(b->h_obs + (size_t)n * 2 * NOBS);
+    for (int i = 0; i < n; i++) {
+        lbehd_handle *h = b->inst[i];
+        if (observe_enqueue(h, b->h_obs + (size_t)i * 2 * NOBS, flags + i))
+            return bfail(b, LBEHD_ERR_CUDA, "instance " + std::to_string(i) + ": " + h->err);
+    }
+    BCK(b, cudaStreamSynchronize(b->stream));
+    int worst = LBEHD_OK;
+    for (int i = 0; i < n; i++) {
+        lbehd_handle *h = b->inst[i];
+        const int rc = observe_fill(h, b->h_obs + (size_t)i * 2 * NOBS, flags[i], out + i);
+        if (rc) {
+            worst = rc;
+            b->err = "instance " + std::to_string(i) + ": " + h->err;
+        }
+    }
+    return worst;
+}
+
+int lbehd_batch_set_option(lbehd_batch *b, int option, long long value)
+{
+    if (!b)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch");
+    for (size_t i = 0; i < b->inst.size(); i++) {
+        const int rc = set_option_impl(b->inst[i], option, value);
+        if (rc)
+            return bfail(b, rc, "instance " + std::to_string(i) + ": " + b->inst[i]->err);
+    }
+    drop_batch_graphs(b);
+    return LBEHD_OK;
+}
+
+int lbehd_batch_autotune(lbehd_batch *b, int reps, int *variants, double *ms)
+{
+    if (!b)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch");
+    for (size_t i = 0; i < b->inst.size(); i++) {
+        lbehd_handle *h = b->inst[i];
+        const int rc = b->dim == 2 ? autotune_impl<2>(h, reps, ms ? ms + 4 * i : nullptr)
+                                   : autotune_impl<3>(h, reps, ms ? ms + 4 * i : nullptr);
+        if (rc < 0)
+            return bfail(b, rc, "instance " + std::to_string(i) + ": " + h->err);
+        if (variants)
+            variants[i] = rc;
+    }
+    drop_batch_graphs(b);
+    return LBEHD_OK;
+}
+
+int lbehd_batch_get_stats(lbehd_batch *b, lbehd_stats *out)
+{
+    if (!b || !out)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch or output");
+    for (lbehd_handle *h : b->inst)
+        BCK(b, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->steps = b->inst.empty() ? 0 : b->inst[0]->step;
+    out->graph_launches = b->graph_launches;
+    out->kernels = b->launches;
+    for (lbehd_handle *h : b->inst) {
+        out->poisson_iters += h->h_cg->total_iters;
+        // eager launches of the instance (first step, autotuning) and the kernels run
+        // inside its Poisson loops during batch graph replays
+        out->kernels += h->launches;
+        if (h->graph_launches_started)
+            out->kernels += (h->h_cg->total_iters - h->graph_iters0) * h->iter_kernels;
+    }
+    return LBEHD_OK;
+}
+
+const char *lbehd_batch_last_error(lbehd_batch *b) { return b ? b->err.c_str() : g_init_error.c_str(); }
+
+void lbehd_batch_destroy(lbehd_batch *b)
+{
+    if (!b)
+        return;
+    batch_release(b);
+    delete b;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot"
 POISSON_HOST, POISSON_FIXED, POISSON_GRAPH = 0, 1, 2
 OPT_COLLIDE, OPT_MG_REFRESH = 1, 2
 COLLIDE_AUTO, COLLIDE_GLOBAL, COLLIDE_STAGED = 0, 1, 2
+COLLIDE_STAGED_64x2, COLLIDE_STAGED_16x8 = 3, 4
 
 # Storage convention of LBEHD_G: the library keeps g_n - w_n (lattice weights in the
 # documented velocity order).
@@ -84,8 +85,11 @@ _lib = None
 
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
-           "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable", "lbehd_profile_read",
-           "lbehd_last_error", "lbehd_destroy")
+           "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable",
+           "lbehd_profile_read", "lbehd_autotune", "lbehd_last_error", "lbehd_destroy",
+           "lbehd_batch_init", "lbehd_batch_step", "lbehd_batch_size", "lbehd_batch_instance",
+           "lbehd_batch_observe", "lbehd_batch_set_option", "lbehd_batch_autotune",
+           "lbehd_batch_get_stats", "lbehd_batch_last_error", "lbehd_batch_destroy")
 KERNEL_CLASSES = ("fields", "mg", "cg", "collide", "obs")
 
 
@@ -119,6 +123,21 @@ def load():
     lib.lbehd_last_error.restype = ctypes.c_char_p
     lib.lbehd_destroy.argtypes = [P]
     lib.lbehd_destroy.restype = None
+    lib.lbehd_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.lbehd_batch_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(P)]
+    lib.lbehd_batch_step.argtypes = [P, ctypes.c_int]
+    lib.lbehd_batch_size.argtypes = [P]
+    lib.lbehd_batch_instance.argtypes = [P, ctypes.c_int]
+    lib.lbehd_batch_instance.restype = P
+    lib.lbehd_batch_observe.argtypes = [P, ctypes.POINTER(Obs)]
+    lib.lbehd_batch_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
+    lib.lbehd_batch_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.lbehd_batch_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lbehd_batch_last_error.argtypes = [P]
+    lib.lbehd_batch_last_error.restype = ctypes.c_char_p
+    lib.lbehd_batch_destroy.argtypes = [P]
+    lib.lbehd_batch_destroy.restype = None
     if lib.lbehd_config_size() != ctypes.sizeof(Config):
         raise RuntimeError("lbehd_config layout mismatch between the binding and the library")
     _lib = lib
@@ -129,85 +148,74 @@ def _dptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-class Simulation:
-    """One coupled LB-EHD run on the GPU.
+def _obs_dict(o):
+    return {
+        "step": o.step, "M1": o.M1, "centroid": np.array(o.centroid[:]),
+        "velocity": np.array(o.velocity[:]), "f_ele": np.array(o.f_ele[:]),
+        "f_ele_total": np.array(o.f_ele_total[:]), "f_drag": np.array(o.f_drag[:]),
+        "mass": np.array(o.mass[:]), "charge": o.charge, "poisson_iters": o.poisson_iters,
+        "poisson_resid": o.poisson_resid, "status": o.status,
+    }
 
-    ``workload``: a ``workloads.Workload`` (geometry, initial Phi, parameters).
-    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream).
-    ``torch_alloc``: take device memory from PyTorch's caching allocator.
-    """
 
-    def __init__(self, workload, *, stream=None, torch_alloc=True, poisson_mode=POISSON_HOST,
-                 poisson_check_every=1, poisson_fixed_iters=2, mg_nu=0, mg_coarse_sweeps=0,
-                 mg_max_levels=0, mg_scale=0.0, device=0):
-        import torch
-        self._torch = torch
-        lib = load()
-        self.workload = w = workload
+def make_config(w, c, *, poisson_mode=POISSON_HOST, poisson_check_every=1, poisson_fixed_iters=2,
+                mg_nu=0, mg_coarse_sweeps=0, mg_max_levels=0, mg_scale=0.0):
+    """Fill Config ``c`` from a ``workloads.Workload``; returns the host arrays it points
+    to (keep them alive until the init call returns)."""
+    nz, ny, nx = w.shape
+    p = w.params
+    solid = np.ascontiguousarray(w.solid, dtype=np.uint8).reshape(-1)
+    elec = np.ascontiguousarray(w.elec, dtype=np.int16).reshape(-1)
+    phi = np.ascontiguousarray(w.phi_init, dtype=np.float64).reshape(-1)
+    V = np.ascontiguousarray(p.get("V", []), dtype=np.float64)
+    c.dim, c.nx, c.ny, c.nz = w.dim, nx, ny, nz
+    c.solid, c.electrode_id, c.phi_init = (_dptr(solid, ctypes.c_uint8),
+                                           _dptr(elec, ctypes.c_int16),
+                                           _dptr(phi, ctypes.c_double))
+    for k in range(3):
+        c.nu[k], c.eps[k], c.sigma[k] = p["nu"][k], p["eps"][k], p["sig"][k]
+        c.body_force[k] = p.get("body", (0.0, 0.0, 0.0))[k]
+    c.gamma12, c.gamma13, c.gamma23 = p["gamma12"], p["gamma13"], p["gamma23"]
+    c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
+    c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
+    c.s_bulk = p.get("s_bulk", 1.0)
+    c.poisson_tol = p.get("poisson_tol", 1e-7)
+    c.poisson_max_iter = int(p.get("poisson_max_iter", 100))
+    c.poisson_check_every = int(poisson_check_every)
+    c.poisson_mode = int(poisson_mode)
+    c.poisson_fixed_iters = int(poisson_fixed_iters)
+    c.mg_nu, c.mg_coarse_sweeps = int(mg_nu), int(mg_coarse_sweeps)
+    c.mg_max_levels, c.mg_scale = int(mg_max_levels), float(mg_scale)
+    c.n_electrodes = len(V)
+    c.electrode_V = _dptr(V, ctypes.c_double) if len(V) else None
+    return (solid, elec, phi, V)
+
+
+def _torch_allocator(torch, device, stream):
+    def _alloc(nbytes, ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=stream)
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class _HandleOps:
+    """Calls on one lbehd_handle (a Simulation, or one instance of a Batch)."""
+
+    def _setup_shape(self, w):
+        self.workload = w
         self.dim, self.shape = w.dim, tuple(w.shape)
         nz, ny, nx = self.shape
         self.N = nx * ny * nz
         self.Q, self.QS = (9, 5) if w.dim == 2 else (19, 7)
-        self.device = torch.device("cuda", device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        p = w.params
-        solid = np.ascontiguousarray(w.solid, dtype=np.uint8).reshape(-1)
-        elec = np.ascontiguousarray(w.elec, dtype=np.int16).reshape(-1)
-        phi = np.ascontiguousarray(w.phi_init, dtype=np.float64).reshape(-1)
-        V = np.ascontiguousarray(p.get("V", []), dtype=np.float64)
-        c = Config()
-        c.dim, c.nx, c.ny, c.nz = w.dim, nx, ny, nz
-        c.solid, c.electrode_id, c.phi_init = (_dptr(solid, ctypes.c_uint8),
-                                               _dptr(elec, ctypes.c_int16),
-                                               _dptr(phi, ctypes.c_double))
-        for k in range(3):
-            c.nu[k], c.eps[k], c.sigma[k] = p["nu"][k], p["eps"][k], p["sig"][k]
-            c.body_force[k] = p.get("body", (0.0, 0.0, 0.0))[k]
-        c.gamma12, c.gamma13, c.gamma23 = p["gamma12"], p["gamma13"], p["gamma23"]
-        c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
-        c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
-        c.s_bulk = p.get("s_bulk", 1.0)
-        c.poisson_tol = p.get("poisson_tol", 1e-7)
-        c.poisson_max_iter = int(p.get("poisson_max_iter", 100))
-        c.poisson_check_every = int(poisson_check_every)
-        c.poisson_mode = int(poisson_mode)
-        c.poisson_fixed_iters = int(poisson_fixed_iters)
-        c.mg_nu, c.mg_coarse_sweeps = int(mg_nu), int(mg_coarse_sweeps)
-        c.mg_max_levels, c.mg_scale = int(mg_max_levels), float(mg_scale)
-        c.n_electrodes = len(V)
-        c.electrode_V = _dptr(V, ctypes.c_double) if len(V) else None
-        if torch_alloc:
-            dev, st = self.device, self.stream
-
-            def _alloc(nbytes, ctx):
-                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=st)
-
-            def _free(ptr, ctx):
-                torch.cuda.caching_allocator_delete(ptr)
-
-            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
-            c.alloc, c.free = self._alloc_cb, self._free_cb
-        c.stream = ctypes.c_void_p(self.stream.cuda_stream)
-        self._cfg = c
-        h = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
-            rc = lib.lbehd_init(ctypes.byref(c), ctypes.byref(h))
-        if rc != 0:
-            raise LBEHDError(rc, lib.lbehd_last_error(None).decode())
-        self._h = h
-        self._lib = lib
-        self.n_electrodes = len(V)
-
-    # ----------------------------------------------------------------- calls
+        self.n_electrodes = len(w.params.get("V", []))
 
     def _check(self, rc, allow=()):
         if rc != 0 and rc not in allow:
             raise LBEHDError(rc, self._lib.lbehd_last_error(self._h).decode())
         return rc
-
-    def step(self, n=1):
-        """Advance n steps; returns 0 or -3 (a Poisson solve hit its cap)."""
-        return self._check(self._lib.lbehd_step(self._h, int(n)), allow=(-3,))
 
     def set_electrodes(self, V):
         V = np.ascontiguousarray(V, dtype=np.float64)
@@ -216,13 +224,7 @@ class Simulation:
     def observe(self):
         o = Obs()
         self._check(self._lib.lbehd_observe(self._h, ctypes.byref(o)))
-        return {
-            "step": o.step, "M1": o.M1, "centroid": np.array(o.centroid[:]),
-            "velocity": np.array(o.velocity[:]), "f_ele": np.array(o.f_ele[:]),
-            "f_ele_total": np.array(o.f_ele_total[:]), "f_drag": np.array(o.f_drag[:]),
-            "mass": np.array(o.mass[:]), "charge": o.charge, "poisson_iters": o.poisson_iters,
-            "poisson_resid": o.poisson_resid, "status": o.status,
-        }
+        return _obs_dict(o)
 
     def _shape_of(self, which):
         nz, ny, nx = self.shape
@@ -258,6 +260,53 @@ class Simulation:
                                         "stream": None}
         return self._torch.as_tensor(_View(), device=self.device)
 
+    def stats(self):
+        """Counters since init: steps, Poisson CG iterations, graph replays, kernels."""
+        st = Stats()
+        self._check(self._lib.lbehd_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def launch_count(self):
+        return int(self._lib.lbehd_launch_count(self._h))
+
+
+class Simulation(_HandleOps):
+    """One coupled LB-EHD run on the GPU.
+
+    ``workload``: a ``workloads.Workload`` (geometry, initial Phi, parameters).
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream).
+    ``torch_alloc``: take device memory from PyTorch's caching allocator.
+    """
+
+    def __init__(self, workload, *, stream=None, torch_alloc=True, device=0, **config_kw):
+        import torch
+        self._torch = torch
+        lib = load()
+        self._setup_shape(workload)
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        c = Config()
+        keep = make_config(workload, c, **config_kw)
+        if torch_alloc:
+            self._alloc_cb, self._free_cb = _torch_allocator(torch, self.device, self.stream)
+            c.alloc, c.free = self._alloc_cb, self._free_cb
+        c.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self._cfg = c
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lbehd_init(ctypes.byref(c), ctypes.byref(h))
+        del keep
+        if rc != 0:
+            raise LBEHDError(rc, lib.lbehd_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    # ----------------------------------------------------------------- calls
+
+    def step(self, n=1):
+        """Advance n steps; returns 0 or -3 (a Poisson solve hit its cap)."""
+        return self._check(self._lib.lbehd_step(self._h, int(n)), allow=(-3,))
+
     def profile(self, enable=True):
         """Record per-kernel device time with CUDA events on the library's stream."""
         self._check(self._lib.lbehd_profile_enable(self._h, int(bool(enable))))
@@ -272,19 +321,116 @@ class Simulation:
     def set_option(self, option, value):
         self._check(self._lib.lbehd_set_option(self._h, int(option), int(value)))
 
-    def stats(self):
-        """Counters since init: steps, Poisson CG iterations, graph replays, kernels."""
-        st = Stats()
-        self._check(self._lib.lbehd_get_stats(self._h, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in Stats._fields_}
-
-    def launch_count(self):
-        return int(self._lib.lbehd_launch_count(self._h))
+    def autotune(self, reps=20):
+        """Time every collide kernel this lattice can run (state untouched), keep the
+        fastest; returns (chosen variant, {variant: ms per launch})."""
+        ms = (ctypes.c_double * 4)()
+        rc = self._lib.lbehd_autotune(self._h, int(reps), ms)
+        if rc < 0:
+            self._check(rc)
+        return rc, {v + 1: ms[v] for v in range(4) if ms[v] >= 0}
 
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lbehd_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchInstance(_HandleOps):
+    """Instance i of a Batch: observables, arrays and electrode switching of that
+    instance. Stepping and options go through the Batch."""
+
+    def __init__(self, batch, i, h, workload):
+        self._batch = batch   # keeps the batch (which owns the handle) alive
+        self._torch = batch._torch
+        self._lib = batch._lib
+        self._h = ctypes.c_void_p(h)
+        self.index = i
+        self.device = batch.device
+        self._setup_shape(workload)
+
+
+class Batch:
+    """Many independent instances (``workloads``, same dim, any sizes and parameters)
+    advanced together: one CUDA graph launch per step for the whole batch."""
+
+    def __init__(self, workloads, *, stream=None, torch_alloc=True, device=0, **config_kw):
+        import torch
+        self._torch = torch
+        lib = load()
+        self._lib = lib
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cfgs = (Config * n)()
+        keep = [make_config(w, cfgs[i], **config_kw) for i, w in enumerate(self.workloads)]
+        if torch_alloc:
+            self._alloc_cb, self._free_cb = _torch_allocator(torch, self.device, self.stream)
+        for c in cfgs:
+            if torch_alloc:
+                c.alloc, c.free = self._alloc_cb, self._free_cb
+            c.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        b = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lbehd_batch_init(cfgs, n, ctypes.byref(b))
+        del keep
+        if rc != 0:
+            raise LBEHDError(rc, lib.lbehd_last_error(None).decode())
+        self._b = b
+        self.instances = [BatchInstance(self, i, lib.lbehd_batch_instance(b, i), w)
+                          for i, w in enumerate(self.workloads)]
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            raise LBEHDError(rc, self._lib.lbehd_batch_last_error(self._b).decode())
+        return rc
+
+    def step(self, n=1):
+        """Advance every instance n steps; returns 0 or -3 (a Poisson solve hit its cap)."""
+        return self._check(self._lib.lbehd_batch_step(self._b, int(n)), allow=(-3,))
+
+    def observe(self):
+        """Observables of every instance (one synchronisation)."""
+        n = len(self.instances)
+        out = (Obs * n)()
+        self._check(self._lib.lbehd_batch_observe(self._b, out))
+        return [_obs_dict(o) for o in out]
+
+    def set_option(self, option, value):
+        self._check(self._lib.lbehd_batch_set_option(self._b, int(option), int(value)))
+
+    def autotune(self, reps=20):
+        """Per-instance collide kernel choice; returns (variants, [{variant: ms}])."""
+        n = len(self.instances)
+        var, ms = (ctypes.c_int * n)(), (ctypes.c_double * (4 * n))()
+        self._check(self._lib.lbehd_batch_autotune(self._b, int(reps), var, ms))
+        return list(var), [{v + 1: ms[4 * i + v] for v in range(4) if ms[4 * i + v] >= 0}
+                           for i in range(n)]
+
+    def stats(self):
+        st = Stats()
+        self._check(self._lib.lbehd_batch_get_stats(self._b, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for inst in self.instances:
+                inst._h = None
+            self._lib.lbehd_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

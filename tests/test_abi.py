@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_binding_layout_matches_library(lib):
     from paper_2608_12868_b300 import lbehd
-    assert lib.lbehd_abi_version() == 1
+    assert lib.lbehd_abi_version() == 2
     assert lib.lbehd_config_size() == ctypes.sizeof(lbehd.Config)
     assert set(lbehd.EXPORTS) <= set(_declared())
 
@@ -62,3 +62,15 @@ def test_init_rejects_bad_configs_before_touching_the_gpu(lib):
     c.dim, c.nx, c.ny, c.nz = 3, 15, 8, 8
     assert lib.lbehd_init(ctypes.byref(c), ctypes.byref(h)) == -1
     assert b"even" in lib.lbehd_last_error(None)
+
+
+def test_batch_init_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_2608_12868_b300 import lbehd
+    cfgs = (lbehd.Config * 2)()
+    cfgs[0].dim, cfgs[1].dim = 3, 2
+    b = ctypes.c_void_p()
+    assert lib.lbehd_batch_init(cfgs, 0, ctypes.byref(b)) == -1
+    assert lib.lbehd_batch_init(cfgs, 2, ctypes.byref(b)) == -1
+    assert b"share dim" in lib.lbehd_last_error(None)
+    assert lib.lbehd_batch_size(None) == 0
+    assert lib.lbehd_batch_instance(None, 0) is None
