@@ -54,28 +54,30 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons, sampled every 50 ms with timestamps from before
+    the warm-up to the end of the last timed region; summary(t0, t1) keeps the samples
+    taken inside one timed region (host wall-clock seconds)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
 
-    def __exit__(self, *a):
-        self.lines = []
+    def stop(self):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -84,24 +86,37 @@ class ClockSampler:
                 self.proc.kill()
                 out = ""
             self.lines = [l for l in out.splitlines() if l.strip()]
+            self.proc = None
 
-    def summary(self):
+    @staticmethod
+    def _epoch(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def summary(self, t0, t1):
         sm, smax, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in getattr(self, "lines", []):
+        for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
+                continue
+            t = self._epoch(parts[0])
+            if t is None or not (t0 <= t <= t1):
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                sm.append(float(parts[2]))
+                smax = float(parts[3])
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
+            for name, val in zip(names, parts[6:10]):
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window_s": round(t1 - t0, 3), "sampler": "nvidia-smi -lms 50"}
 
 
 def dist_setup(args):
@@ -195,6 +210,7 @@ def run_ours(args, world, rank, local):
         sim.set_option(lbehd.OPT_COLLIDE, COLLIDE_CHOICES[args.collide])
     L = args.lb_steps
     fluid = int((w.solid == 0).sum())
+    clk = ClockSampler(local).start()
     for _ in range(args.warmup):
         sim.step(L)
     torch.cuda.synchronize(dev)
@@ -210,12 +226,13 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            sim.step(L)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
+    t_region0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(L)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_region1 = time.time()
     barrier(world)
     ms = ev0.elapsed_time(ev1)
     st1 = sim.stats()
@@ -265,7 +282,10 @@ def run_ours(args, world, rank, local):
 
     batched = None
     if args.batched > 0:
-        batched = run_batched(args, dev, value / world, peak, peak_kind)
+        batched = run_batched(args, dev, value / world, peak, peak_kind, clk)
+    clk.stop()
+    if batched is not None:
+        batched["clocks"] = clk.summary(*batched.pop("window"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -274,7 +294,7 @@ def run_ours(args, world, rank, local):
                "sample": f"first {done} coupled steps of the same lattice, FP64, {dt:.1f} s"}
 
     if rank == 0:
-        clocks = clk.summary()
+        clocks = clk.summary(t_region0, t_region1)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -311,7 +331,7 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def run_batched(args, dev, plain_mlups, peak, peak_kind):
+def run_batched(args, dev, plain_mlups, peak, peak_kind, clk):
     """The 64-instance sweep (uneven 3D lattices from 48^3 to 128x64x64, viscosity ratio,
     contact angle and electrode potential drawn per instance) as one batch: per-instance
     collide kernels from the autotuner, one graph launch per coupled step for all
@@ -328,7 +348,7 @@ def run_batched(args, dev, plain_mlups, peak, peak_kind):
     variants, _ = batch.autotune(reps=10)
     torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t0
-    L = args.lb_steps
+    L = args.batched_lb_steps
     for _ in range(args.warmup):
         batch.step(L)
     torch.cuda.synchronize(dev)
@@ -340,11 +360,13 @@ def run_batched(args, dev, plain_mlups, peak, peak_kind):
     st0 = batch.stats()
     steps = max(1, args.batched_steps)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_region0 = time.time()
     ev0.record(stream)
     for _ in range(steps):
         batch.step(L)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    t_region1 = time.time()
     ms = ev0.elapsed_time(ev1)
     st1 = batch.stats()
     obs = batch.observe()
@@ -366,7 +388,7 @@ def run_batched(args, dev, plain_mlups, peak, peak_kind):
         "step_gbs_model": gbs, "step_model_frac": gbs / peak, "peak_source": peak_kind,
         "collide_variants": dict(collections.Counter(VARIANT_NAMES[v] for v in variants)),
         "setup_s": setup_s, "status_all_ok": all(o["status"] == 0 for o in obs),
-        "mass_drift": drift,
+        "mass_drift": drift, "window": (t_region0, t_region1),
     }
     batch.close()
     return out
@@ -404,12 +426,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="droplet_3d_128x64x64")
-    ap.add_argument("--lb-steps", type=int, default=20)
+    ap.add_argument("--lb-steps", type=int, default=200,
+                    help="coupled steps per benchmark step (200: ~42 ms on 128x64x64)")
     ap.add_argument("--warmup-seconds", type=float, default=2.0)
     ap.add_argument("--collide", choices=["tune"] + list(COLLIDE_CHOICES), default="tune")
     ap.add_argument("--batched", type=int, default=64,
                     help="instances of the batched sweep measured after the plain arm (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-lb-steps", type=int, default=20,
+                    help="coupled steps per timed batched step (20: ~0.2 s for 64 instances)")
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)

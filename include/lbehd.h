@@ -266,8 +266,8 @@ void lbehd_destroy(lbehd_handle *h);
  * cfgs[i].poisson_mode says. */
 typedef struct lbehd_batch lbehd_batch;
 
-/* Initialise n >= 1 instances from cfgs[0..n) (each as lbehd_init would; host arrays are
- * borrowed for the call). On failure nothing is left allocated and the message is in
+/* Initialise 1 <= n <= 64 instances from cfgs[0..n) (each as lbehd_init would; host arrays
+ * are borrowed for the call). On failure nothing is left allocated and the message is in
  * lbehd_last_error(NULL). */
 int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out);
 
@@ -299,6 +299,12 @@ int lbehd_batch_autotune(lbehd_batch *b, int reps, int *variants, double *ms);
 /* Counters of the whole batch: steps (per instance), Poisson iterations and kernels summed
  * over instances, graph_launches = batch step graphs launched. Synchronises. */
 int lbehd_batch_get_stats(lbehd_batch *b, lbehd_stats *out);
+
+/* Per-kernel device time of the batch, as lbehd_profile_enable / lbehd_profile_read for one
+ * handle: while enabled, batch steps run as eager launches (the same kernels as the step
+ * graph, the loop conditions read back by the host) bracketed by CUDA events. */
+int lbehd_batch_profile_enable(lbehd_batch *b, int enable);
+int lbehd_batch_profile_read(lbehd_batch *b, double *ms, long long *count);
 
 /* Message of the batch's last error. */
 const char *lbehd_batch_last_error(lbehd_batch *b);

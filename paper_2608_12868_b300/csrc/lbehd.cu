@@ -16,6 +16,7 @@
 #include "batch.cuh"
 #include "kernels.cuh"
 #include "poisson.cuh"
+#include "poisson_batch.cuh"
 
 namespace lbehd {
 
@@ -72,6 +73,7 @@ struct lbehd_handle {
     CgScalars *h_cg = nullptr;     // pinned copy for the host convergence check
     dim3 grid1d;
     size_t nblocks1d = 0;
+    size_t nblocks_site = 0;       // blocks of BX consecutive sites (stencil reductions)
     // CUDA graphs of one step per step parity (LBEHD_POISSON_GRAPH)
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][refresh]
     cudaGraphConditionalHandle cond = 0, cond_ref = 0;
@@ -303,9 +305,10 @@ void pcg_iteration(lbehd_handle *h, float *x)
         k_pcg_dot<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_r, L0.x, h->cg_partials);
         cg_scalar(h, 1, 1, h->nblocks1d);
         k_pcg_p<<<h->grid1d, h->block, 0, h->ls>>>(h->N, L0.x, h->cg_p, h->cg_s);
-        k_pcg_Ap<D><<<L0.grid, h->block, 0, h->ls>>>(h->P, h->eps, h->info, L0.D, h->cg_p,
-                                                      h->cg_q, h->cg_partials);
-        cg_scalar(h, 1, 2, h->nblocks);
+        k_pcg_Ap<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(L0.d, h->eps, h->info, L0.D,
+                                                                       h->cg_p, h->cg_q,
+                                                                       h->cg_partials);
+        cg_scalar(h, 1, 2, h->nblocks_site);
         k_pcg_update<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_p, h->cg_q, x, h->cg_r,
                                                              h->cg_s, h->cg_partials);
         cg_scalar(h, 1, 3, h->nblocks1d);
@@ -325,10 +328,10 @@ void pcg_start(lbehd_handle *h, const float *x, int op = 0)
 {
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_CG, 2, [&] {
-        k_pcg_init<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->pot, h->pot_lo, x, h->eps,
-                                                            h->rho[h->pcur], h->info, L0.D,
-                                                            h->cg_r, h->cg_partials);
-        cg_scalar(h, 2, op, h->nblocks);
+        k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
+            L0.d, h->pot, h->pot_lo, x, h->eps, h->rho[h->pcur], h->info, L0.D, h->cg_r,
+            h->cg_partials);
+        cg_scalar(h, 2, op, h->nblocks_site);
     });
 }
 
@@ -369,7 +372,7 @@ void mg_setup(lbehd_handle *h)
 {
     auto &L0 = h->mg[0];
     launch(h, LBEHD_KC_MG, (int)h->mg.size(), [&] {
-        k_mg_setup0<D><<<h->grid, h->block, 0, h->ls>>>(h->P, h->eps, h->info, L0.D, L0.kx,
+        k_mg_setup0<D><<<h->grid, h->block, 0, h->ls>>>(L0.d, h->eps, h->info, L0.D, L0.kx,
                                                              L0.ky, L0.kz);
         for (size_t l = 0; l + 1 < h->mg.size(); l++) {
             const auto &F = h->mg[l];
@@ -845,6 +848,7 @@ int init_impl(lbehd_handle *h)
         h->grid1d = dim3((unsigned)std::min(want, cap), 1, 1);
     }
     h->nblocks1d = h->grid1d.x;
+    h->nblocks_site = (N + BX - 1) / BX;
     h->inc[0] = (float *)dev_alloc(h, N * fb);
     h->inc[1] = (float *)dev_alloc(h, N * fb);
     h->delta2 = (float *)dev_alloc(h, N * fb);
@@ -856,7 +860,7 @@ int init_impl(lbehd_handle *h)
     if (!h->inc[0] || !h->inc[1] || !h->delta2 || !h->cg_r || !h->cg_p || !h->cg_q || !h->cg_partials || !h->cg_s)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (Poisson)");
     {
-        MgDims d{h->nx, h->ny, h->nz};
+        MgDims d = mg_dims(h->nx, h->ny, h->nz);
         const int maxl = c.mg_max_levels > 0 ? c.mg_max_levels : 16;
         while ((int)h->mg.size() < maxl) {
             lbehd_handle::Level L;
@@ -878,13 +882,17 @@ int init_impl(lbehd_handle *h)
             h->mg.push_back(L);
             if (!more)
                 break;
-            d = MgDims{d.nx / 2, d.ny / 2, h->dim == 3 ? (d.nz + 1) / 2 : 1};
+            d = mg_dims(d.nx / 2, d.ny / 2, h->dim == 3 ? (d.nz + 1) / 2 : 1);
         }
         h->mg.back().cz2 = 0;
-        // shared-memory tail: the first level with <= TAIL_MAX_CELLS cells and all below
+        // shared-memory tail: the first level from which all coarser levels together have
+        // <= TAIL_MAX_TOTAL cells
         for (size_t l = 0; l < h->mg.size(); l++) {
             const size_t nl = h->mg.size() - l;
-            if (h->mg[l].n <= (size_t)TAIL_MAX_CELLS && nl <= (size_t)TAIL_MAX_LEVELS) {
+            size_t cells_below = 0;
+            for (size_t k = l; k < h->mg.size(); k++)
+                cells_below += h->mg[k].n;
+            if (cells_below <= (size_t)TAIL_MAX_TOTAL && nl <= (size_t)TAIL_MAX_LEVELS) {
                 TailLevels &T = h->tail;
                 T.nl = (int)nl;
                 T.nu = h->mg_nu;
@@ -904,9 +912,10 @@ int init_impl(lbehd_handle *h)
                 T.total = off;
                 h->tail_smem = 6 * (size_t)off * sizeof(float);
                 h->tail_level = (int)l;
-                if (h->tail_smem > 48 * 1024)
-                    CK(h, cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)h->tail_smem));
+                // the attribute belongs to the kernel, not the handle: set it to the largest
+                // tail any handle can have
+                CK(h, cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)TAIL_SMEM_MAX));
                 break;
             }
         }
@@ -1171,11 +1180,27 @@ struct lbehd_batch {
     void (*free)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
     PopMaps *maps = nullptr;           // device: [2][n] tensor maps, per step parity
+    TailLevels *tails = nullptr;       // device: [n] shared-memory tails (b0, x0 set)
+    ActiveLists *act = nullptr;        // device: instances active in each mode
+    int cta_cap = 2368;                // CTAs of a batched Poisson launch (16 per SM)
+    int *counters = nullptr;           // device: loop-condition counts [3], then loop passes
+                                       //   [3] main CG, [4] refinement CG, [5] refinement blocks
     double *h_obs = nullptr;           // pinned: [n][2 NOBS] observables, then [n] flags
+    cudaStream_t aux = nullptr, aux2 = nullptr;   // capture of conditional-node bodies
+    cudaStream_t ls = nullptr;         // stream the batched launches are enqueued on
+    size_t tail_smem = 0;              // largest tail's shared memory
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][refresh]
     long long static_kernels[2][2] = {{0, 0}, {0, 0}};
-    long long launches = 0, graph_launches = 0;
+    long long loop_kernels[3] = {0, 0, 0};   // kernels per main / refinement CG pass, per
+                                             //   refinement block (outside its loop)
+    long long *count = nullptr;        // where the launch being recorded is counted
+    long long counters0[3] = {0, 0, 0};   // loop passes when graph replays began
+    long long launches = 0, graph_launches = 0, launches_rec = 0;
     bool graphs_started = false;
+    int *h_flags = nullptr;            // pinned: loop conditions of an eager step
+    bool prof = false;                 // eager steps with CUDA events around every launch
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[LBEHD_NKC];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::string err;
 };
 
@@ -1228,13 +1253,503 @@ template <int D>
 void launch_collide_chunk(lbehd_batch *b, int v, const CollideBatch &A, int blocks)
 {
     if (v == 1)
-        k_collide_batch<D><<<blocks, BX, 0, b->stream>>>(A);
+        k_collide_batch<D><<<blocks, BX, 0, b->ls>>>(A);
     else if (v == 2)
-        k_collide_staged_batch<D, 4><<<blocks, BX, staged_smem_bytes<D, 4>(), b->stream>>>(A);
+        k_collide_staged_batch<D, 4><<<blocks, BX, staged_smem_bytes<D, 4>(), b->ls>>>(A);
     else if (v == 3)
-        k_collide_staged_batch<D, 2><<<blocks, BX, staged_smem_bytes<D, 2>(), b->stream>>>(A);
+        k_collide_staged_batch<D, 2><<<blocks, BX, staged_smem_bytes<D, 2>(), b->ls>>>(A);
     else
-        k_collide_staged_batch<D, 8><<<blocks, BX, staged_smem_bytes<D, 8>(), b->stream>>>(A);
+        k_collide_staged_batch<D, 8><<<blocks, BX, staged_smem_bytes<D, 8>(), b->ls>>>(A);
+}
+
+// ------------------------------------------------------------ batched Gauss-law solve
+
+// Table header of a batched Poisson launch over instances `ids` with `blocks(k)` blocks for
+// instance k; returns the launch's block count.
+// Table header of a batched Poisson launch: instances `ids` take part with blocks(k) work
+// items each (the others with none); returns the grid: one CTA per work item of all of
+// them, capped at b->cta_cap (the CTAs then walk the work items of the active instances).
+template <class NB>
+int fill_grid_set(lbehd_batch *b, GridSet &g, const std::vector<int> &ids, int mode, NB blocks)
+{
+    const int n = (int)b->inst.size();
+    g.n = n;
+    g.mode = mode;
+    g.act = b->act;
+    for (int k = 0; k < n; k++) {
+        g.blocks[k] = 0;
+        g.s[k] = b->inst[k]->cg_s;
+    }
+    long long tot = 0;
+    for (int k : ids) {
+        g.blocks[k] = (int)blocks(k);
+        tot += g.blocks[k];
+    }
+    return (int)std::min<long long>(tot, b->cta_cap);
+}
+
+inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
+inline long long dims_cells(const MgDims &d) { return (long long)d.nx * d.ny * d.nz; }
+
+// MgBatch for level level(k) of each instance k in ids (the coarser level's arrays too).
+template <class LV>
+void fill_mg(lbehd_batch *b, MgBatch &A, const std::vector<int> &ids, LV level)
+{
+    for (int k : ids) {
+        const lbehd_handle *h = b->inst[k];
+        const int l = level(k);
+        const auto &L = h->mg[l];
+        MgInst &m = A.m[k];
+        std::memset(&m, 0, sizeof(m));
+        m.f = L.d;
+        m.cz2 = L.cz2;
+        m.scale = h->mg_scale;
+        m.eps = h->eps;
+        m.info = h->info;
+        m.D = L.D;
+        m.kx = L.kx;
+        m.ky = L.ky;
+        m.kz = L.kz;
+        m.b = L.b;
+        m.x = L.x;
+        if (l + 1 < (int)h->mg.size()) {
+            const auto &C = h->mg[l + 1];
+            m.c = C.d;
+            m.Dc = C.D;
+            m.kxc = C.kx;
+            m.kyc = C.ky;
+            m.kzc = C.kz;
+            m.bc = C.b;
+            m.xc = C.x;
+        }
+    }
+}
+
+// Launch through here: counts the launch and, while profiling, brackets it with events.
+template <class F>
+void blaunch_fn(lbehd_batch *b, int kc, F &&fn)
+{
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (b->prof) {
+        if (!b->ev_pool.empty()) {
+            ev = b->ev_pool.back();
+            b->ev_pool.pop_back();
+        } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
+                   cudaEventCreate(&ev.second) != cudaSuccess) {
+            ev = {nullptr, nullptr};
+        }
+        if (ev.first)
+            cudaEventRecord(ev.first, b->ls);
+    }
+    fn();
+    if (b->count)
+        ++*b->count;
+    if (ev.first) {
+        cudaEventRecord(ev.second, b->ls);
+        b->ev_pending[kc].push_back(ev);
+    }
+}
+
+template <class K, class T>
+void blaunch(lbehd_batch *b, K kernel, const T &tab, int blocks, int threads, size_t smem = 0,
+             int kc = LBEHD_KC_MG)
+{
+    if (blocks <= 0)
+        return;
+    blaunch_fn(b, kc, [&] { kernel<<<blocks, threads, smem, b->ls>>>(tab); });
+}
+
+// Multigrid levels of instance k handled by separate launches: those above its shared-memory
+// tail, or all but the coarsest when it has none.
+int mg_depth(const lbehd_handle *h)
+{
+    return h->tail_level >= 0 ? h->tail_level : (int)h->mg.size() - 1;
+}
+
+// One symmetric V-cycle of every active instance, level-synchronous: the same sequence of
+// operations as vcycle() per instance.
+void batch_vcycle(lbehd_batch *b, MgBatch &A, int mode)
+{
+    const int n = (int)b->inst.size();
+    int maxd = 0, max_nu = 0, max_coarse = 0;
+    for (int k = 0; k < n; k++) {
+        maxd = std::max(maxd, mg_depth(b->inst[k]));
+        max_nu = std::max(max_nu, b->inst[k]->mg_nu);
+        max_coarse = std::max(max_coarse, b->inst[k]->mg_coarse);
+    }
+    auto above = [&](int l) {
+        std::vector<int> ids;
+        for (int k = 0; k < n; k++)
+            if (l < mg_depth(b->inst[k]))
+                ids.push_back(k);
+        return ids;
+    };
+    auto at = [](int l) { return [l](int) { return l; }; };
+    // the instances of ids still sweeping at sweep index sw (reps(k) sweeps each)
+    auto sweeping = [](const std::vector<int> &ids, int sw, auto reps) {
+        std::vector<int> out;
+        for (int k : ids)
+            if (sw < reps(k))
+                out.push_back(k);
+        return out;
+    };
+    auto nu_of = [&b](int k) { return b->inst[k]->mg_nu; };
+    auto cells_f = [&](int l) {
+        return [&b, l](int k) { return ceil_div(dims_cells(b->inst[k]->mg[l].d), BX); };
+    };
+    for (int l = 0; l < maxd; l++) {
+        const std::vector<int> ids = above(l);
+        fill_mg(b, A, ids, at(l));
+        blaunch(b, k_mg_zero_batch, A, fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
+        auto half = [&b, l](int k) {
+            const MgDims &d = b->inst[k]->mg[l].d;
+            return ceil_div((long long)(d.nx / 2) * d.ny * d.nz, BX);
+        };
+        for (int sw = 0; sw < max_nu; sw++) {
+            const int hb = fill_grid_set(b, A.g, sweeping(ids, sw, nu_of), mode, half);
+            for (int color = 0; color < 2; color++) {
+                A.color = color;
+                A.sweep = sw;
+                blaunch(b, k_mg_gs_batch, A, hb, BX);
+            }
+        }
+        auto coarse_cells = [&b, l](int k) {
+            return ceil_div(dims_cells(b->inst[k]->mg[l + 1].d), BX);
+        };
+        blaunch(b, k_mg_restrict_batch, A, fill_grid_set(b, A.g, ids, mode, coarse_cells), BX);
+    }
+    // bottom: shared-memory tails, and the coarsest-level sweeps of instances without one
+    {
+        std::vector<int> tail_ids, coarse_ids;
+        for (int k = 0; k < n; k++)
+            (b->inst[k]->tail_level >= 0 ? tail_ids : coarse_ids).push_back(k);
+        if (!tail_ids.empty()) {
+            std::unique_ptr<TailBatch> T(new TailBatch);
+            std::memset(T.get(), 0, sizeof(TailBatch));
+            const int blocks = fill_grid_set(b, T->g, tail_ids, mode, [](int) { return 1; });
+            for (int k : tail_ids)
+                T->T[k] = b->tails + k;
+            blaunch(b, k_mg_tail_batch, *T, blocks, TAIL_THREADS, b->tail_smem);
+        }
+        if (!coarse_ids.empty()) {
+            auto lev = [&b](int k) { return (int)b->inst[k]->mg.size() - 1; };
+            fill_mg(b, A, coarse_ids, lev);
+            blaunch(b, k_mg_zero_batch, A, fill_grid_set(b, A.g, coarse_ids, mode, [&b, &lev](int k) {
+                        return ceil_div(dims_cells(b->inst[k]->mg[lev(k)].d), BX);
+                    }), BX);
+            auto coarse_of = [&b](int k) { return b->inst[k]->mg_coarse; };
+            for (int sw = 0; sw < max_coarse; sw++) {
+                const int hb = fill_grid_set(b, A.g, sweeping(coarse_ids, sw, coarse_of), mode,
+                                             [&b, &lev](int k) {
+                                                 const MgDims &d = b->inst[k]->mg[lev(k)].d;
+                                                 return ceil_div((long long)(d.nx / 2) * d.ny * d.nz, BX);
+                                             });
+                for (int color : {0, 1, 1, 0}) {
+                    A.color = color;
+                    A.sweep = sw;
+                    blaunch(b, k_mg_gs_batch, A, hb, BX);
+                }
+            }
+        }
+    }
+    for (int l = maxd - 1; l >= 0; l--) {
+        const std::vector<int> ids = above(l);
+        fill_mg(b, A, ids, at(l));
+        blaunch(b, k_mg_prolong_batch, A, fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
+        auto half = [&b, l](int k) {
+            const MgDims &d = b->inst[k]->mg[l].d;
+            return ceil_div((long long)(d.nx / 2) * d.ny * d.nz, BX);
+        };
+        for (int sw = 0; sw < max_nu; sw++) {
+            const int hb = fill_grid_set(b, A.g, sweeping(ids, sw, nu_of), mode, half);
+            for (int color = 1; color >= 0; color--) {
+                A.color = color;
+                A.sweep = sw;
+                blaunch(b, k_mg_gs_batch, A, hb, BX);
+            }
+        }
+    }
+}
+
+// CG table of every instance; x(h) is the increment solved for, acc(h) where apply adds it.
+template <class XF, class AF>
+void fill_cg(lbehd_batch *b, CgBatch &C, int parity, XF xsel, AF accsel)
+{
+    for (size_t k = 0; k < b->inst.size(); k++) {
+        lbehd_handle *h = b->inst[k];
+        CgInst &c = C.c[k];
+        std::memset(&c, 0, sizeof(c));
+        c.d = h->mg[0].d;
+        c.nbs = (int)h->nblocks_site;
+        c.nb1d = (int)h->nblocks1d;
+        c.pot = h->pot;
+        c.pot_lo = h->pot_lo;
+        c.eps = h->eps;
+        c.rho = h->rho[parity];
+        c.info = h->info;
+        c.Dg = h->mg[0].D;
+        c.r = h->cg_r;
+        c.p = h->cg_p;
+        c.q = h->cg_q;
+        c.z = h->mg[0].x;
+        c.x = xsel(h);
+        c.acc = accsel(h);
+        c.partials = h->cg_partials;
+    }
+}
+
+std::vector<int> all_ids(const lbehd_batch *b)
+{
+    std::vector<int> ids(b->inst.size());
+    for (size_t k = 0; k < ids.size(); k++)
+        ids[k] = (int)k;
+    return ids;
+}
+
+int part3d(const lbehd_handle *h) { return (int)h->nblocks_site; }
+int part1d(const lbehd_handle *h) { return (int)h->nblocks1d; }
+
+void batch_scalar(lbehd_batch *b, ScalarBatch &S, int mode, int nv, int op, bool by3d,
+                  int loop_mode, cudaGraphConditionalHandle cond, bool set_ref,
+                  cudaGraphConditionalHandle cond_ref)
+{
+    std::memset(&S, 0, sizeof(S));
+    const std::vector<int> ids = all_ids(b);
+    fill_grid_set(b, S.g, ids, mode, [](int) { return 1; });
+    for (size_t k = 0; k < ids.size(); k++) {
+        const lbehd_handle *h = b->inst[k];
+        S.partials[k] = h->cg_partials;
+        S.nblocks[k] = by3d ? part3d(h) : part1d(h);
+    }
+    S.nv = nv;
+    S.op = op;
+    S.loop_mode = loop_mode;
+    S.set_ref = set_ref ? 1 : 0;
+    S.cond = cond;
+    S.cond_ref = cond_ref;
+    S.counters = b->counters;
+    S.act = b->act;
+    S.eager = b->prof ? 1 : 0;
+    blaunch(b, k_pcg_scalar_batch, S, (int)ids.size(), SCALAR_THREADS, 0, LBEHD_KC_CG);
+}
+
+// r = b - A (phi + x) and the CG start of every instance active in `mode`.
+template <int D>
+void batch_pcg_start(lbehd_batch *b, CgBatch &C, ScalarBatch &S, int mode, int op, int loop_mode,
+                     cudaGraphConditionalHandle cond, bool set_ref,
+                     cudaGraphConditionalHandle cond_ref)
+{
+    const std::vector<int> ids = all_ids(b);
+    const int blocks = fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part3d(b->inst[k]); });
+    blaunch(b, k_pcg_init_batch<D>, C, blocks, BX, 0, LBEHD_KC_CG);
+    batch_scalar(b, S, mode, 2, op, true, loop_mode, cond, set_ref, cond_ref);
+}
+
+// One preconditioned CG iteration of every instance active in `mode`.
+template <int D>
+void batch_pcg_iteration(lbehd_batch *b, MgBatch &A, CgBatch &C, ScalarBatch &S, int mode,
+                         int op, cudaGraphConditionalHandle cond, bool set_ref,
+                         cudaGraphConditionalHandle cond_ref)
+{
+    const std::vector<int> ids = all_ids(b);
+    batch_vcycle(b, A, mode);
+    const int b1 = fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part1d(b->inst[k]); });
+    blaunch(b, k_pcg_dot_batch, C, b1, BX, 0, LBEHD_KC_CG);
+    batch_scalar(b, S, mode, 1, 1, false, -1, cond, false, cond_ref);
+    fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part1d(b->inst[k]); });
+    blaunch(b, k_pcg_p_batch, C, b1, BX, 0, LBEHD_KC_CG);
+    const int b3 = fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part3d(b->inst[k]); });
+    blaunch(b, k_pcg_Ap_batch<D>, C, b3, BX, 0, LBEHD_KC_CG);
+    batch_scalar(b, S, mode, 1, 2, true, -1, cond, false, cond_ref);
+    fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part1d(b->inst[k]); });
+    blaunch(b, k_pcg_update_batch, C, b1, BX, 0, LBEHD_KC_CG);
+    batch_scalar(b, S, mode, 1, op, false, mode, cond, set_ref, cond_ref);
+}
+
+void batch_pcg_apply(lbehd_batch *b, CgBatch &C, int mode)
+{
+    const int b1 = fill_grid_set(b, C.g, all_ids(b), mode, [&b](int k) { return part1d(b->inst[k]); });
+    blaunch(b, k_pcg_apply_batch, C, b1, BX, 0, LBEHD_KC_CG);
+}
+
+// Conditional node on the ongoing capture of `cap`, body captured from `body` on `bs`.
+template <class F>
+int batch_add_cond(lbehd_batch *b, cudaStream_t cap, cudaStream_t bs,
+                   cudaGraphConditionalHandle cond, cudaGraphConditionalNodeType type, F &&body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    BCK(b, cudaStreamGetCaptureInfo(cap, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    BCK(b, cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+    BCK(b, cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+    const cudaStream_t prev = b->ls;
+    b->ls = bs;
+    const int rc = body();
+    b->ls = prev;
+    cudaGraph_t out = nullptr;
+    BCK(b, cudaStreamEndCapture(bs, &out));
+    if (rc)
+        return rc;
+    BCK(b, cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies));
+    return LBEHD_OK;
+}
+
+// Multigrid hierarchy of every instance from this step's permittivity.
+template <int D>
+void batch_mg_setup(lbehd_batch *b, MgBatch &A)
+{
+    const std::vector<int> ids = all_ids(b);
+    const int n = (int)ids.size();
+    fill_mg(b, A, ids, [](int) { return 0; });
+    blaunch(b, k_mg_setup0_batch<D>, A, fill_grid_set(b, A.g, ids, 0, [&b](int k) {
+                return ceil_div((long long)b->inst[k]->N, BX);
+            }), BX);
+    int levels = 0;
+    for (int k = 0; k < n; k++)
+        levels = std::max(levels, (int)b->inst[k]->mg.size());
+    for (int l = 0; l + 1 < levels; l++) {
+        std::vector<int> lid;
+        for (int k = 0; k < n; k++)
+            if (l + 1 < (int)b->inst[k]->mg.size())
+                lid.push_back(k);
+        fill_mg(b, A, lid, [l](int) { return l; });
+        blaunch(b, k_mg_coarsen_batch, A, fill_grid_set(b, A.g, lid, 0, [&b, l](int k) {
+                    return ceil_div(dims_cells(b->inst[k]->mg[l + 1].d), BX);
+                }), BX);
+    }
+}
+
+// delta2 = 0 on the instances active in `mode`.
+void batch_zero_delta2(lbehd_batch *b, MgBatch &A, int mode)
+{
+    const std::vector<int> ids = all_ids(b);
+    fill_mg(b, A, ids, [](int) { return 0; });
+    for (size_t k = 0; k < ids.size(); k++)
+        A.m[k].x = b->inst[k]->delta2;
+    blaunch(b, k_mg_zero_batch, A, fill_grid_set(b, A.g, ids, mode, [&b](int k) {
+                return ceil_div((long long)b->inst[k]->N, BX);
+            }), BX, 0, LBEHD_KC_CG);
+}
+
+int read_flags(lbehd_batch *b, int &act, int &ref)
+{
+    BCK(b, cudaMemcpyAsync(b->h_flags, b->counters + 6, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    act = b->h_flags[0];
+    ref = b->h_flags[1];
+    return LBEHD_OK;
+}
+
+// The same solve as record_batch_poisson with the loop conditions read back by the host
+// (eager launches, for profiling).
+template <int D>
+int eager_batch_poisson(lbehd_batch *b, int parity, int refresh)
+{
+    std::unique_ptr<MgBatch> A(new MgBatch);
+    std::unique_ptr<CgBatch> C(new CgBatch);
+    std::unique_ptr<ScalarBatch> S(new ScalarBatch);
+    std::memset(A.get(), 0, sizeof(MgBatch));
+    std::memset(C.get(), 0, sizeof(CgBatch));
+    if (refresh)
+        batch_mg_setup<D>(b, *A);
+    auto inc = [parity](lbehd_handle *h) { return h->inc[parity]; };
+    auto none = [](lbehd_handle *) -> float * { return nullptr; };
+    auto del = [](lbehd_handle *h) { return h->delta2; };
+    int act = 0, ref = 0, junk = 0, rc;
+    fill_cg(b, *C, parity, inc, none);
+    batch_pcg_start<D>(b, *C, *S, 0, 0, 1, 0, true, 0);
+    if ((rc = read_flags(b, act, ref)))
+        return rc;
+    while (act) {
+        batch_pcg_iteration<D>(b, *A, *C, *S, 1, 3, 0, true, 0);
+        if ((rc = read_flags(b, act, ref)))
+            return rc;
+    }
+    batch_pcg_apply(b, *C, 0);
+    if (!ref)
+        return LBEHD_OK;
+    batch_zero_delta2(b, *A, 2);
+    fill_cg(b, *C, parity, del, none);
+    batch_pcg_start<D>(b, *C, *S, 2, 4, 3, 0, false, 0);
+    if ((rc = read_flags(b, act, junk)))
+        return rc;
+    while (act) {
+        batch_pcg_iteration<D>(b, *A, *C, *S, 3, 5, 0, false, 0);
+        if ((rc = read_flags(b, act, junk)))
+            return rc;
+    }
+    fill_cg(b, *C, parity, del, inc);
+    batch_pcg_apply(b, *C, 2);
+    return LBEHD_OK;
+}
+
+// The Gauss-law solves of all instances for one step (the batched counterpart of the
+// Poisson part of record_step): multigrid rebuild when `refresh`; start; CG loop while any
+// instance is unconverged; apply; then, if any instance iterated, the refinement block for
+// those instances with its own loop.
+template <int D>
+int record_batch_poisson(lbehd_batch *b, cudaGraph_t g, int parity, int refresh)
+{
+    std::unique_ptr<MgBatch> A(new MgBatch);
+    std::unique_ptr<CgBatch> C(new CgBatch);
+    std::unique_ptr<ScalarBatch> S(new ScalarBatch);
+    std::memset(A.get(), 0, sizeof(MgBatch));
+    std::memset(C.get(), 0, sizeof(CgBatch));
+    const std::vector<int> ids = all_ids(b);
+    if (refresh)
+        batch_mg_setup<D>(b, *A);
+    cudaGraphConditionalHandle c1 = 0, c2 = 0, cr = 0;
+    BCK(b, cudaGraphConditionalHandleCreate(&c1, g, 0, 0));
+    BCK(b, cudaGraphConditionalHandleCreate(&c2, g, 0, 0));
+    BCK(b, cudaGraphConditionalHandleCreate(&cr, g, 0, 0));
+    auto inc = [parity](lbehd_handle *h) { return h->inc[parity]; };
+    auto none = [](lbehd_handle *) -> float * { return nullptr; };
+    auto del = [](lbehd_handle *h) { return h->delta2; };
+    fill_cg(b, *C, parity, inc, none);
+    batch_pcg_start<D>(b, *C, *S, 0, 0, 1, c1, true, cr);
+    int rc = batch_add_cond(b, b->stream, b->aux, c1, cudaGraphCondTypeWhile, [&]() -> int {
+        long long *prev = b->count;
+        b->loop_kernels[0] = 0;
+        b->count = &b->loop_kernels[0];
+        batch_pcg_iteration<D>(b, *A, *C, *S, 1, 3, c1, true, cr);
+        b->count = prev;
+        return LBEHD_OK;
+    });
+    if (rc)
+        return rc;
+    batch_pcg_apply(b, *C, 0);
+    rc = batch_add_cond(b, b->stream, b->aux, cr, cudaGraphCondTypeIf, [&]() -> int {
+        long long *prev = b->count;
+        b->loop_kernels[2] = 0;
+        b->count = &b->loop_kernels[2];
+        batch_zero_delta2(b, *A, 2);
+        fill_cg(b, *C, parity, del, none);
+        batch_pcg_start<D>(b, *C, *S, 2, 4, 3, c2, false, cr);
+        const int r2 = batch_add_cond(b, b->aux, b->aux2, c2, cudaGraphCondTypeWhile, [&]() -> int {
+            long long *prev2 = b->count;
+            b->loop_kernels[1] = 0;
+            b->count = &b->loop_kernels[1];
+            batch_pcg_iteration<D>(b, *A, *C, *S, 3, 5, c2, false, cr);
+            b->count = prev2;
+            return LBEHD_OK;
+        });
+        fill_cg(b, *C, parity, del, inc);
+        batch_pcg_apply(b, *C, 2);
+        b->count = prev;
+        return r2;
+    });
+    return rc;
 }
 
 // Blocks of one instance in the batched collide launch of variant v.
@@ -1243,15 +1758,12 @@ long long collide_blocks(const lbehd_handle *h, int v)
     return v == 1 ? (long long)((h->N + BX - 1) / BX) : (long long)h->nblocks_tile[tile_shape(v)];
 }
 
-// The whole batch's step for one parity as one graph: the moments of every instance (one
-// launch per 64 instances), then each instance's Poisson solve as its own branch, then
-// the collide kernels (one launch per group of instances running the same kernel, the
-// groups as parallel branches), then the observable sums of every instance.
-template <int D>
-int capture_batch(lbehd_batch *b, int parity, int refresh)
+// Instances grouped by collide kernel (order[]), and their tensor maps for `parity` in that
+// order in the device table.
+int batch_prepare_collide(lbehd_batch *b, int parity, std::vector<int> &order)
 {
     const int n = (int)b->inst.size();
-    std::vector<int> order;   // instances grouped by collide kernel
+    order.clear();
     for (int v = 1; v <= 4; v++)
         for (int i = 0; i < n; i++)
             if (resolved_variant(b->inst[i]) == v)
@@ -1265,102 +1777,120 @@ int capture_batch(lbehd_batch *b, int parity, int refresh)
         else
             std::memset(&hm[k], 0, sizeof(PopMaps));
     }
-    PopMaps *dmaps = b->maps + (size_t)parity * n;
-    BCK(b, cudaMemcpyAsync(dmaps, hm.data(), n * sizeof(PopMaps), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->maps + (size_t)parity * n, hm.data(), n * sizeof(PopMaps),
+                           cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
+    return LBEHD_OK;
+}
 
-    cudaGraph_t g = nullptr;
-    BCK(b, cudaGraphCreate(&g, 0));
-    int rc = LBEHD_OK;
-    long long kernels = 0;
+// Moments + ghosts of every instance, one launch.
+template <int D>
+void batch_fields(lbehd_batch *b, int parity)
+{
     std::unique_ptr<FieldsBatch> FA(new FieldsBatch);
+    std::memset(FA.get(), 0, sizeof(FieldsBatch));
+    const int n = (int)b->inst.size();
+    FA->n = n;
+    long long blocks = 0;
+    for (int k = 0; k < n; k++) {
+        const lbehd_handle *h = b->inst[k];
+        FA->start[k] = (int)blocks;
+        FA->P[k] = h->P;
+        FA->F[k] = field_ptrs(h, parity, parity);
+        blocks += (long long)((h->N + BX - 1) / BX);
+    }
+    FA->start[n] = (int)blocks;
+    blaunch_fn(b, LBEHD_KC_FIELDS,
+               [&] { k_fields_batch<D><<<(unsigned)blocks, BX, 0, b->ls>>>(*FA); });
+}
+
+// Collide + stream: one launch per group of instances running the same collide kernel (in
+// a capture, the groups are parallel branches), then the observable sums of every instance.
+template <int D>
+int batch_collide(lbehd_batch *b, int parity, const std::vector<int> &order, bool capture)
+{
+    const int n = (int)b->inst.size();
     std::unique_ptr<CollideBatch> CA(new CollideBatch);
     std::unique_ptr<ObsBatch> OA(new ObsBatch);
-    auto body = [&]() -> int {
-        BCK(b, cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0,
-                                             cudaStreamCaptureModeRelaxed));
-        // moments + ghosts
-        for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
-            const int m = std::min(BATCH_MAX, n - c0);
-            std::memset(FA.get(), 0, sizeof(FieldsBatch));
-            FA->n = m;
-            long long blocks = 0;
-            for (int k = 0; k < m; k++) {
-                const lbehd_handle *h = b->inst[c0 + k];
-                FA->start[k] = (int)blocks;
-                FA->P[k] = h->P;
-                FA->F[k] = field_ptrs(h, parity, parity);
-                blocks += (long long)((h->N + BX - 1) / BX);
+    std::vector<cudaGraphNode_t> ends, cends, tmp;
+    int r;
+    if (capture && (r = capture_deps(b, ends)))
+        return r;
+    const PopMaps *dmaps = b->maps + (size_t)parity * n;
+    for (int k0 = 0; k0 < n;) {
+        const int v = resolved_variant(b->inst[order[k0]]);
+        int m = 0;
+        while (k0 + m < n && resolved_variant(b->inst[order[k0 + m]]) == v)
+            m++;
+        std::memset(CA.get(), 0, sizeof(CollideBatch));
+        CA->n = m;
+        CA->first = 0;
+        CA->maps = dmaps + k0;
+        long long blocks = 0;
+        for (int k = 0; k < m; k++) {
+            const lbehd_handle *h = b->inst[order[k0 + k]];
+            CA->start[k] = (int)blocks;
+            if (v != 1) {
+                CA->tiles_x[k] = (int)h->grid_tile[tile_shape(v)].x;
+                CA->tiles_y[k] = (int)h->grid_tile[tile_shape(v)].y;
             }
-            FA->start[m] = (int)blocks;
-            k_fields_batch<D><<<(unsigned)blocks, BX, 0, b->stream>>>(*FA);
-            kernels++;
+            CA->P[k] = h->P;
+            CA->S[k] = collide_state(h, parity, parity);
+            blocks += collide_blocks(h, v);
         }
-        // Poisson, one branch per instance
-        std::vector<cudaGraphNode_t> fork, ends, tmp;
-        int r = capture_deps(b, fork);
-        if (r)
+        CA->start[m] = (int)blocks;
+        if (capture && (r = set_deps(b, ends)))
             return r;
-        for (lbehd_handle *h : b->inst) {
-            if ((r = set_deps(b, fork)))
-                return r;
-            r = record_step<D>(h, g, parity, refresh, false);
-            if (r)
-                return bfail(b, r, "instance Poisson capture: " + h->err);
-            kernels += h->graph_static_kernels[parity][refresh];
-            if ((r = capture_deps(b, tmp)))
-                return r;
-            ends.insert(ends.end(), tmp.begin(), tmp.end());
-        }
-        // collide + stream: one launch per chunk of a kernel group, chunks in parallel
-        std::vector<cudaGraphNode_t> cends;
-        for (int k0 = 0; k0 < n;) {
-            const int v = resolved_variant(b->inst[order[k0]]);
-            int m = 0;
-            while (k0 + m < n && m < BATCH_MAX && resolved_variant(b->inst[order[k0 + m]]) == v)
-                m++;
-            std::memset(CA.get(), 0, sizeof(CollideBatch));
-            CA->n = m;
-            CA->first = 0;
-            CA->maps = dmaps + k0;
-            long long blocks = 0;
-            for (int k = 0; k < m; k++) {
-                const lbehd_handle *h = b->inst[order[k0 + k]];
-                CA->start[k] = (int)blocks;
-                if (v != 1) {
-                    CA->tiles_x[k] = (int)h->grid_tile[tile_shape(v)].x;
-                    CA->tiles_y[k] = (int)h->grid_tile[tile_shape(v)].y;
-                }
-                CA->P[k] = h->P;
-                CA->S[k] = collide_state(h, parity, parity);
-                blocks += collide_blocks(h, v);
-            }
-            CA->start[m] = (int)blocks;
-            if ((r = set_deps(b, ends)))
-                return r;
-            launch_collide_chunk<D>(b, v, *CA, (int)blocks);
-            kernels++;
+        blaunch_fn(b, LBEHD_KC_COLLIDE, [&] { launch_collide_chunk<D>(b, v, *CA, (int)blocks); });
+        if (capture) {
             if ((r = capture_deps(b, tmp)))
                 return r;
             cends.insert(cends.end(), tmp.begin(), tmp.end());
-            k0 += m;
         }
-        if ((r = set_deps(b, cends)))
+        k0 += m;
+    }
+    if (capture && (r = set_deps(b, cends)))
+        return r;
+    std::memset(OA.get(), 0, sizeof(ObsBatch));
+    OA->n = n;
+    for (int k = 0; k < n; k++) {
+        const lbehd_handle *h = b->inst[k];
+        OA->partials[k] = h->obs_partials;
+        OA->nblocks[k] = collide_blocks(h, resolved_variant(h));
+        OA->obs[k] = h->obs;
+    }
+    blaunch_fn(b, LBEHD_KC_OBS,
+               [&] { k_obs_final_batch<<<dim3(NOBS, n), OBS_THREADS, 0, b->ls>>>(*OA); });
+    return LBEHD_OK;
+}
+
+// The whole batch's step for one parity as one graph: the moments of every instance (one
+// launch), the Gauss-law solves of all instances in lockstep, the collide kernels (one
+// launch per group of instances running the same kernel, the groups as parallel branches),
+// then the observable sums of every instance.
+template <int D>
+int capture_batch(lbehd_batch *b, int parity, int refresh)
+{
+    std::vector<int> order;
+    int rc = batch_prepare_collide(b, parity, order);
+    if (rc)
+        return rc;
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaGraphCreate(&g, 0));
+    b->launches_rec = 0;
+    b->count = &b->launches_rec;
+    const bool prof = b->prof;
+    b->prof = false;
+    auto body = [&]() -> int {
+        BCK(b, cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+        b->ls = b->stream;
+        batch_fields<D>(b, parity);
+        int r = record_batch_poisson<D>(b, g, parity, refresh);
+        if (r)
             return r;
-        // observable sums
-        for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
-            const int m = std::min(BATCH_MAX, n - c0);
-            std::memset(OA.get(), 0, sizeof(ObsBatch));
-            OA->n = m;
-            for (int k = 0; k < m; k++) {
-                const lbehd_handle *h = b->inst[c0 + k];
-                OA->partials[k] = h->obs_partials;
-                OA->nblocks[k] = collide_blocks(h, resolved_variant(h));
-                OA->obs[k] = h->obs;
-            }
-            k_obs_final_batch<<<dim3(NOBS, m), OBS_THREADS, 0, b->stream>>>(*OA);
-            kernels++;
-        }
+        if ((r = batch_collide<D>(b, parity, order, true)))
+            return r;
         BCK(b, cudaGetLastError());
         cudaGraph_t out = nullptr;
         BCK(b, cudaStreamEndCapture(b->stream, &out));
@@ -1369,14 +1899,37 @@ int capture_batch(lbehd_batch *b, int parity, int refresh)
     };
     rc = body();
     if (rc) {
-        for (lbehd_handle *h : b->inst)
-            for (cudaStream_t sx : {h->aux2, h->aux})
-                abort_capture(sx);
-        abort_capture(b->stream);
+        for (cudaStream_t sx : {b->aux2, b->aux, b->stream})
+            abort_capture(sx);
         cudaGetLastError();
     }
     cudaGraphDestroy(g);
-    b->static_kernels[parity][refresh] = kernels;
+    b->static_kernels[parity][refresh] = b->launches_rec;
+    b->count = nullptr;
+    b->prof = prof;
+    return rc;
+}
+
+// One batch step of eager launches (profiling): the graph's sequence, loops checked on the
+// host.
+template <int D>
+int eager_batch_step(lbehd_batch *b, int parity, int refresh)
+{
+    std::vector<int> order;
+    int rc = batch_prepare_collide(b, parity, order);
+    if (rc)
+        return rc;
+    b->ls = b->stream;
+    b->count = &b->launches;
+    batch_fields<D>(b, parity);
+    if (!(rc = eager_batch_poisson<D>(b, parity, refresh)))
+        rc = batch_collide<D>(b, parity, order, false);
+    b->count = nullptr;
+    if (!rc) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            rc = bfail(b, LBEHD_ERR_CUDA, std::string("eager batch step: ") + cudaGetErrorString(e));
+    }
     return rc;
 }
 
@@ -1406,22 +1959,32 @@ int batch_step_one(lbehd_batch *b)
             return bfail(b, LBEHD_ERR_INVALID_ARG, "batch instances are out of step");
         refresh |= mg_due(h) ? 1 : 0;
     }
+    if (b->prof) {
+        const int rc = eager_batch_step<D>(b, parity, refresh);
+        if (rc)
+            return rc;
+        for (lbehd_handle *h : b->inst) {
+            h->cur ^= 1;
+            h->pcur ^= 1;
+            h->step++;
+            if (refresh)
+                h->mg_valid = true;
+        }
+        return LBEHD_OK;
+    }
     if (!b->gexec[parity][refresh]) {
         const int rc = capture_batch<D>(b, parity, refresh);
         if (rc)
             return rc;
     }
     if (!b->graphs_started) {
-        // kernels inside the Poisson while loops are counted from the device iteration
-        // counters: remember where they stood
-        for (lbehd_handle *h : b->inst)
-            BCK(b, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost,
-                                   b->stream));
+        // kernels inside the batch's loops are counted from the device loop-pass counters:
+        // remember where they stood
+        int c[6] = {0, 0, 0, 0, 0, 0};
+        BCK(b, cudaMemcpyAsync(c, b->counters, sizeof(c), cudaMemcpyDeviceToHost, b->stream));
         BCK(b, cudaStreamSynchronize(b->stream));
-        for (lbehd_handle *h : b->inst) {
-            h->graph_iters0 = h->h_cg->total_iters;
-            h->graph_launches_started = true;
-        }
+        for (int k = 0; k < 3; k++)
+            b->counters0[k] = c[3 + k];
         b->graphs_started = true;
     }
     BCK(b, cudaGraphLaunch(b->gexec[parity][refresh], b->stream));
@@ -1432,6 +1995,8 @@ int batch_step_one(lbehd_batch *b)
         h->pcur ^= 1;
         h->step++;
         h->graph_launches++;
+        if (refresh)
+            h->mg_valid = true;   // the graph rebuilt the hierarchy
     }
     return LBEHD_OK;
 }
@@ -1446,16 +2011,39 @@ void batch_release(lbehd_batch *b)
         delete h;
     }
     b->inst.clear();
-    if (b->maps) {
+    for (void *p : {(void *)b->maps, (void *)b->tails, (void *)b->counters, (void *)b->act}) {
+        if (!p)
+            continue;
         if (b->free)
-            b->free(b->maps, b->alloc_ctx);
+            b->free(p, b->alloc_ctx);
         else
-            cudaFree(b->maps);
+            cudaFree(p);
     }
     b->maps = nullptr;
+    b->tails = nullptr;
+    b->counters = nullptr;
+    b->act = nullptr;
+    for (cudaStream_t *sx : {&b->aux, &b->aux2})
+        if (*sx) {
+            cudaStreamDestroy(*sx);
+            *sx = nullptr;
+        }
     if (b->h_obs)
         cudaFreeHost(b->h_obs);
     b->h_obs = nullptr;
+    if (b->h_flags)
+        cudaFreeHost(b->h_flags);
+    b->h_flags = nullptr;
+    for (auto &v : b->ev_pending) {
+        for (auto &e : v)
+            b->ev_pool.push_back(e);
+        v.clear();
+    }
+    for (auto &e : b->ev_pool) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    b->ev_pool.clear();
     if (b->own_stream)
         cudaStreamDestroy(b->own_stream);
     b->own_stream = nullptr;
@@ -1734,6 +2322,8 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
 {
     if (!cfgs || !out || n < 1)
         return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null configs or output, or n < 1");
+    if (n > BATCH_MAX)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "at most 64 instances per batch");
     *out = nullptr;
     for (int i = 1; i < n; i++)
         if (cfgs[i].dim != cfgs[0].dim)
@@ -1758,6 +2348,12 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
             return bail(LBEHD_ERR_CUDA, "cudaStreamCreate failed");
         b->stream = b->own_stream;
     }
+    {
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        b->cta_cap = 16 * nsm;
+    }
     if ((b->dim == 2 ? batch_kernel_attributes<2>() : batch_kernel_attributes<3>()) != LBEHD_OK)
         return bail(LBEHD_ERR_CUDA, "cudaFuncSetAttribute failed for the batched kernels");
     for (int i = 0; i < n; i++) {
@@ -1771,14 +2367,48 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
         h->batch_owned = true;
         b->inst.push_back(h);
     }
-    const size_t mb = 2 * (size_t)n * sizeof(PopMaps);
-    if (b->alloc)
-        b->maps = (PopMaps *)b->alloc(mb, b->alloc_ctx);
-    else if (cudaMalloc((void **)&b->maps, mb) != cudaSuccess)
-        b->maps = nullptr;
-    if (!b->maps)
-        return bail(LBEHD_ERR_OOM, "device allocation of the batch tensor-map table failed");
-    if (cudaMallocHost((void **)&b->h_obs, (size_t)n * (2 * NOBS + 1) * sizeof(double)) != cudaSuccess)
+    auto balloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (b->alloc)
+            p = b->alloc(bytes, b->alloc_ctx);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess)
+            p = nullptr;
+        return p;
+    };
+    b->maps = (PopMaps *)balloc(2 * (size_t)n * sizeof(PopMaps));
+    b->tails = (TailLevels *)balloc((size_t)n * sizeof(TailLevels));
+    b->counters = (int *)balloc(8 * sizeof(int));
+    b->act = (ActiveLists *)balloc(sizeof(ActiveLists));
+    if (!b->maps || !b->tails || !b->counters || !b->act)
+        return bail(LBEHD_ERR_OOM, "device allocation of the batch tables failed");
+    {
+        // shared-memory tails of the instances, with their level's arrays filled in
+        std::vector<TailLevels> T(n);
+        for (int i = 0; i < n; i++) {
+            const lbehd_handle *h = b->inst[i];
+            std::memset(&T[i], 0, sizeof(TailLevels));
+            if (h->tail_level >= 0) {
+                T[i] = h->tail;
+                T[i].b0 = h->mg[h->tail_level].b;
+                T[i].x0 = h->mg[h->tail_level].x;
+                b->tail_smem = std::max(b->tail_smem, h->tail_smem);
+            }
+        }
+        if (cudaMemcpyAsync(b->tails, T.data(), n * sizeof(TailLevels), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->counters, 0, 8 * sizeof(int), b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->act, 0, sizeof(ActiveLists), b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            return bail(LBEHD_ERR_CUDA, "upload of the batch tables failed");
+        if (cudaFuncSetAttribute(k_mg_tail_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TAIL_SMEM_MAX) != cudaSuccess)
+            return bail(LBEHD_ERR_CUDA, "cudaFuncSetAttribute failed for the batched tail");
+    }
+    if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->aux2, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(LBEHD_ERR_CUDA, "cudaStreamCreate failed");
+    if (cudaMallocHost((void **)&b->h_obs, (size_t)n * (2 * NOBS + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_flags, 8 * sizeof(int)) != cudaSuccess)
         return bail(LBEHD_ERR_OOM, "pinned host allocation failed");
     *out = b;
     return LBEHD_OK;
@@ -1879,11 +2509,47 @@ int lbehd_batch_get_stats(lbehd_batch *b, lbehd_stats *out)
     out->kernels = b->launches;
     for (lbehd_handle *h : b->inst) {
         out->poisson_iters += h->h_cg->total_iters;
-        // eager launches of the instance (first step, autotuning) and the kernels run
-        // inside its Poisson loops during batch graph replays
-        out->kernels += h->launches;
-        if (h->graph_launches_started)
-            out->kernels += (h->h_cg->total_iters - h->graph_iters0) * h->iter_kernels;
+        out->kernels += h->launches;   // eager launches: first step, autotuning
+    }
+    if (b->graphs_started) {
+        // kernels inside the batch graphs' loops and refinement blocks
+        int c[6] = {0, 0, 0, 0, 0, 0};
+        BCK(b, cudaMemcpyAsync(c, b->counters, sizeof(c), cudaMemcpyDeviceToHost, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        for (int k = 0; k < 3; k++)
+            out->kernels += (c[3 + k] - b->counters0[k]) * b->loop_kernels[k];
+    }
+    return LBEHD_OK;
+}
+
+int lbehd_batch_profile_enable(lbehd_batch *b, int enable)
+{
+    if (!b)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null batch");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (auto &v : b->ev_pending) {
+        for (auto &e : v)
+            b->ev_pool.push_back(e);
+        v.clear();
+    }
+    b->prof = enable != 0;
+    return LBEHD_OK;
+}
+
+int lbehd_batch_profile_read(lbehd_batch *b, double *ms, long long *count)
+{
+    if (!b || !ms || !count)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null argument");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < LBEHD_NKC; k++) {
+        double acc = 0.0;
+        for (auto &e : b->ev_pending[k]) {
+            float t = 0.0f;
+            BCK(b, cudaEventElapsedTime(&t, e.first, e.second));
+            acc += t;
+        }
+        ms[k] = acc;
+        count[k] = (long long)b->ev_pending[k].size();
     }
     return LBEHD_OK;
 }

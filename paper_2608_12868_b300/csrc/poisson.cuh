@@ -22,6 +22,13 @@
 //
 // CG scalars (alpha, beta, r.z, ...) stay in device memory, so an iteration needs no host
 // round trip; reductions are FP32 within a warp and FP64 across warps and blocks.
+//
+// Every multiply-add of these kernels is written out with the rounding intrinsics (fmul /
+// fadd / fma), so the compiler cannot fuse or split operations differently from one kernel to
+// the next: the single-instance and the batched kernels, which inline the same bodies,
+// produce the same bits. The stencil bodies issue all their loads before testing the node
+// classes (every index is in range), so a thread waits for one memory round trip, not a
+// chain of dependent ones.
 #pragma once
 
 #include <cstdint>
@@ -30,9 +37,37 @@
 
 namespace lbehd {
 
+// Lattice extents of one level, with the constants of a multiply-high division by nx, ny and
+// nx / 2 (cell coordinates from a flat index without a hardware divide).
 struct MgDims {
     int nx, ny, nz;
+    uint32_t mx, my, mh;         // multipliers
+    uint32_t sx, sy, sh;         // shifts
 };
+
+// n / d for 0 <= n < 2^31 as (hi32(n m) + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1 (round-up method; the sum fits 32 bits for n < 2^31).
+inline void fastdiv_constants(uint32_t d, uint32_t &m, uint32_t &s)
+{
+    s = 0;
+    while ((1ull << s) < d)
+        s++;
+    m = (uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+}
+
+inline MgDims mg_dims(int nx, int ny, int nz)
+{
+    MgDims d{nx, ny, nz, 0, 0, 0, 0, 0, 0};
+    fastdiv_constants((uint32_t)nx, d.mx, d.sx);
+    fastdiv_constants((uint32_t)ny, d.my, d.sy);
+    fastdiv_constants((uint32_t)(nx / 2 > 0 ? nx / 2 : 1), d.mh, d.sh);
+    return d;
+}
+
+__device__ __forceinline__ int fdiv(int n, uint32_t m, uint32_t s)
+{
+    return (int)((__umulhi((uint32_t)n, m) + (uint32_t)n) >> s);
+}
 
 struct CgScalars {
     double rz;        // r . z of the current iteration
@@ -48,20 +83,47 @@ struct CgScalars {
     int converged;
     int step_iters;   // iterations of the current step, all passes
     int nonconv;      // sticky: some pass stopped at max_iter without converging
+    int refine;       // the step's first pass iterated (a refinement check follows)
     long long total_iters;
 };
 
-__device__ __forceinline__ size_t cell(const MgDims &d, int x, int y, int z)
+// Site indices fit 32 bits (19 N < 2^31 is checked at init).
+__device__ __forceinline__ int cell(const MgDims &d, int x, int y, int z)
 {
-    return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
+    return x + d.nx * (y + d.ny * z);
 }
 
-__device__ __forceinline__ int wrapp(int v, int n) { return v + 1 == n ? 0 : v + 1; }
-__device__ __forceinline__ int wrapm(int v, int n) { return v == 0 ? n - 1 : v - 1; }
+__device__ __forceinline__ void cell_xyz(const MgDims &d, int c, int &x, int &y, int &z)
+{
+    const int r = fdiv(c, d.mx, d.sx);
+    x = c - r * d.nx;
+    z = fdiv(r, d.my, d.sy);
+    y = r - z * d.ny;
+}
+
+// Indices of the six neighbours of cell i = (x, y, z), periodic in every direction
+// (+x, -x, +y, -y, +z, -z; in 2D the z neighbours are the cell itself).
+struct Nb6 {
+    int n[6];
+};
+
+__device__ __forceinline__ Nb6 nb6(const MgDims &d, int i, int x, int y, int z)
+{
+    const int sy = d.nx, sz = d.nx * d.ny, sn = sz * d.nz;
+    Nb6 r;
+    r.n[0] = i + (x + 1 == d.nx ? 1 - d.nx : 1);
+    r.n[1] = i + (x == 0 ? d.nx - 1 : -1);
+    r.n[2] = i + (y + 1 == d.ny ? sy - sz : sy);
+    r.n[3] = i + (y == 0 ? sz - sy : -sy);
+    r.n[4] = i + (z + 1 == d.nz ? sz - sn : sz);
+    r.n[5] = i + (z == 0 ? sn - sz : -sz);
+    return r;
+}
 
 // Block reduction of up to 4 FP32 values into FP64 partials[k * nblk + blk].
 template <int NV>
-__device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
+__device__ __forceinline__ void block_partials(float (&v)[NV], double *partials, size_t blk,
+                                               size_t nblk)
 {
     __shared__ double sm[NV][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -77,10 +139,14 @@ __device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
 #pragma unroll
         for (int w = 0; w < BX / 32; w++)
             acc += sm[threadIdx.x][w];
-        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
-        const size_t blk = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
         partials[threadIdx.x * nblk + blk] = acc;
     }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
+{
+    block_partials<NV>(v, partials, grid_block_index(), grid_block_count());
 }
 
 // ---------------------------------------------------------------- level-0 operator
@@ -88,33 +154,35 @@ __device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
 // Face coefficients to the +x/+y/+z neighbours and the diagonal (all faces, Dirichlet
 // faces included) from eps and the node classes.
 template <int D>
-__global__ void __launch_bounds__(BX) k_mg_setup0(Params P, const float *__restrict__ eps,
-                                                  const uint8_t *__restrict__ info,
-                                                  float *__restrict__ Dg, float *__restrict__ kx,
-                                                  float *__restrict__ ky, float *__restrict__ kz)
+__device__ __forceinline__ void mg_setup0_cell(const MgDims &d, const float *__restrict__ eps,
+                                               const uint8_t *__restrict__ info,
+                                               float *__restrict__ Dg, float *__restrict__ kx,
+                                               float *__restrict__ ky, float *__restrict__ kz,
+                                               int x, int y, int z)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx)
-        return;
-    const MgDims d{P.nx, P.ny, P.nz};
-    const size_t i = cell(d, x, y, z);
+    const int i = cell(d, x, y, z);
     float kp[3] = {0.f, 0.f, 0.f}, diag = 0.0f;
-    if ((info[i] & 3) == PT_FLUID) {
-        const float ei = eps[i];
-        const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
-                              cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
-                              cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
+    const Nb6 nb = nb6(d, i, x, y, z);
+    const int pti = info[i] & 3;
+    const float ei = eps[i];
+    int pt[2 * D];
+    float ej[2 * D];
+#pragma unroll
+    for (int f = 0; f < 2 * D; f++) {
+        pt[f] = info[nb.n[f]] & 3;
+        ej[f] = eps[nb.n[f]];
+    }
+    if (pti == PT_FLUID) {
 #pragma unroll
         for (int f = 0; f < 2 * D; f++) {
-            const int pt = info[nb[f]] & 3;
             float k = 0.0f;
-            if (pt == PT_FLUID)
-                k = 0.5f * (ei + eps[nb[f]]);
-            else if (pt == PT_DIRICHLET)
+            if (pt[f] == PT_FLUID)
+                k = __fmul_rn(0.5f, __fadd_rn(ei, ej[f]));
+            else if (pt[f] == PT_DIRICHLET)
                 k = ei;
-            diag += k;
+            diag = __fadd_rn(diag, k);
             if ((f & 1) == 0)
-                kp[f >> 1] = pt == PT_FLUID ? k : 0.0f;
+                kp[f >> 1] = pt[f] == PT_FLUID ? k : 0.0f;
         }
     }
     Dg[i] = diag;
@@ -123,18 +191,27 @@ __global__ void __launch_bounds__(BX) k_mg_setup0(Params P, const float *__restr
     kz[i] = kp[2];
 }
 
-// Galerkin coarsening (scaled) of one level.
-__global__ void __launch_bounds__(BX) k_mg_coarsen(MgDims f, MgDims c, int cz2, float scale,
-                                                   const float *__restrict__ Df,
-                                                   const float *__restrict__ kxf,
-                                                   const float *__restrict__ kyf,
-                                                   const float *__restrict__ kzf,
-                                                   float *__restrict__ Dc, float *__restrict__ kxc,
-                                                   float *__restrict__ kyc, float *__restrict__ kzc)
+template <int D>
+__global__ void __launch_bounds__(BX) k_mg_setup0(MgDims d, const float *__restrict__ eps,
+                                                  const uint8_t *__restrict__ info,
+                                                  float *__restrict__ Dg, float *__restrict__ kx,
+                                                  float *__restrict__ ky, float *__restrict__ kz)
 {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
-    if (X >= c.nx)
-        return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < d.nx)
+        mg_setup0_cell<D>(d, eps, info, Dg, kx, ky, kz, x, blockIdx.y, blockIdx.z);
+}
+
+// Galerkin coarsening (scaled) of one level.
+__device__ __forceinline__ void mg_coarsen_cell(const MgDims &f, const MgDims &c, int cz2,
+                                                float scale, const float *__restrict__ Df,
+                                                const float *__restrict__ kxf,
+                                                const float *__restrict__ kyf,
+                                                const float *__restrict__ kzf,
+                                                float *__restrict__ Dc, float *__restrict__ kxc,
+                                                float *__restrict__ kyc, float *__restrict__ kzc,
+                                                int X, int Y, int Z)
+{
     const int nzc = cz2 ? 2 : 1;
     float dsum = 0.f, internal = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int a = 0; a < 2; a++)
@@ -143,49 +220,79 @@ __global__ void __launch_bounds__(BX) k_mg_coarsen(MgDims f, MgDims c, int cz2, 
                 const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
                 if (x >= f.nx || y >= f.ny || z >= f.nz)
                     continue;
-                const size_t i = cell(f, x, y, z);
-                dsum += Df[i];
+                const int i = cell(f, x, y, z);
+                dsum = __fadd_rn(dsum, Df[i]);
                 // +x face: internal if the +x child exists in this coarse cell
                 if (a == 0 && x + 1 < f.nx)
-                    internal += kxf[i];
+                    internal = __fadd_rn(internal, kxf[i]);
                 else
-                    fx += kxf[i];
+                    fx = __fadd_rn(fx, kxf[i]);
                 if (b == 0 && y + 1 < f.ny)
-                    internal += kyf[i];
+                    internal = __fadd_rn(internal, kyf[i]);
                 else
-                    fy += kyf[i];
+                    fy = __fadd_rn(fy, kyf[i]);
                 if (cz2) {
                     if (g == 0 && z + 1 < f.nz)
-                        internal += kzf[i];
+                        internal = __fadd_rn(internal, kzf[i]);
                     else
-                        fz += kzf[i];
+                        fz = __fadd_rn(fz, kzf[i]);
                 }
             }
-    const size_t I = cell(c, X, Y, Z);
-    const float dc = dsum - 2.0f * internal;
-    Dc[I] = dc > 0.0f ? scale * dc : 0.0f;
-    kxc[I] = scale * fx;
-    kyc[I] = scale * fy;
-    kzc[I] = scale * fz;
+    const int I = cell(c, X, Y, Z);
+    const float dc = __fmaf_rn(-2.0f, internal, dsum);
+    Dc[I] = dc > 0.0f ? __fmul_rn(scale, dc) : 0.0f;
+    kxc[I] = __fmul_rn(scale, fx);
+    kyc[I] = __fmul_rn(scale, fy);
+    kzc[I] = __fmul_rn(scale, fz);
+}
+
+__global__ void __launch_bounds__(BX) k_mg_coarsen(MgDims f, MgDims c, int cz2, float scale,
+                                                   const float *__restrict__ Df,
+                                                   const float *__restrict__ kxf,
+                                                   const float *__restrict__ kyf,
+                                                   const float *__restrict__ kzf,
+                                                   float *__restrict__ Dc, float *__restrict__ kxc,
+                                                   float *__restrict__ kyc, float *__restrict__ kzc)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X < c.nx)
+        mg_coarsen_cell(f, c, cz2, scale, Df, kxf, kyf, kzf, Dc, kxc, kyc, kzc, X, blockIdx.y,
+                        blockIdx.z);
 }
 
 // ---------------------------------------------------------------- smoother / transfers
 
-__device__ __forceinline__ float offdiag_sum(const MgDims &d, size_t i, int x, int y, int z,
+__device__ __forceinline__ float offdiag_sum(const MgDims &d, int i, int x, int y, int z,
                                              const float *__restrict__ kx,
                                              const float *__restrict__ ky,
                                              const float *__restrict__ kz,
                                              const float *__restrict__ v)
 {
-    const int xp = wrapp(x, d.nx), xm = wrapm(x, d.nx);
-    const int yp = wrapp(y, d.ny), ym = wrapm(y, d.ny);
-    float s = kx[i] * v[cell(d, xp, y, z)] + kx[cell(d, xm, y, z)] * v[cell(d, xm, y, z)] +
-              ky[i] * v[cell(d, x, yp, z)] + ky[cell(d, x, ym, z)] * v[cell(d, x, ym, z)];
+    const Nb6 nb = nb6(d, i, x, y, z);
+    float s = __fmul_rn(kx[i], v[nb.n[0]]);
+    s = __fmaf_rn(kx[nb.n[1]], v[nb.n[1]], s);
+    s = __fmaf_rn(ky[i], v[nb.n[2]], s);
+    s = __fmaf_rn(ky[nb.n[3]], v[nb.n[3]], s);
     if (d.nz > 1) {
-        const int zp = wrapp(z, d.nz), zm = wrapm(z, d.nz);
-        s += kz[i] * v[cell(d, x, y, zp)] + kz[cell(d, x, y, zm)] * v[cell(d, x, y, zm)];
+        s = __fmaf_rn(kz[i], v[nb.n[4]], s);
+        s = __fmaf_rn(kz[nb.n[5]], v[nb.n[5]], s);
     }
     return s;
+}
+
+// Gauss-Seidel update of one cell of A x = b.
+__device__ __forceinline__ void mg_gs_cell(const MgDims &d, const float *__restrict__ Dg,
+                                           const float *__restrict__ kx,
+                                           const float *__restrict__ ky,
+                                           const float *__restrict__ kz,
+                                           const float *__restrict__ b, float *__restrict__ xv,
+                                           int x, int y, int z)
+{
+    const int i = cell(d, x, y, z);
+    const float di = Dg[i], bi = b[i];
+    const float off = offdiag_sum(d, i, x, y, z, kx, ky, kz, xv);
+    if (di > 0.0f)
+        xv[i] = __fdiv_rn(__fadd_rn(bi, off), di);
 }
 
 // One red-black Gauss-Seidel half sweep of A x = b on one level.
@@ -198,16 +305,37 @@ __global__ void __launch_bounds__(BX) k_mg_gs(MgDims d, const float *__restrict_
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((y + z + color) & 1);
-    if (x >= d.nx)
-        return;
-    const size_t i = cell(d, x, y, z);
-    const float di = Dg[i];
-    if (di <= 0.0f)
-        return;
-    xv[i] = (b[i] + offdiag_sum(d, i, x, y, z, kx, ky, kz, xv)) / di;
+    if (x < d.nx)
+        mg_gs_cell(d, Dg, kx, ky, kz, b, xv, x, y, z);
 }
 
 // b_c = restriction (sum over children) of the fine residual b_f - A_f x_f.
+__device__ __forceinline__ void mg_restrict_cell(const MgDims &f, const MgDims &c, int cz2,
+                                                 const float *__restrict__ Df,
+                                                 const float *__restrict__ kx,
+                                                 const float *__restrict__ ky,
+                                                 const float *__restrict__ kz,
+                                                 const float *__restrict__ bf,
+                                                 const float *__restrict__ xf,
+                                                 float *__restrict__ bc, int X, int Y, int Z)
+{
+    const int nzc = cz2 ? 2 : 1;
+    float acc = 0.0f;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int g = 0; g < nzc; g++) {
+                const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
+                if (x >= f.nx || y >= f.ny || z >= f.nz)
+                    continue;
+                const int i = cell(f, x, y, z);
+                const float di = Df[i], xi = xf[i], bi = bf[i];
+                const float Ax = __fmaf_rn(di, xi, -offdiag_sum(f, i, x, y, z, kx, ky, kz, xf));
+                if (di > 0.0f)
+                    acc = __fadd_rn(acc, __fsub_rn(bi, Ax));
+            }
+    bc[cell(c, X, Y, Z)] = acc;
+}
+
 __global__ void __launch_bounds__(BX) k_mg_restrict(MgDims f, MgDims c, int cz2,
                                                     const float *__restrict__ Df,
                                                     const float *__restrict__ kx,
@@ -217,46 +345,39 @@ __global__ void __launch_bounds__(BX) k_mg_restrict(MgDims f, MgDims c, int cz2,
                                                     const float *__restrict__ xf,
                                                     float *__restrict__ bc)
 {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
-    if (X >= c.nx)
-        return;
-    const int nzc = cz2 ? 2 : 1;
-    float acc = 0.0f;
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            for (int g = 0; g < nzc; g++) {
-                const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
-                if (x >= f.nx || y >= f.ny || z >= f.nz)
-                    continue;
-                const size_t i = cell(f, x, y, z);
-                const float di = Df[i];
-                if (di <= 0.0f)
-                    continue;
-                acc += bf[i] - (di * xf[i] - offdiag_sum(f, i, x, y, z, kx, ky, kz, xf));
-            }
-    bc[cell(c, X, Y, Z)] = acc;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X < c.nx)
+        mg_restrict_cell(f, c, cz2, Df, kx, ky, kz, bf, xf, bc, X, blockIdx.y, blockIdx.z);
 }
 
 // x_f += x_c(parent) on active fine cells.
+__device__ __forceinline__ void mg_prolong_cell(const MgDims &f, const MgDims &c, int cz2,
+                                                const float *__restrict__ Df,
+                                                const float *__restrict__ xc,
+                                                float *__restrict__ xf, int x, int y, int z)
+{
+    const int i = cell(f, x, y, z);
+    const float di = Df[i], xi = xf[i], xp = xc[cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
+    if (di > 0.0f)
+        xf[i] = __fadd_rn(xi, xp);
+}
+
 __global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
                                                    const float *__restrict__ Df,
                                                    const float *__restrict__ xc,
                                                    float *__restrict__ xf)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= f.nx)
-        return;
-    const size_t i = cell(f, x, y, z);
-    if (Df[i] <= 0.0f)
-        return;
-    xf[i] += xc[cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < f.nx)
+        mg_prolong_cell(f, c, cz2, Df, xc, xf, x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------- small-level tail
 
 constexpr int TAIL_MAX_LEVELS = 8;
-constexpr int TAIL_MAX_CELLS = 1024;   // cells of the finest tail level
+constexpr int TAIL_MAX_TOTAL = 8192;   // cells of all tail levels (6 floats each: 192 KB)
 constexpr int TAIL_THREADS = 1024;
+constexpr size_t TAIL_SMEM_MAX = 6 * sizeof(float) * TAIL_MAX_TOTAL;   // dynamic shared memory
 
 struct TailLevels {
     int nl;                            // levels in the tail (the last is the coarsest)
@@ -271,47 +392,43 @@ struct TailLevels {
     int total;                         // cells of all tail levels
 };
 
-// The V-cycle on every level from the tail's finest down, in shared memory, one CTA. Thread t
-// owns cell t of every tail level (levels have <= TAIL_THREADS cells), so its coordinates are
-// computed once. Same arithmetic, cell by cell, as the multi-launch levels above it.
-__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
+// The V-cycle on every level from the tail's finest down, in shared memory, one CTA; the
+// threads stride over the cells of each level. Same arithmetic, cell by cell, as the
+// multi-launch levels above it (and the same for any assignment of cells to threads: a
+// red-black half sweep reads only cells of the other colour).
+__device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
 {
-    extern __shared__ float sm[];
     const int tot = T.total, t = threadIdx.x;
     float *sD = sm, *skx = sm + tot, *sky = sm + 2 * tot, *skz = sm + 3 * tot, *sx = sm + 4 * tot,
           *sb = sm + 5 * tot;
-    int cx[TAIL_MAX_LEVELS], cy[TAIL_MAX_LEVELS], cz[TAIL_MAX_LEVELS];
-    bool own[TAIL_MAX_LEVELS];
-#pragma unroll
-    for (int l = 0; l < TAIL_MAX_LEVELS; l++) {
-        own[l] = false;
-        cx[l] = cy[l] = cz[l] = 0;
-        if (l < T.nl) {
-            const MgDims d = T.d[l];
-            const int n = d.nx * d.ny * d.nz, o = T.off[l];
-            own[l] = t < n;
-            if (own[l]) {
-                cx[l] = t % d.nx;
-                cy[l] = (t / d.nx) % d.ny;
-                cz[l] = t / (d.nx * d.ny);
-                sD[o + t] = T.D[l][t];
-                skx[o + t] = T.kx[l][t];
-                sky[o + t] = T.ky[l][t];
-                skz[o + t] = T.kz[l][t];
-                sx[o + t] = 0.0f;
-                if (l == 0)
-                    sb[t] = T.b0[t];
-            }
+    auto ncell = [&](int l) { return T.d[l].nx * T.d[l].ny * T.d[l].nz; };
+#pragma unroll 1
+    for (int l = 0; l < T.nl; l++) {
+        const int n = ncell(l), o = T.off[l];
+        for (int c = t; c < n; c += TAIL_THREADS) {
+            sD[o + c] = T.D[l][c];
+            skx[o + c] = T.kx[l][c];
+            sky[o + c] = T.ky[l][c];
+            skz[o + c] = T.kz[l][c];
+            sx[o + c] = 0.0f;
+            if (l == 0)
+                sb[c] = T.b0[c];
         }
     }
     __syncthreads();
     auto gs = [&](int l, int color) {
-        if (own[l] && ((cx[l] + cy[l] + cz[l]) & 1) == color) {
-            const int o = T.off[l];
-            const float di = sD[o + t];
+        const MgDims d = T.d[l];
+        const int n = ncell(l), o = T.off[l];
+        for (int c = t; c < n; c += TAIL_THREADS) {
+            int x, y, z;
+            cell_xyz(d, c, x, y, z);
+            if (((x + y + z) & 1) != color)
+                continue;
+            const float di = sD[o + c];
             if (di > 0.0f)
-                sx[o + t] = (sb[o + t] + offdiag_sum(T.d[l], t, cx[l], cy[l], cz[l], skx + o, sky + o,
-                                                     skz + o, sx + o)) / di;
+                sx[o + c] = __fdiv_rn(__fadd_rn(sb[o + c], offdiag_sum(d, c, x, y, z, skx + o,
+                                                                       sky + o, skz + o, sx + o)),
+                                      di);
         }
         __syncthreads();
     };
@@ -322,25 +439,28 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
             gs(l, 0);
             gs(l, 1);
         }
-        if (own[l + 1]) {
-            const MgDims f = T.d[l];
-            const int fo = T.off[l], nzc = T.cz2[l] ? 2 : 1;
+        const MgDims f = T.d[l], cd = T.d[l + 1];
+        const int fo = T.off[l], co = T.off[l + 1], nzc = T.cz2[l] ? 2 : 1, nc = ncell(l + 1);
+        for (int C = t; C < nc; C += TAIL_THREADS) {
+            int X, Y, Z;
+            cell_xyz(cd, C, X, Y, Z);
             float acc = 0.0f;
             for (int a = 0; a < 2; a++)
                 for (int b = 0; b < 2; b++)
                     for (int g = 0; g < nzc; g++) {
-                        const int x = 2 * cx[l + 1] + a, y = 2 * cy[l + 1] + b,
-                                  z = nzc * cz[l + 1] + g;
+                        const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
                         if (x >= f.nx || y >= f.ny || z >= f.nz)
                             continue;
                         const int i = (int)cell(f, x, y, z);
                         const float di = sD[fo + i];
                         if (di <= 0.0f)
                             continue;
-                        acc += sb[fo + i] - (di * sx[fo + i] - offdiag_sum(f, i, x, y, z, skx + fo,
-                                                                           sky + fo, skz + fo, sx + fo));
+                        const float Ax = __fmaf_rn(di, sx[fo + i],
+                                                   -offdiag_sum(f, i, x, y, z, skx + fo, sky + fo,
+                                                                skz + fo, sx + fo));
+                        acc = __fadd_rn(acc, __fsub_rn(sb[fo + i], Ax));
                     }
-            sb[T.off[l + 1] + t] = acc;
+            sb[co + C] = acc;
         }
         __syncthreads();
     }
@@ -356,11 +476,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
     // up: prolong, smooth
 #pragma unroll 1
     for (int l = T.nl - 2; l >= 0; l--) {
-        if (own[l]) {
-            const int fo = T.off[l];
-            if (sD[fo + t] > 0.0f)
-                sx[fo + t] += sx[T.off[l + 1] + (int)cell(T.d[l + 1], cx[l] >> 1, cy[l] >> 1,
-                                                           T.cz2[l] ? (cz[l] >> 1) : cz[l])];
+        const MgDims f = T.d[l], cd = T.d[l + 1];
+        const int fo = T.off[l], co = T.off[l + 1], n = ncell(l);
+        for (int c = t; c < n; c += TAIL_THREADS) {
+            if (sD[fo + c] <= 0.0f)
+                continue;
+            int x, y, z;
+            cell_xyz(f, c, x, y, z);
+            sx[fo + c] = __fadd_rn(sx[fo + c],
+                                   sx[co + (int)cell(cd, x >> 1, y >> 1, T.cz2[l] ? (z >> 1) : z)]);
         }
         __syncthreads();
         for (int s = 0; s < T.nu; s++) {
@@ -368,8 +492,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
             gs(l, 0);
         }
     }
-    if (own[0])
-        T.x0[t] = sx[t];
+    const int n0 = ncell(0);
+    for (int c = t; c < n0; c += TAIL_THREADS)
+        T.x0[c] = sx[c];
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
+{
+    extern __shared__ float sm[];
+    mg_tail_block(T, sm);
 }
 
 // ---------------------------------------------------------------- CG on level 0
@@ -380,7 +511,57 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
 // are close, so their difference is exact in FP32, and r keeps the accuracy an FP64
 // evaluation of b - A phi would have, in FP32 arithmetic.
 template <int D>
-__global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restrict__ pot,
+__device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *__restrict__ pot,
+                                              const float *__restrict__ pot_lo,
+                                              const float *__restrict__ delta,
+                                              const float *__restrict__ eps,
+                                              const float *__restrict__ rho,
+                                              const uint8_t *__restrict__ info,
+                                              const float *__restrict__ Dg, float *__restrict__ r,
+                                              int x, int y, int z, float (&v)[2])
+{
+    {
+        const int i = cell(d, x, y, z);
+        const Nb6 nb = nb6(d, i, x, y, z);
+        const float Di = Dg[i], ei = eps[i], hi = pot[i], lo = pot_lo[i], di = delta[i];
+        const float rh = rho[i];
+        int pt[2 * D];
+        float ph[2 * D], pl[2 * D], dl[2 * D], ej[2 * D];
+#pragma unroll
+        for (int f = 0; f < 2 * D; f++) {
+            const int j = nb.n[f];
+            pt[f] = info[j] & 3;
+            ph[f] = pot[j];
+            pl[f] = pot_lo[j];
+            dl[f] = delta[j];
+            ej[f] = eps[j];
+        }
+        float ri = 0.0f;
+        if (Di > 0.0f) {
+            float b = rh;
+            ri = b;
+#pragma unroll
+            for (int f = 0; f < 2 * D; f++) {
+                if (pt[f] == PT_FLUID) {
+                    const float dphi = __fadd_rn(__fadd_rn(__fsub_rn(ph[f], hi), __fsub_rn(pl[f], lo)),
+                                                 __fsub_rn(dl[f], di));
+                    ri = __fmaf_rn(__fmul_rn(0.5f, __fadd_rn(ei, ej[f])), dphi, ri);
+                } else if (pt[f] == PT_DIRICHLET) {
+                    const float dphi =
+                        __fsub_rn(__fadd_rn(__fsub_rn(ph[f], hi), __fsub_rn(pl[f], lo)), di);
+                    ri = __fmaf_rn(ei, dphi, ri);
+                    b = __fmaf_rn(ei, __fadd_rn(ph[f], pl[f]), b);
+                }
+            }
+            v[0] = __fmul_rn(ri, ri);
+            v[1] = __fmul_rn(b, b);
+        }
+        r[i] = ri;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init(MgDims d, const float *__restrict__ pot,
                                                  const float *__restrict__ pot_lo,
                                                  const float *__restrict__ delta,
                                                  const float *__restrict__ eps,
@@ -389,116 +570,131 @@ __global__ void __launch_bounds__(BX) k_pcg_init(Params P, const float *__restri
                                                  const float *__restrict__ Dg,
                                                  float *__restrict__ r, double *__restrict__ partials)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const int i = blockIdx.x * BX + threadIdx.x;
     float v[2] = {0.f, 0.f};
-    if (x < P.nx) {
-        const MgDims d{P.nx, P.ny, P.nz};
-        const size_t i = cell(d, x, y, z);
-        float ri = 0.0f;
-        if (Dg[i] > 0.0f) {
-            const float ei = eps[i], hi = pot[i], lo = pot_lo[i], di = delta[i];
-            float b = rho[i];
-            ri = b;
-            const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
-                                  cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
-                                  cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
-#pragma unroll
-            for (int f = 0; f < 2 * D; f++) {
-                const size_t j = nb[f];
-                const int pt = info[j] & 3;
-                if (pt == PT_FLUID) {
-                    const float dphi = (pot[j] - hi) + (pot_lo[j] - lo) + (delta[j] - di);
-                    ri += 0.5f * (ei + eps[j]) * dphi;
-                } else if (pt == PT_DIRICHLET) {
-                    const float dphi = (pot[j] - hi) + (pot_lo[j] - lo) - di;
-                    ri += ei * dphi;
-                    b += ei * (pot[j] + pot_lo[j]);
-                }
-            }
-            v[0] = ri * ri;
-            v[1] = b * b;
-        }
-        r[i] = ri;
+    if (i < d.nx * d.ny * d.nz) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        pcg_init_site<D>(d, pot, pot_lo, delta, eps, rho, info, Dg, r, x, y, z, v);
     }
     block_partials<2>(v, partials);
 }
 
 // p = z + beta p (beta = 0 on the first iteration).
+// The 1D CG kernels walk the sites with a grid stride: block b of nb covers sites
+// b BX + t, (b + nb) BX + t, ... (the partition fixes each partial sum).
+__device__ __forceinline__ void pcg_p_range(int n, const float *__restrict__ zv,
+                                            float *__restrict__ p, const CgScalars *__restrict__ s,
+                                            int b, int nb)
+{
+    const float beta = s->iters == 0 ? 0.0f : (float)s->beta;
+    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX)
+        p[i] = beta != 0.0f ? __fmaf_rn(beta, p[i], zv[i]) : zv[i];
+}
+
 __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict__ zv,
                                               float *__restrict__ p, const CgScalars *__restrict__ s)
 {
-    const float beta = s->iters == 0 ? 0.0f : (float)s->beta;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        p[i] = zv[i] + (beta != 0.0f ? beta * p[i] : 0.0f);
+    pcg_p_range((int)n, zv, p, s, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // q = A p with the operator of this step (from eps and the node classes; the multigrid
 // hierarchy may be a few steps old, which only changes the preconditioner) and partials of
 // p . q. Dirichlet neighbours hold no correction (p = 0 there).
 template <int D>
-__global__ void __launch_bounds__(BX) k_pcg_Ap(Params P, const float *__restrict__ eps,
+__device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *__restrict__ eps,
+                                            const uint8_t *__restrict__ info,
+                                            const float *__restrict__ Dg,
+                                            const float *__restrict__ p, float *__restrict__ q,
+                                            int x, int y, int z, float (&v)[1])
+{
+    {
+        const int i = cell(d, x, y, z);
+        const Nb6 nb = nb6(d, i, x, y, z);
+        const float Di = Dg[i], ei = eps[i], pi = p[i];
+        int pt[2 * D];
+        float ej[2 * D], pj[2 * D];
+#pragma unroll
+        for (int f = 0; f < 2 * D; f++) {
+            const int j = nb.n[f];
+            pt[f] = info[j] & 3;
+            ej[f] = eps[j];
+            pj[f] = p[j];
+        }
+        float qi = 0.0f;
+        if (Di > 0.0f) {
+#pragma unroll
+            for (int f = 0; f < 2 * D; f++) {
+                if (pt[f] == PT_FLUID)
+                    qi = __fmaf_rn(__fmul_rn(0.5f, __fadd_rn(ei, ej[f])), __fsub_rn(pi, pj[f]), qi);
+                else if (pt[f] == PT_DIRICHLET)
+                    qi = __fmaf_rn(ei, pi, qi);
+            }
+            v[0] = __fmul_rn(pi, qi);
+        }
+        q[i] = qi;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_Ap(MgDims d, const float *__restrict__ eps,
                                                const uint8_t *__restrict__ info,
                                                const float *__restrict__ Dg,
                                                const float *__restrict__ p, float *__restrict__ q,
                                                double *__restrict__ partials)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const int i = blockIdx.x * BX + threadIdx.x;
     float v[1] = {0.f};
-    if (x < P.nx) {
-        const MgDims d{P.nx, P.ny, P.nz};
-        const size_t i = cell(d, x, y, z);
-        float qi = 0.0f;
-        if (Dg[i] > 0.0f) {
-            const float ei = eps[i], pi = p[i];
-            const size_t nb[6] = {cell(d, wrapp(x, d.nx), y, z), cell(d, wrapm(x, d.nx), y, z),
-                                  cell(d, x, wrapp(y, d.ny), z), cell(d, x, wrapm(y, d.ny), z),
-                                  cell(d, x, y, wrapp(z, d.nz)), cell(d, x, y, wrapm(z, d.nz))};
-#pragma unroll
-            for (int f = 0; f < 2 * D; f++) {
-                const size_t j = nb[f];
-                const int pt = info[j] & 3;
-                if (pt == PT_FLUID)
-                    qi += 0.5f * (ei + eps[j]) * (pi - p[j]);
-                else if (pt == PT_DIRICHLET)
-                    qi += ei * pi;
-            }
-            v[0] = pi * qi;
-        }
-        q[i] = qi;
+    if (i < d.nx * d.ny * d.nz) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        pcg_Ap_site<D>(d, eps, info, Dg, p, q, x, y, z, v);
     }
     block_partials<1>(v, partials);
 }
 
 // delta += alpha p, r -= alpha q, partials of ||r||^2.
+__device__ __forceinline__ void pcg_update_range(int n, const float *__restrict__ p,
+                                                 const float *__restrict__ q,
+                                                 float *__restrict__ delta, float *__restrict__ r,
+                                                 const CgScalars *__restrict__ s, int b, int nb,
+                                                 float (&v)[1])
+{
+    const float a = (float)s->alpha;
+    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX) {
+        delta[i] = __fmaf_rn(a, p[i], delta[i]);
+        const float ri = __fmaf_rn(-a, q[i], r[i]);
+        r[i] = ri;
+        v[0] = __fmaf_rn(ri, ri, v[0]);
+    }
+}
+
 __global__ void __launch_bounds__(BX) k_pcg_update(size_t n, const float *__restrict__ p,
                                                    const float *__restrict__ q,
                                                    float *__restrict__ delta, float *__restrict__ r,
                                                    const CgScalars *__restrict__ s,
                                                    double *__restrict__ partials)
 {
-    const float a = (float)s->alpha;
     float v[1] = {0.f};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        delta[i] += a * p[i];
-        const float ri = r[i] - a * q[i];
-        r[i] = ri;
-        v[0] += ri * ri;
-    }
-    // 1D grid: reuse the generic block reduction (gridDim.y = gridDim.z = 1)
+    pcg_update_range((int)n, p, q, delta, r, s, (int)blockIdx.x, (int)gridDim.x, v);
     block_partials<1>(v, partials);
 }
 
 // partials of r . z
+__device__ __forceinline__ void pcg_dot_range(int n, const float *__restrict__ a,
+                                              const float *__restrict__ b, int blk, int nb,
+                                              float (&v)[1])
+{
+    for (int i = blk * BX + threadIdx.x; i < n; i += nb * BX)
+        v[0] = __fmaf_rn(a[i], b[i], v[0]);
+}
+
 __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restrict__ a,
                                                 const float *__restrict__ b,
                                                 double *__restrict__ partials)
 {
     float v[1] = {0.0f};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        v[0] += a[i] * b[i];
+    pcg_dot_range((int)n, a, b, (int)blockIdx.x, (int)gridDim.x, v);
     block_partials<1>(v, partials);
 }
 
@@ -507,17 +703,15 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 //   op 4: restart   as op 0 for a refinement pass (keeps the step counter)
 //   op 1: r.z       rz                -> beta = rz / rz_old, rz_old = rz
 //   op 2: p.Ap      pq                -> alpha = rz / pq
-//   op 3: ||r||^2   rr                -> iters++, done / converged
-// With use_cond, ops 0, 4 and 3 also set the graph's while-loop condition to !done; with
-// use_ref, op 0 clears and op 3 sets the condition of the refinement block.
+//   op 3: ||r||^2   rr                -> iters++, done / converged, refine = 1
+//   op 5: ||r||^2   as op 3, for a refinement pass (leaves refine alone)
+// (op 0 clears refine.) pcg_scalar_block returns true in thread 0 after updating *s.
+// k_pcg_scalar: with use_cond, ops 0, 4, 3 and 5 also set the graph's while-loop condition
+// to !done; with use_ref, op 0 clears and op 3 sets the condition of the refinement block.
 constexpr int SCALAR_THREADS = 1024;
-__global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__restrict__ partials,
-                                                               long long nblocks, int nv, int op,
-                                                               CgScalars *__restrict__ s,
-                                                               cudaGraphConditionalHandle cond,
-                                                               int use_cond,
-                                                               cudaGraphConditionalHandle cond_ref,
-                                                               int use_ref)
+__device__ __forceinline__ bool pcg_scalar_block(const double *__restrict__ partials,
+                                                 long long nblocks, int nv, int op,
+                                                 CgScalars *__restrict__ s)
 {
     __shared__ double sm[2][SCALAR_THREADS / 32];
     double tot[2] = {0.0, 0.0};
@@ -549,13 +743,15 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
         }
     }
     if (threadIdx.x != 0)
-        return;
+        return false;
     if (op == 0 || op == 4) {
         s->rr = tot[0];
         s->bb = tot[1];
         s->iters = 0;
-        if (op == 0)
+        if (op == 0) {
             s->step_iters = 0;
+            s->refine = 0;
+        }
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->max_iter <= 0;
     } else if (op == 1) {
@@ -570,11 +766,26 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
         s->iters += 1;
         s->step_iters += 1;
         s->total_iters += 1;
+        if (op == 3)
+            s->refine = 1;
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->iters >= s->max_iter;
         if (s->done && !s->converged)
             s->nonconv = 1;
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__restrict__ partials,
+                                                               long long nblocks, int nv, int op,
+                                                               CgScalars *__restrict__ s,
+                                                               cudaGraphConditionalHandle cond,
+                                                               int use_cond,
+                                                               cudaGraphConditionalHandle cond_ref,
+                                                               int use_ref)
+{
+    if (!pcg_scalar_block(partials, nblocks, nv, op, s))
+        return;
     if (use_cond && op != 1 && op != 2)
         cudaGraphSetConditional(cond, s->done ? 0u : 1u);
     // refinement check runs only when the main pass iterated
@@ -587,14 +798,12 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
 // phi += delta on active cells, phi kept as the compensated pair hi + lo (two-sum in FP32:
 // the rounding error of hi + delta is carried into lo); acc += delta when acc is given
 // (accumulates a refinement correction into the step's increment).
-__global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
-                                                  const float *__restrict__ delta,
-                                                  float *__restrict__ acc,
-                                                  float *__restrict__ pot,
-                                                  float *__restrict__ pot_lo)
+__device__ __forceinline__ void pcg_apply_range(int n, const float *__restrict__ Dg,
+                                                const float *__restrict__ delta,
+                                                float *__restrict__ acc, float *__restrict__ pot,
+                                                float *__restrict__ pot_lo, int b, int nb)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX) {
         if (Dg[i] <= 0.0f)
             continue;
         const float d = delta[i];
@@ -609,6 +818,15 @@ __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restr
         pot[i] = s;
         pot_lo[i] = lo - (s - t);
     }
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,
+                                                  const float *__restrict__ delta,
+                                                  float *__restrict__ acc,
+                                                  float *__restrict__ pot,
+                                                  float *__restrict__ pot_lo)
+{
+    pcg_apply_range((int)n, Dg, delta, acc, pot, pot_lo, (int)blockIdx.x, (int)gridDim.x);
 }
 
 }  // namespace lbehd

@@ -1,0 +1,423 @@
+// poisson_batch.cuh -- the Gauss-law solve (Eq. 13) of many instances in lockstep: every
+// multigrid and CG stage is one launch over all instances, and one device-side loop
+// iterates while any instance's CG pass is unconverged.
+//
+// Each launch is a fixed grid of CTAs walking work items (instance k, block b of that
+// instance's partition of this stage). At start a CTA builds, in shared memory, the table of
+// the instances taking part in the launch: all of them, or those the activity mode selects
+// (a list the CG scalar kernel rewrites after every update, so a converged instance
+// costs nothing), with their block offsets. The launch's per-instance parameters travel in
+// kernel parameter space. The per-site arithmetic is the single-instance kernels' own (the
+// *_cell / *_site / *_range bodies of poisson.cuh), and every reduction keeps that
+// instance's single-instance partition (blocks of BX consecutive sites for the stencil
+// reductions, a grid stride over nb1d blocks for the vector reductions), so the partial
+// sums, and hence every CG scalar, are bitwise those of the single-instance solve.
+#pragma once
+
+#include "batch.cuh"
+#include "poisson.cuh"
+
+namespace lbehd {
+
+// Activity modes: 0 every instance; 1 instances whose current CG pass is not done; 2
+// instances refining this step (their first pass iterated); 3 refining and not done.
+__device__ __forceinline__ bool batch_active(int mode, const CgScalars *s)
+{
+    if (mode == 0)
+        return true;
+    const int done = s->done, ref = s->refine;
+    if (mode == 1)
+        return !done;
+    if (mode == 2)
+        return ref != 0;
+    return ref != 0 && !done;
+}
+
+// Instances active in modes 1-3 (index 0 unused), rewritten by k_pcg_scalar_batch.
+struct ActiveLists {
+    int count[4];
+    int ids[4][BATCH_MAX];
+};
+
+struct GridSet {
+    int n, mode;
+    int blocks[BATCH_MAX];              // work items of instance k in this launch (0: none)
+    CgScalars *s[BATCH_MAX];
+    const ActiveLists *act;
+};
+
+// The CTA's table of the launch's instances: ids[j] owns work items [start[j], start[j+1]).
+struct WorkTable {
+    int n;
+    int ids[BATCH_MAX];
+    int start[BATCH_MAX + 1];
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total)
+{
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += t;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+__device__ __forceinline__ void load_work(const GridSet &g, WorkTable &W)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int cnt = g.mode == 0 ? g.n : g.act->count[g.mode];
+        int base = 0;
+#pragma unroll
+        for (int h = 0; h < BATCH_MAX / 32; h++) {
+            const int j = h * 32 + lane;
+            const int id = j < cnt ? (g.mode == 0 ? j : g.act->ids[g.mode][j]) : 0;
+            const int nb = j < cnt ? g.blocks[id] : 0;
+            int tot;
+            const int ex = warp_excl_scan(nb, lane, tot);
+            W.ids[j] = id;
+            W.start[j] = base + ex;
+            base += tot;
+        }
+        if (lane == 0) {
+            W.n = cnt;
+            W.start[cnt] = base;
+        }
+    }
+    __syncthreads();
+}
+
+// Largest j with W.start[j] <= w (w < W.start[W.n]).
+__device__ __forceinline__ int work_slot(const WorkTable &W, int w)
+{
+    int lo = 0, hi = W.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (W.start[mid] <= w)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// for (each work item of this CTA) body(k, b); uniform across the CTA.
+template <class F>
+__device__ __forceinline__ void for_work(const GridSet &g, F &&body)
+{
+    __shared__ WorkTable W;
+    load_work(g, W);
+    const int total = W.start[W.n];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int j = work_slot(W, w);
+        body(W.ids[j], w - W.start[j]);
+    }
+}
+
+// block_partials for use inside a work loop: the shared scratch is free again on return.
+template <int NV>
+__device__ __forceinline__ void block_partials_loop(float (&v)[NV], double *partials, int blk,
+                                                    int nblk)
+{
+    block_partials<NV>(v, partials, (size_t)blk, (size_t)nblk);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- multigrid
+
+struct MgInst {
+    MgDims f, c;                              // this level and the next coarser one
+    int cz2, reps;                            // coarsening halves z; sweeps of this instance
+    float scale;
+    const float *eps;                         // level-0 set-up
+    const uint8_t *info;
+    float *D, *kx, *ky, *kz, *b, *x;          // this level
+    float *Dc, *kxc, *kyc, *kzc, *bc, *xc;    // the coarser level
+};
+
+struct MgBatch {
+    GridSet g;
+    int color, sweep;                         // Gauss-Seidel colour and sweep index
+    MgInst m[BATCH_MAX];
+};
+
+__device__ __forceinline__ int cells(const MgDims &d) { return d.nx * d.ny * d.nz; }
+
+// x = 0 on this level (one cell per thread).
+__global__ void __launch_bounds__(BX) k_mg_zero_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const int i = b * BX + threadIdx.x;
+        if (i < cells(A.m[k].f))
+            A.m[k].x[i] = 0.0f;
+    });
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_mg_setup0_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.f))
+            return;
+        int x, y, z;
+        cell_xyz(m.f, i, x, y, z);
+        mg_setup0_cell<D>(m.f, m.eps, m.info, m.D, m.kx, m.ky, m.kz, x, y, z);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_mg_coarsen_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.c))
+            return;
+        int X, Y, Z;
+        cell_xyz(m.c, i, X, Y, Z);
+        mg_coarsen_cell(m.f, m.c, m.cz2, m.scale, m.D, m.kx, m.ky, m.kz, m.Dc, m.kxc, m.kyc,
+                        m.kzc, X, Y, Z);
+    });
+}
+
+// One red-black half sweep: thread -> cell (2 x2 + colour offset, y, z) of this level (nx is
+// even on every level). Instances whose sweep count is below A.sweep + 1 take no part.
+__global__ void __launch_bounds__(BX) k_mg_gs_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int half = m.f.nx >> 1;
+        const int i = b * BX + threadIdx.x;
+        if (i >= half * m.f.ny * m.f.nz)
+            return;
+        const int r = fdiv(i, m.f.mh, m.f.sh), z = fdiv(r, m.f.my, m.f.sy), y = r - z * m.f.ny;
+        const int x = 2 * (i - r * half) + ((y + z + A.color) & 1);
+        mg_gs_cell(m.f, m.D, m.kx, m.ky, m.kz, m.b, m.x, x, y, z);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_mg_restrict_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.c))
+            return;
+        int X, Y, Z;
+        cell_xyz(m.c, i, X, Y, Z);
+        mg_restrict_cell(m.f, m.c, m.cz2, m.D, m.kx, m.ky, m.kz, m.b, m.x, m.bc, X, Y, Z);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_mg_prolong_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.f))
+            return;
+        int x, y, z;
+        cell_xyz(m.f, i, x, y, z);
+        mg_prolong_cell(m.f, m.c, m.cz2, m.D, m.xc, m.x, x, y, z);
+    });
+}
+
+struct TailBatch {
+    GridSet g;                                // one work item per instance with a tail
+    const TailLevels *T[BATCH_MAX];           // device copies (b0, x0 set)
+};
+
+// The shared-memory tail of every active instance that has one, one CTA each.
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail_batch(const __grid_constant__ TailBatch A)
+{
+    __shared__ TailLevels T;
+    extern __shared__ float sm[];
+    for_work(A.g, [&](int k, int) {
+        constexpr int W = (int)(sizeof(TailLevels) / sizeof(int));
+        static_assert(sizeof(TailLevels) % sizeof(int) == 0, "TailLevels copied as ints");
+        const int *src = reinterpret_cast<const int *>(A.T[k]);
+        int *dst = reinterpret_cast<int *>(&T);
+        for (int w = threadIdx.x; w < W; w += blockDim.x)
+            dst[w] = src[w];
+        __syncthreads();
+        mg_tail_block(T, sm);
+        __syncthreads();
+    });
+}
+
+// ---------------------------------------------------------------- CG on level 0
+
+struct CgInst {
+    MgDims d;
+    int nbs, nb1d;             // site partition: nbs blocks of BX consecutive sites; grid
+                               // stride: nb1d blocks
+    float *pot, *pot_lo;
+    const float *eps, *rho;
+    const uint8_t *info;
+    const float *Dg;           // level-0 diagonal
+    float *r, *p, *q, *z;      // z: the level-0 V-cycle output
+    float *x, *acc;            // the increment solved for; where apply accumulates it (or null)
+    double *partials;
+};
+
+struct CgBatch {
+    GridSet g;
+    CgInst c[BATCH_MAX];
+};
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        const int i = b * BX + threadIdx.x;
+        float v[2] = {0.f, 0.f};
+        if (i < cells(c.d)) {
+            int x, y, z;
+            cell_xyz(c.d, i, x, y, z);
+            pcg_init_site<D>(c.d, c.pot, c.pot_lo, c.x, c.eps, c.rho, c.info, c.Dg, c.r, x, y, z,
+                             v);
+        }
+        block_partials_loop<2>(v, c.partials, b, c.nbs);
+    });
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_Ap_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        const int i = b * BX + threadIdx.x;
+        float v[1] = {0.f};
+        if (i < cells(c.d)) {
+            int x, y, z;
+            cell_xyz(c.d, i, x, y, z);
+            pcg_Ap_site<D>(c.d, c.eps, c.info, c.Dg, c.p, c.q, x, y, z, v);
+        }
+        block_partials_loop<1>(v, c.partials, b, c.nbs);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_dot_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        float v[1] = {0.f};
+        pcg_dot_range(cells(c.d), c.r, c.z, b, c.nb1d, v);
+        block_partials_loop<1>(v, c.partials, b, c.nb1d);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_p_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        pcg_p_range(cells(c.d), c.z, c.p, A.g.s[k], b, c.nb1d);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_update_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        float v[1] = {0.f};
+        pcg_update_range(cells(c.d), c.p, c.q, c.x, c.r, A.g.s[k], b, c.nb1d, v);
+        block_partials_loop<1>(v, c.partials, b, c.nb1d);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_apply_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        pcg_apply_range(cells(c.d), c.Dg, c.x, c.acc, c.pot, c.pot_lo, b, c.nb1d);
+    });
+}
+
+struct ScalarBatch {
+    GridSet g;                                // one block per instance (blocks[] unused)
+    const double *partials[BATCH_MAX];
+    long long nblocks[BATCH_MAX];
+    int nv, op;
+    int loop_mode;                            // >= 0: set `cond` to "some instance active in
+                                              // this mode" after the update
+    int set_ref;                              // set `cond_ref` to "some instance refining"
+    int eager;                                // no graph: write the two conditions to
+                                              // counters[6], [7] for the host instead
+    cudaGraphConditionalHandle cond, cond_ref;
+    int *counters;                            // [2] arrivals (zero between launches); [3..5]
+                                              // pass counts (ops 3, 5, 4); [6..7] eager
+    ActiveLists *act;                         // rewritten after ops 0, 3, 4, 5
+};
+
+// The CG scalar update of every active instance (one block each). The last block to finish
+// (arrival count) rewrites the active lists, sets the batch's loop conditions from them and
+// zeroes the count for the next launch.
+__global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar_batch(const __grid_constant__ ScalarBatch A)
+{
+    const int k = blockIdx.x;
+    CgScalars *s = A.g.s[k];
+    if (batch_active(A.g.mode, s))   // block-uniform: every thread reads before any update
+        pcg_scalar_block(A.partials[k], A.nblocks[k], A.nv, A.op, s);
+    if (A.loop_mode < 0 && !A.set_ref)
+        return;
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&A.counters[2], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32)
+        return;
+    __threadfence();
+    // the last block: every instance's flags are final
+    const int lane = threadIdx.x, n = A.g.n;
+    int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int h = 0; h < BATCH_MAX / 32; h++) {
+        const int j = h * 32 + lane;
+        int done = 1, ref = 0;
+        if (j < n) {
+            const volatile CgScalars *sj = A.g.s[j];
+            done = sj->done;
+            ref = sj->refine;
+        }
+        const bool in[4] = {false, j < n && !done, j < n && ref != 0, j < n && ref != 0 && !done};
+#pragma unroll
+        for (int m = 1; m < 4; m++) {
+            const unsigned bal = __ballot_sync(0xffffffffu, in[m]);
+            if (in[m])
+                A.act->ids[m][cnt[m] + __popc(bal & ((1u << lane) - 1u))] = j;
+            cnt[m] += __popc(bal);
+        }
+    }
+    if (lane != 0)
+        return;
+    for (int m = 1; m < 4; m++)
+        A.act->count[m] = cnt[m];
+    A.counters[2] = 0;
+    const int any_act = A.loop_mode >= 0 ? cnt[A.loop_mode] : 0, any_ref = cnt[2];
+    if (A.eager) {
+        A.counters[6] = any_act;
+        A.counters[7] = any_ref;
+        return;
+    }
+    // passes of the main loop, of the refinement loop, refinement blocks entered
+    if (A.op == 3 || A.op == 5 || A.op == 4)
+        A.counters[A.op == 3 ? 3 : (A.op == 5 ? 4 : 5)] += 1;
+    if (A.loop_mode >= 0)
+        cudaGraphSetConditional(A.cond, any_act > 0 ? 1u : 0u);
+    if (A.set_ref)
+        cudaGraphSetConditional(A.cond_ref, any_ref > 0 ? 1u : 0u);
+}
+
+static_assert(sizeof(MgBatch) <= 32000 && sizeof(CgBatch) <= 32000 &&
+                  sizeof(ScalarBatch) <= 32000 && sizeof(TailBatch) <= 32000,
+              "batch tables must fit the kernel parameter space");
+
+}  // namespace lbehd

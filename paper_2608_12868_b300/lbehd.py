@@ -89,7 +89,8 @@ EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_profile_read", "lbehd_autotune", "lbehd_last_error", "lbehd_destroy",
            "lbehd_batch_init", "lbehd_batch_step", "lbehd_batch_size", "lbehd_batch_instance",
            "lbehd_batch_observe", "lbehd_batch_set_option", "lbehd_batch_autotune",
-           "lbehd_batch_get_stats", "lbehd_batch_last_error", "lbehd_batch_destroy")
+           "lbehd_batch_get_stats", "lbehd_batch_profile_enable", "lbehd_batch_profile_read",
+           "lbehd_batch_last_error", "lbehd_batch_destroy")
 KERNEL_CLASSES = ("fields", "mg", "cg", "collide", "obs")
 
 
@@ -134,6 +135,9 @@ def load():
     lib.lbehd_batch_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_batch_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lbehd_batch_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.lbehd_batch_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_longlong)]
     lib.lbehd_batch_last_error.argtypes = [P]
     lib.lbehd_batch_last_error.restype = ctypes.c_char_p
     lib.lbehd_batch_destroy.argtypes = [P]
@@ -419,6 +423,17 @@ class Batch:
         self._check(self._lib.lbehd_batch_autotune(self._b, int(reps), var, ms))
         return list(var), [{v + 1: ms[4 * i + v] for v in range(4) if ms[4 * i + v] >= 0}
                            for i in range(n)]
+
+    def profile(self, enable=True):
+        """Eager batch steps with CUDA events around every launch."""
+        self._check(self._lib.lbehd_batch_profile_enable(self._b, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} since profiling was enabled."""
+        n = len(KERNEL_CLASSES)
+        ms, cnt = (ctypes.c_double * n)(), (ctypes.c_longlong * n)()
+        self._check(self._lib.lbehd_batch_profile_read(self._b, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
     def stats(self):
         st = Stats()

@@ -185,3 +185,21 @@ def test_batched_sweep_64_instances(gpu):
             assert np.array_equal(batch[i].array(name), sim.array(name)), (i, name)
         sim.close()
     batch.close()
+
+
+def test_batch_eager_profile_steps_match_graph_steps(gpu):
+    """Profiling runs the batch step as eager launches with host-checked loops: the same
+    states as the graph replays, and every kernel class is timed."""
+    ws = uneven_3d()
+    a, b = gpu.Batch(ws), gpu.Batch(ws)
+    a.step(20)
+    b.step(5)
+    b.profile(True)
+    b.step(12)   # includes the multigrid rebuild at step 16
+    prof = b.profile_read()
+    b.profile(False)
+    b.step(3)
+    for i in range(len(ws)):
+        assert_same_state(a[i], b[i], f"eager instance {i}")
+    for k in ("fields", "mg", "cg", "collide", "obs"):
+        assert prof[k][1] > 0 and prof[k][0] > 0, k

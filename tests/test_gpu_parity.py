@@ -256,3 +256,13 @@ def test_zero_copy_views(gpu):
     t = sim.tensor("phi").cpu().numpy()
     assert np.array_equal(t, sim.array("phi"))
     assert sim.launch_count() > 0
+
+
+def test_handles_with_different_tails_coexist(gpu):
+    """Kernel attributes (shared-memory limits) are per kernel, not per handle: a handle
+    created after another with a smaller multigrid tail must not break the first one."""
+    big = gpu.Simulation(W.small_2d(nx=64, ny=40, seed=7, R=9.0, V=0.03))
+    small = gpu.Simulation(W.small_2d())
+    small.step(3)
+    big.step(3)
+    assert big.observe()["status"] == 0 and small.observe()["status"] == 0
