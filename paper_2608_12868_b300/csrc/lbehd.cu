@@ -60,6 +60,7 @@ struct lbehd_handle {
         size_t n = 0;
         int cz2 = 0;               // coarsening to the next level halves z too
         float *D = nullptr, *kx = nullptr, *ky = nullptr, *kz = nullptr, *x = nullptr, *b = nullptr;
+        float *r = nullptr;            // residual scratch of the restriction
         dim3 grid, grid_half;
     };
     std::vector<Level> mg;
@@ -270,8 +271,8 @@ void vcycle(lbehd_handle *h, size_t l)
         mg_gs(h, L, 1);
     }
     const auto &C = h->mg[l + 1];
-    k_mg_restrict<<<C.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.D, L.kx, L.ky, L.kz, L.b,
-                                                       L.x, C.b);
+    k_mg_resid<<<L.grid, h->block, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, L.r);
+    k_mg_restrict_sum<<<C.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.r, C.b);
     vcycle(h, l + 1);
     k_mg_prolong<<<L.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.D, C.x, L.x);
     for (int s = 0; s < h->mg_nu; s++) {
@@ -284,8 +285,8 @@ int vcycle_launches(const lbehd_handle *h)
 {
     const int levels = (int)h->mg.size();
     if (h->tail_level >= 0)
-        return h->tail_level * (4 * h->mg_nu + 2) + 1;   // memsets not counted
-    return (levels - 1) * (4 * h->mg_nu + 2) + 4 * h->mg_coarse;
+        return h->tail_level * (4 * h->mg_nu + 3) + 1;   // memsets not counted
+    return (levels - 1) * (4 * h->mg_nu + 3) + 4 * h->mg_coarse;
 }
 
 void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
@@ -874,7 +875,8 @@ int init_impl(lbehd_handle *h)
             L.kz = (float *)dev_alloc(h, L.n * fb);
             L.x = (float *)dev_alloc(h, L.n * fb);
             L.b = h->mg.empty() ? h->cg_r : (float *)dev_alloc(h, L.n * fb);
-            if (!L.D || !L.kx || !L.ky || !L.kz || !L.x || !L.b)
+            L.r = (float *)dev_alloc(h, L.n * fb);
+            if (!L.D || !L.kx || !L.ky || !L.kz || !L.x || !L.b || !L.r)
                 return fail(h, LBEHD_ERR_OOM, "device allocation failed (multigrid)");
             // keep x and y even on every level (red-black colouring across the periodic wrap)
             const bool more = d.nx % 4 == 0 && d.ny % 4 == 0 && (h->dim == 2 || d.nz >= 4);
@@ -1312,6 +1314,7 @@ void fill_mg(lbehd_batch *b, MgBatch &A, const std::vector<int> &ids, LV level)
         m.kz = L.kz;
         m.b = L.b;
         m.x = L.x;
+        m.r = L.r;
         if (l + 1 < (int)h->mg.size()) {
             const auto &C = h->mg[l + 1];
             m.c = C.d;
@@ -1416,7 +1419,8 @@ void batch_vcycle(lbehd_batch *b, MgBatch &A, int mode)
         auto coarse_cells = [&b, l](int k) {
             return ceil_div(dims_cells(b->inst[k]->mg[l + 1].d), BX);
         };
-        blaunch(b, k_mg_restrict_batch, A, fill_grid_set(b, A.g, ids, mode, coarse_cells), BX);
+        blaunch(b, k_mg_resid_batch, A, fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
+        blaunch(b, k_mg_restrict_sum_batch, A, fill_grid_set(b, A.g, ids, mode, coarse_cells), BX);
     }
     // bottom: shared-memory tails, and the coarsest-level sweeps of instances without one
     {

@@ -309,45 +309,72 @@ __global__ void __launch_bounds__(BX) k_mg_gs(MgDims d, const float *__restrict_
         mg_gs_cell(d, Dg, kx, ky, kz, b, xv, x, y, z);
 }
 
-// b_c = restriction (sum over children) of the fine residual b_f - A_f x_f.
-__device__ __forceinline__ void mg_restrict_cell(const MgDims &f, const MgDims &c, int cz2,
-                                                 const float *__restrict__ Df,
+// Restriction, b_c = sum over the children of the fine residual b_f - A_f x_f, in two
+// passes: the residual of every fine cell (0 on inactive cells), then the sum over each
+// coarse cell's children in the order (x, y, z) = (2X + a, 2Y + b, 2Z + g), a outermost
+// (the shared-memory tail sums in the same order).
+__device__ __forceinline__ void mg_resid_cell(const MgDims &f, const float *__restrict__ Df,
+                                              const float *__restrict__ kx,
+                                              const float *__restrict__ ky,
+                                              const float *__restrict__ kz,
+                                              const float *__restrict__ bf,
+                                              const float *__restrict__ xf, float *__restrict__ rf,
+                                              int x, int y, int z)
+{
+    const int i = cell(f, x, y, z);
+    const float di = Df[i], xi = xf[i], bi = bf[i];
+    const float Ax = __fmaf_rn(di, xi, -offdiag_sum(f, i, x, y, z, kx, ky, kz, xf));
+    rf[i] = di > 0.0f ? __fsub_rn(bi, Ax) : 0.0f;
+}
+
+__device__ __forceinline__ void mg_restrict_sum_cell(const MgDims &f, const MgDims &c, int cz2,
+                                                     const float *__restrict__ rf,
+                                                     float *__restrict__ bc, int X, int Y, int Z)
+{
+    // fine nx, ny are twice the coarse ones; only z may end on a single child
+    const int z0 = cz2 ? 2 * Z : Z;
+    const bool z1 = cz2 && z0 + 1 < f.nz;
+    const int i = cell(f, 2 * X, 2 * Y, z0), sy = f.nx, sz = f.nx * f.ny;
+    const float r000 = rf[i], r001 = z1 ? rf[i + sz] : 0.0f;
+    const float r010 = rf[i + sy], r011 = z1 ? rf[i + sy + sz] : 0.0f;
+    const float r100 = rf[i + 1], r101 = z1 ? rf[i + 1 + sz] : 0.0f;
+    const float r110 = rf[i + 1 + sy], r111 = z1 ? rf[i + 1 + sy + sz] : 0.0f;
+    float acc = 0.0f;
+    acc = __fadd_rn(acc, r000);
+    if (z1)
+        acc = __fadd_rn(acc, r001);
+    acc = __fadd_rn(acc, r010);
+    if (z1)
+        acc = __fadd_rn(acc, r011);
+    acc = __fadd_rn(acc, r100);
+    if (z1)
+        acc = __fadd_rn(acc, r101);
+    acc = __fadd_rn(acc, r110);
+    if (z1)
+        acc = __fadd_rn(acc, r111);
+    bc[cell(c, X, Y, Z)] = acc;
+}
+
+__global__ void __launch_bounds__(BX) k_mg_resid(MgDims f, const float *__restrict__ Df,
                                                  const float *__restrict__ kx,
                                                  const float *__restrict__ ky,
                                                  const float *__restrict__ kz,
                                                  const float *__restrict__ bf,
                                                  const float *__restrict__ xf,
-                                                 float *__restrict__ bc, int X, int Y, int Z)
+                                                 float *__restrict__ rf)
 {
-    const int nzc = cz2 ? 2 : 1;
-    float acc = 0.0f;
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            for (int g = 0; g < nzc; g++) {
-                const int x = 2 * X + a, y = 2 * Y + b, z = nzc * Z + g;
-                if (x >= f.nx || y >= f.ny || z >= f.nz)
-                    continue;
-                const int i = cell(f, x, y, z);
-                const float di = Df[i], xi = xf[i], bi = bf[i];
-                const float Ax = __fmaf_rn(di, xi, -offdiag_sum(f, i, x, y, z, kx, ky, kz, xf));
-                if (di > 0.0f)
-                    acc = __fadd_rn(acc, __fsub_rn(bi, Ax));
-            }
-    bc[cell(c, X, Y, Z)] = acc;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < f.nx)
+        mg_resid_cell(f, Df, kx, ky, kz, bf, xf, rf, x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(BX) k_mg_restrict(MgDims f, MgDims c, int cz2,
-                                                    const float *__restrict__ Df,
-                                                    const float *__restrict__ kx,
-                                                    const float *__restrict__ ky,
-                                                    const float *__restrict__ kz,
-                                                    const float *__restrict__ bf,
-                                                    const float *__restrict__ xf,
-                                                    float *__restrict__ bc)
+__global__ void __launch_bounds__(BX) k_mg_restrict_sum(MgDims f, MgDims c, int cz2,
+                                                        const float *__restrict__ rf,
+                                                        float *__restrict__ bc)
 {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     if (X < c.nx)
-        mg_restrict_cell(f, c, cz2, Df, kx, ky, kz, bf, xf, bc, X, blockIdx.y, blockIdx.z);
+        mg_restrict_sum_cell(f, c, cz2, rf, bc, X, blockIdx.y, blockIdx.z);
 }
 
 // x_f += x_c(parent) on active fine cells.

@@ -135,7 +135,7 @@ struct MgInst {
     float scale;
     const float *eps;                         // level-0 set-up
     const uint8_t *info;
-    float *D, *kx, *ky, *kz, *b, *x;          // this level
+    float *D, *kx, *ky, *kz, *b, *x, *r;      // this level (r: residual scratch)
     float *Dc, *kxc, *kyc, *kzc, *bc, *xc;    // the coarser level
 };
 
@@ -201,7 +201,20 @@ __global__ void __launch_bounds__(BX) k_mg_gs_batch(const __grid_constant__ MgBa
     });
 }
 
-__global__ void __launch_bounds__(BX) k_mg_restrict_batch(const __grid_constant__ MgBatch A)
+__global__ void __launch_bounds__(BX) k_mg_resid_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.f))
+            return;
+        int x, y, z;
+        cell_xyz(m.f, i, x, y, z);
+        mg_resid_cell(m.f, m.D, m.kx, m.ky, m.kz, m.b, m.x, m.r, x, y, z);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_mg_restrict_sum_batch(const __grid_constant__ MgBatch A)
 {
     for_work(A.g, [&](int k, int b) {
         const MgInst &m = A.m[k];
@@ -210,7 +223,7 @@ __global__ void __launch_bounds__(BX) k_mg_restrict_batch(const __grid_constant_
             return;
         int X, Y, Z;
         cell_xyz(m.c, i, X, Y, Z);
-        mg_restrict_cell(m.f, m.c, m.cz2, m.D, m.kx, m.ky, m.kz, m.b, m.x, m.bc, X, Y, Z);
+        mg_restrict_sum_cell(m.f, m.c, m.cz2, m.r, m.bc, X, Y, Z);
     });
 }
 
