@@ -396,11 +396,29 @@ def run_batched(args, dev, plain_mlups, peak, peak_kind, clk):
 
 def run_profile_window(args, local):
     """Warm up, then bracket --profile-steps eager coupled steps with cudaProfilerStart /
-    Stop (for `ncu --profile-from-start off`). Prints one line, no timing."""
+    Stop (for `ncu --profile-from-start off`). Prints one line, no timing. With
+    --profile-batched N the window covers eager steps of the N-instance batched sweep."""
     import torch
     from paper_2608_12868_b300 import lbehd
     from paper_2608_12868_b300 import workloads as W
     torch.cuda.set_device(local)
+    if args.profile_batched:
+        ws = W.batched_sweep(n=args.profile_batched)
+        stream = torch.cuda.Stream()
+        batch = lbehd.Batch(ws, stream=stream, device=local)
+        batch.step(1)
+        batch.autotune(reps=5)
+        batch.step(args.warmup * args.batched_lb_steps)
+        batch.profile(True)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        batch.step(args.profile_steps)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profile_window": args.profile_steps,
+                          "workload": f"batched_sweep_{len(ws)}", "stats": batch.stats(),
+                          "eager_class_ms": batch.profile_read()}))
+        return
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream()
     sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=lbehd.POISSON_HOST)
@@ -442,6 +460,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run a profiler window of this many eager steps (for ncu)")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="with --profile-steps: profile the batched sweep of this many instances")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     if args.profile_steps:
