@@ -244,6 +244,33 @@ int lbehd_phase_moments_noalloc(int dim, int nx, int ny, int nz, const float *ph
  * owned by a batch (use lbehd_batch_autotune). */
 int lbehd_autotune(lbehd_handle *h, int reps, double *ms);
 
+/* ---------------------------------------------------------------- discrete adjoint
+ * Gradients of the droplet's x centroid after a run with respect to the electrode
+ * potentials, which are piecewise constant in time (the programmable switching of the
+ * Results): V[k * n_electrodes + e] is electrode e's potential during segment k, which
+ * lasts seg_steps steps.
+ *
+ * lbehd_adjoint_forward runs the n_segments * seg_steps steps from the handle's current state
+ * (as lbehd_step would, the potentials set segment by segment). On the way it keeps the state
+ * every K ~ sqrt(steps) steps (K a multiple of 16) in device memory. It returns the loss
+ * L = sum Phi_1 x / sum Phi_1 over the fluid nodes after the last step (the x centroid
+ * lbehd_observe reports). The handle is left after the last step.
+ *
+ * lbehd_adjoint_backward returns grad[k * n_electrodes + e] = dL/dV[k][e], the discrete
+ * adjoint of the recorded run. It replays one checkpoint interval at a time, keeping every
+ * step's input state and potential, and runs the reversed steps: the reverse of the fused
+ * collide kernel, the gather of the stencils' adjoints, one adjoint Gauss-law solve with the
+ * same symmetric operator (preconditioned CG), the reverse of the moments and wetting ghosts,
+ * and the per-electrode sums. The first step of a fresh handle has no backward differences
+ * and contributes none. Afterwards the handle is again in the state after the last step.
+ * Memory: (ceil(steps / K) + K + 1) saved states of (4 Q + Q_s + 12) floats per site.
+ * Synchronise. Errors: LBEHD_ERR_INVALID_ARG (no recorded run, bad sizes, batch instance),
+ * LBEHD_ERR_OOM, LBEHD_ERR_CUDA; LBEHD_ERR_POISSON_NOCONV from the forward is reported but
+ * the run completes. */
+int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int seg_steps,
+                          double *loss);
+int lbehd_adjoint_backward(lbehd_handle *h, double *grad);
+
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
 const char *lbehd_last_error(lbehd_handle *h);
 

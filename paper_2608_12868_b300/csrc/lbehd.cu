@@ -17,6 +17,7 @@
 #include "kernels.cuh"
 #include "poisson.cuh"
 #include "poisson_batch.cuh"
+#include "adjoint.cuh"
 
 namespace lbehd {
 
@@ -110,6 +111,29 @@ struct lbehd_handle {
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[LBEHD_NKC];
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    // discrete adjoint (lbehd_adjoint_forward / lbehd_adjoint_backward)
+    struct HostState {
+        long long step;
+        int cur, pcur;
+        bool first, mg_valid;
+    };
+    struct Adj {
+        int S = 0, E = 0, seg = 0, T = 0, K = 0;   // segments, electrodes, steps per segment,
+                                                   // steps, checkpoint spacing
+        std::vector<double> V;                      // [S][E] schedule of the recorded run
+        std::vector<float *> ckpt, slot;            // states at 0, K, 2K, ...; one interval
+        std::vector<HostState> ckpt_host;
+        float *fin = nullptr;                       // state after the last step
+        HostState fin_host{};
+        bool have = false;                          // a forward run is recorded
+        double xc = 0.0, M1 = 0.0;                  // loss (x centroid) and droplet volume
+        float *lg[2] = {}, *lf[2] = {}, *lr[2] = {}, *lp[2] = {};
+        float *rec = nullptr, *loc = nullptr, *phibar = nullptr, *potbar = nullptr;
+        float *mu = nullptr, *rhs = nullptr, *seed = nullptr;
+        double *grad = nullptr;
+        size_t grad_cap = 0;
+        long long steps_replayed = 0, adj_steps = 0, adj_iters = 0;
+    } adj;
 };
 
 namespace {
@@ -1167,6 +1191,311 @@ int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
                        : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
     if (flag)
         return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
+    return LBEHD_OK;
+}
+
+// ------------------------------------------------------------ discrete adjoint
+
+// Floats per site of a saved state: populations, Phi^{n-1}, rho^{n-1}, u^{n-1}, Q^{n-1},
+// then the potential (hi, lo) and both warm-start increments.
+size_t adj_state_floats(const lbehd_handle *h) { return (size_t)(4 * h->Q + h->QS + 12); }
+
+struct StateView {
+    float *g, *fphi, *frho, *phi_prev, *rho_prev, *u, *q, *pot, *pot_lo, *inc0, *inc1;
+};
+
+StateView state_view(const lbehd_handle *h, float *base)
+{
+    const size_t N = h->N;
+    StateView v;
+    v.g = base;
+    v.fphi = v.g + h->Q * N;
+    v.frho = v.fphi + 3 * h->Q * N;
+    v.phi_prev = v.frho + h->QS * N;
+    v.rho_prev = v.phi_prev + 3 * N;
+    v.u = v.rho_prev + N;
+    v.q = v.u + 3 * N;
+    v.pot = v.q + N;
+    v.pot_lo = v.pot + N;
+    v.inc0 = v.pot_lo + N;
+    v.inc1 = v.inc0 + N;
+    return v;
+}
+
+// Copy the handle's state into / out of a saved state (device to device, on the stream).
+int adj_save(lbehd_handle *h, float *dst)
+{
+    const size_t N = h->N, fb = sizeof(float);
+    const StateView v = state_view(h, dst);
+    auto cp = [&](float *d, const float *s, size_t n) {
+        return cudaMemcpyAsync(d, s, n * fb, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    CK(h, cp(v.g, h->g[h->cur], h->Q * N));
+    CK(h, cp(v.fphi, h->fphi[h->cur], 3 * h->Q * N));
+    CK(h, cp(v.frho, h->frho[h->cur], h->QS * N));
+    CK(h, cp(v.phi_prev, h->phi[h->pcur ^ 1], 3 * N));
+    CK(h, cp(v.rho_prev, h->rho[h->pcur ^ 1], N));
+    CK(h, cp(v.u, h->u, 3 * N));
+    CK(h, cp(v.q, h->q, N));
+    CK(h, cp(v.pot, h->pot, N));
+    CK(h, cp(v.pot_lo, h->pot_lo, N));
+    CK(h, cp(v.inc0, h->inc[0], N));
+    CK(h, cp(v.inc1, h->inc[1], N));
+    return LBEHD_OK;
+}
+
+lbehd_handle::HostState host_state(const lbehd_handle *h)
+{
+    return lbehd_handle::HostState{h->step, h->cur, h->pcur, h->first, h->mg_valid};
+}
+
+int adj_restore(lbehd_handle *h, const float *src, const lbehd_handle::HostState &hs)
+{
+    h->step = hs.step;
+    h->cur = hs.cur;
+    h->pcur = hs.pcur;
+    h->first = hs.first;
+    h->mg_valid = false;   // rebuilt from this state's permittivity at the next step
+    const size_t N = h->N, fb = sizeof(float);
+    const StateView v = state_view(h, const_cast<float *>(src));
+    auto cp = [&](float *d, const float *s, size_t n) {
+        return cudaMemcpyAsync(d, s, n * fb, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    CK(h, cp(h->g[h->cur], v.g, h->Q * N));
+    CK(h, cp(h->fphi[h->cur], v.fphi, 3 * h->Q * N));
+    CK(h, cp(h->frho[h->cur], v.frho, h->QS * N));
+    CK(h, cp(h->phi[h->pcur ^ 1], v.phi_prev, 3 * N));
+    CK(h, cp(h->rho[h->pcur ^ 1], v.rho_prev, N));
+    CK(h, cp(h->u, v.u, 3 * N));
+    CK(h, cp(h->q, v.q, N));
+    CK(h, cp(h->pot, v.pot, N));
+    CK(h, cp(h->pot_lo, v.pot_lo, N));
+    CK(h, cp(h->inc[0], v.inc0, N));
+    CK(h, cp(h->inc[1], v.inc1, N));
+    return LBEHD_OK;
+}
+
+int adj_set_V(lbehd_handle *h, int t)
+{
+    auto &a = h->adj;
+    if (a.E == 0)
+        return LBEHD_OK;
+    const double *v = a.V.data() + (size_t)(t / a.seg) * a.E;
+    CK(h, cudaMemcpyAsync(h->V, v, a.E * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    return LBEHD_OK;
+}
+
+template <int D>
+int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *loss)
+{
+    auto &a = h->adj;
+    const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
+    a.S = S;
+    a.seg = seg;
+    a.E = h->cfg.n_electrodes;
+    a.T = S * seg;
+    // checkpoints every K steps: K ~ sqrt(T), a multiple of the 16-step multigrid refresh
+    a.K = std::max(16, (int)std::ceil(std::sqrt((double)a.T) / 16.0) * 16);
+    const int nck = (a.T + a.K - 1) / a.K;
+    a.V.assign(V, V + (size_t)S * a.E);
+    while ((int)a.ckpt.size() < nck) {
+        float *p = (float *)dev_alloc(h, SS * N * fb);
+        if (!p)
+            return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint checkpoints)");
+        a.ckpt.push_back(p);
+    }
+    a.ckpt_host.assign(nck, lbehd_handle::HostState{});
+    if (!a.fin && !(a.fin = (float *)dev_alloc(h, SS * N * fb)))
+        return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint final state)");
+    int worst = LBEHD_OK;
+    for (int t = 0; t < a.T; t++) {
+        if (t % a.K == 0) {
+            int rc = adj_save(h, a.ckpt[t / a.K]);
+            if (rc)
+                return rc;
+            a.ckpt_host[t / a.K] = host_state(h);
+        }
+        int rc = adj_set_V(h, t);
+        if (rc)
+            return rc;
+        rc = do_step<D>(h);
+        if (rc == LBEHD_ERR_POISSON_NOCONV)
+            worst = rc;
+        else if (rc)
+            return rc;
+    }
+    double o[2 * NOBS];
+    CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    a.M1 = o[0];
+    a.xc = o[0] != 0.0 ? o[1] / o[0] : 0.0;
+    int rc = adj_save(h, a.fin);
+    if (rc)
+        return rc;
+    a.fin_host = host_state(h);
+    a.have = true;
+    *loss = a.xc;
+    return worst;
+}
+
+int adj_alloc(lbehd_handle *h)
+{
+    auto &a = h->adj;
+    const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
+    while ((int)a.slot.size() < a.K) {
+        float *p = (float *)dev_alloc(h, SS * N * fb);
+        if (!p)
+            return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint replay)");
+        a.slot.push_back(p);
+    }
+    if (!a.rec) {
+        for (int b = 0; b < 2; b++) {
+            a.lg[b] = (float *)dev_alloc(h, h->Q * N * fb);
+            a.lf[b] = (float *)dev_alloc(h, 3 * h->Q * N * fb);
+            a.lr[b] = (float *)dev_alloc(h, h->QS * N * fb);
+            a.lp[b] = (float *)dev_alloc(h, 8 * N * fb);
+            if (!a.lg[b] || !a.lf[b] || !a.lr[b] || !a.lp[b])
+                return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint state)");
+        }
+        a.rec = (float *)dev_alloc(h, ADJ_REC * N * fb);
+        a.loc = (float *)dev_alloc(h, 5 * N * fb);
+        a.phibar = (float *)dev_alloc(h, 3 * N * fb);
+        a.potbar = (float *)dev_alloc(h, N * fb);
+        a.mu = (float *)dev_alloc(h, N * fb);
+        a.rhs = (float *)dev_alloc(h, N * fb);
+        a.seed = (float *)dev_alloc(h, 3 * N * fb);
+        if (!a.rec || !a.loc || !a.phibar || !a.potbar || !a.mu || !a.rhs || !a.seed)
+            return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint work arrays)");
+    }
+    const size_t ng = (size_t)std::max(1, a.S * a.E);
+    if (a.grad_cap < ng) {
+        a.grad = (double *)dev_alloc(h, ng * sizeof(double));
+        if (!a.grad)
+            return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint gradient)");
+        a.grad_cap = ng;
+    }
+    return LBEHD_OK;
+}
+
+// One reversed step t: lambda[ia] holds lambda^{t+1}; lambda[ia ^ 1] receives lambda^t.
+template <int D>
+int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
+{
+    auto &a = h->adj;
+    const size_t N = h->N;
+    const int ib = ia ^ 1;
+    const StateView v = state_view(h, slot);
+    int rc = adj_set_V(h, t);
+    if (rc)
+        return rc;
+    h->ls = h->stream;
+    // the step's fields Phi^n, rho^n, eps^n from its populations
+    const FieldPtrs F{v.fphi, v.frho, h->phi[0], h->rho[0], h->eps, v.pot, v.pot_lo,
+                      h->info, h->normal, h->elec, h->V};
+    k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, F);
+    mg_setup<D>(h);   // preconditioner of the adjoint solve, from eps^n
+    AdjFwd fw{v.g, v.fphi, v.frho, v.phi_prev, v.rho_prev, v.u, v.q, h->phi[0], h->rho[0],
+              h->eps, v.pot, v.pot_lo, h->info, h->normal};
+    const bool last = t == a.T - 1;
+    if (last)
+        k_adj_seed<<<h->nblocks1d, BX, 0, h->stream>>>(h->P, h->info, a.xc, a.M1, a.seed);
+    AdjBuf ab;
+    ab.lg_in = a.lg[ia];
+    ab.lf_in = a.lf[ia];
+    ab.lr_in = a.lr[ia];
+    ab.lPp_in = a.lp[ia];
+    ab.lrp_in = a.lp[ia] + 3 * N;
+    ab.lup_in = a.lp[ia] + 4 * N;
+    ab.lqp_in = a.lp[ia] + 7 * N;
+    ab.lg_out = a.lg[ib];
+    ab.lf_out = a.lf[ib];
+    ab.lr_out = a.lr[ib];
+    ab.lPp_out = a.lp[ib];
+    ab.lrp_out = a.lp[ib] + 3 * N;
+    ab.lup_out = a.lp[ib] + 4 * N;
+    ab.lqp_out = a.lp[ib] + 7 * N;
+    ab.rec = a.rec;
+    ab.loc = a.loc;
+    ab.phibar = a.phibar;
+    ab.potbar = a.potbar;
+    ab.mu = a.mu;
+    ab.seed = last ? a.seed : nullptr;
+    const int first = (t == 0 && a.ckpt_host[0].first) ? 1 : 0;
+    k_adj_collide<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab, first);
+    k_adj_gather<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab);
+    k_adj_rhs<<<h->grid1d, h->block, 0, h->stream>>>((long long)N, h->info, a.potbar, a.rhs);
+    // adjoint Gauss-law solve: A mu = phi_bar (A symmetric), from mu = 0
+    CK(h, cudaMemsetAsync(a.mu, 0, N * sizeof(float), h->stream));
+    k_adj_pcg_init<<<(unsigned)h->nblocks_site, h->block, 0, h->stream>>>(
+        (int)N, h->mg[0].D, a.rhs, h->cg_r, h->cg_partials);
+    cg_scalar(h, 2, 0, h->nblocks_site);
+    rc = pcg_host_loop<D>(h, a.mu);
+    if (rc)
+        return rc;
+    a.adj_iters += h->h_cg->iters;
+    AdjFieldsArgs fa{h->P.cos12, h->P.cos13, h->P.cos23, 4.0f / h->P.W, a.rhs};
+    k_adj_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab, fa);
+    k_adj_vgrad<D><<<std::min<size_t>(h->nblocks1d, 148 * 4), VGRAD_THREADS, 0, h->stream>>>(
+        h->P, fw, ab, h->elec, a.E, a.grad + (size_t)(t / a.seg) * a.E);
+    CK(h, cudaGetLastError());
+    h->launches += 9 + (last ? 1 : 0);
+    a.adj_steps++;
+    return LBEHD_OK;
+}
+
+template <int D>
+int adjoint_backward(lbehd_handle *h, double *grad)
+{
+    auto &a = h->adj;
+    if (!a.have)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "no recorded forward run (lbehd_adjoint_forward)");
+    int rc = adj_alloc(h);
+    if (rc)
+        return rc;
+    const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
+    CK(h, cudaMemsetAsync(a.grad, 0, (size_t)std::max(1, a.S * a.E) * sizeof(double), h->stream));
+    int ia = 0;
+    CK(h, cudaMemsetAsync(a.lg[ia], 0, h->Q * N * fb, h->stream));
+    CK(h, cudaMemsetAsync(a.lf[ia], 0, 3 * h->Q * N * fb, h->stream));
+    CK(h, cudaMemsetAsync(a.lr[ia], 0, h->QS * N * fb, h->stream));
+    CK(h, cudaMemsetAsync(a.lp[ia], 0, 8 * N * fb, h->stream));
+    const int nck = (a.T + a.K - 1) / a.K;
+    for (int ck = nck - 1; ck >= 0; ck--) {
+        const int t0 = ck * a.K, t1 = std::min(a.T, t0 + a.K);
+        if ((rc = adj_restore(h, a.ckpt[ck], a.ckpt_host[ck])))
+            return rc;
+        // replay the interval, keeping every step's input state and its potential
+        for (int t = t0; t < t1; t++) {
+            float *sl = a.slot[t - t0];
+            if ((rc = adj_save(h, sl)))
+                return rc;
+            if ((rc = adj_set_V(h, t)))
+                return rc;
+            rc = do_step<D>(h);
+            if (rc && rc != LBEHD_ERR_POISSON_NOCONV)
+                return rc;
+            const StateView v = state_view(h, sl);
+            CK(h, cudaMemcpyAsync(v.pot, h->pot, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(v.pot_lo, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+            a.steps_replayed++;
+        }
+        for (int t = t1 - 1; t >= t0; t--) {
+            if ((rc = adjoint_step<D>(h, t, ia, a.slot[t - t0])))
+                return rc;
+            ia ^= 1;
+        }
+    }
+    std::vector<double> g((size_t)std::max(1, a.S * a.E));
+    CK(h, cudaMemcpyAsync(g.data(), a.grad, g.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::copy(g.begin(), g.begin() + (size_t)a.S * a.E, grad);
+    (void)SS;
+    // leave the handle as the forward run left it
+    if ((rc = adj_restore(h, a.fin, a.fin_host)))
+        return rc;
+    h->mg_valid = false;
+    CK(h, cudaStreamSynchronize(h->stream));
     return LBEHD_OK;
 }
 
@@ -2251,6 +2580,30 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
     if (h->batch_owned)
         return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_set_option");
     return set_option_impl(h, option, value);
+}
+
+int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int seg_steps,
+                          double *loss)
+{
+    if (!h || !loss || (h->cfg.n_electrodes > 0 && !V))
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle, schedule or loss");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: the adjoint is per handle");
+    if (n_segments < 1 || seg_steps < 1 || (long long)n_segments * seg_steps > (1 << 24))
+        return fail(h, LBEHD_ERR_INVALID_ARG, "need n_segments >= 1, seg_steps >= 1");
+    if (h->prof)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "disable profiling before an adjoint run");
+    return h->dim == 2 ? adjoint_forward<2>(h, V, n_segments, seg_steps, loss)
+                       : adjoint_forward<3>(h, V, n_segments, seg_steps, loss);
+}
+
+int lbehd_adjoint_backward(lbehd_handle *h, double *grad)
+{
+    if (!h || !grad)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or gradient");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: the adjoint is per handle");
+    return h->dim == 2 ? adjoint_backward<2>(h, grad) : adjoint_backward<3>(h, grad);
 }
 
 int lbehd_autotune(lbehd_handle *h, int reps, double *ms)

@@ -86,7 +86,8 @@ _lib = None
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
            "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable",
-           "lbehd_profile_read", "lbehd_autotune", "lbehd_last_error", "lbehd_destroy",
+           "lbehd_profile_read", "lbehd_autotune", "lbehd_adjoint_forward",
+           "lbehd_adjoint_backward", "lbehd_last_error", "lbehd_destroy",
            "lbehd_batch_init", "lbehd_batch_step", "lbehd_batch_size", "lbehd_batch_instance",
            "lbehd_batch_observe", "lbehd_batch_set_option", "lbehd_batch_autotune",
            "lbehd_batch_get_stats", "lbehd_batch_profile_enable", "lbehd_batch_profile_read",
@@ -125,6 +126,9 @@ def load():
     lib.lbehd_destroy.argtypes = [P]
     lib.lbehd_destroy.restype = None
     lib.lbehd_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.lbehd_adjoint_forward.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.lbehd_adjoint_backward.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_batch_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(P)]
     lib.lbehd_batch_step.argtypes = [P, ctypes.c_int]
     lib.lbehd_batch_size.argtypes = [P]
@@ -334,6 +338,26 @@ class Simulation(_HandleOps):
             self._check(rc)
         return rc, {v + 1: ms[v] for v in range(4) if ms[v] >= 0}
 
+    def adjoint_forward(self, V, seg_steps):
+        """Run the potential schedule V ((segments, electrodes), seg_steps steps each) from
+        the current state, recording it for adjoint_backward; returns the loss (the droplet's
+        x centroid after the last step)."""
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        if V.ndim != 2 or V.shape[1] != self.n_electrodes:
+            raise ValueError("V must have shape (segments, n_electrodes)")
+        loss = ctypes.c_double()
+        self._check(self._lib.lbehd_adjoint_forward(self._h, _dptr(V, ctypes.c_double),
+                                                    V.shape[0], int(seg_steps),
+                                                    ctypes.byref(loss)), allow=(-3,))
+        self._adj_shape = V.shape
+        return loss.value
+
+    def adjoint_backward(self):
+        """dL/dV of the recorded run, shape (segments, electrodes)."""
+        g = np.zeros(self._adj_shape, dtype=np.float64)
+        self._check(self._lib.lbehd_adjoint_backward(self._h, _dptr(g, ctypes.c_double)))
+        return g
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lbehd_destroy(self._h)
@@ -452,3 +476,37 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class _ScheduleLoss:
+    """Built lazily so that importing this module does not import torch."""
+    fn = None
+
+    @classmethod
+    def get(cls):
+        if cls.fn is None:
+            import torch
+
+            class ScheduleLoss(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, V, sim, seg_steps):
+                    loss = sim.adjoint_forward(V.detach().cpu().double().numpy(), seg_steps)
+                    ctx.sim = sim
+                    ctx.meta = (V.dtype, V.device)
+                    return torch.tensor(loss, dtype=V.dtype, device=V.device)
+
+                @staticmethod
+                def backward(ctx, gL):
+                    dtype, device = ctx.meta
+                    g = torch.as_tensor(ctx.sim.adjoint_backward(), dtype=dtype, device=device)
+                    return g * gL, None, None
+
+            cls.fn = ScheduleLoss
+        return cls.fn
+
+
+def schedule_loss(sim, V, seg_steps):
+    """L(V) = droplet x centroid after running the electrode-potential schedule V
+    (tensor (segments, electrodes), seg_steps steps per segment) on ``sim`` from its current
+    state; differentiable: backward runs the library's discrete adjoint."""
+    return _ScheduleLoss.get().apply(V, sim, seg_steps)
