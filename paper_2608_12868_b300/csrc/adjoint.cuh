@@ -56,6 +56,8 @@ struct AdjBuf {
     float *lg_out, *lf_out, *lr_out;           // lambda of the populations at n
     float *lPp_out, *lrp_out, *lup_out, *lqp_out;   // lambda of Phi^{n-1}, rho^{n-1}, u^{n-1}, Q^{n-1}
     float *rec;                                // [ADJ_REC][N]
+    float *jb;                                 // [12][N]: adjoints of the first moments of
+                                               // f_Phi_1..3 (3 x 3) and f_rho (3)
     float *loc;                                // [5][N]: Phi_bar (3), rho_bar, phi_bar (site's own)
     float *phibar;                             // [3][N] gathered Phi_bar
     float *potbar;                             // [N] gathered phi_bar
@@ -106,6 +108,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
 
     // ================= forward recomputation (as in collide_site)
     float Pc[3];
+#pragma unroll
     for (int c = 0; c < 3; c++)
         Pc[c] = Fw.phi[c * N + i];
     const float pot_i = Fw.pot[i], lo_i = Fw.pot_lo[i];
@@ -114,11 +117,13 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     float sP[3] = {0.f, 0.f, 0.f}, gpot[3] = {0.f, 0.f, 0.f};
     float qsrc = 0.0f, Sg_self[3] = {0.f, 0.f, 0.f}, Sq_self = 0.0f, Sq_dph = 0.0f;
     unsigned fluid_nb = 1u;
+#pragma unroll
     for (int n = 1; n < Q; n++) {
         const int j = i + off(n);
         const float wn = L::w(n);
         const int pt = Fw.info[j] & 3;
         float Pn[3];
+#pragma unroll
         for (int c = 0; c < 3; c++) {
             Pn[c] = Fw.phi[c * N + j];
             sP[c] += wn * Pn[c];
@@ -144,8 +149,10 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         }
     }
     float lP[3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         lP[c] = 2.0f * inv_cs2 * (sP[c] - wmov * Pc[c]);
+#pragma unroll
         for (int a = 0; a < 3; a++)
             gP[c][a] *= inv_cs2;
     }
@@ -153,12 +160,15 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     const float ktri = 24.0f * P.YT / W;
     const float tri = ktri * Pc[0] * Pc[1] * Pc[2];
     float mu[3], Fs[3] = {0.f, 0.f, 0.f}, geps[3], E[3], E2 = 0.0f;
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         mu[c] = 24.0f * P.Y[c] / W * Pc[c] * (Pc[c] - 1.0f) * (Pc[c] - 0.5f) - tri -
                 0.75f * P.Y[c] * W * lP[c];
+#pragma unroll
         for (int a = 0; a < 3; a++)
             Fs[a] += mu[c] * gP[c][a];
     }
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         geps[a] = P.eps[0] * gP[0][a] + P.eps[1] * gP[1][a] + P.eps[2] * gP[2][a];
         E[a] = -inv_cs2 * gpot[a];
@@ -166,14 +176,17 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     }
     const float rho = Fw.rho[i];
     float Fe[3], F[3];
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         Fe[a] = rho * E[a] - 0.5f * E2 * geps[a];
         F[a] = Fs[a] + Fe[a] + P.body[a];
     }
     float gn[3], lam[3], ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f, FPhi[3][3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         gn[c] = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] + gP[c][2] * gP[c][2] + 1e-10f);
         lam[c] = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn[c];
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             ln[c][a] = lam[c] * gP[c][a];
             J[a] += ln[c][a];
@@ -182,13 +195,16 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     }
     const float inv_sumsq = 1.0f / sumsq;
     float rr[3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         rr[c] = Pc[c] * Pc[c] * inv_sumsq;
+#pragma unroll
         for (int a = 0; a < 3; a++)
             FPhi[c][a] = ln[c][a] - rr[c] * J[a];
     }
     float gs[Q], dp = 0.0f, jm[3] = {0.f, 0.f, 0.f};
     float m2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
     for (int n = 0; n < Q; n++) {
         const float v = Fw.g[n * N + i];
         gs[n] = v;
@@ -208,9 +224,11 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
             m2[5] += L::ey(n) * L::ez(n) > 0 ? v : -v;
     }
     float u[3];
+#pragma unroll
     for (int a = 0; a < 3; a++)
         u[a] = jm[a] + 0.5f * F[a];
     float uo[3], Po[3], rho_o = 0.0f, q_o = 0.0f;
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         uo[a] = first ? 0.0f : Fw.u_prev[a * N + i];
         Po[a] = first ? 0.0f : Fw.phi_prev[a * N + i];
@@ -230,6 +248,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     };
     float ub[3], Fb[3] = {0.f, 0.f, 0.f}, Pcb[3] = {0.f, 0.f, 0.f};
     float rhob = 0.0f, qb = A.lqp_in[i];
+#pragma unroll
     for (int a = 0; a < 3; a++)
         ub[a] = A.lup_in[a * N + i];
     float Pob[3] = {0.f, 0.f, 0.f}, uob[3] = {0.f, 0.f, 0.f}, rhoob = 0.0f, qob = 0.0f;
@@ -251,6 +270,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         const float dxy = m2[3] - u[0] * u[1] - 0.5f * (u[0] * F[1] + u[1] * F[0]);
         const float dxz = m2[4] - u[0] * u[2] - 0.5f * (u[0] * F[2] + u[2] * F[0]);
         const float dyz = m2[5] - u[1] * u[2] - 0.5f * (u[1] * F[2] + u[2] * F[1]);
+#pragma unroll
         for (int n = 1; n < Q; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
             const int e2 = cx * cx + cy * cy + cz * cz;
@@ -319,22 +339,26 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         Fb[1] += -0.5f * (dxyb * u[0] + dyzb * u[2]);
         Fb[2] += -0.5f * (dxzb * u[0] + dyzb * u[1]);
         dpb += -(float)D * (1.0f / 3.0f) * dTb;
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             ub[a] += -dTb * (2.0f * u[a] + F[a]);
             Fb[a] += -dTb * u[a];
         }
         // c_nu = 1 - 1/(3 nu + 0.5)
         const float nub = c_nub * inv_cs2 / (den * den);
+#pragma unroll
         for (int c = 0; c < 3; c++)
             Pcb[c] += nub * P.nu[c];
         // C0 = dp - 1.5 uu - 1.5 uF; V = 3u + 1.5F
         dpb += C0b;
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             ub[a] += -C0b * (3.0f * u[a] + 1.5f * F[a]) + 3.0f * Vb[a];
             Fb[a] += -1.5f * C0b * u[a] + 1.5f * Vb[a];
         }
         (void)uu;
         // moments of gs: dp, jm (= u - F/2, back-propagated below with the full u_bar), m2
+#pragma unroll
         for (int n = 0; n < Q; n++) {
             float v = dpb;
             if (L::ex(n))
@@ -355,10 +379,12 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
 
     // ---- phase-field collisions
     const float c_phi = 1.0f - P.inv_tau_phi;
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         const float *lin = A.lf_in + (size_t)c * Q * N;
         const float b0 = post_bar(lin, 0);   // rest: Pc - sum_{n>=1} v_n
         float Ppb = b0, Bb[3] = {0.f, 0.f, 0.f}, delb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
         for (int n = 1; n < Q; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
             const float an = post_bar(lin, n) - b0;
@@ -369,6 +395,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         }
         const float Pp = Pc[c];
         float jfb[3], Ab[3];
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             // del = c_phi/2 (jf - Pp u + A/2), B = 3 Pp u + 1.5 A
             jfb[a] = 0.5f * c_phi * delb[a];
@@ -385,10 +412,10 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
             }
         }
         Pcb[c] += Ppb;
-        // jf = sum e_n f_n (the site's own phase populations)
-        float *lo = A.lf_out + (size_t)c * Q * N;
-        for (int n = 0; n < Q; n++)
-            lo[(size_t)n * N + i] = edot<L>(n, jfb);
+        // jf = sum e_n f_n: lambda of f_Phi_c,n gets e_n . jfb (written by k_adj_fields)
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            A.jb[(size_t)(3 * c + a) * N + i] = jfb[a];
     }
 
     // ---- charge collision
@@ -397,6 +424,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         const float c_rho = 1.0f - P.inv_tau_rho;
         const float b0 = post_bar(A.lr_in, 0);   // rest: C0 - sum_{n>=1} v_n
         float C0b = b0, Bb[3] = {0.f, 0.f, 0.f}, delb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
         for (int n = 1; n < QS; n++) {
             const float an = post_bar(A.lr_in, n) - b0;
             C0b += L::ws(n) * an;
@@ -412,6 +440,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
             qob += -0.5f * C0b;
         }
         float jrb[3];
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             // del = c_rho/2 (jr - rho u + Dm/2), B = inv_cs2s (rho u + Dm/2)
             jrb[a] = 0.5f * c_rho * delb[a];
@@ -426,30 +455,37 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
                 uob[a] += -Dmb * rho_o;
             }
         }
-        for (int n = 0; n < QS; n++)
-            A.lr_out[(size_t)n * N + i] = edot<L>(n, jrb);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            A.jb[(size_t)(9 + a) * N + i] = jrb[a];
     }
 
     // ---- u = jm + F/2 (ub is now complete)
+#pragma unroll
     for (int a = 0; a < 3; a++)
         Fb[a] += 0.5f * ub[a];
+#pragma unroll
     for (int n = 0; n < Q; n++)
         A.lg_out[(size_t)n * N + i] = gsb[n] + edot<L>(n, ub);
 
     // ---- forces: F = Fs + Fe + body; Fe = rho E - E2 geps / 2; Fs = sum mu_c gP_c
     float gPb[3][3], gpotb[3], gepsb[3], Eb[3], E2b = 0.0f, mub[3];
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         rhob += Fb[a] * E[a];
         Eb[a] = Fb[a] * rho;
         E2b += -0.5f * Fb[a] * geps[a];
         gepsb[a] = -0.5f * E2 * Fb[a];
     }
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         Eb[a] += 2.0f * E[a] * E2b;
         gpotb[a] = -inv_cs2 * Eb[a];
     }
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         mub[c] = 0.0f;
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             mub[c] += Fb[a] * gP[c][a];
             gPb[c][a] = mu[c] * Fb[a] + P.eps[c] * gepsb[a];
@@ -457,6 +493,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     }
     // mu_c = 24 Y_c/W Pc (Pc - 1)(Pc - 1/2) - tri - 3/4 Y_c W lP_c
     float trib = 0.0f, lPb[3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         Pcb[c] += mub[c] * 24.0f * P.Y[c] / W * (3.0f * Pc[c] * Pc[c] - 3.0f * Pc[c] + 0.5f);
         trib += -mub[c];
@@ -466,6 +503,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     Pcb[1] += trib * ktri * Pc[0] * Pc[2];
     Pcb[2] += trib * ktri * Pc[0] * Pc[1];
     float sPb[3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         sPb[c] = 2.0f * inv_cs2 * lPb[c];
         Pcb[c] += -2.0f * inv_cs2 * wmov * lPb[c];
@@ -473,24 +511,30 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     // ---- sharpening flux: FPhi_c = ln_c - r_c J, ln_c = lam_c gP_c, J = sum ln_c
     {
         float Jb[3] = {0.f, 0.f, 0.f}, lnb[3][3], rb[3];
+#pragma unroll
         for (int c = 0; c < 3; c++) {
             rb[c] = 0.0f;
+#pragma unroll
             for (int a = 0; a < 3; a++) {
                 rb[c] += -FPhib[c][a] * J[a];
                 Jb[a] += -rr[c] * FPhib[c][a];
             }
         }
         float sumsqb = 0.0f;
+#pragma unroll
         for (int c = 0; c < 3; c++) {
+#pragma unroll
             for (int a = 0; a < 3; a++)
                 lnb[c][a] = FPhib[c][a] + Jb[a];
             // r_c = Pc^2 / sumsq
             Pcb[c] += rb[c] * 2.0f * Pc[c] * inv_sumsq;
             sumsqb += -rb[c] * Pc[c] * Pc[c] * inv_sumsq * inv_sumsq;
         }
+#pragma unroll
         for (int c = 0; c < 3; c++) {
             Pcb[c] += 2.0f * Pc[c] * sumsqb;
             float lamb = 0.0f;
+#pragma unroll
             for (int a = 0; a < 3; a++) {
                 lamb += lnb[c][a] * gP[c][a];
                 gPb[c][a] += lam[c] * lnb[c][a];
@@ -500,34 +544,44 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
             const float sg = s > 0.0f ? 1.0f : (s < 0.0f ? -1.0f : 0.0f);
             Pcb[c] += lamb * 4.0f / W * sg * (1.0f - 2.0f * Pc[c]) / gn[c];
             const float gnb = -lamb * lam[c] / gn[c];
+#pragma unroll
             for (int a = 0; a < 3; a++)
                 gPb[c][a] += gnb * gP[c][a] / gn[c];
         }
     }
     // ---- the conduction source's own-site terms: sig_i and -phi_i
+#pragma unroll
     for (int c = 0; c < 3; c++)
         Pcb[c] += qb * Sq_dph * P.sig[c];
     float potb = -qb * Sq_self;
+#pragma unroll
     for (int a = 0; a < 3; a++)
         potb += -gpotb[a] * Sg_self[a];
 
     // ---- records for the neighbours (gather pass) and the site's own adjoints
     float *rec = A.rec;
+#pragma unroll
     for (int c = 0; c < 3; c++)
+#pragma unroll
         for (int a = 0; a < 3; a++)
             rec[(size_t)(3 * c + a) * N + i] = gPb[c][a] * inv_cs2;   // d/d(raw weighted sum)
+#pragma unroll
     for (int c = 0; c < 3; c++)
         rec[(size_t)(9 + c) * N + i] = sPb[c];
+#pragma unroll
     for (int a = 0; a < 3; a++)
         rec[(size_t)(12 + a) * N + i] = gpotb[a];
     rec[(size_t)15 * N + i] = qb;
+#pragma unroll
     for (int c = 0; c < 3; c++)
         A.loc[(size_t)c * N + i] = Pcb[c];
     A.loc[(size_t)3 * N + i] = rhob;
     A.loc[(size_t)4 * N + i] = potb;
+#pragma unroll
     for (int c = 0; c < 3; c++)
         A.lPp_out[(size_t)c * N + i] = Pob[c];
     A.lrp_out[i] = rhoob;
+#pragma unroll
     for (int a = 0; a < 3; a++)
         A.lup_out[(size_t)a * N + i] = uob[a];
     A.lqp_out[i] = qob;
@@ -545,19 +599,18 @@ __global__ void __launch_bounds__(BX) k_adj_collide(Params P, AdjFwd Fw, AdjBuf 
         adj_collide_site<D>(P, Fw, A, first, x, y, z);
         return;
     }
-    // solid site: no populations, no stencil of its own
+    // solid site: no populations, no stencil of its own (k_adj_fields zeroes f_Phi, f_rho)
     using L = Lat<D>;
-    for (int n = 0; n < L::Q; n++) {
+#pragma unroll
+    for (int n = 0; n < L::Q; n++)
         A.lg_out[(size_t)n * N + i] = 0.0f;
-        for (int c = 0; c < 3; c++)
-            A.lf_out[((size_t)c * L::Q + n) * N + i] = 0.0f;
-    }
-    for (int n = 0; n < L::QS; n++)
-        A.lr_out[(size_t)n * N + i] = 0.0f;
+#pragma unroll
     for (int k = 0; k < ADJ_REC; k++)
         A.rec[(size_t)k * N + i] = 0.0f;
+#pragma unroll
     for (int k = 0; k < 5; k++)
         A.loc[(size_t)k * N + i] = 0.0f;
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         A.lPp_out[(size_t)c * N + i] = 0.0f;
         A.lup_out[(size_t)c * N + i] = 0.0f;
@@ -581,12 +634,15 @@ __global__ void __launch_bounds__(BX) k_adj_gather(Params P, AdjFwd Fw, AdjBuf A
     const int i = x0 + nx * (y0 + ny * z0);
     const int pt_y = Fw.info[i] & 3;
     float Pb[3], potb;
+#pragma unroll
     for (int c = 0; c < 3; c++)
         Pb[c] = A.loc[(size_t)c * N + i];
     potb = A.loc[(size_t)4 * N + i];
     float sig_y = 0.0f, phi_y = Fw.pot[i] + Fw.pot_lo[i];
+#pragma unroll
     for (int c = 0; c < 3; c++)
         sig_y += Fw.phi[c * N + i] * P.sig[c];
+#pragma unroll
     for (int n = 1; n < L::Q; n++) {
         // x = y - e_n reads y as its neighbour n
         int X = x0 - L::ex(n), Y = y0 - L::ey(n), Z = z0 - L::ez(n);
@@ -597,6 +653,7 @@ __global__ void __launch_bounds__(BX) k_adj_gather(Params P, AdjFwd Fw, AdjBuf A
         if ((Fw.info[xs] & 3) != PT_FLUID)
             continue;
         const float wn = L::w(n);
+#pragma unroll
         for (int c = 0; c < 3; c++) {
             float v = wn * A.rec[(size_t)(9 + c) * N + xs];
             if (L::ex(n))
@@ -620,14 +677,17 @@ __global__ void __launch_bounds__(BX) k_adj_gather(Params P, AdjFwd Fw, AdjBuf A
         if (pt_y == PT_FLUID && n <= 2 * D) {
             const float qb = A.rec[(size_t)15 * N + xs];
             float sig_x = 0.0f;
+#pragma unroll
             for (int c = 0; c < 3; c++)
                 sig_x += Fw.phi[c * N + xs] * P.sig[c];
             const float dph = phi_y - (Fw.pot[xs] + Fw.pot_lo[xs]);
             potb += qb * 0.5f * (sig_x + sig_y);
+#pragma unroll
             for (int c = 0; c < 3; c++)
                 Pb[c] += qb * 0.5f * dph * P.sig[c];
         }
     }
+#pragma unroll
     for (int c = 0; c < 3; c++)
         A.phibar[(size_t)c * N + i] = Pb[c];
     A.potbar[i] = potb;
@@ -662,8 +722,15 @@ __global__ void __launch_bounds__(BX) k_adj_fields(Params P, AdjFwd Fw, AdjBuf A
         return;
     const int N = (int)P.N, nx = P.nx, ny = P.ny, nz = P.nz;
     const int i = x0 + nx * (y0 + ny * z0);
-    if ((Fw.info[i] & 3) != PT_FLUID)
+    if ((Fw.info[i] & 3) != PT_FLUID) {
+#pragma unroll
+        for (int m = 0; m < 3 * L::Q; m++)
+            A.lf_out[(size_t)m * N + i] = 0.0f;
+#pragma unroll
+        for (int n = 0; n < L::QS; n++)
+            A.lr_out[(size_t)n * N + i] = 0.0f;
         return;
+    }
     auto site = [&](int n, int sgn) {
         int X = x0 + sgn * L::ex(n), Y = y0 + sgn * L::ey(n), Z = z0 + sgn * L::ez(n);
         X += X < 0 ? nx : (X >= nx ? -nx : 0);
@@ -672,6 +739,7 @@ __global__ void __launch_bounds__(BX) k_adj_fields(Params P, AdjFwd Fw, AdjBuf A
         return X + nx * (Y + ny * Z);
     };
     float Pb[3];
+#pragma unroll
     for (int c = 0; c < 3; c++) {
         Pb[c] = A.phibar[(size_t)c * N + i] + A.lPp_in[(size_t)c * N + i];
         if (A.seed)
@@ -681,6 +749,7 @@ __global__ void __launch_bounds__(BX) k_adj_fields(Params P, AdjFwd Fw, AdjBuf A
     // coefficients (eps_i + eps_j)/2 (fluid j) and eps_i (Dirichlet j)
     const float mu_i = A.mu[i], phi_i = Fw.pot[i] + Fw.pot_lo[i];
     float epsb = 0.0f, rhob = A.loc[(size_t)3 * N + i] + mu_i + A.lrp_in[i];
+#pragma unroll
     for (int n = 1; n < LS::QS; n++) {
         const int j = site(n, 1);
         const int pt = Fw.info[j] & 3;
@@ -690,10 +759,12 @@ __global__ void __launch_bounds__(BX) k_adj_fields(Params P, AdjFwd Fw, AdjBuf A
         else if (pt == PT_DIRICHLET)
             epsb += -mu_i * dphi;
     }
+#pragma unroll
     for (int c = 0; c < 3; c++)
         Pb[c] += epsb * P.eps[c];
     // wetting ghosts whose fluid source is this site: ghost s = y - e_k with normal k
     const float P1 = Fw.phi[i], P2 = Fw.phi[N + i], P3 = Fw.phi[2 * N + i];
+#pragma unroll
     for (int k = 1; k < L::Q; k++) {
         const int s = site(k, -1);
         if ((Fw.info[s] & 3) == PT_FLUID || Fw.normal[s] != k)
@@ -713,12 +784,23 @@ __global__ void __launch_bounds__(BX) k_adj_fields(Params P, AdjFwd Fw, AdjBuf A
         Pb[1] += g2 - q * (g1 * (-c12 * P1) + g2 * (c12 * P1 - c23 * P3) + g3 * (c23 * P3));
         Pb[2] += g3 - q * (g1 * (-c13 * P1) + g2 * (-c23 * P2) + g3 * (c23 * P2 + c13 * P1));
     }
-    // moments: Phi_c = sum_n f_Phi_c,n, rho = sum_n f_rho,n
-    for (int c = 0; c < 3; c++)
+    // moments: Phi_c = sum_n f_Phi_c,n, rho = sum_n f_rho,n; plus the collisions' first-moment
+    // terms e_n . jb
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float jf[3] = {A.jb[(size_t)(3 * c) * N + i], A.jb[(size_t)(3 * c + 1) * N + i],
+                             A.jb[(size_t)(3 * c + 2) * N + i]};
+#pragma unroll
         for (int n = 0; n < L::Q; n++)
-            A.lf_out[((size_t)c * L::Q + n) * N + i] += Pb[c];
-    for (int n = 0; n < L::QS; n++)
-        A.lr_out[(size_t)n * N + i] += rhob;
+            A.lf_out[((size_t)c * L::Q + n) * N + i] = edot<L>(n, jf) + Pb[c];
+    }
+    {
+        const float jr[3] = {A.jb[(size_t)9 * N + i], A.jb[(size_t)10 * N + i],
+                             A.jb[(size_t)11 * N + i]};
+#pragma unroll
+        for (int n = 0; n < L::QS; n++)
+            A.lr_out[(size_t)n * N + i] = edot<L>(n, jr) + rhob;
+    }
 }
 
 // dL/dV of one step: sum over each electrode's Dirichlet nodes of their phi_bar, and of
@@ -744,6 +826,7 @@ __global__ void __launch_bounds__(VGRAD_THREADS) k_adj_vgrad(Params P, AdjFwd Fw
         } else if (pt == PT_FLUID) {
             const int x0 = i % nx, y0 = (i / nx) % ny, z0 = i / (nx * ny);
             const float t = A.mu[i] * Fw.eps[i];
+#pragma unroll
             for (int n = 1; n < L::QS; n++) {
                 int X = x0 + L::ex(n), Y = y0 + L::ey(n), Z = z0 + L::ez(n);
                 X += X < 0 ? nx : (X >= nx ? -nx : 0);
@@ -777,22 +860,43 @@ __global__ void __launch_bounds__(BX) k_adj_seed(Params P, const uint8_t *__rest
     }
 }
 
-// Start of the adjoint Gauss-law solve A mu = rhs from mu = 0: r = rhs on the active cells,
-// partials of ||r||^2 and ||rhs||^2 over blocks of BX consecutive sites.
-__global__ void __launch_bounds__(BX) k_adj_pcg_init(int N, const float *__restrict__ Dg,
+constexpr double ADJ_POISSON_TOL = 1e-4;   // relative residual of the adjoint solves
+
+// Start of the adjoint Gauss-law solve A mu = rhs from the warm start mu: r = rhs - A mu on
+// the active cells, partials of ||r||^2 and ||rhs||^2 over blocks of BX consecutive sites.
+template <int D>
+__global__ void __launch_bounds__(BX) k_adj_pcg_init(MgDims d, const float *__restrict__ eps,
+                                                     const uint8_t *__restrict__ info,
+                                                     const float *__restrict__ Dg,
+                                                     const float *__restrict__ mu,
                                                      const float *__restrict__ rhs,
                                                      float *__restrict__ r,
                                                      double *__restrict__ partials)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
     float v[2] = {0.f, 0.f};
-    if (i < N) {
-        const float ri = Dg[i] > 0.0f ? rhs[i] : 0.0f;
+    if (i < d.nx * d.ny * d.nz) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float dummy[1] = {0.f};
+        pcg_Ap_site<D>(d, eps, info, Dg, mu, r, x, y, z, dummy);   // r = A mu
+        const float b = Dg[i] > 0.0f ? rhs[i] : 0.0f;
+        const float ri = Dg[i] > 0.0f ? __fsub_rn(b, r[i]) : 0.0f;
         r[i] = ri;
         v[0] = __fmul_rn(ri, ri);
-        v[1] = v[0];
+        v[1] = __fmul_rn(b, b);
     }
     block_partials<2>(v, partials);
+}
+
+// Warm start of the adjoint solve: mu = 2 mu1 - mu2 (linear extrapolation in time).
+__global__ void __launch_bounds__(BX) k_adj_extrapolate(long long n, const float *__restrict__ mu1,
+                                                        const float *__restrict__ mu2,
+                                                        float *__restrict__ mu)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        mu[i] = __fmaf_rn(2.0f, mu1[i], -mu2[i]);
 }
 
 }  // namespace lbehd

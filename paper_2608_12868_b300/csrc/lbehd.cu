@@ -128,11 +128,14 @@ struct lbehd_handle {
         bool have = false;                          // a forward run is recorded
         double xc = 0.0, M1 = 0.0;                  // loss (x centroid) and droplet volume
         float *lg[2] = {}, *lf[2] = {}, *lr[2] = {}, *lp[2] = {};
-        float *rec = nullptr, *loc = nullptr, *phibar = nullptr, *potbar = nullptr;
+        float *rec = nullptr, *loc = nullptr, *phibar = nullptr, *potbar = nullptr, *jb = nullptr;
         float *mu = nullptr, *rhs = nullptr, *seed = nullptr;
+        float *mu3[3] = {};                         // adjoint potentials, rotating by step
+        cudaGraphExec_t solve[3] = {};              // adjoint Gauss-law solve into mu3[k]
         double *grad = nullptr;
         size_t grad_cap = 0;
         long long steps_replayed = 0, adj_steps = 0, adj_iters = 0;
+        int dev_seg = -1;                           // segment whose potentials are on the device
     } adj;
 };
 
@@ -911,14 +914,18 @@ int init_impl(lbehd_handle *h)
             d = mg_dims(d.nx / 2, d.ny / 2, h->dim == 3 ? (d.nz + 1) / 2 : 1);
         }
         h->mg.back().cz2 = 0;
-        // shared-memory tail: the first level from which all coarser levels together have
-        // <= TAIL_MAX_TOTAL cells
+        // shared-memory tail: from the first level with <= 1024 cells; when no level is that
+        // small, the coarsest level alone if it has <= TAIL_MAX_TOTAL cells (one CTA then
+        // replaces its many sweep launches)
+        int tail_from = -1;
+        for (size_t l = 0; l < h->mg.size() && tail_from < 0; l++)
+            if (h->mg[l].n <= 1024 && h->mg.size() - l <= (size_t)TAIL_MAX_LEVELS)
+                tail_from = (int)l;
+        if (tail_from < 0 && h->mg.back().n <= (size_t)TAIL_MAX_TOTAL)
+            tail_from = (int)h->mg.size() - 1;
         for (size_t l = 0; l < h->mg.size(); l++) {
             const size_t nl = h->mg.size() - l;
-            size_t cells_below = 0;
-            for (size_t k = l; k < h->mg.size(); k++)
-                cells_below += h->mg[k].n;
-            if (cells_below <= (size_t)TAIL_MAX_TOTAL && nl <= (size_t)TAIL_MAX_LEVELS) {
+            if ((int)l == tail_from) {
                 TailLevels &T = h->tail;
                 T.nl = (int)nl;
                 T.nu = h->mg_nu;
@@ -1041,6 +1048,11 @@ void release(lbehd_handle *h)
         for (auto &e : row)
             if (e)
                 cudaGraphExecDestroy(e);
+    for (auto &e : h->adj.solve)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
     if (h->aux)
         cudaStreamDestroy(h->aux);
     h->aux = nullptr;
@@ -1275,11 +1287,13 @@ int adj_restore(lbehd_handle *h, const float *src, const lbehd_handle::HostState
     return LBEHD_OK;
 }
 
+// Electrode potentials of step t on the device (copied only when the segment changes).
 int adj_set_V(lbehd_handle *h, int t)
 {
     auto &a = h->adj;
-    if (a.E == 0)
+    if (a.E == 0 || t / a.seg == a.dev_seg)
         return LBEHD_OK;
+    a.dev_seg = t / a.seg;
     const double *v = a.V.data() + (size_t)(t / a.seg) * a.E;
     CK(h, cudaMemcpyAsync(h->V, v, a.E * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     return LBEHD_OK;
@@ -1305,6 +1319,7 @@ int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *lo
         a.ckpt.push_back(p);
     }
     a.ckpt_host.assign(nck, lbehd_handle::HostState{});
+    a.dev_seg = -1;
     if (!a.fin && !(a.fin = (float *)dev_alloc(h, SS * N * fb)))
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint final state)");
     int worst = LBEHD_OK;
@@ -1358,13 +1373,17 @@ int adj_alloc(lbehd_handle *h)
                 return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint state)");
         }
         a.rec = (float *)dev_alloc(h, ADJ_REC * N * fb);
+        a.jb = (float *)dev_alloc(h, 12 * N * fb);
         a.loc = (float *)dev_alloc(h, 5 * N * fb);
         a.phibar = (float *)dev_alloc(h, 3 * N * fb);
         a.potbar = (float *)dev_alloc(h, N * fb);
-        a.mu = (float *)dev_alloc(h, N * fb);
+        for (int k = 0; k < 3; k++)
+            a.mu3[k] = (float *)dev_alloc(h, N * fb);
+        a.mu = a.mu3[0];
         a.rhs = (float *)dev_alloc(h, N * fb);
         a.seed = (float *)dev_alloc(h, 3 * N * fb);
-        if (!a.rec || !a.loc || !a.phibar || !a.potbar || !a.mu || !a.rhs || !a.seed)
+        if (!a.rec || !a.jb || !a.loc || !a.phibar || !a.potbar || !a.mu3[0] || !a.mu3[1] ||
+            !a.mu3[2] || !a.rhs || !a.seed)
             return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint work arrays)");
     }
     const size_t ng = (size_t)std::max(1, a.S * a.E);
@@ -1375,6 +1394,54 @@ int adj_alloc(lbehd_handle *h)
         a.grad_cap = ng;
     }
     return LBEHD_OK;
+}
+
+// The adjoint Gauss-law solve as a graph: multigrid set-up from eps, r = rhs - A mu, then CG
+// iterations on mu while the residual is above ADJ_POISSON_TOL (conditional while node).
+template <int D>
+int capture_adj_solve(lbehd_handle *h, int km)
+{
+    auto &a = h->adj;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess)
+        return fail(h, LBEHD_ERR_CUDA, "cudaGraphCreate failed");
+    const long long launches = h->launches;
+    int rc = LBEHD_OK;
+    auto body = [&]() -> int {
+        CK(h, cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeRelaxed));
+        cudaGraphConditionalHandle c = 0;
+        CK(h, cudaGraphConditionalHandleCreate(&c, g, 0, 0));
+        h->ls = h->stream;
+        h->use_cond = 1;
+        h->use_ref = 0;
+        h->cond = c;
+        mg_setup<D>(h);
+        k_adj_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->stream>>>(
+            h->mg[0].d, h->eps, h->info, h->mg[0].D, a.mu3[km], a.rhs, h->cg_r, h->cg_partials);
+        cg_scalar(h, 2, 0, h->nblocks_site);
+        const int r = add_cond(h, h->stream, h->aux, c, cudaGraphCondTypeWhile, [&]() -> int {
+            pcg_iteration<D>(h, a.mu3[km]);
+            return LBEHD_OK;
+        });
+        if (r)
+            return r;
+        cudaGraph_t out = nullptr;
+        CK(h, cudaStreamEndCapture(h->stream, &out));
+        CK(h, cudaGraphInstantiate(&a.solve[km], g, 0));
+        return LBEHD_OK;
+    };
+    rc = body();
+    if (rc) {
+        for (cudaStream_t sx : {h->aux, h->stream})
+            abort_capture(sx);
+        cudaGetLastError();
+    }
+    h->use_cond = 0;
+    h->cond = 0;
+    h->launches = launches;
+    cudaGraphDestroy(g);
+    return rc;
 }
 
 // One reversed step t: lambda[ia] holds lambda^{t+1}; lambda[ia ^ 1] receives lambda^t.
@@ -1393,7 +1460,6 @@ int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
     const FieldPtrs F{v.fphi, v.frho, h->phi[0], h->rho[0], h->eps, v.pot, v.pot_lo,
                       h->info, h->normal, h->elec, h->V};
     k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, F);
-    mg_setup<D>(h);   // preconditioner of the adjoint solve, from eps^n
     AdjFwd fw{v.g, v.fphi, v.frho, v.phi_prev, v.rho_prev, v.u, v.q, h->phi[0], h->rho[0],
               h->eps, v.pot, v.pot_lo, h->info, h->normal};
     const bool last = t == a.T - 1;
@@ -1415,24 +1481,27 @@ int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
     ab.lup_out = a.lp[ib] + 4 * N;
     ab.lqp_out = a.lp[ib] + 7 * N;
     ab.rec = a.rec;
+    ab.jb = a.jb;
     ab.loc = a.loc;
     ab.phibar = a.phibar;
     ab.potbar = a.potbar;
+    // the adjoint potential of step t, warm-started from the linear extrapolation of those of
+    // steps t + 1 and t + 2 (buffers rotate with t)
+    const int km = t % 3;
+    a.mu = a.mu3[km];
     ab.mu = a.mu;
     ab.seed = last ? a.seed : nullptr;
     const int first = (t == 0 && a.ckpt_host[0].first) ? 1 : 0;
     k_adj_collide<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab, first);
     k_adj_gather<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab);
     k_adj_rhs<<<h->grid1d, h->block, 0, h->stream>>>((long long)N, h->info, a.potbar, a.rhs);
-    // adjoint Gauss-law solve: A mu = phi_bar (A symmetric), from mu = 0
-    CK(h, cudaMemsetAsync(a.mu, 0, N * sizeof(float), h->stream));
-    k_adj_pcg_init<<<(unsigned)h->nblocks_site, h->block, 0, h->stream>>>(
-        (int)N, h->mg[0].D, a.rhs, h->cg_r, h->cg_partials);
-    cg_scalar(h, 2, 0, h->nblocks_site);
-    rc = pcg_host_loop<D>(h, a.mu);
-    if (rc)
+    // adjoint Gauss-law solve A mu = phi_bar (A symmetric): one graph launch (multigrid
+    // preconditioner from eps^n, start, device-side CG loop)
+    if (!a.solve[km] && (rc = capture_adj_solve<D>(h, km)))
         return rc;
-    a.adj_iters += h->h_cg->iters;
+    k_adj_extrapolate<<<h->grid1d, h->block, 0, h->stream>>>((long long)N, a.mu3[(t + 1) % 3],
+                                                              a.mu3[(t + 2) % 3], a.mu);
+    CK(h, cudaGraphLaunch(a.solve[km], h->stream));
     AdjFieldsArgs fa{h->P.cos12, h->P.cos13, h->P.cos23, 4.0f / h->P.W, a.rhs};
     k_adj_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab, fa);
     k_adj_vgrad<D><<<std::min<size_t>(h->nblocks1d, 148 * 4), VGRAD_THREADS, 0, h->stream>>>(
@@ -1454,11 +1523,17 @@ int adjoint_backward(lbehd_handle *h, double *grad)
         return rc;
     const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
     CK(h, cudaMemsetAsync(a.grad, 0, (size_t)std::max(1, a.S * a.E) * sizeof(double), h->stream));
+    a.dev_seg = -1;
     int ia = 0;
     CK(h, cudaMemsetAsync(a.lg[ia], 0, h->Q * N * fb, h->stream));
     CK(h, cudaMemsetAsync(a.lf[ia], 0, 3 * h->Q * N * fb, h->stream));
     CK(h, cudaMemsetAsync(a.lr[ia], 0, h->QS * N * fb, h->stream));
     CK(h, cudaMemsetAsync(a.lp[ia], 0, 8 * N * fb, h->stream));
+    for (int k = 0; k < 3; k++)
+        CK(h, cudaMemsetAsync(a.mu3[k], 0, N * fb, h->stream));
+    // the adjoint solves stop at a relative residual of ADJ_POISSON_TOL
+    const double tol2 = ADJ_POISSON_TOL * ADJ_POISSON_TOL;
+    const double tol2_fwd = h->cfg.poisson_tol * h->cfg.poisson_tol;
     const int nck = (a.T + a.K - 1) / a.K;
     for (int ck = nck - 1; ck >= 0; ck--) {
         const int t0 = ck * a.K, t1 = std::min(a.T, t0 + a.K);
@@ -1479,11 +1554,15 @@ int adjoint_backward(lbehd_handle *h, double *grad)
             CK(h, cudaMemcpyAsync(v.pot_lo, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice, h->stream));
             a.steps_replayed++;
         }
+        CK(h, cudaMemcpyAsync(&h->cg_s->tol2, &tol2, sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
         for (int t = t1 - 1; t >= t0; t--) {
             if ((rc = adjoint_step<D>(h, t, ia, a.slot[t - t0])))
                 return rc;
             ia ^= 1;
         }
+        CK(h, cudaMemcpyAsync(&h->cg_s->tol2, &tol2_fwd, sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
     }
     std::vector<double> g((size_t)std::max(1, a.S * a.E));
     CK(h, cudaMemcpyAsync(g.data(), a.grad, g.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1493,6 +1572,8 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     (void)SS;
     // leave the handle as the forward run left it
     if ((rc = adj_restore(h, a.fin, a.fin_host)))
+        return rc;
+    if ((rc = adj_set_V(h, a.T - 1)))
         return rc;
     h->mg_valid = false;
     CK(h, cudaStreamSynchronize(h->stream));
