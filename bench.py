@@ -7,6 +7,10 @@ and wetting ghosts, Poisson solve, forces, fused collide + stream of all populat
 observable reductions) of the workload, whose state (~350 MB for the 128x64x64 lattice)
 is larger than L2, so no L2 flush is needed between steps.
 
+Beside the plain line: the 64-instance batched sweep ("batched") and the adjoint of the
+differentiable-control case ("adjoint": forward + backward cost per step against the plain
+step of the same schedule).
+
 Arms:
   default            the CUDA library through its C ABI, inputs resident in HBM;
   --impl reference   the FP64 CPU oracle on the host cores (a deliberately slow program;
@@ -283,9 +287,13 @@ def run_ours(args, world, rank, local):
     batched = None
     if args.batched > 0:
         batched = run_batched(args, dev, value / world, peak, peak_kind, clk)
+    adjoint = None
+    if args.adjoint_segments > 0 and args.adjoint_seg_steps > 0:
+        adjoint = run_adjoint(args, dev)
     clk.stop()
-    if batched is not None:
-        batched["clocks"] = clk.summary(*batched.pop("window"))
+    for extra in (batched, adjoint):
+        if extra is not None:
+            extra["clocks"] = clk.summary(*extra.pop("window"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -325,6 +333,7 @@ def run_ours(args, world, rank, local):
             "clocks": clocks,
             "autotune": tuned,
             "batched": batched,
+            "adjoint": adjoint,
             "obs_status": obs["status"],
             "mass_drift": float(np.abs(obs["mass"] / warm_obs["mass"] - 1).max()),
         }
@@ -394,6 +403,75 @@ def run_batched(args, dev, plain_mlups, peak, peak_kind, clk):
     return out
 
 
+def run_adjoint(args, dev):
+    """The differentiable-control case (96x64x64, 16 electrodes x 20 segments of 200
+    steps). Two handles from the same initial state run the same trajectory: handle A
+    records a forward run and its backward pass once untimed (checkpoint allocation, graph
+    capture), then is timed on a second forward + backward; handle B runs the schedule
+    plainly twice, the second time timed, so that its timed steps are A's timed steps.
+    CUDA events on each handle's stream."""
+    import torch
+    from paper_2608_12868_b300 import lbehd
+    from paper_2608_12868_b300 import workloads as W
+    w = W.control_3d_96x64x64()
+    V = np.array([v for _, v in w.schedule])[:args.adjoint_segments]
+    seg = args.adjoint_seg_steps
+    T = V.shape[0] * seg
+
+    def timed(stream, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), out
+
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    A = lbehd.Simulation(w, stream=sa, device=dev.index)
+    B = lbehd.Simulation(w, stream=sb, device=dev.index)
+    for sim in (A, B):
+        sim.step(1)
+    variant, _ = A.autotune(reps=10)
+    B.set_option(lbehd.OPT_COLLIDE, variant)
+
+    def plain():
+        for k in range(V.shape[0]):
+            B.set_electrodes(V[k])
+            B.step(seg)
+
+    A.adjoint_forward(V, seg)
+    A.adjoint_backward()
+    plain()
+    torch.cuda.synchronize(dev)
+    t_region0 = time.time()
+    it0 = B.stats()["poisson_iters"]
+    plain_ms, _ = timed(sb, plain)
+    plain_iters = (B.stats()["poisson_iters"] - it0) / T
+    fwd_ms, L = timed(sa, lambda: A.adjoint_forward(V, seg))
+    bwd_ms, g = timed(sa, A.adjoint_backward)
+    t_region1 = time.time()
+    info = A.adjoint_info()
+    A.close()
+    B.close()
+    return {
+        "workload": f"{w.name}: {V.shape[1]} electrodes x {V.shape[0]} segments of {seg} "
+                    f"steps ({V.size} parameters), loss = final droplet x centroid",
+        "steps": T, "timed_steps": f"{T + 1}..{2 * T} of the run",
+        "checkpoint_every": info["checkpoint_every"], "checkpoints": info["checkpoints"],
+        "potential_trajectory": bool(info["trajectory"]),
+        "plain_ms_per_step": plain_ms / T, "forward_ms_per_step": fwd_ms / T,
+        "backward_ms_per_step": bwd_ms / T,
+        "cost_vs_plain": (fwd_ms + bwd_ms) / plain_ms,
+        "backward_vs_plain": bwd_ms / plain_ms,
+        "plain_poisson_iters_per_step": plain_iters,
+        "adjoint_cg_iters_per_step": info["adjoint_cg_iters"] / max(info["steps_reversed"], 1),
+        "device_gb": info["device_bytes"] / 1e9,
+        "loss": L, "grad_max_abs": float(np.abs(g).max()),
+        "timing": "CUDA events on each simulation's stream; same steps for plain and adjoint",
+        "window": (t_region0, t_region1),
+    }
+
+
 def run_profile_window(args, local):
     """Warm up, then bracket --profile-steps eager coupled steps with cudaProfilerStart /
     Stop (for `ncu --profile-from-start off`). Prints one line, no timing. With
@@ -453,6 +531,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-lb-steps", type=int, default=20,
                     help="coupled steps per timed batched step (20: ~0.2 s for 64 instances)")
+    ap.add_argument("--adjoint-segments", type=int, default=20,
+                    help="segments of the differentiable-control schedule (0: skip the adjoint)")
+    ap.add_argument("--adjoint-seg-steps", type=int, default=200)
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)

@@ -177,6 +177,11 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   every `value` steps (default 16). The CG operator itself is formed from this step's
  *   permittivity every step, so the refresh period only affects convergence speed. */
 #define LBEHD_OPT_MG_REFRESH 2
+/*   LBEHD_OPT_ADJ_TRAJECTORY: 1 (default) lbehd_adjoint_forward records every step's
+ *   potential (8 bytes per site per step) when the allocation succeeds, so that the
+ *   backward replays need no Gauss-law solve; 0 never records it (replays solve again and
+ *   reproduce the same potential bit for bit). */
+#define LBEHD_OPT_ADJ_TRAJECTORY 3
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 
 /* Counters since init (synchronises: reads the device-side iteration counter). */
@@ -252,24 +257,37 @@ int lbehd_autotune(lbehd_handle *h, int reps, double *ms);
  *
  * lbehd_adjoint_forward runs the n_segments * seg_steps steps from the handle's current state
  * (as lbehd_step would, the potentials set segment by segment). On the way it keeps the state
- * every K ~ sqrt(steps) steps (K a multiple of 16) in device memory. It returns the loss
+ * every K ~ sqrt(steps) steps (K a multiple of 16) in device memory, and (see
+ * LBEHD_OPT_ADJ_TRAJECTORY) the potential of every step. It returns the loss
  * L = sum Phi_1 x / sum Phi_1 over the fluid nodes after the last step (the x centroid
  * lbehd_observe reports). The handle is left after the last step.
  *
  * lbehd_adjoint_backward returns grad[k * n_electrodes + e] = dL/dV[k][e], the discrete
- * adjoint of the recorded run. It replays one checkpoint interval at a time, keeping every
- * step's input state and potential, and runs the reversed steps: the reverse of the fused
+ * adjoint of the recorded run. It replays one checkpoint interval at a time (moments and
+ * collide with the recorded potential, or whole steps without a recorded trajectory),
+ * keeping every step's input state, and runs the reversed steps: the reverse of the fused
  * collide kernel, the gather of the stencils' adjoints, one adjoint Gauss-law solve with the
  * same symmetric operator (preconditioned CG), the reverse of the moments and wetting ghosts,
  * and the per-electrode sums. The first step of a fresh handle has no backward differences
  * and contributes none. Afterwards the handle is again in the state after the last step.
- * Memory: (ceil(steps / K) + K + 1) saved states of (4 Q + Q_s + 12) floats per site.
+ * Memory: (ceil(steps / K) + K + 1) saved states of (4 Q + Q_s + 12) floats per site, plus
+ * 2 floats per site per step for the recorded potential.
  * Synchronise. Errors: LBEHD_ERR_INVALID_ARG (no recorded run, bad sizes, batch instance),
  * LBEHD_ERR_OOM, LBEHD_ERR_CUDA; LBEHD_ERR_POISSON_NOCONV from the forward is reported but
  * the run completes. */
 int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int seg_steps,
                           double *loss);
 int lbehd_adjoint_backward(lbehd_handle *h, double *grad);
+
+/* The recorded adjoint run: its steps, checkpoint spacing K and count, whether every step's
+ * potential was recorded, the steps replayed and reversed by the last backward pass, the
+ * adjoint CG iterations it took, and the device bytes the adjoint holds (checkpoints,
+ * replay slots, trajectory, work arrays). All zero before the first forward run. */
+typedef struct lbehd_adjoint_info {
+    long long steps, checkpoint_every, checkpoints, trajectory;
+    long long steps_replayed, steps_reversed, adjoint_cg_iters, device_bytes;
+} lbehd_adjoint_info;
+int lbehd_adjoint_get_info(lbehd_handle *h, lbehd_adjoint_info *out);
 
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
 const char *lbehd_last_error(lbehd_handle *h);

@@ -130,11 +130,17 @@ struct lbehd_handle {
         float *lg[2] = {}, *lf[2] = {}, *lr[2] = {}, *lp[2] = {};
         float *rec = nullptr, *loc = nullptr, *phibar = nullptr, *potbar = nullptr, *jb = nullptr;
         float *mu = nullptr, *rhs = nullptr, *seed = nullptr;
+        float *ptraj = nullptr;                     // [T][2][N] potential (hi, lo) of each step
+        size_t ptraj_cap = 0;                       //   (null: replays re-solve Gauss's law)
+        bool use_traj = true;
+        int mg_age = 0;                             // reversed steps since the multigrid rebuild
         float *mu3[3] = {};                         // adjoint potentials, rotating by step
         cudaGraphExec_t solve[3] = {};              // adjoint Gauss-law solve into mu3[k]
         double *grad = nullptr;
         size_t grad_cap = 0;
-        long long steps_replayed = 0, adj_steps = 0, adj_iters = 0;
+        long long steps_replayed = 0, adj_steps = 0, adj_iters = 0;   // last backward pass
+        size_t bytes = 0;                                              // device memory held
+        long long fwd_iters = 0;                    // CG iterations of the recorded run
         int dev_seg = -1;                           // segment whose potentials are on the device
     } adj;
 };
@@ -175,6 +181,19 @@ void *dev_alloc(lbehd_handle *h, size_t bytes)
     if (p)
         h->bufs.push_back({p, bytes});
     return p;
+}
+
+void dev_free(lbehd_handle *h, void *p)
+{
+    for (size_t k = 0; k < h->bufs.size(); k++)
+        if (h->bufs[k].ptr == p) {
+            if (h->cfg.free)
+                h->cfg.free(p, h->cfg.alloc_ctx);
+            else
+                cudaFree(p);
+            h->bufs.erase(h->bufs.begin() + (long)k);
+            return;
+        }
 }
 
 // Lattice normal of a boundary solid node: the fluid neighbour direction maximising
@@ -1157,6 +1176,19 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
         CK(h, cudaStreamSynchronize(h->stream));
         h->mg_refresh = (int)value;
         h->mg_valid = false;
+    } else if (option == LBEHD_OPT_ADJ_TRAJECTORY) {
+        if (value < 0 || value > 1)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_ADJ_TRAJECTORY takes 0 or 1");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->adj.use_traj = value != 0;
+        if (!h->adj.use_traj && h->adj.ptraj) {   // a recorded run needs its trajectory
+            dev_free(h, h->adj.ptraj);
+            h->adj.bytes -= h->adj.ptraj_cap * sizeof(float);
+            h->adj.ptraj = nullptr;
+            h->adj.ptraj_cap = 0;
+            h->adj.have = false;
+        }
+        return LBEHD_OK;
     } else {
         return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
     }
@@ -1235,7 +1267,26 @@ StateView state_view(const lbehd_handle *h, float *base)
 }
 
 // Copy the handle's state into / out of a saved state (device to device, on the stream).
-int adj_save(lbehd_handle *h, float *dst)
+// The device-side count of CG iterations so far (synchronises).
+int cg_total_iters(lbehd_handle *h, long long *v)
+{
+    CgScalars s0;
+    CK(h, cudaMemcpyAsync(&s0, h->cg_s, sizeof(s0), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *v = s0.total_iters;
+    return LBEHD_OK;
+}
+
+// Device allocation held by the adjoint (counted in adj.bytes).
+float *adj_alloc_floats(lbehd_handle *h, size_t n)
+{
+    float *p = (float *)dev_alloc(h, n * sizeof(float));
+    if (p)
+        h->adj.bytes += n * sizeof(float);
+    return p;
+}
+
+int adj_save(lbehd_handle *h, float *dst, bool with_potential = true)
 {
     const size_t N = h->N, fb = sizeof(float);
     const StateView v = state_view(h, dst);
@@ -1249,6 +1300,8 @@ int adj_save(lbehd_handle *h, float *dst)
     CK(h, cp(v.rho_prev, h->rho[h->pcur ^ 1], N));
     CK(h, cp(v.u, h->u, 3 * N));
     CK(h, cp(v.q, h->q, N));
+    if (!with_potential)
+        return LBEHD_OK;
     CK(h, cp(v.pot, h->pot, N));
     CK(h, cp(v.pot_lo, h->pot_lo, N));
     CK(h, cp(v.inc0, h->inc[0], N));
@@ -1313,16 +1366,31 @@ int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *lo
     const int nck = (a.T + a.K - 1) / a.K;
     a.V.assign(V, V + (size_t)S * a.E);
     while ((int)a.ckpt.size() < nck) {
-        float *p = (float *)dev_alloc(h, SS * N * fb);
+        float *p = adj_alloc_floats(h, SS * N);
         if (!p)
             return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint checkpoints)");
         a.ckpt.push_back(p);
     }
     a.ckpt_host.assign(nck, lbehd_handle::HostState{});
     a.dev_seg = -1;
-    if (!a.fin && !(a.fin = (float *)dev_alloc(h, SS * N * fb)))
+    if (!a.fin && !(a.fin = adj_alloc_floats(h, SS * N)))
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint final state)");
+    // the potential of every step (8 N bytes a step), so that replays need no Gauss-law solve;
+    // without room for it the replays solve again (same iterates, same bits)
+    const size_t ptraj_need = (size_t)a.T * 2 * N;
+    if (a.use_traj && a.ptraj_cap < ptraj_need) {
+        if (a.ptraj) {
+            dev_free(h, a.ptraj);
+            a.bytes -= a.ptraj_cap * fb;
+        }
+        a.ptraj = adj_alloc_floats(h, ptraj_need);
+        a.ptraj_cap = a.ptraj ? ptraj_need : 0;
+    }
     int worst = LBEHD_OK;
+    long long it0 = 0;
+    int rc0 = cg_total_iters(h, &it0);
+    if (rc0)
+        return rc0;
     for (int t = 0; t < a.T; t++) {
         if (t % a.K == 0) {
             int rc = adj_save(h, a.ckpt[t / a.K]);
@@ -1338,12 +1406,21 @@ int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *lo
             worst = rc;
         else if (rc)
             return rc;
+        if (a.ptraj) {
+            float *pt = a.ptraj + (size_t)t * 2 * N;
+            CK(h, cudaMemcpyAsync(pt, h->pot, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(pt + N, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+        }
     }
     double o[2 * NOBS];
     CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     a.M1 = o[0];
     a.xc = o[0] != 0.0 ? o[1] / o[0] : 0.0;
+    long long it1 = 0;
+    if ((rc0 = cg_total_iters(h, &it1)))
+        return rc0;
+    a.fwd_iters = it1 - it0;
     int rc = adj_save(h, a.fin);
     if (rc)
         return rc;
@@ -1356,32 +1433,32 @@ int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *lo
 int adj_alloc(lbehd_handle *h)
 {
     auto &a = h->adj;
-    const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
+    const size_t N = h->N, SS = adj_state_floats(h);
     while ((int)a.slot.size() < a.K) {
-        float *p = (float *)dev_alloc(h, SS * N * fb);
+        float *p = adj_alloc_floats(h, SS * N);
         if (!p)
             return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint replay)");
         a.slot.push_back(p);
     }
     if (!a.rec) {
         for (int b = 0; b < 2; b++) {
-            a.lg[b] = (float *)dev_alloc(h, h->Q * N * fb);
-            a.lf[b] = (float *)dev_alloc(h, 3 * h->Q * N * fb);
-            a.lr[b] = (float *)dev_alloc(h, h->QS * N * fb);
-            a.lp[b] = (float *)dev_alloc(h, 8 * N * fb);
+            a.lg[b] = adj_alloc_floats(h, h->Q * N);
+            a.lf[b] = adj_alloc_floats(h, 3 * h->Q * N);
+            a.lr[b] = adj_alloc_floats(h, h->QS * N);
+            a.lp[b] = adj_alloc_floats(h, 8 * N);
             if (!a.lg[b] || !a.lf[b] || !a.lr[b] || !a.lp[b])
                 return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint state)");
         }
-        a.rec = (float *)dev_alloc(h, ADJ_REC * N * fb);
-        a.jb = (float *)dev_alloc(h, 12 * N * fb);
-        a.loc = (float *)dev_alloc(h, 5 * N * fb);
-        a.phibar = (float *)dev_alloc(h, 3 * N * fb);
-        a.potbar = (float *)dev_alloc(h, N * fb);
+        a.rec = adj_alloc_floats(h, ADJ_REC * N);
+        a.jb = adj_alloc_floats(h, 12 * N);
+        a.loc = adj_alloc_floats(h, 5 * N);
+        a.phibar = adj_alloc_floats(h, 3 * N);
+        a.potbar = adj_alloc_floats(h, N);
         for (int k = 0; k < 3; k++)
-            a.mu3[k] = (float *)dev_alloc(h, N * fb);
+            a.mu3[k] = adj_alloc_floats(h, N);
         a.mu = a.mu3[0];
-        a.rhs = (float *)dev_alloc(h, N * fb);
-        a.seed = (float *)dev_alloc(h, 3 * N * fb);
+        a.rhs = adj_alloc_floats(h, N);
+        a.seed = adj_alloc_floats(h, 3 * N);
         if (!a.rec || !a.jb || !a.loc || !a.phibar || !a.potbar || !a.mu3[0] || !a.mu3[1] ||
             !a.mu3[2] || !a.rhs || !a.seed)
             return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint work arrays)");
@@ -1391,13 +1468,14 @@ int adj_alloc(lbehd_handle *h)
         a.grad = (double *)dev_alloc(h, ng * sizeof(double));
         if (!a.grad)
             return fail(h, LBEHD_ERR_OOM, "device allocation failed (adjoint gradient)");
+        a.bytes += ng * sizeof(double);
         a.grad_cap = ng;
     }
     return LBEHD_OK;
 }
 
-// The adjoint Gauss-law solve as a graph: multigrid set-up from eps, r = rhs - A mu, then CG
-// iterations on mu while the residual is above ADJ_POISSON_TOL (conditional while node).
+// The adjoint Gauss-law solve as a graph: r = rhs - A mu, then CG iterations on mu while the
+// residual is above ADJ_POISSON_TOL (conditional while node).
 template <int D>
 int capture_adj_solve(lbehd_handle *h, int km)
 {
@@ -1416,7 +1494,6 @@ int capture_adj_solve(lbehd_handle *h, int km)
         h->use_cond = 1;
         h->use_ref = 0;
         h->cond = c;
-        mg_setup<D>(h);
         k_adj_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->stream>>>(
             h->mg[0].d, h->eps, h->info, h->mg[0].D, a.mu3[km], a.rhs, h->cg_r, h->cg_partials);
         cg_scalar(h, 2, 0, h->nblocks_site);
@@ -1456,12 +1533,15 @@ int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
     if (rc)
         return rc;
     h->ls = h->stream;
+    // the step's potential (recorded trajectory, else the replay's copy in the slot)
+    float *pot = a.ptraj ? a.ptraj + (size_t)t * 2 * N : v.pot;
+    float *pot_lo = a.ptraj ? pot + N : v.pot_lo;
     // the step's fields Phi^n, rho^n, eps^n from its populations
-    const FieldPtrs F{v.fphi, v.frho, h->phi[0], h->rho[0], h->eps, v.pot, v.pot_lo,
+    const FieldPtrs F{v.fphi, v.frho, h->phi[0], h->rho[0], h->eps, pot, pot_lo,
                       h->info, h->normal, h->elec, h->V};
     k_fields<D><<<h->grid, h->block, 0, h->stream>>>(h->P, F);
     AdjFwd fw{v.g, v.fphi, v.frho, v.phi_prev, v.rho_prev, v.u, v.q, h->phi[0], h->rho[0],
-              h->eps, v.pot, v.pot_lo, h->info, h->normal};
+              h->eps, pot, pot_lo, h->info, h->normal};
     const bool last = t == a.T - 1;
     if (last)
         k_adj_seed<<<h->nblocks1d, BX, 0, h->stream>>>(h->P, h->info, a.xc, a.M1, a.seed);
@@ -1495,8 +1575,11 @@ int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
     k_adj_collide<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab, first);
     k_adj_gather<D><<<h->grid, h->block, 0, h->stream>>>(h->P, fw, ab);
     k_adj_rhs<<<h->grid1d, h->block, 0, h->stream>>>((long long)N, h->info, a.potbar, a.rhs);
-    // adjoint Gauss-law solve A mu = phi_bar (A symmetric): one graph launch (multigrid
-    // preconditioner from eps^n, start, device-side CG loop)
+    // adjoint Gauss-law solve A mu = phi_bar (A symmetric, built from eps^n): one graph launch
+    // (start, device-side CG loop). The multigrid preconditioner is rebuilt from eps^n every
+    // 16 reversed steps, as in the forward run.
+    if (a.mg_age++ % 16 == 0)
+        mg_setup<D>(h);
     if (!a.solve[km] && (rc = capture_adj_solve<D>(h, km)))
         return rc;
     k_adj_extrapolate<<<h->grid1d, h->block, 0, h->stream>>>((long long)N, a.mu3[(t + 1) % 3],
@@ -1512,6 +1595,30 @@ int adjoint_step(lbehd_handle *h, int t, int ia, float *slot)
     return LBEHD_OK;
 }
 
+// A replayed forward step t with the recorded potential of that step in place of the
+// Gauss-law solve: the same moments and collide kernels as the recorded step, so the same
+// bits.
+template <int D>
+int replay_step(lbehd_handle *h, int t)
+{
+    auto &a = h->adj;
+    const size_t N = h->N, fb = sizeof(float);
+    h->ls = h->stream;
+    int rc = launch_fields<D>(h);
+    if (rc)
+        return rc;
+    const float *pt = a.ptraj + (size_t)t * 2 * N;
+    CK(h, cudaMemcpyAsync(h->pot, pt, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->pot_lo, pt + N, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+    collide<D>(h);
+    CK(h, cudaGetLastError());
+    h->cur ^= 1;
+    h->pcur ^= 1;
+    h->first = false;
+    h->step++;
+    return LBEHD_OK;
+}
+
 template <int D>
 int adjoint_backward(lbehd_handle *h, double *grad)
 {
@@ -1524,6 +1631,11 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     const size_t N = h->N, fb = sizeof(float), SS = adj_state_floats(h);
     CK(h, cudaMemsetAsync(a.grad, 0, (size_t)std::max(1, a.S * a.E) * sizeof(double), h->stream));
     a.dev_seg = -1;
+    a.mg_age = 0;
+    a.steps_replayed = a.adj_steps = 0;
+    long long it0 = 0, it1 = 0;
+    if ((rc = cg_total_iters(h, &it0)))
+        return rc;
     int ia = 0;
     CK(h, cudaMemsetAsync(a.lg[ia], 0, h->Q * N * fb, h->stream));
     CK(h, cudaMemsetAsync(a.lf[ia], 0, 3 * h->Q * N * fb, h->stream));
@@ -1539,23 +1651,31 @@ int adjoint_backward(lbehd_handle *h, double *grad)
         const int t0 = ck * a.K, t1 = std::min(a.T, t0 + a.K);
         if ((rc = adj_restore(h, a.ckpt[ck], a.ckpt_host[ck])))
             return rc;
-        // replay the interval, keeping every step's input state and its potential
+        // replay the interval, keeping every step's input state (and, without a recorded
+        // trajectory, its potential)
         for (int t = t0; t < t1; t++) {
             float *sl = a.slot[t - t0];
-            if ((rc = adj_save(h, sl)))
+            if ((rc = adj_save(h, sl, a.ptraj == nullptr)))
                 return rc;
             if ((rc = adj_set_V(h, t)))
                 return rc;
-            rc = do_step<D>(h);
-            if (rc && rc != LBEHD_ERR_POISSON_NOCONV)
-                return rc;
-            const StateView v = state_view(h, sl);
-            CK(h, cudaMemcpyAsync(v.pot, h->pot, N * fb, cudaMemcpyDeviceToDevice, h->stream));
-            CK(h, cudaMemcpyAsync(v.pot_lo, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+            if (a.ptraj) {
+                if ((rc = replay_step<D>(h, t)))
+                    return rc;
+            } else {
+                rc = do_step<D>(h);
+                if (rc && rc != LBEHD_ERR_POISSON_NOCONV)
+                    return rc;
+                const StateView v = state_view(h, sl);
+                CK(h, cudaMemcpyAsync(v.pot, h->pot, N * fb, cudaMemcpyDeviceToDevice, h->stream));
+                CK(h, cudaMemcpyAsync(v.pot_lo, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice,
+                                      h->stream));
+            }
             a.steps_replayed++;
         }
         CK(h, cudaMemcpyAsync(&h->cg_s->tol2, &tol2, sizeof(double), cudaMemcpyHostToDevice,
                               h->stream));
+        a.mg_age = 0;   // preconditioner rebuilt at the interval's last step, then every 16
         for (int t = t1 - 1; t >= t0; t--) {
             if ((rc = adjoint_step<D>(h, t, ia, a.slot[t - t0])))
                 return rc;
@@ -1567,7 +1687,10 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     std::vector<double> g((size_t)std::max(1, a.S * a.E));
     CK(h, cudaMemcpyAsync(g.data(), a.grad, g.size() * sizeof(double), cudaMemcpyDeviceToHost,
                           h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    if ((rc = cg_total_iters(h, &it1)))
+        return rc;
+    // replays without a trajectory repeat the recorded run's solves, iteration for iteration
+    a.adj_iters = it1 - it0 - (a.ptraj ? 0 : a.fwd_iters);
     std::copy(g.begin(), g.begin() + (size_t)a.S * a.E, grad);
     (void)SS;
     // leave the handle as the forward run left it
@@ -2676,6 +2799,25 @@ int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int 
         return fail(h, LBEHD_ERR_INVALID_ARG, "disable profiling before an adjoint run");
     return h->dim == 2 ? adjoint_forward<2>(h, V, n_segments, seg_steps, loss)
                        : adjoint_forward<3>(h, V, n_segments, seg_steps, loss);
+}
+
+int lbehd_adjoint_get_info(lbehd_handle *h, lbehd_adjoint_info *out)
+{
+    if (!h || !out)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or output");
+    const auto &a = h->adj;
+    std::memset(out, 0, sizeof(*out));
+    if (a.T == 0)
+        return LBEHD_OK;
+    out->steps = a.T;
+    out->checkpoint_every = a.K;
+    out->checkpoints = (a.T + a.K - 1) / a.K;
+    out->trajectory = a.ptraj ? 1 : 0;
+    out->steps_replayed = a.steps_replayed;
+    out->steps_reversed = a.adj_steps;
+    out->adjoint_cg_iters = a.adj_iters;
+    out->device_bytes = (long long)a.bytes;
+    return LBEHD_OK;
 }
 
 int lbehd_adjoint_backward(lbehd_handle *h, double *grad)

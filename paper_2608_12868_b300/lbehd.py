@@ -20,7 +20,7 @@ G, FPHI, FRHO, PHI, RHO, POT, U, QSRC, EPS, POT_LO = range(10)
 ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot": POT,
                "u": U, "qsrc": QSRC, "eps": EPS, "pot_lo": POT_LO}
 POISSON_HOST, POISSON_FIXED, POISSON_GRAPH = 0, 1, 2
-OPT_COLLIDE, OPT_MG_REFRESH = 1, 2
+OPT_COLLIDE, OPT_MG_REFRESH, OPT_ADJ_TRAJECTORY, OPT_POISSON_KERNEL = 1, 2, 3, 4
 COLLIDE_AUTO, COLLIDE_GLOBAL, COLLIDE_STAGED = 0, 1, 2
 COLLIDE_STAGED_64x2, COLLIDE_STAGED_16x8 = 3, 4
 
@@ -75,6 +75,12 @@ class Stats(ctypes.Structure):
                 ("graph_launches", ctypes.c_longlong), ("kernels", ctypes.c_longlong)]
 
 
+class AdjointInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in (
+        "steps", "checkpoint_every", "checkpoints", "trajectory", "steps_replayed",
+        "steps_reversed", "adjoint_cg_iters", "device_bytes")]
+
+
 class LBEHDError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"lbehd error {code} ({ERRORS.get(code, '?')}): {msg}")
@@ -87,7 +93,8 @@ EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
            "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable",
            "lbehd_profile_read", "lbehd_autotune", "lbehd_adjoint_forward",
-           "lbehd_adjoint_backward", "lbehd_last_error", "lbehd_destroy",
+           "lbehd_adjoint_backward", "lbehd_adjoint_get_info", "lbehd_last_error",
+           "lbehd_destroy",
            "lbehd_batch_init", "lbehd_batch_step", "lbehd_batch_size", "lbehd_batch_instance",
            "lbehd_batch_observe", "lbehd_batch_set_option", "lbehd_batch_autotune",
            "lbehd_batch_get_stats", "lbehd_batch_profile_enable", "lbehd_batch_profile_read",
@@ -129,6 +136,7 @@ def load():
     lib.lbehd_adjoint_forward.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_adjoint_backward.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.lbehd_adjoint_get_info.argtypes = [P, ctypes.POINTER(AdjointInfo)]
     lib.lbehd_batch_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(P)]
     lib.lbehd_batch_step.argtypes = [P, ctypes.c_int]
     lib.lbehd_batch_size.argtypes = [P]
@@ -201,7 +209,10 @@ def make_config(w, c, *, poisson_mode=POISSON_HOST, poisson_check_every=1, poiss
 
 def _torch_allocator(torch, device, stream):
     def _alloc(nbytes, ctx):
-        return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=stream)
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=stream)
+        except torch.cuda.OutOfMemoryError:
+            return 0   # the library reports LBEHD_ERR_OOM (or takes its low-memory path)
 
     def _free(ptr, ctx):
         torch.cuda.caching_allocator_delete(ptr)
@@ -357,6 +368,14 @@ class Simulation(_HandleOps):
         g = np.zeros(self._adj_shape, dtype=np.float64)
         self._check(self._lib.lbehd_adjoint_backward(self._h, _dptr(g, ctypes.c_double)))
         return g
+
+    def adjoint_info(self):
+        """The recorded adjoint run: steps, checkpoint spacing and count, whether the
+        potential trajectory was recorded, the last backward pass's replayed and reversed
+        steps and adjoint CG iterations, and the adjoint's device bytes."""
+        out = AdjointInfo()
+        self._check(self._lib.lbehd_adjoint_get_info(self._h, ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in AdjointInfo._fields_}
 
     def close(self):
         if getattr(self, "_h", None):

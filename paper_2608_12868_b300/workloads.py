@@ -236,6 +236,21 @@ def control_3d_96x64x64(seed=4):
     return w
 
 
+def control_3d_24x16x16(seed=4, segments=4, seg_steps=5):
+    """A 24x16x16 copy of the differentiable-control case, small enough for the FP64
+    discrete-adjoint reference: 4 bottom electrodes (width 6 lu, pitch 6 from x = 0,
+    y in [4, 12)), pillars of height 3, droplet R = 4 at x = 8, `segments` piecewise-constant
+    segments of `seg_steps` steps seeded uniform in [0, 0.06]."""
+    electrodes = [(6 * k, 6 * k + 6, 4, 12) for k in range(4)]
+    rng = np.random.default_rng(seed)
+    sched = rng.uniform(0.0, 0.06, size=(segments, 4))
+    w = droplet_3d(24, 16, 16, R=4.0, xc=8.0, pillar_h=3, electrodes=electrodes,
+                   V=list(sched[0]), seed=seed, name="control_3d_24x16x16",
+                   steps=segments * seg_steps)
+    w.schedule = [(seg_steps * s, list(sched[s])) for s in range(segments)]
+    return w
+
+
 def small_3d(nx=24, ny=16, nz=16, seed=3, R=5.0, V=0.05):
     """Small 3D case for full-field parity: a few pillars, a droplet and one electrode."""
     return droplet_3d(nx, ny, nz, R=R, xc=0.35 * nx, pillar_h=3,

@@ -4,8 +4,10 @@
   differentiable PyTorch) on tiny 3D and 2D lattices: the gradient of the droplet's x
   centroid with respect to a piecewise-constant electrode schedule, within 1e-3 of the
   largest gradient component (FP32 state against FP64).
-* Against central finite differences of the GPU forward itself on a larger lattice and a
-  longer schedule (1e-2 of the largest component: FP32 forward differences).
+* The 24x16x16 copy of the differentiable-control case against the same reference.
+* Against central finite differences of the GPU forward itself: a 40x16x16 lattice (1e-2
+  of the largest component), and the full 96x64x64 control case, 4000 steps and 320
+  parameters, on 8 sampled parameters (1e-3 of the largest component).
 * Through torch.autograd (schedule_loss), and with the handle left in the post-run state.
 """
 import numpy as np
@@ -59,6 +61,54 @@ def test_adjoint_matches_fp64_reference(gpu, oracle_mod, case):
     assert np.abs(g - g_ref).max() <= 1e-3 * np.abs(g_ref).max(), (g, g_ref)
 
 
+def test_control_copy_24x16x16_matches_fp64_reference(gpu, oracle_mod):
+    """The 24x16x16 copy of the differentiable-control case (4 electrodes x 4 segments of
+    5 steps): loss and all 16 gradient components against the FP64 discrete adjoint."""
+    w = W.control_3d_24x16x16(segments=4, seg_steps=5)
+    V = np.array([v for _, v in w.schedule])
+    L_ref, g_ref = reference_grad(oracle_mod, w, V, 5)
+    sim = gpu.Simulation(w)
+    L = sim.adjoint_forward(V, 5)
+    g = sim.adjoint_backward()
+    assert abs(L - L_ref) <= 1e-6 * abs(L_ref)
+    assert np.abs(g - g_ref).max() <= 1e-3 * np.abs(g_ref).max(), (g, g_ref)
+
+
+def test_control_96x64x64_matches_finite_differences(gpu):
+    """The differentiable-control case at full size (96x64x64, 16 electrodes x 20 segments
+    of 200 steps, 4000 steps): the adjoint gradient against central differences of the
+    GPU forward on 8 sampled parameters (seeded, among those above 5 % of the largest).
+    h = 1e-3: at h = 1e-4 the FP32 forward's rounding, divided by h, reaches 1e-3 of the
+    largest component by itself."""
+    w = W.control_3d_96x64x64()
+    V = np.array([v for _, v in w.schedule])
+    seg = 200
+    sim = gpu.Simulation(w)
+    sim.adjoint_forward(V, seg)
+    g = sim.adjoint_backward()
+    info = sim.adjoint_info()
+    sim.close()
+    assert info["steps"] == 4000 and info["checkpoint_every"] == 64
+    assert info["steps_reversed"] == 4000 and info["steps_replayed"] == 4000
+    scale = np.abs(g).max()
+    cand = np.argwhere(np.abs(g) > 0.05 * scale)
+    pick = cand[np.random.default_rng(11).choice(len(cand), 8, replace=False)]
+
+    def loss(Vx):
+        s = gpu.Simulation(w)
+        L = s.adjoint_forward(Vx, seg)
+        s.close()
+        return L
+
+    h = 1e-3
+    for k, e in pick:
+        Vp, Vm = V.copy(), V.copy()
+        Vp[k, e] += h
+        Vm[k, e] -= h
+        fd = (loss(Vp) - loss(Vm)) / (2 * h)
+        assert abs(fd - g[k, e]) <= 1e-3 * scale, (k, e, fd, g[k, e], scale)
+
+
 def test_adjoint_matches_finite_differences(gpu):
     """A 40x16x16 lattice, 3 electrodes, 4 segments of 25 steps: the adjoint gradient against
     central differences (h = 2e-3) of the GPU forward on 4 sampled parameters."""
@@ -110,3 +160,21 @@ def test_schedule_loss_autograd_and_state(gpu):
         s.step(4)
     for name in ("g", "fphi", "frho", "phi"):
         assert np.abs(sim.array(name) - plain.array(name)).max() <= 1e-6, name
+
+
+def test_recorded_potential_and_replayed_solve_agree(gpu):
+    """Backward replays with the recorded potential trajectory, and replays that solve
+    Gauss's law again (LBEHD_OPT_ADJ_TRAJECTORY = 0), give the same gradient bit for bit:
+    the replayed solve reproduces the recorded potential exactly. 52 steps, so four
+    checkpoint intervals, the last one short."""
+    w = tiny_3d()
+    V = np.array([[0.03, 0.05], [0.06, 0.01], [0.0, 0.04], [0.05, 0.05]])
+    grads, losses = [], []
+    for traj in (1, 0):
+        sim = gpu.Simulation(w)
+        sim.set_option(gpu.OPT_ADJ_TRAJECTORY, traj)
+        losses.append(sim.adjoint_forward(V, 13))
+        grads.append(sim.adjoint_backward())
+        sim.close()
+    assert losses[0] == losses[1]
+    assert np.array_equal(grads[0], grads[1]), np.abs(grads[0] - grads[1]).max()
