@@ -182,7 +182,17 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   backward replays need no Gauss-law solve; 0 never records it (replays solve again and
  *   reproduce the same potential bit for bit). */
 #define LBEHD_OPT_ADJ_TRAJECTORY 3
+/*   LBEHD_OPT_POISSON_KERNEL: 1 (default) in LBEHD_POISSON_GRAPH mode each Gauss-law solve
+ *   (start, CG iterations with their V-cycles, potential update, refinement pass) is one
+ *   persistent cooperative kernel with grid-wide barriers, where the lattice allows it (a
+ *   shared-memory tail level, even nx on the levels above it); 0 the multi-launch graph
+ *   with conditional nodes. Both give the same bits. */
+#define LBEHD_OPT_POISSON_KERNEL 4
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
+/* The value in effect: for LBEHD_OPT_COLLIDE the kernel the automatic choice resolved to,
+ * for LBEHD_OPT_POISSON_KERNEL 1 only if the persistent solve is on and this lattice allows
+ * it. Errors: LBEHD_ERR_INVALID_ARG (unknown option, null output). */
+int lbehd_get_option(lbehd_handle *h, int option, long long *value);
 
 /* Counters since init (synchronises: reads the device-side iteration counter). */
 typedef struct lbehd_stats {

@@ -865,6 +865,23 @@ constexpr double ADJ_POISSON_TOL = 1e-4;   // relative residual of the adjoint s
 // Start of the adjoint Gauss-law solve A mu = rhs from the warm start mu: r = rhs - A mu on
 // the active cells, partials of ||r||^2 and ||rhs||^2 over blocks of BX consecutive sites.
 template <int D>
+__device__ __forceinline__ void adj_pcg_init_site(const MgDims &d, const float *eps,
+                                                  const uint8_t *info, const float *Dg,
+                                                  const float *mu, const float *rhs, float *r,
+                                                  int i, float (&v)[2])
+{
+    int x, y, z;
+    cell_xyz(d, i, x, y, z);
+    float dummy[1] = {0.f};
+    pcg_Ap_site<D>(d, eps, info, Dg, mu, r, x, y, z, dummy);   // r = A mu
+    const float b = Dg[i] > 0.0f ? rhs[i] : 0.0f;
+    const float ri = Dg[i] > 0.0f ? __fsub_rn(b, r[i]) : 0.0f;
+    r[i] = ri;
+    v[0] = __fmul_rn(ri, ri);
+    v[1] = __fmul_rn(b, b);
+}
+
+template <int D>
 __global__ void __launch_bounds__(BX) k_adj_pcg_init(MgDims d, const float *__restrict__ eps,
                                                      const uint8_t *__restrict__ info,
                                                      const float *__restrict__ Dg,
@@ -875,17 +892,8 @@ __global__ void __launch_bounds__(BX) k_adj_pcg_init(MgDims d, const float *__re
 {
     const int i = blockIdx.x * BX + threadIdx.x;
     float v[2] = {0.f, 0.f};
-    if (i < d.nx * d.ny * d.nz) {
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        float dummy[1] = {0.f};
-        pcg_Ap_site<D>(d, eps, info, Dg, mu, r, x, y, z, dummy);   // r = A mu
-        const float b = Dg[i] > 0.0f ? rhs[i] : 0.0f;
-        const float ri = Dg[i] > 0.0f ? __fsub_rn(b, r[i]) : 0.0f;
-        r[i] = ri;
-        v[0] = __fmul_rn(ri, ri);
-        v[1] = __fmul_rn(b, b);
-    }
+    if (i < d.nx * d.ny * d.nz)
+        adj_pcg_init_site<D>(d, eps, info, Dg, mu, rhs, r, i, v);
     block_partials<2>(v, partials);
 }
 

@@ -18,6 +18,7 @@
 #include "poisson.cuh"
 #include "poisson_batch.cuh"
 #include "adjoint.cuh"
+#include "poisson_persistent.cuh"
 
 namespace lbehd {
 
@@ -95,6 +96,14 @@ struct lbehd_handle {
     int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
     TailLevels tail{};
     size_t tail_smem = 0;
+    // persistent Gauss-law solve (k_poisson_solve): one cooperative launch per solve
+    bool ps_ok = false;            // this lattice allows it (see ps_setup)
+    bool ps_on = true;             // LBEHD_OPT_POISSON_KERNEL
+    int ps_grid = 0;               // CTAs: one per SM
+    PsArgs ps{};                   // arguments but the per-launch ones
+    PsBarrier *ps_bar = nullptr;
+    double *ps_part = nullptr;
+    unsigned *h_ps_err = nullptr;  // pinned copy of ps_bar->error
     float mg_scale = 0.6f;
     int cur = 0;                   // population buffer holding the state at time n
     int pcur = 0;                  // phi / rho buffer holding the last step's fields
@@ -285,6 +294,95 @@ int launch_fields(lbehd_handle *h)
     return LBEHD_OK;
 }
 
+// The persistent solve needs the shared-memory tail below at least one level smoothed by grid
+// phases, an even nx on those levels, cooperative launches and one resident 1024-thread CTA
+// (with the tail's shared memory) per SM; otherwise the multi-launch form runs.
+template <int D>
+int ps_setup(lbehd_handle *h)
+{
+    int coop = 0, dev = 0, nsm = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    bool ok = coop != 0 && h->tail_level >= 1 && h->tail_level < PS_MAX_LEVELS &&
+              h->N < (size_t)1 << 30;
+    for (int l = 0; ok && l < h->tail_level; l++)
+        ok = h->mg[l].d.nx % 2 == 0;
+    if (!ok)
+        return LBEHD_OK;
+    CK(h, cudaFuncSetAttribute(k_poisson_solve<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TAIL_SMEM_MAX));
+    int per_sm = 0;
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson_solve<D>, PS_THREADS,
+                                                        h->tail_smem));
+    if (per_sm < 1)
+        return LBEHD_OK;
+    const size_t pn = 2 * std::max(h->nblocks_site, h->nblocks1d);
+    h->ps_part = (double *)dev_alloc(h, 2 * pn * sizeof(double));
+    h->ps_bar = (PsBarrier *)dev_alloc(h, sizeof(PsBarrier));
+    if (!h->ps_part || !h->ps_bar)
+        return fail(h, LBEHD_ERR_OOM, "device allocation failed (persistent Poisson)");
+    CK(h, cudaMemsetAsync(h->ps_bar, 0, sizeof(PsBarrier), h->stream));
+    CK(h, cudaMallocHost(&h->h_ps_err, sizeof(unsigned)));
+    *h->h_ps_err = 0;
+    PsArgs &A = h->ps;
+    A.nl = h->tail_level;
+    A.nu = h->mg_nu;
+    A.N = (int)h->N;
+    A.nbs = (int)h->nblocks_site;
+    A.nb1 = (int)h->nblocks1d;
+    for (int l = 0; l <= h->tail_level; l++) {
+        const auto &L = h->mg[l];
+        A.L[l] = PsLevel{L.d, L.cz2, (int)L.n, L.D, L.kx, L.ky, L.kz, L.b, L.x};
+    }
+    A.tail = h->tail;
+    A.tail.b0 = h->mg[h->tail_level].b;
+    A.tail.x0 = h->mg[h->tail_level].x;
+    A.pot = h->pot;
+    A.pot_lo = h->pot_lo;
+    A.eps = h->eps;
+    A.info = h->info;
+    A.delta2 = h->delta2;
+    A.r = h->cg_r;
+    A.p = h->cg_p;
+    A.q = h->cg_q;
+    A.part[0] = h->ps_part;
+    A.part[1] = h->ps_part + pn;
+    A.s = h->cg_s;
+    A.bar = h->ps_bar;
+    h->ps_grid = nsm;
+    h->ps_ok = true;
+    return LBEHD_OK;
+}
+
+bool ps_use(const lbehd_handle *h) { return h->ps_ok && h->ps_on; }
+
+// One persistent solve on h->ls: the forward step's (increment x, this step's charge rho) or
+// the adjoint's (solution x, right-hand side rhs). The barrier counter is reset first.
+template <int D>
+int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float *rhs)
+{
+    PsArgs A = h->ps;
+    A.mode = mode;
+    A.x = x;
+    A.rho = rho;
+    A.rhs = rhs;
+    CK(h, cudaMemsetAsync(&h->ps_bar->count, 0, sizeof(unsigned), h->ls));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)h->ps_grid);
+    cfg.blockDim = dim3(PS_THREADS);
+    cfg.dynamicSmemBytes = h->tail_smem;
+    cfg.stream = h->ls;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(h, cudaLaunchKernelEx(&cfg, k_poisson_solve<D>, A));
+    h->launches += 1;
+    return LBEHD_OK;
+}
+
 void mg_gs(lbehd_handle *h, const lbehd_handle::Level &L, int color)
 {
     k_mg_gs<<<L.grid_half, h->block, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, color);
@@ -442,6 +540,14 @@ int poisson(lbehd_handle *h)
     const lbehd_config &c = h->cfg;
     if (mg_due(h))
         mg_setup<D>(h);
+    if (c.poisson_mode == LBEHD_POISSON_GRAPH && !h->first && ps_use(h)) {
+        // eager form of a graph step (profiling): the same persistent solve
+        int rc = LBEHD_OK;
+        launch(h, LBEHD_KC_CG, 0, [&] {
+            rc = ps_launch<D>(h, PS_FORWARD, h->inc[h->step & 1], h->rho[h->pcur], nullptr);
+        });
+        return rc;
+    }
     float *x = h->inc[h->step & 1];   // holds the increment of step - 2: the warm start
     pcg_start<D>(h, x);
     bool converged = true;
@@ -597,10 +703,23 @@ int record_step(lbehd_handle *h, cudaGraph_t g, int parity, int refresh, bool fu
     h->prof = false;
     cudaGraphConditionalHandle c1 = 0, c2 = 0, cr = 0;
     auto body = [&]() -> int {
+        h->ls = h->stream;
+        if (ps_use(h)) {   // one persistent solve: no conditional nodes
+            if (full)
+                launch_fields<D>(h);
+            if (refresh)
+                mg_setup<D>(h);
+            const int r = ps_launch<D>(h, PS_FORWARD, h->inc[parity], h->rho[h->pcur], nullptr);
+            if (r)
+                return r;
+            h->iter_kernels = 0;
+            if (full)
+                collide<D>(h);
+            return LBEHD_OK;
+        }
         CK(h, cudaGraphConditionalHandleCreate(&c1, g, 0, 0));
         CK(h, cudaGraphConditionalHandleCreate(&c2, g, 0, 0));
         CK(h, cudaGraphConditionalHandleCreate(&cr, g, 0, 0));
-        h->ls = h->stream;
         h->use_cond = 1;
         if (full)
             launch_fields<D>(h);
@@ -973,6 +1092,11 @@ int init_impl(lbehd_handle *h)
         }
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
+    {
+        int rc = ps_setup<D>(h);
+        if (rc)
+            return rc;
+    }
     CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     CK(h, cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
     if (h->nx % 4 == 0) {
@@ -1062,6 +1186,9 @@ void release(lbehd_handle *h)
     h->bufs.clear();
     if (h->h_cg)
         cudaFreeHost(h->h_cg);
+    if (h->h_ps_err)
+        cudaFreeHost(h->h_ps_err);
+    h->h_ps_err = nullptr;
     h->h_cg = nullptr;
     for (auto &row : h->gexec)
         for (auto &e : row)
@@ -1176,6 +1303,16 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
         CK(h, cudaStreamSynchronize(h->stream));
         h->mg_refresh = (int)value;
         h->mg_valid = false;
+    } else if (option == LBEHD_OPT_POISSON_KERNEL) {
+        if (value < 0 || value > 1)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_POISSON_KERNEL takes 0 or 1");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->ps_on = value != 0;
+        for (auto &e : h->adj.solve)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
     } else if (option == LBEHD_OPT_ADJ_TRAJECTORY) {
         if (value < 0 || value > 1)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_ADJ_TRAJECTORY takes 0 or 1");
@@ -1208,6 +1345,9 @@ int observe_enqueue(lbehd_handle *h, double *o, int *flag)
     CK(h, cudaMemcpyAsync(o, h->obs, 2 * NOBS * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
+    if (h->ps_bar)
+        CK(h, cudaMemcpyAsync(h->h_ps_err, &h->ps_bar->error, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, h->stream));
     return LBEHD_OK;
 }
 
@@ -1235,6 +1375,10 @@ int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
                        : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
     if (flag)
         return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
+    if (h->h_ps_err && *h->h_ps_err) {
+        out->status = LBEHD_ERR_CUDA;
+        return fail(h, LBEHD_ERR_CUDA, "persistent Poisson solve: a grid barrier timed out");
+    }
     return LBEHD_OK;
 }
 
@@ -1488,9 +1632,18 @@ int capture_adj_solve(lbehd_handle *h, int km)
     auto body = [&]() -> int {
         CK(h, cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeRelaxed));
+        h->ls = h->stream;
+        if (ps_use(h)) {   // one persistent solve
+            const int r = ps_launch<D>(h, PS_ADJOINT, a.mu3[km], nullptr, a.rhs);
+            if (r)
+                return r;
+            cudaGraph_t out = nullptr;
+            CK(h, cudaStreamEndCapture(h->stream, &out));
+            CK(h, cudaGraphInstantiate(&a.solve[km], g, 0));
+            return LBEHD_OK;
+        }
         cudaGraphConditionalHandle c = 0;
         CK(h, cudaGraphConditionalHandleCreate(&c, g, 0, 0));
-        h->ls = h->stream;
         h->use_cond = 1;
         h->use_ref = 0;
         h->cond = c;
@@ -2784,6 +2937,23 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
     if (h->batch_owned)
         return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_set_option");
     return set_option_impl(h, option, value);
+}
+
+int lbehd_get_option(lbehd_handle *h, int option, long long *value)
+{
+    if (!h || !value)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or output");
+    if (option == LBEHD_OPT_COLLIDE)
+        *value = resolved_variant(h);
+    else if (option == LBEHD_OPT_MG_REFRESH)
+        *value = h->mg_refresh;
+    else if (option == LBEHD_OPT_ADJ_TRAJECTORY)
+        *value = h->adj.use_traj ? 1 : 0;
+    else if (option == LBEHD_OPT_POISSON_KERNEL)
+        *value = ps_use(h) ? 1 : 0;
+    else
+        return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
+    return LBEHD_OK;
 }
 
 int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int seg_steps,

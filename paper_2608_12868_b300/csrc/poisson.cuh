@@ -154,10 +154,10 @@ __device__ __forceinline__ void block_partials(float (&v)[NV], double *partials)
 // Face coefficients to the +x/+y/+z neighbours and the diagonal (all faces, Dirichlet
 // faces included) from eps and the node classes.
 template <int D>
-__device__ __forceinline__ void mg_setup0_cell(const MgDims &d, const float *__restrict__ eps,
-                                               const uint8_t *__restrict__ info,
-                                               float *__restrict__ Dg, float *__restrict__ kx,
-                                               float *__restrict__ ky, float *__restrict__ kz,
+__device__ __forceinline__ void mg_setup0_cell(const MgDims &d, const float *eps,
+                                               const uint8_t *info,
+                                               float *Dg, float *kx,
+                                               float *ky, float *kz,
                                                int x, int y, int z)
 {
     const int i = cell(d, x, y, z);
@@ -204,12 +204,12 @@ __global__ void __launch_bounds__(BX) k_mg_setup0(MgDims d, const float *__restr
 
 // Galerkin coarsening (scaled) of one level.
 __device__ __forceinline__ void mg_coarsen_cell(const MgDims &f, const MgDims &c, int cz2,
-                                                float scale, const float *__restrict__ Df,
-                                                const float *__restrict__ kxf,
-                                                const float *__restrict__ kyf,
-                                                const float *__restrict__ kzf,
-                                                float *__restrict__ Dc, float *__restrict__ kxc,
-                                                float *__restrict__ kyc, float *__restrict__ kzc,
+                                                float scale, const float *Df,
+                                                const float *kxf,
+                                                const float *kyf,
+                                                const float *kzf,
+                                                float *Dc, float *kxc,
+                                                float *kyc, float *kzc,
                                                 int X, int Y, int Z)
 {
     const int nzc = cz2 ? 2 : 1;
@@ -263,10 +263,10 @@ __global__ void __launch_bounds__(BX) k_mg_coarsen(MgDims f, MgDims c, int cz2, 
 // ---------------------------------------------------------------- smoother / transfers
 
 __device__ __forceinline__ float offdiag_sum(const MgDims &d, int i, int x, int y, int z,
-                                             const float *__restrict__ kx,
-                                             const float *__restrict__ ky,
-                                             const float *__restrict__ kz,
-                                             const float *__restrict__ v)
+                                             const float *kx,
+                                             const float *ky,
+                                             const float *kz,
+                                             const float *v)
 {
     const Nb6 nb = nb6(d, i, x, y, z);
     float s = __fmul_rn(kx[i], v[nb.n[0]]);
@@ -281,11 +281,11 @@ __device__ __forceinline__ float offdiag_sum(const MgDims &d, int i, int x, int 
 }
 
 // Gauss-Seidel update of one cell of A x = b.
-__device__ __forceinline__ void mg_gs_cell(const MgDims &d, const float *__restrict__ Dg,
-                                           const float *__restrict__ kx,
-                                           const float *__restrict__ ky,
-                                           const float *__restrict__ kz,
-                                           const float *__restrict__ b, float *__restrict__ xv,
+__device__ __forceinline__ void mg_gs_cell(const MgDims &d, const float *Dg,
+                                           const float *kx,
+                                           const float *ky,
+                                           const float *kz,
+                                           const float *b, float *xv,
                                            int x, int y, int z)
 {
     const int i = cell(d, x, y, z);
@@ -313,12 +313,12 @@ __global__ void __launch_bounds__(BX) k_mg_gs(MgDims d, const float *__restrict_
 // passes: the residual of every fine cell (0 on inactive cells), then the sum over each
 // coarse cell's children in the order (x, y, z) = (2X + a, 2Y + b, 2Z + g), a outermost
 // (the shared-memory tail sums in the same order).
-__device__ __forceinline__ void mg_resid_cell(const MgDims &f, const float *__restrict__ Df,
-                                              const float *__restrict__ kx,
-                                              const float *__restrict__ ky,
-                                              const float *__restrict__ kz,
-                                              const float *__restrict__ bf,
-                                              const float *__restrict__ xf, float *__restrict__ rf,
+__device__ __forceinline__ void mg_resid_cell(const MgDims &f, const float *Df,
+                                              const float *kx,
+                                              const float *ky,
+                                              const float *kz,
+                                              const float *bf,
+                                              const float *xf, float *rf,
                                               int x, int y, int z)
 {
     const int i = cell(f, x, y, z);
@@ -328,8 +328,8 @@ __device__ __forceinline__ void mg_resid_cell(const MgDims &f, const float *__re
 }
 
 __device__ __forceinline__ void mg_restrict_sum_cell(const MgDims &f, const MgDims &c, int cz2,
-                                                     const float *__restrict__ rf,
-                                                     float *__restrict__ bc, int X, int Y, int Z)
+                                                     const float *rf,
+                                                     float *bc, int X, int Y, int Z)
 {
     // fine nx, ny are twice the coarse ones; only z may end on a single child
     const int z0 = cz2 ? 2 * Z : Z;
@@ -379,9 +379,9 @@ __global__ void __launch_bounds__(BX) k_mg_restrict_sum(MgDims f, MgDims c, int 
 
 // x_f += x_c(parent) on active fine cells.
 __device__ __forceinline__ void mg_prolong_cell(const MgDims &f, const MgDims &c, int cz2,
-                                                const float *__restrict__ Df,
-                                                const float *__restrict__ xc,
-                                                float *__restrict__ xf, int x, int y, int z)
+                                                const float *Df,
+                                                const float *xc,
+                                                float *xf, int x, int y, int z)
 {
     const int i = cell(f, x, y, z);
     const float di = Df[i], xi = xf[i], xp = xc[cell(c, x >> 1, y >> 1, cz2 ? (z >> 1) : z)];
@@ -538,13 +538,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
 // are close, so their difference is exact in FP32, and r keeps the accuracy an FP64
 // evaluation of b - A phi would have, in FP32 arithmetic.
 template <int D>
-__device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *__restrict__ pot,
-                                              const float *__restrict__ pot_lo,
-                                              const float *__restrict__ delta,
-                                              const float *__restrict__ eps,
-                                              const float *__restrict__ rho,
-                                              const uint8_t *__restrict__ info,
-                                              const float *__restrict__ Dg, float *__restrict__ r,
+__device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *pot,
+                                              const float *pot_lo,
+                                              const float *delta,
+                                              const float *eps,
+                                              const float *rho,
+                                              const uint8_t *info,
+                                              const float *Dg, float *r,
                                               int x, int y, int z, float (&v)[2])
 {
     {
@@ -609,14 +609,25 @@ __global__ void __launch_bounds__(BX) k_pcg_init(MgDims d, const float *__restri
 
 // p = z + beta p (beta = 0 on the first iteration).
 // The 1D CG kernels walk the sites with a grid stride: block b of nb covers sites
-// b BX + t, (b + nb) BX + t, ... (the partition fixes each partial sum).
-__device__ __forceinline__ void pcg_p_range(int n, const float *__restrict__ zv,
-                                            float *__restrict__ p, const CgScalars *__restrict__ s,
+// b BX + t, (b + nb) BX + t, ... (the partition fixes each partial sum). The _t forms take
+// the thread's index t within its BX-thread block explicitly.
+__device__ __forceinline__ float pcg_beta(const CgScalars *s)
+{
+    return s->iters == 0 ? 0.0f : (float)s->beta;
+}
+
+__device__ __forceinline__ void pcg_p_site(int i, float beta, const float *zv, float *p)
+{
+    p[i] = beta != 0.0f ? __fmaf_rn(beta, p[i], zv[i]) : zv[i];
+}
+
+__device__ __forceinline__ void pcg_p_range(int n, const float *zv,
+                                            float *p, const CgScalars *s,
                                             int b, int nb)
 {
-    const float beta = s->iters == 0 ? 0.0f : (float)s->beta;
+    const float beta = pcg_beta(s);
     for (int i = b * BX + threadIdx.x; i < n; i += nb * BX)
-        p[i] = beta != 0.0f ? __fmaf_rn(beta, p[i], zv[i]) : zv[i];
+        pcg_p_site(i, beta, zv, p);
 }
 
 __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict__ zv,
@@ -629,10 +640,10 @@ __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict_
 // hierarchy may be a few steps old, which only changes the preconditioner) and partials of
 // p . q. Dirichlet neighbours hold no correction (p = 0 there).
 template <int D>
-__device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *__restrict__ eps,
-                                            const uint8_t *__restrict__ info,
-                                            const float *__restrict__ Dg,
-                                            const float *__restrict__ p, float *__restrict__ q,
+__device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *eps,
+                                            const uint8_t *info,
+                                            const float *Dg,
+                                            const float *p, float *q,
                                             int x, int y, int z, float (&v)[1])
 {
     {
@@ -681,19 +692,28 @@ __global__ void __launch_bounds__(BX) k_pcg_Ap(MgDims d, const float *__restrict
 }
 
 // delta += alpha p, r -= alpha q, partials of ||r||^2.
-__device__ __forceinline__ void pcg_update_range(int n, const float *__restrict__ p,
-                                                 const float *__restrict__ q,
-                                                 float *__restrict__ delta, float *__restrict__ r,
-                                                 const CgScalars *__restrict__ s, int b, int nb,
-                                                 float (&v)[1])
+__device__ __forceinline__ void pcg_update_range_t(int n, const float *p,
+                                                   const float *q,
+                                                   float *delta, float *r,
+                                                   const CgScalars *s, int b, int nb, int t,
+                                                   float (&v)[1])
 {
     const float a = (float)s->alpha;
-    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX) {
+    for (int i = b * BX + t; i < n; i += nb * BX) {
         delta[i] = __fmaf_rn(a, p[i], delta[i]);
         const float ri = __fmaf_rn(-a, q[i], r[i]);
         r[i] = ri;
         v[0] = __fmaf_rn(ri, ri, v[0]);
     }
+}
+
+__device__ __forceinline__ void pcg_update_range(int n, const float *p,
+                                                 const float *q,
+                                                 float *delta, float *r,
+                                                 const CgScalars *s, int b, int nb,
+                                                 float (&v)[1])
+{
+    pcg_update_range_t(n, p, q, delta, r, s, b, nb, (int)threadIdx.x, v);
 }
 
 __global__ void __launch_bounds__(BX) k_pcg_update(size_t n, const float *__restrict__ p,
@@ -708,12 +728,19 @@ __global__ void __launch_bounds__(BX) k_pcg_update(size_t n, const float *__rest
 }
 
 // partials of r . z
-__device__ __forceinline__ void pcg_dot_range(int n, const float *__restrict__ a,
-                                              const float *__restrict__ b, int blk, int nb,
+__device__ __forceinline__ void pcg_dot_range_t(int n, const float *a,
+                                                const float *b, int blk, int nb, int t,
+                                                float (&v)[1])
+{
+    for (int i = blk * BX + t; i < n; i += nb * BX)
+        v[0] = __fmaf_rn(a[i], b[i], v[0]);
+}
+
+__device__ __forceinline__ void pcg_dot_range(int n, const float *a,
+                                              const float *b, int blk, int nb,
                                               float (&v)[1])
 {
-    for (int i = blk * BX + threadIdx.x; i < n; i += nb * BX)
-        v[0] = __fmaf_rn(a[i], b[i], v[0]);
+    pcg_dot_range_t(n, a, b, blk, nb, (int)threadIdx.x, v);
 }
 
 __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restrict__ a,
@@ -736,9 +763,9 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 // k_pcg_scalar: with use_cond, ops 0, 4, 3 and 5 also set the graph's while-loop condition
 // to !done; with use_ref, op 0 clears and op 3 sets the condition of the refinement block.
 constexpr int SCALAR_THREADS = 1024;
-__device__ __forceinline__ bool pcg_scalar_block(const double *__restrict__ partials,
+__device__ __forceinline__ bool pcg_scalar_block(const double *partials,
                                                  long long nblocks, int nv, int op,
-                                                 CgScalars *__restrict__ s)
+                                                 CgScalars *s)
 {
     __shared__ double sm[2][SCALAR_THREADS / 32];
     double tot[2] = {0.0, 0.0};
@@ -825,26 +852,31 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
 // phi += delta on active cells, phi kept as the compensated pair hi + lo (two-sum in FP32:
 // the rounding error of hi + delta is carried into lo); acc += delta when acc is given
 // (accumulates a refinement correction into the step's increment).
-__device__ __forceinline__ void pcg_apply_range(int n, const float *__restrict__ Dg,
-                                                const float *__restrict__ delta,
-                                                float *__restrict__ acc, float *__restrict__ pot,
-                                                float *__restrict__ pot_lo, int b, int nb)
+__device__ __forceinline__ void pcg_apply_site(int i, const float *Dg, const float *delta,
+                                               float *acc, float *pot, float *pot_lo)
 {
-    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX) {
-        if (Dg[i] <= 0.0f)
-            continue;
-        const float d = delta[i];
-        if (acc)
-            acc[i] += d;
-        const float hi = pot[i];
-        const float t = hi + d;                       // two-sum: t + err = hi + d exactly
-        const float bv = t - hi;
-        const float err = (hi - (t - bv)) + (d - bv);
-        const float lo = pot_lo[i] + err;
-        const float s = t + lo;                       // renormalise the pair
-        pot[i] = s;
-        pot_lo[i] = lo - (s - t);
-    }
+    if (Dg[i] <= 0.0f)
+        return;
+    const float d = delta[i];
+    if (acc)
+        acc[i] += d;
+    const float hi = pot[i];
+    const float t = hi + d;                       // two-sum: t + err = hi + d exactly
+    const float bv = t - hi;
+    const float err = (hi - (t - bv)) + (d - bv);
+    const float lo = pot_lo[i] + err;
+    const float s = t + lo;                       // renormalise the pair
+    pot[i] = s;
+    pot_lo[i] = lo - (s - t);
+}
+
+__device__ __forceinline__ void pcg_apply_range(int n, const float *Dg,
+                                                const float *delta,
+                                                float *acc, float *pot,
+                                                float *pot_lo, int b, int nb)
+{
+    for (int i = b * BX + threadIdx.x; i < n; i += nb * BX)
+        pcg_apply_site(i, Dg, delta, acc, pot, pot_lo);
 }
 
 __global__ void __launch_bounds__(BX) k_pcg_apply(size_t n, const float *__restrict__ Dg,

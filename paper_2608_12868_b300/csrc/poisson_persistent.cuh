@@ -1,0 +1,386 @@
+// poisson_persistent.cuh -- the Gauss-law solve of one step (Eq. 13) as one persistent
+// kernel: start, every preconditioned-CG iteration (the V-cycle included), the update of the
+// potential and the refinement pass, with grid-wide barriers in place of kernel boundaries.
+//
+// One CTA of PS_THREADS = 1024 threads per SM, launched cooperatively (all CTAs resident).
+// The CG loop of the multi-launch form is latency-bound: a V-cycle of ~36 small dependent
+// launches plus 7 CG launches per iteration. Here each of those becomes a phase of this
+// kernel ended by a barrier instead of a launch.
+//
+// Same bits as the multi-launch form, by construction:
+//  * each phase calls the same per-cell bodies (poisson.cuh), which are written with explicit
+//    rounding intrinsics; smoothing, restriction and prolongation results do not depend on
+//    which thread handles which cell (a red-black half sweep reads only the other colour);
+//  * dot products keep their partition into BX-site virtual blocks: the 128-thread group g of
+//    a CTA plays virtual block blockIdx.x * PS_GROUPS + g, ... and reduces like
+//    block_partials (warp sums in FP32, then FP64 over the four warps in order);
+//  * every CTA sums the partial arrays with pcg_scalar_block itself (the 1024-thread fixed
+//    order of k_pcg_scalar) and applies the same scalar update to its shared copy of the CG
+//    scalars, so all CTAs take the same branches; CTA 0 writes the scalars back at the end;
+//  * the shared-memory tail runs in CTA 0 with the 1024-thread k_mg_tail body;
+//  * two fused phases reproduce a pair of launches exactly: "zero, then the first red half
+//    sweep" (every neighbour is 0, so x = (b + 0) / D on red cells and 0 elsewhere), and
+//    "residual, then the sum over each coarse cell's children" (the residual of each child
+//    evaluated in registers, summed in the restriction's order).
+//
+// Barrier: a monotonic arrival counter (reset by the host before each launch) that barrier
+// k waits to reach k * gridDim.x; thread 0 of each CTA spins with a backoff and an
+// iteration limit. On time-out it raises the error word, and every CTA leaves at its next
+// barrier; the host reads the word and reports the step as failed.
+#pragma once
+
+#include "adjoint.cuh"
+#include "poisson.cuh"
+
+namespace lbehd {
+
+constexpr int PS_THREADS = 1024;
+constexpr int PS_GROUPS = PS_THREADS / BX;        // virtual blocks per CTA
+constexpr int PS_MAX_LEVELS = 12;
+constexpr unsigned PS_SPIN_LIMIT = 1u << 23;      // x >= 64 ns backoff: ~0.5 s at least
+
+static_assert(PS_THREADS == SCALAR_THREADS && PS_THREADS == TAIL_THREADS,
+              "the persistent solve runs the 1024-thread scalar and tail bodies as they are");
+
+struct PsBarrier {
+    unsigned int count;    // arrivals (zeroed before each launch)
+    unsigned int error;    // sticky: a barrier timed out
+    unsigned int where;    // barrier index of the first time-out
+    unsigned int pad;
+};
+
+struct PsLevel {
+    MgDims d;
+    int cz2, n;
+    const float *D, *kx, *ky, *kz;
+    float *b, *x;
+};
+
+struct PsArgs {
+    int mode;                  // PS_FORWARD or PS_ADJOINT
+    int nl;                    // levels smoothed by grid phases: 0 .. nl - 1
+    int nu;                    // red-black sweeps before and after the coarse correction
+    int N, nbs, nb1;           // sites, BX-site blocks, 1D blocks (the partial partitions)
+    PsLevel L[PS_MAX_LEVELS];  // 0 .. nl (level nl is the tail's finest)
+    TailLevels tail;           // b0 = L[nl].b, x0 = L[nl].x
+    // forward: compensated potential, this step's charge, the warm-started increment
+    float *pot, *pot_lo;
+    const float *eps, *rho;
+    const uint8_t *info;
+    float *x, *delta2;
+    // adjoint: right-hand side (the solution is in x)
+    const float *rhs;
+    float *r, *p, *q;          // r is L[0].b; z is L[0].x
+    double *part[2];           // partial arrays, alternating so a scalar read never races
+    CgScalars *s;
+    PsBarrier *bar;
+};
+
+constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
+
+__device__ __forceinline__ void ps_named_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(BX) : "memory");
+}
+
+__device__ __forceinline__ unsigned ps_load_volatile(const unsigned *p)
+{
+    return *(const volatile unsigned *)p;
+}
+
+// Grid barrier number `epoch` (1, 2, ...). Returns false once any CTA has timed out.
+__device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok_sh)
+{
+    epoch++;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(&bar->count, 1u);
+        const unsigned target = epoch * gridDim.x;
+        unsigned spins = 0;
+        while (ps_load_volatile(&bar->count) < target) {
+            if (ps_load_volatile(&bar->error)) {
+                ok = 0;
+                break;
+            }
+            if (++spins > PS_SPIN_LIMIT) {
+                if (atomicExch(&bar->error, 1u) == 0u)
+                    bar->where = epoch;
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *ok_sh = ok;
+    }
+    __syncthreads();
+    return *ok_sh != 0;
+}
+
+// block_partials for the virtual block played by this thread's 128-thread group.
+template <int NV>
+__device__ __forceinline__ void ps_group_partials(float (&v)[NV], double *partials, int blk,
+                                                  int nblk, double (*sm)[2][BX / 32])
+{
+    const int g = threadIdx.x / BX, t = threadIdx.x % BX;
+    const int lane = t & 31, wid = t >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const float s = warp_sum(v[k]);
+        if (lane == 0)
+            sm[g][k][wid] = (double)s;
+    }
+    ps_named_sync(1 + g);
+    if (t < NV) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < BX / 32; w++)
+            acc += sm[g][t][w];
+        partials[(size_t)t * nblk + blk] = acc;
+    }
+    ps_named_sync(1 + g);   // the group's slice is rewritten by its next virtual block
+}
+
+// Flat grid-stride loop over n items.
+template <class F>
+__device__ __forceinline__ void ps_for(int n, F &&f)
+{
+    for (int i = blockIdx.x * PS_THREADS + threadIdx.x; i < n; i += gridDim.x * PS_THREADS)
+        f(i);
+}
+
+// Loop over virtual blocks 0 .. nvb - 1 (group-uniform): f(vb, t).
+template <class F>
+__device__ __forceinline__ void ps_for_vblocks(int nvb, F &&f)
+{
+    const int g = threadIdx.x / BX, t = threadIdx.x % BX;
+    for (int vb = blockIdx.x * PS_GROUPS + g; vb < nvb; vb += gridDim.x * PS_GROUPS)
+        f(vb, t);
+}
+
+// One red-black half sweep (colour c) of level L, cells in flat order (nx even).
+__device__ __forceinline__ void ps_gs(const PsLevel &L, int color)
+{
+    const MgDims &d = L.d;
+    const int hx = d.nx >> 1;
+    ps_for(L.n >> 1, [&](int k) {
+        const int row = fdiv(k, d.mh, d.sh);
+        const int j = k - row * hx;
+        const int z = fdiv(row, d.my, d.sy);
+        const int y = row - z * d.ny;
+        const int x = 2 * j + ((y + z + color) & 1);
+        mg_gs_cell(d, L.D, L.kx, L.ky, L.kz, L.b, L.x, x, y, z);
+    });
+}
+
+// x = 0 then the first red half sweep: every neighbour is 0, so the update of a red cell is
+// (b + 0) / D (offdiag_sum of zeros is +0), black and inactive cells keep 0.
+__device__ __forceinline__ void ps_gs_first(const PsLevel &L)
+{
+    const MgDims &d = L.d;
+    ps_for(L.n, [&](int c) {
+        int x, y, z;
+        cell_xyz(d, c, x, y, z);
+        const float di = L.D[c], bi = L.b[c];
+        float v = 0.0f;
+        if (((x + y + z) & 1) == 0 && di > 0.0f)
+            v = __fdiv_rn(__fadd_rn(bi, 0.0f), di);
+        L.x[c] = v;
+    });
+}
+
+// Residual b - A x of one fine cell (0 on inactive cells), as mg_resid_cell computes it.
+__device__ __forceinline__ float ps_resid(const PsLevel &F, int x, int y, int z)
+{
+    const MgDims &f = F.d;
+    const int i = cell(f, x, y, z);
+    const float di = F.D[i], xi = F.x[i], bi = F.b[i];
+    const float Ax = __fmaf_rn(di, xi, -offdiag_sum(f, i, x, y, z, F.kx, F.ky, F.kz, F.x));
+    return di > 0.0f ? __fsub_rn(bi, Ax) : 0.0f;
+}
+
+// b_c = sum over each coarse cell's children of the fine residual, in the order of
+// mg_restrict_sum_cell ((x, y, z) = (2X + a, 2Y + b, z0 + g), a outermost).
+__device__ __forceinline__ void ps_resid_restrict(const PsLevel &F, const PsLevel &C)
+{
+    const MgDims &f = F.d, &c = C.d;
+    ps_for(C.n, [&](int I) {
+        int X, Y, Z;
+        cell_xyz(c, I, X, Y, Z);
+        const int z0 = F.cz2 ? 2 * Z : Z;
+        const bool z1 = F.cz2 && z0 + 1 < f.nz;
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                acc = __fadd_rn(acc, ps_resid(F, 2 * X + a, 2 * Y + b, z0));
+                if (z1)
+                    acc = __fadd_rn(acc, ps_resid(F, 2 * X + a, 2 * Y + b, z0 + 1));
+            }
+        C.b[I] = acc;
+    });
+}
+
+__device__ __forceinline__ void ps_prolong(const PsLevel &F, const PsLevel &C)
+{
+    ps_for(F.n, [&](int c) {
+        int x, y, z;
+        cell_xyz(F.d, c, x, y, z);
+        mg_prolong_cell(F.d, C.d, F.cz2, F.D, C.x, F.x, x, y, z);
+    });
+}
+
+template <int D>
+__global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_constant__ PsArgs A)
+{
+    extern __shared__ float tail_sm[];
+    __shared__ CgScalars s;
+    __shared__ double gsm[PS_GROUPS][2][BX / 32];
+    __shared__ int ok_sh;
+    unsigned epoch = 0;
+    if (threadIdx.x == 0)
+        s = *A.s;
+    __syncthreads();
+    bool ok = true;
+    auto sync = [&]() {
+        if (ok)
+            ok = ps_sync(A.bar, epoch, &ok_sh);
+    };
+    auto scalar = [&](const double *part, int nv, int op, int nblk) {
+        pcg_scalar_block(part, nblk, nv, op, &s);
+        __syncthreads();
+    };
+    const PsLevel &L0 = A.L[0];
+    float *z = L0.x;
+
+    // one symmetric V-cycle: z ~= A^-1 r
+    auto vcycle = [&]() {
+        for (int l = 0; l < A.nl && ok; l++) {
+            const PsLevel &L = A.L[l];
+            ps_gs_first(L);
+            sync();
+            ps_gs(L, 1);
+            sync();
+            for (int k = 1; k < A.nu && ok; k++) {
+                ps_gs(L, 0);
+                sync();
+                ps_gs(L, 1);
+                sync();
+            }
+            ps_resid_restrict(L, A.L[l + 1]);
+            sync();
+        }
+        if (!ok)
+            return;
+        if (blockIdx.x == 0)
+            mg_tail_block(A.tail, tail_sm);
+        sync();
+        for (int l = A.nl - 1; l >= 0 && ok; l--) {
+            const PsLevel &L = A.L[l];
+            ps_prolong(L, A.L[l + 1]);
+            sync();
+            for (int k = 0; k < A.nu && ok; k++) {
+                ps_gs(L, 1);
+                sync();
+                ps_gs(L, 0);
+                sync();
+            }
+        }
+    };
+
+    // one preconditioned CG iteration on the increment (or adjoint potential) xv
+    auto iteration = [&](float *xv) {
+        vcycle();
+        if (!ok)
+            return;
+        ps_for_vblocks(A.nb1, [&](int vb, int t) {
+            float v[1] = {0.0f};
+            pcg_dot_range_t(A.N, A.r, z, vb, A.nb1, t, v);
+            ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
+        });
+        sync();
+        if (!ok)
+            return;
+        scalar(A.part[0], 1, 1, A.nb1);
+        const float beta = pcg_beta(&s);
+        ps_for(A.N, [&](int i) { pcg_p_site(i, beta, z, A.p); });
+        sync();
+        ps_for_vblocks(A.nbs, [&](int vb, int t) {
+            const int i = vb * BX + t;
+            float v[1] = {0.0f};
+            if (i < A.N) {
+                int x, y, zz;
+                cell_xyz(L0.d, i, x, y, zz);
+                pcg_Ap_site<D>(L0.d, A.eps, A.info, L0.D, A.p, A.q, x, y, zz, v);
+            }
+            ps_group_partials<1>(v, A.part[1], vb, A.nbs, gsm);
+        });
+        sync();
+        if (!ok)
+            return;
+        scalar(A.part[1], 1, 2, A.nbs);
+        ps_for_vblocks(A.nb1, [&](int vb, int t) {
+            float v[1] = {0.0f};
+            pcg_update_range_t(A.N, A.p, A.q, xv, A.r, &s, vb, A.nb1, t, v);
+            ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
+        });
+        sync();
+        if (!ok)
+            return;
+        scalar(A.part[0], 1, 3, A.nb1);
+    };
+
+    // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4
+    auto start = [&](float *xv, int op) {
+        ps_for_vblocks(A.nbs, [&](int vb, int t) {
+            const int i = vb * BX + t;
+            float v[2] = {0.0f, 0.0f};
+            if (i < A.N) {
+                if (A.mode == PS_ADJOINT) {
+                    adj_pcg_init_site<D>(L0.d, A.eps, A.info, L0.D, xv, A.rhs, A.r, i, v);
+                } else {
+                    int x, y, zz;
+                    cell_xyz(L0.d, i, x, y, zz);
+                    pcg_init_site<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D, A.r,
+                                     x, y, zz, v);
+                }
+            }
+            ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
+        });
+        sync();
+        if (ok)
+            scalar(A.part[1], 2, op, A.nbs);
+    };
+
+    start(A.x, 0);
+    while (ok && !s.done)
+        iteration(A.x);
+    if (ok && A.mode == PS_FORWARD) {
+        ps_for(A.N, [&](int i) { pcg_apply_site(i, L0.D, A.x, nullptr, A.pot, A.pot_lo); });
+        sync();
+        // refinement: the true residual of the updated potential, once, if the pass iterated
+        if (ok && s.refine) {
+            ps_for(A.N, [&](int i) { A.delta2[i] = 0.0f; });
+            sync();
+            start(A.delta2, 4);
+            while (ok && !s.done)
+                iteration(A.delta2);
+            if (ok)
+                ps_for(A.N, [&](int i) {
+                    pcg_apply_site(i, L0.D, A.delta2, A.x, A.pot, A.pot_lo);
+                });
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!ok) {
+            s.done = 1;
+            s.nonconv = 1;
+        }
+        *A.s = s;
+    }
+}
+
+}  // namespace lbehd

@@ -91,7 +91,7 @@ _lib = None
 
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
-           "lbehd_launch_count", "lbehd_set_option", "lbehd_get_stats", "lbehd_profile_enable",
+           "lbehd_launch_count", "lbehd_set_option", "lbehd_get_option", "lbehd_get_stats", "lbehd_profile_enable",
            "lbehd_profile_read", "lbehd_autotune", "lbehd_adjoint_forward",
            "lbehd_adjoint_backward", "lbehd_adjoint_get_info", "lbehd_last_error",
            "lbehd_destroy",
@@ -125,6 +125,7 @@ def load():
     lib.lbehd_launch_count.restype = ctypes.c_longlong
     lib.lbehd_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.lbehd_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
+    lib.lbehd_get_option.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbehd_profile_enable.argtypes = [P, ctypes.c_int]
     lib.lbehd_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
@@ -339,6 +340,12 @@ class Simulation(_HandleOps):
 
     def set_option(self, option, value):
         self._check(self._lib.lbehd_set_option(self._h, int(option), int(value)))
+
+    def get_option(self, option):
+        """The value in effect (see lbehd_get_option)."""
+        v = ctypes.c_longlong()
+        self._check(self._lib.lbehd_get_option(self._h, int(option), ctypes.byref(v)))
+        return v.value
 
     def autotune(self, reps=20):
         """Time every collide kernel this lattice can run (state untouched), keep the
