@@ -473,9 +473,11 @@ def run_adjoint(args, dev):
 
 
 def run_profile_window(args, local):
-    """Warm up, then bracket --profile-steps eager coupled steps with cudaProfilerStart /
-    Stop (for `ncu --profile-from-start off`). Prints one line, no timing. With
-    --profile-batched N the window covers eager steps of the N-instance batched sweep."""
+    """Warm up, then bracket --profile-steps coupled steps with cudaProfilerStart / Stop
+    (for `ncu --profile-from-start off`): replayed step graphs with --poisson graph (the
+    default; each step's kernels are plain graph nodes), eager launches with --poisson host.
+    Prints one line, no timing. With --profile-batched N the window covers eager steps of the
+    N-instance batched sweep."""
     import torch
     from paper_2608_12868_b300 import lbehd
     from paper_2608_12868_b300 import workloads as W
@@ -499,7 +501,9 @@ def run_profile_window(args, local):
         return
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream()
-    sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=lbehd.POISSON_HOST)
+    mode = {"fixed": lbehd.POISSON_FIXED, "host": lbehd.POISSON_HOST,
+            "graph": lbehd.POISSON_GRAPH}[args.poisson]
+    sim = lbehd.Simulation(w, stream=stream, device=local, poisson_mode=mode)
     if args.collide == "tune":
         sim.step(1)
         sim.autotune(reps=20)

@@ -459,12 +459,63 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
         }
         __syncthreads();
     };
+    // nsw red-black half sweeps of level l (colour color_of(k) for sweep k) when the level has
+    // at most TAIL_THREADS cells: thread t owns cell t, whose coordinates, neighbours,
+    // coefficients and right-hand side stay in registers across the sweeps (b is fixed while
+    // a level is smoothed). Same arithmetic as gs, in offdiag_sum's order.
+    auto owned = [&](int l, int nsw, auto color_of) {
+        const MgDims d = T.d[l];
+        const int n = ncell(l), o = T.off[l];
+        const bool own = t < n;
+        int col = -1, n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0;
+        float di = 0.f, bi = 0.f, kxi = 0.f, kxm = 0.f, kyi = 0.f, kym = 0.f, kzi = 0.f, kzm = 0.f;
+        if (own) {
+            int x, y, z;
+            cell_xyz(d, t, x, y, z);
+            const Nb6 nb = nb6(d, t, x, y, z);
+            n0 = nb.n[0];
+            n1 = nb.n[1];
+            n2 = nb.n[2];
+            n3 = nb.n[3];
+            n4 = nb.n[4];
+            n5 = nb.n[5];
+            di = sD[o + t];
+            bi = sb[o + t];
+            kxi = skx[o + t];
+            kxm = skx[o + n1];
+            kyi = sky[o + t];
+            kym = sky[o + n3];
+            kzi = skz[o + t];
+            kzm = skz[o + n5];
+            col = di > 0.0f ? ((x + y + z) & 1) : -1;
+        }
+        const float *v = sx + o;
+#pragma unroll 1
+        for (int k = 0; k < nsw; k++) {
+            if (col == color_of(k)) {
+                float s = __fmul_rn(kxi, v[n0]);
+                s = __fmaf_rn(kxm, v[n1], s);
+                s = __fmaf_rn(kyi, v[n2], s);
+                s = __fmaf_rn(kym, v[n3], s);
+                if (d.nz > 1) {
+                    s = __fmaf_rn(kzi, v[n4], s);
+                    s = __fmaf_rn(kzm, v[n5], s);
+                }
+                sx[o + t] = __fdiv_rn(__fadd_rn(bi, s), di);
+            }
+            __syncthreads();
+        }
+    };
     // down: smooth, restrict
 #pragma unroll 1
     for (int l = 0; l + 1 < T.nl; l++) {
-        for (int s = 0; s < T.nu; s++) {
-            gs(l, 0);
-            gs(l, 1);
+        if (ncell(l) <= TAIL_THREADS) {
+            owned(l, 2 * T.nu, [](int k) { return k & 1; });
+        } else {
+            for (int s = 0; s < T.nu; s++) {
+                gs(l, 0);
+                gs(l, 1);
+            }
         }
         const MgDims f = T.d[l], cd = T.d[l + 1];
         const int fo = T.off[l], co = T.off[l + 1], nzc = T.cz2[l] ? 2 : 1, nc = ncell(l + 1);
@@ -493,12 +544,16 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
     }
     // coarsest: symmetric sweeps
     const int lc = T.nl - 1;
+    if (ncell(lc) <= TAIL_THREADS) {
+        owned(lc, 4 * T.coarse, [](int k) { return ((k & 3) == 1 || (k & 3) == 2) ? 1 : 0; });
+    } else {
 #pragma unroll 1
-    for (int s = 0; s < T.coarse; s++) {
-        gs(lc, 0);
-        gs(lc, 1);
-        gs(lc, 1);
-        gs(lc, 0);
+        for (int s = 0; s < T.coarse; s++) {
+            gs(lc, 0);
+            gs(lc, 1);
+            gs(lc, 1);
+            gs(lc, 0);
+        }
     }
     // up: prolong, smooth
 #pragma unroll 1
@@ -514,9 +569,13 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
                                    sx[co + (int)cell(cd, x >> 1, y >> 1, T.cz2[l] ? (z >> 1) : z)]);
         }
         __syncthreads();
-        for (int s = 0; s < T.nu; s++) {
-            gs(l, 1);
-            gs(l, 0);
+        if (n <= TAIL_THREADS) {
+            owned(l, 2 * T.nu, [](int k) { return (k & 1) ? 0 : 1; });
+        } else {
+            for (int s = 0; s < T.nu; s++) {
+                gs(l, 1);
+                gs(l, 0);
+            }
         }
     }
     const int n0 = ncell(0);

@@ -18,10 +18,11 @@
 //    order of k_pcg_scalar) and applies the same scalar update to its shared copy of the CG
 //    scalars, so all CTAs take the same branches; CTA 0 writes the scalars back at the end;
 //  * the shared-memory tail runs in CTA 0 with the 1024-thread k_mg_tail body;
-//  * two fused phases reproduce a pair of launches exactly: "zero, then the first red half
-//    sweep" (every neighbour is 0, so x = (b + 0) / D on red cells and 0 elsewhere), and
-//    "residual, then the sum over each coarse cell's children" (the residual of each child
-//    evaluated in registers, summed in the restriction's order).
+//  * three fused phases reproduce a pair of launches exactly: "zero, then the first red half
+//    sweep" (every neighbour is 0, so x = (b + 0) / D on red cells and 0 elsewhere),
+//    "residual, then the sum over each coarse cell's children" (each child's residual on its
+//    own lane, summed in the restriction's order), and "prolongation, then the first black
+//    half sweep" (neighbours read as prolongation leaves them).
 //
 // Barrier: a monotonic arrival counter (reset by the host before each launch) that barrier
 // k waits to reach k * gridDim.x; thread 0 of each CTA spins with a backoff and an
@@ -37,7 +38,7 @@ namespace lbehd {
 constexpr int PS_THREADS = 1024;
 constexpr int PS_GROUPS = PS_THREADS / BX;        // virtual blocks per CTA
 constexpr int PS_MAX_LEVELS = 12;
-constexpr unsigned PS_SPIN_LIMIT = 1u << 23;      // x >= 64 ns backoff: ~0.5 s at least
+constexpr unsigned PS_SPIN_LIMIT = 1u << 24;      // x >= 32 ns backoff: ~0.5 s at least
 
 static_assert(PS_THREADS == SCALAR_THREADS && PS_THREADS == TAIL_THREADS,
               "the persistent solve runs the 1024-thread scalar and tail bodies as they are");
@@ -96,10 +97,10 @@ __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        atomicAdd(&bar->count, 1u);
         const unsigned target = epoch * gridDim.x;
+        const unsigned last = atomicAdd(&bar->count, 1u) + 1u;   // == target: everyone is in
         unsigned spins = 0;
-        while (ps_load_volatile(&bar->count) < target) {
+        while (last < target && ps_load_volatile(&bar->count) < target) {
             if (ps_load_volatile(&bar->error)) {
                 ok = 0;
                 break;
@@ -110,7 +111,7 @@ __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         __threadfence();
         *ok_sh = ok;
@@ -202,34 +203,79 @@ __device__ __forceinline__ float ps_resid(const PsLevel &F, int x, int y, int z)
 }
 
 // b_c = sum over each coarse cell's children of the fine residual, in the order of
-// mg_restrict_sum_cell ((x, y, z) = (2X + a, 2Y + b, z0 + g), a outermost).
+// mg_restrict_sum_cell ((x, y, z) = (2X + a, 2Y + b, z0 + g), a outermost). Eight lanes per
+// coarse cell: lane ch = 4a + 2b + g of the group evaluates one child, the group's first
+// lane gathers the eight by shuffles and sums them in that order.
 __device__ __forceinline__ void ps_resid_restrict(const PsLevel &F, const PsLevel &C)
 {
     const MgDims &f = F.d, &c = C.d;
-    ps_for(C.n, [&](int I) {
-        int X, Y, Z;
-        cell_xyz(c, I, X, Y, Z);
-        const int z0 = F.cz2 ? 2 * Z : Z;
-        const bool z1 = F.cz2 && z0 + 1 < f.nz;
-        float acc = 0.0f;
+    const int span = (C.n * 8 + 31) & ~31;   // whole warps: every lane reaches the shuffles
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * PS_THREADS + threadIdx.x; k < span; k += gridDim.x * PS_THREADS) {
+        const int I = k >> 3, ch = k & 7;
+        bool z1 = false;
+        float r = 0.0f;
+        if (I < C.n) {
+            int X, Y, Z;
+            cell_xyz(c, I, X, Y, Z);
+            const int z0 = F.cz2 ? 2 * Z : Z;
+            z1 = F.cz2 && z0 + 1 < f.nz;
+            const int a = ch >> 2, b = (ch >> 1) & 1, g = ch & 1;
+            if (g == 0 || z1)
+                r = ps_resid(F, 2 * X + a, 2 * Y + b, z0 + g);
+        }
+        float v[8];
 #pragma unroll
-        for (int a = 0; a < 2; a++)
+        for (int j = 0; j < 8; j++)
+            v[j] = __shfl_sync(0xffffffffu, r, (lane & ~7) + j);
+        if (ch == 0 && I < C.n) {
+            float acc = 0.0f;
 #pragma unroll
-            for (int b = 0; b < 2; b++) {
-                acc = __fadd_rn(acc, ps_resid(F, 2 * X + a, 2 * Y + b, z0));
-                if (z1)
-                    acc = __fadd_rn(acc, ps_resid(F, 2 * X + a, 2 * Y + b, z0 + 1));
-            }
-        C.b[I] = acc;
-    });
+            for (int j = 0; j < 8; j++)
+                if ((j & 1) == 0 || z1)
+                    acc = __fadd_rn(acc, v[j]);
+            C.b[I] = acc;
+        }
+    }
 }
 
-__device__ __forceinline__ void ps_prolong(const PsLevel &F, const PsLevel &C)
+// Prolongation fused into the first black half sweep after it: a black cell's update reads
+// its (red) neighbours as the prolongation would have left them, x_j + x_c(parent of j) on
+// active cells, computed on the fly in the order offdiag_sum uses. Red cells are not
+// written: the red half sweep that follows overwrites every active red cell without reading
+// it, and prolongation leaves inactive cells alone. Same bits as prolong, then sweep.
+__device__ __forceinline__ void ps_prolong_gs1(const PsLevel &F, const PsLevel &C)
 {
-    ps_for(F.n, [&](int c) {
-        int x, y, z;
-        cell_xyz(F.d, c, x, y, z);
-        mg_prolong_cell(F.d, C.d, F.cz2, F.D, C.x, F.x, x, y, z);
+    const MgDims &d = F.d, &c = C.d;
+    const int hx = d.nx >> 1;
+    auto xp = [&](int j, int x, int y, int z) {
+        const float xj = F.x[j];
+        return F.D[j] > 0.0f
+                   ? __fadd_rn(xj, C.x[cell(c, x >> 1, y >> 1, F.cz2 ? (z >> 1) : z)])
+                   : xj;
+    };
+    ps_for(F.n >> 1, [&](int k) {
+        const int row = fdiv(k, d.mh, d.sh);
+        const int jx = k - row * hx;
+        const int z = fdiv(row, d.my, d.sy);
+        const int y = row - z * d.ny;
+        const int x = 2 * jx + ((y + z + 1) & 1);
+        const int i = cell(d, x, y, z);
+        const Nb6 nb = nb6(d, i, x, y, z);
+        const int xm = x == 0 ? d.nx - 1 : x - 1, xq = x + 1 == d.nx ? 0 : x + 1;
+        const int ym = y == 0 ? d.ny - 1 : y - 1, yq = y + 1 == d.ny ? 0 : y + 1;
+        const float di = F.D[i], bi = F.b[i];
+        float s = __fmul_rn(F.kx[i], xp(nb.n[0], xq, y, z));
+        s = __fmaf_rn(F.kx[nb.n[1]], xp(nb.n[1], xm, y, z), s);
+        s = __fmaf_rn(F.ky[i], xp(nb.n[2], x, yq, z), s);
+        s = __fmaf_rn(F.ky[nb.n[3]], xp(nb.n[3], x, ym, z), s);
+        if (d.nz > 1) {
+            const int zm = z == 0 ? d.nz - 1 : z - 1, zq = z + 1 == d.nz ? 0 : z + 1;
+            s = __fmaf_rn(F.kz[i], xp(nb.n[4], x, y, zq), s);
+            s = __fmaf_rn(F.kz[nb.n[5]], xp(nb.n[5], x, y, zm), s);
+        }
+        if (di > 0.0f)
+            F.x[i] = __fdiv_rn(__fadd_rn(bi, s), di);
     });
 }
 
@@ -280,10 +326,11 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         sync();
         for (int l = A.nl - 1; l >= 0 && ok; l--) {
             const PsLevel &L = A.L[l];
-            ps_prolong(L, A.L[l + 1]);
-            sync();
             for (int k = 0; k < A.nu && ok; k++) {
-                ps_gs(L, 1);
+                if (k == 0)
+                    ps_prolong_gs1(L, A.L[l + 1]);
+                else
+                    ps_gs(L, 1);
                 sync();
                 ps_gs(L, 0);
                 sync();
