@@ -482,6 +482,25 @@ def run_profile_window(args, local):
     from paper_2608_12868_b300 import lbehd
     from paper_2608_12868_b300 import workloads as W
     torch.cuda.set_device(local)
+    if args.profile_adjoint:
+        # the backward pass of an adjoint run of the control case: S segments of 16 steps
+        w = W.control_3d_96x64x64()
+        V = np.array([v for _, v in w.schedule])[:args.profile_adjoint]
+        stream = torch.cuda.Stream()
+        sim = lbehd.Simulation(w, stream=stream, device=local)
+        sim.step(1)
+        sim.autotune(reps=5)
+        sim.adjoint_forward(V, 16)
+        sim.adjoint_backward()      # untimed: allocation and graph capture
+        sim.adjoint_forward(V, 16)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        sim.adjoint_backward()
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profile_window": "adjoint backward", "workload": w.name,
+                          "steps": int(V.shape[0]) * 16, "info": sim.adjoint_info()}))
+        return
     if args.profile_batched:
         ws = W.batched_sweep(n=args.profile_batched)
         stream = torch.cuda.Stream()
@@ -545,11 +564,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run a profiler window of this many eager steps (for ncu)")
+    ap.add_argument("--profile-adjoint", type=int, default=0,
+                    help="only profile the backward pass of an adjoint run of this many "
+                         "16-step segments of the control case")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="with --profile-steps: profile the batched sweep of this many instances")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
-    if args.profile_steps:
+    if args.profile_steps or args.profile_adjoint:
         run_profile_window(args, int(os.environ.get("LOCAL_RANK", "0")))
         return
     world, rank, local = dist_setup(args)
