@@ -320,7 +320,8 @@ int ps_setup(lbehd_handle *h)
     const size_t pn = 2 * std::max(h->nblocks_site, h->nblocks1d);
     h->ps_part = (double *)dev_alloc(h, 2 * pn * sizeof(double));
     h->ps_bar = (PsBarrier *)dev_alloc(h, sizeof(PsBarrier));
-    if (!h->ps_part || !h->ps_bar)
+    h->ps.wsum = (double *)dev_alloc(h, 2 * 32 * sizeof(double));
+    if (!h->ps_part || !h->ps_bar || !h->ps.wsum)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (persistent Poisson)");
     CK(h, cudaMemsetAsync(h->ps_bar, 0, sizeof(PsBarrier), h->stream));
     CK(h, cudaMallocHost(&h->h_ps_err, sizeof(unsigned)));

@@ -596,15 +596,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
 // phi_j - phi_i = (hi_j - hi_i) + (lo_j - lo_i) + (delta_j - delta_i). Neighbouring hi parts
 // are close, so their difference is exact in FP32, and r keeps the accuracy an FP64
 // evaluation of b - A phi would have, in FP32 arithmetic.
+// pcg_init_value returns r_i without storing it (so that several sites' loads can be in
+// flight together); pcg_init_site stores it.
 template <int D>
-__device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *pot,
-                                              const float *pot_lo,
-                                              const float *delta,
-                                              const float *eps,
-                                              const float *rho,
-                                              const uint8_t *info,
-                                              const float *Dg, float *r,
-                                              int x, int y, int z, float (&v)[2])
+__device__ __forceinline__ float pcg_init_value(const MgDims &d, const float *pot,
+                                                const float *pot_lo, const float *delta,
+                                                const float *eps, const float *rho,
+                                                const uint8_t *info, const float *Dg, int x,
+                                                int y, int z, float (&v)[2])
 {
     {
         const int i = cell(d, x, y, z);
@@ -642,8 +641,21 @@ __device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *pot,
             v[0] = __fmul_rn(ri, ri);
             v[1] = __fmul_rn(b, b);
         }
-        r[i] = ri;
+        return ri;
     }
+}
+
+template <int D>
+__device__ __forceinline__ void pcg_init_site(const MgDims &d, const float *pot,
+                                              const float *pot_lo,
+                                              const float *delta,
+                                              const float *eps,
+                                              const float *rho,
+                                              const uint8_t *info,
+                                              const float *Dg, float *r,
+                                              int x, int y, int z, float (&v)[2])
+{
+    r[cell(d, x, y, z)] = pcg_init_value<D>(d, pot, pot_lo, delta, eps, rho, info, Dg, x, y, z, v);
 }
 
 template <int D>
@@ -699,11 +711,10 @@ __global__ void __launch_bounds__(BX) k_pcg_p(size_t n, const float *__restrict_
 // hierarchy may be a few steps old, which only changes the preconditioner) and partials of
 // p . q. Dirichlet neighbours hold no correction (p = 0 there).
 template <int D>
-__device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *eps,
-                                            const uint8_t *info,
-                                            const float *Dg,
-                                            const float *p, float *q,
-                                            int x, int y, int z, float (&v)[1])
+__device__ __forceinline__ float pcg_Ap_value(const MgDims &d, const float *eps,
+                                              const uint8_t *info, const float *Dg,
+                                              const float *p, int x, int y, int z,
+                                              float (&v)[1])
 {
     {
         const int i = cell(d, x, y, z);
@@ -729,8 +740,18 @@ __device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *eps,
             }
             v[0] = __fmul_rn(pi, qi);
         }
-        q[i] = qi;
+        return qi;
     }
+}
+
+template <int D>
+__device__ __forceinline__ void pcg_Ap_site(const MgDims &d, const float *eps,
+                                            const uint8_t *info,
+                                            const float *Dg,
+                                            const float *p, float *q,
+                                            int x, int y, int z, float (&v)[1])
+{
+    q[cell(d, x, y, z)] = pcg_Ap_value<D>(d, eps, info, Dg, p, x, y, z, v);
 }
 
 template <int D>
@@ -822,41 +843,30 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 // k_pcg_scalar: with use_cond, ops 0, 4, 3 and 5 also set the graph's while-loop condition
 // to !done; with use_ref, op 0 clears and op 3 sets the condition of the refinement block.
 constexpr int SCALAR_THREADS = 1024;
-__device__ __forceinline__ bool pcg_scalar_block(const double *partials,
-                                                 long long nblocks, int nv, int op,
-                                                 CgScalars *s)
+
+// The fixed summation order, in two pieces that may run on different SMs: the sum of
+// virtual warp w (lanes = threads 32 w .. 32 w + 31 of the 1024-thread order: each lane's
+// strided pair of accumulators, then a butterfly), and the butterfly over the 32 warp sums.
+__device__ __forceinline__ double pcg_vwarp_sum(const double *p, long long nblocks, int vt)
 {
-    __shared__ double sm[2][SCALAR_THREADS / 32];
-    double tot[2] = {0.0, 0.0};
-    for (int k = 0; k < nv; k++) {
-        const double *p = partials + k * nblocks;
-        double a0 = 0.0, a1 = 0.0;
-        long long b = threadIdx.x;
-        for (; b + SCALAR_THREADS < nblocks; b += 2 * SCALAR_THREADS) {
-            a0 += p[b];
-            a1 += p[b + SCALAR_THREADS];
-        }
-        if (b < nblocks)
-            a0 += p[b];
-        double a = a0 + a1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-        if ((threadIdx.x & 31) == 0)
-            sm[k][threadIdx.x >> 5] = a;
+    double a0 = 0.0, a1 = 0.0;
+    long long b = vt;
+    for (; b + SCALAR_THREADS < nblocks; b += 2 * SCALAR_THREADS) {
+        a0 += p[b];
+        a1 += p[b + SCALAR_THREADS];
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        for (int k = 0; k < nv; k++) {
-            double a = sm[k][threadIdx.x];
+    if (b < nblocks)
+        a0 += p[b];
+    double a = a0 + a1;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-            tot[k] = a;
-        }
-    }
-    if (threadIdx.x != 0)
-        return false;
+    for (int o = 16; o > 0; o >>= 1)
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// CG scalar update (thread 0) from the totals of the op's partial arrays.
+__device__ __forceinline__ void pcg_scalar_update(const double (&tot)[2], int op, CgScalars *s)
+{
     if (op == 0 || op == 4) {
         s->rr = tot[0];
         s->bb = tot[1];
@@ -886,6 +896,32 @@ __device__ __forceinline__ bool pcg_scalar_block(const double *partials,
         if (s->done && !s->converged)
             s->nonconv = 1;
     }
+}
+
+__device__ __forceinline__ bool pcg_scalar_block(const double *partials,
+                                                 long long nblocks, int nv, int op,
+                                                 CgScalars *s)
+{
+    __shared__ double sm[2][SCALAR_THREADS / 32];
+    double tot[2] = {0.0, 0.0};
+    for (int k = 0; k < nv; k++) {
+        const double a = pcg_vwarp_sum(partials + k * nblocks, nblocks, (int)threadIdx.x);
+        if ((threadIdx.x & 31) == 0)
+            sm[k][threadIdx.x >> 5] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < nv; k++) {
+            double a = sm[k][threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+            tot[k] = a;
+        }
+    }
+    if (threadIdx.x != 0)
+        return false;
+    pcg_scalar_update(tot, op, s);
     return true;
 }
 
@@ -911,6 +947,19 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
 // phi += delta on active cells, phi kept as the compensated pair hi + lo (two-sum in FP32:
 // the rounding error of hi + delta is carried into lo); acc += delta when acc is given
 // (accumulates a refinement correction into the step's increment).
+// (hi, lo) + d as a renormalised pair (two-sum of hi + d, error carried into lo).
+__device__ __forceinline__ void pcg_apply_pair(float hi, float lo0, float d, float &hi_out,
+                                               float &lo_out)
+{
+    const float t = __fadd_rn(hi, d);             // two-sum: t + err = hi + d exactly
+    const float bv = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(d, bv));
+    const float lo = __fadd_rn(lo0, err);
+    const float s = __fadd_rn(t, lo);             // renormalise the pair
+    hi_out = s;
+    lo_out = __fsub_rn(lo, __fsub_rn(s, t));
+}
+
 __device__ __forceinline__ void pcg_apply_site(int i, const float *Dg, const float *delta,
                                                float *acc, float *pot, float *pot_lo)
 {
@@ -918,15 +967,8 @@ __device__ __forceinline__ void pcg_apply_site(int i, const float *Dg, const flo
         return;
     const float d = delta[i];
     if (acc)
-        acc[i] += d;
-    const float hi = pot[i];
-    const float t = hi + d;                       // two-sum: t + err = hi + d exactly
-    const float bv = t - hi;
-    const float err = (hi - (t - bv)) + (d - bv);
-    const float lo = pot_lo[i] + err;
-    const float s = t + lo;                       // renormalise the pair
-    pot[i] = s;
-    pot_lo[i] = lo - (s - t);
+        acc[i] = __fadd_rn(acc[i], d);
+    pcg_apply_pair(pot[i], pot_lo[i], d, pot[i], pot_lo[i]);
 }
 
 __device__ __forceinline__ void pcg_apply_range(int n, const float *Dg,

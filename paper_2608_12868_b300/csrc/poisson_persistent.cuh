@@ -14,9 +14,12 @@
 //  * dot products keep their partition into BX-site virtual blocks: the 128-thread group g of
 //    a CTA plays virtual block blockIdx.x * PS_GROUPS + g, ... and reduces like
 //    block_partials (warp sums in FP32, then FP64 over the four warps in order);
-//  * every CTA sums the partial arrays with pcg_scalar_block itself (the 1024-thread fixed
-//    order of k_pcg_scalar) and applies the same scalar update to its shared copy of the CG
-//    scalars, so all CTAs take the same branches; CTA 0 writes the scalars back at the end;
+//  * the partial arrays are summed in the fixed order of k_pcg_scalar (1024 threads: per
+//    thread two strided accumulators, butterflies within and across warps); every CTA keeps
+//    an identical copy of the CG scalars, so all CTAs take the same branches. Small sums are
+//    done by every CTA; large ones are split: 32 CTAs (per array) each form one warp's sum,
+//    then, after a barrier, every CTA finishes the butterfly (FP64 adds are slow on this
+//    part, and the split spreads them over SMs);
 //  * the shared-memory tail runs in CTA 0 with the 1024-thread k_mg_tail body;
 //  * three fused phases reproduce a pair of launches exactly: "zero, then the first red half
 //    sweep" (every neighbour is 0, so x = (b + 0) / D on red cells and 0 elsewhere),
@@ -73,11 +76,19 @@ struct PsArgs {
     const float *rhs;
     float *r, *p, *q;          // r is L[0].b; z is L[0].x
     double *part[2];           // partial arrays, alternating so a scalar read never races
+    double *wsum;              // [2][32] virtual-warp sums of a split scalar reduction
     CgScalars *s;
     PsBarrier *bar;
 };
 
 constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
+
+// Reductions of at least PS_SPLIT_MIN partials have their 32 virtual-warp sums computed on
+// separate CTAs (FP64 adds are slow on this part; one CTA summing 8192 partials takes ~10 us).
+constexpr long long PS_SPLIT_MIN = 2048;
+// The defect and Ap phases can handle two of a group's virtual blocks per pass (measured a
+// little slower on 128x64x64: more spilled registers; kept off).
+constexpr bool PS_PAIRS = false;
 
 __device__ __forceinline__ void ps_named_sync(int id)
 {
@@ -89,6 +100,14 @@ __device__ __forceinline__ unsigned ps_load_volatile(const unsigned *p)
     return *(const volatile unsigned *)p;
 }
 
+// Release / acquire fences at GPU scope (lighter than the sequentially consistent fence of
+// __threadfence); with them the relaxed arrival and the polling load form the release and
+// the acquire of the barrier.
+__device__ __forceinline__ void ps_fence()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 // Grid barrier number `epoch` (1, 2, ...). Returns false once any CTA has timed out.
 __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok_sh)
 {
@@ -96,7 +115,7 @@ __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
+        ps_fence();
         const unsigned target = epoch * gridDim.x;
         const unsigned last = atomicAdd(&bar->count, 1u) + 1u;   // == target: everyone is in
         unsigned spins = 0;
@@ -113,7 +132,7 @@ __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok
             }
             __nanosleep(32);
         }
-        __threadfence();
+        ps_fence();
         *ok_sh = ok;
     }
     __syncthreads();
@@ -161,6 +180,136 @@ __device__ __forceinline__ void ps_for_vblocks(int nvb, F &&f)
         f(vb, t);
 }
 
+// Pointwise and 1D phases handle up to PS_B sites per thread per pass with every load issued
+// before any store (the bodies carry no restrict qualifiers, so otherwise each site's loads
+// would wait for the previous site's stores); per-site arithmetic and accumulation order
+// are those of the range bodies in poisson.cuh.
+constexpr int PS_B = 4;
+
+// phi += delta (compensated pair), acc += delta, on active cells.
+__device__ __forceinline__ void ps_apply(int n, const float *Dg, const float *delta, float *acc,
+                                         float *pot, float *pot_lo)
+{
+    const int S = gridDim.x * PS_THREADS;
+    for (int i0 = blockIdx.x * PS_THREADS + threadIdx.x; i0 < n; i0 += PS_B * S) {
+        float dg[PS_B], d[PS_B], hi[PS_B], lo[PS_B], ac[PS_B];
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            dg[j] = d[j] = hi[j] = lo[j] = ac[j] = 0.0f;
+            if (i < n) {
+                dg[j] = Dg[i];
+                d[j] = delta[i];
+                hi[j] = pot[i];
+                lo[j] = pot_lo[i];
+                if (acc)
+                    ac[j] = acc[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            if (i < n && dg[j] > 0.0f) {
+                if (acc)
+                    acc[i] = __fadd_rn(ac[j], d[j]);
+                float h, l;
+                pcg_apply_pair(hi[j], lo[j], d[j], h, l);
+                pot[i] = h;
+                pot_lo[i] = l;
+            }
+        }
+    }
+}
+
+// p = z + beta p.
+__device__ __forceinline__ void ps_p(int n, float beta, const float *zv, float *p)
+{
+    const int S = gridDim.x * PS_THREADS;
+    for (int i0 = blockIdx.x * PS_THREADS + threadIdx.x; i0 < n; i0 += PS_B * S) {
+        float zz[PS_B], pp[PS_B];
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            zz[j] = pp[j] = 0.0f;
+            if (i < n) {
+                zz[j] = zv[i];
+                pp[j] = p[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            if (i < n)
+                p[i] = beta != 0.0f ? __fmaf_rn(beta, pp[j], zz[j]) : zz[j];
+        }
+    }
+}
+
+// r . z over the sites of virtual block b (of nb) for this thread, in site order.
+__device__ __forceinline__ void ps_dot_range(int n, const float *a, const float *b_, int b,
+                                             int nb, int t, float (&v)[1])
+{
+    const int S = nb * BX;
+    for (int i0 = b * BX + t; i0 < n; i0 += PS_B * S) {
+        float x[PS_B], y[PS_B];
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            x[j] = y[j] = 0.0f;
+            if (i < n) {
+                x[j] = a[i];
+                y[j] = b_[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PS_B; j++)
+            if (i0 + j * S < n)
+                v[0] = __fmaf_rn(x[j], y[j], v[0]);
+    }
+}
+
+// delta += alpha p, r -= alpha q, ||r||^2 over the sites of virtual block b, in site order.
+__device__ __forceinline__ void ps_update_range(int n, const float *p, const float *q,
+                                                float *delta, float *r, float a, int b, int nb,
+                                                int t, float (&v)[1])
+{
+    const int S = nb * BX;
+    for (int i0 = b * BX + t; i0 < n; i0 += PS_B * S) {
+        float pp[PS_B], qq[PS_B], dd[PS_B], rr[PS_B];
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            pp[j] = qq[j] = dd[j] = rr[j] = 0.0f;
+            if (i < n) {
+                pp[j] = p[i];
+                qq[j] = q[i];
+                dd[j] = delta[i];
+                rr[j] = r[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int i = i0 + j * S;
+            if (i < n) {
+                delta[i] = __fmaf_rn(a, pp[j], dd[j]);
+                const float ri = __fmaf_rn(-a, qq[j], rr[j]);
+                r[i] = ri;
+                v[0] = __fmaf_rn(ri, ri, v[0]);
+            }
+        }
+    }
+}
+
+// Loop over virtual blocks two at a time (group-uniform): f(vb, vb2, t) with vb2 the group's
+// next block (vb2 >= nvb: none), so that two sites' loads are in flight together.
+template <class F>
+__device__ __forceinline__ void ps_for_vblock_pairs(int nvb, F &&f)
+{
+    const int g = threadIdx.x / BX, t = threadIdx.x % BX, st = gridDim.x * PS_GROUPS;
+    for (int vb = blockIdx.x * PS_GROUPS + g; vb < nvb; vb += 2 * st)
+        f(vb, vb + st, t);
+}
+
 // One red-black half sweep (colour c) of level L, cells in flat order (nx even).
 __device__ __forceinline__ void ps_gs(const PsLevel &L, int color)
 {
@@ -181,15 +330,31 @@ __device__ __forceinline__ void ps_gs(const PsLevel &L, int color)
 __device__ __forceinline__ void ps_gs_first(const PsLevel &L)
 {
     const MgDims &d = L.d;
-    ps_for(L.n, [&](int c) {
-        int x, y, z;
-        cell_xyz(d, c, x, y, z);
-        const float di = L.D[c], bi = L.b[c];
-        float v = 0.0f;
-        if (((x + y + z) & 1) == 0 && di > 0.0f)
-            v = __fdiv_rn(__fadd_rn(bi, 0.0f), di);
-        L.x[c] = v;
-    });
+    const int S = gridDim.x * PS_THREADS, n = L.n;
+    for (int c0 = blockIdx.x * PS_THREADS + threadIdx.x; c0 < n; c0 += PS_B * S) {
+        float dg[PS_B], bb[PS_B];
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int c = c0 + j * S;
+            dg[j] = bb[j] = 0.0f;
+            if (c < n) {
+                dg[j] = L.D[c];
+                bb[j] = L.b[c];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PS_B; j++) {
+            const int c = c0 + j * S;
+            if (c < n) {
+                int x, y, z;
+                cell_xyz(d, c, x, y, z);
+                float v = 0.0f;
+                if (((x + y + z) & 1) == 0 && dg[j] > 0.0f)
+                    v = __fdiv_rn(__fadd_rn(bb[j], 0.0f), dg[j]);
+                L.x[c] = v;
+            }
+        }
+    }
 }
 
 // Residual b - A x of one fine cell (0 on inactive cells), as mg_resid_cell computes it.
@@ -295,8 +460,40 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         if (ok)
             ok = ps_sync(A.bar, epoch, &ok_sh);
     };
-    auto scalar = [&](const double *part, int nv, int op, int nblk) {
-        pcg_scalar_block(part, nblk, nv, op, &s);
+    // barrier, then the CG scalar update from the partial arrays, in the fixed order of
+    // pcg_scalar_block: small reductions are summed by every CTA; large ones have their 32
+    // virtual-warp sums spread over CTAs 0 .. 32 nv - 1, a second barrier, then every CTA
+    // finishes the butterfly over the 32 sums and updates its copy of the scalars
+    auto sync_scalar = [&](const double *part, int nv, int op, int nblk) {
+        sync();
+        if (!ok)
+            return;
+        if ((long long)nv * nblk < PS_SPLIT_MIN || (int)gridDim.x < 32 * nv) {
+            pcg_scalar_block(part, nblk, nv, op, &s);
+            __syncthreads();
+            return;
+        }
+        if (threadIdx.x < 32 && (int)blockIdx.x < 32 * nv) {
+            const int k = blockIdx.x >> 5, w = blockIdx.x & 31;
+            const double a = pcg_vwarp_sum(part + (size_t)k * nblk, nblk, 32 * w + threadIdx.x);
+            if (threadIdx.x == 0)
+                A.wsum[k * 32 + w] = a;
+        }
+        sync();
+        if (!ok)
+            return;
+        if (threadIdx.x < 32) {
+            double tot[2] = {0.0, 0.0};
+            for (int k = 0; k < nv; k++) {
+                double a = __ldcg(A.wsum + k * 32 + threadIdx.x);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                tot[k] = a;
+            }
+            if (threadIdx.x == 0)
+                pcg_scalar_update(tot, op, &s);
+        }
         __syncthreads();
     };
     const PsLevel &L0 = A.L[0];
@@ -345,68 +542,100 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
             return;
         ps_for_vblocks(A.nb1, [&](int vb, int t) {
             float v[1] = {0.0f};
-            pcg_dot_range_t(A.N, A.r, z, vb, A.nb1, t, v);
+            ps_dot_range(A.N, A.r, z, vb, A.nb1, t, v);
             ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
         });
-        sync();
+        sync_scalar(A.part[0], 1, 1, A.nb1);
         if (!ok)
             return;
-        scalar(A.part[0], 1, 1, A.nb1);
-        const float beta = pcg_beta(&s);
-        ps_for(A.N, [&](int i) { pcg_p_site(i, beta, z, A.p); });
+        ps_p(A.N, pcg_beta(&s), z, A.p);
         sync();
-        ps_for_vblocks(A.nbs, [&](int vb, int t) {
-            const int i = vb * BX + t;
-            float v[1] = {0.0f};
+        auto Ap_pass = [&](int vb, int vb2, int t) {
+            // q = A p at one site of each of two virtual blocks, stored after both
+            float v[1] = {0.0f}, w[1] = {0.0f}, q1 = 0.0f, q2 = 0.0f;
+            const int i = vb * BX + t, i2 = vb2 * BX + t;
             if (i < A.N) {
                 int x, y, zz;
                 cell_xyz(L0.d, i, x, y, zz);
-                pcg_Ap_site<D>(L0.d, A.eps, A.info, L0.D, A.p, A.q, x, y, zz, v);
+                q1 = pcg_Ap_value<D>(L0.d, A.eps, A.info, L0.D, A.p, x, y, zz, v);
             }
+            if (vb2 < A.nbs && i2 < A.N) {
+                int x, y, zz;
+                cell_xyz(L0.d, i2, x, y, zz);
+                q2 = pcg_Ap_value<D>(L0.d, A.eps, A.info, L0.D, A.p, x, y, zz, w);
+            }
+            if (i < A.N)
+                A.q[i] = q1;
+            if (vb2 < A.nbs && i2 < A.N)
+                A.q[i2] = q2;
             ps_group_partials<1>(v, A.part[1], vb, A.nbs, gsm);
-        });
-        sync();
+            if (vb2 < A.nbs)
+                ps_group_partials<1>(w, A.part[1], vb2, A.nbs, gsm);
+        };
+        if (PS_PAIRS)
+            ps_for_vblock_pairs(A.nbs, Ap_pass);
+        else
+            ps_for_vblocks(A.nbs, [&](int vb, int t) { Ap_pass(vb, A.nbs, t); });
+        sync_scalar(A.part[1], 1, 2, A.nbs);
         if (!ok)
             return;
-        scalar(A.part[1], 1, 2, A.nbs);
+        const float alpha = (float)s.alpha;
         ps_for_vblocks(A.nb1, [&](int vb, int t) {
             float v[1] = {0.0f};
-            pcg_update_range_t(A.N, A.p, A.q, xv, A.r, &s, vb, A.nb1, t, v);
+            ps_update_range(A.N, A.p, A.q, xv, A.r, alpha, vb, A.nb1, t, v);
             ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
         });
-        sync();
-        if (!ok)
-            return;
-        scalar(A.part[0], 1, 3, A.nb1);
+        sync_scalar(A.part[0], 1, 3, A.nb1);
     };
 
     // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4
     auto start = [&](float *xv, int op) {
-        ps_for_vblocks(A.nbs, [&](int vb, int t) {
-            const int i = vb * BX + t;
-            float v[2] = {0.0f, 0.0f};
-            if (i < A.N) {
-                if (A.mode == PS_ADJOINT) {
+        if (A.mode == PS_ADJOINT) {
+            ps_for_vblocks(A.nbs, [&](int vb, int t) {
+                const int i = vb * BX + t;
+                float v[2] = {0.0f, 0.0f};
+                if (i < A.N)
                     adj_pcg_init_site<D>(L0.d, A.eps, A.info, L0.D, xv, A.rhs, A.r, i, v);
-                } else {
+                ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
+            });
+        } else {
+            auto init_pass = [&](int vb, int vb2, int t) {
+                // the defect at one site of each of two virtual blocks, stored after both
+                float v[2] = {0.0f, 0.0f}, w[2] = {0.0f, 0.0f}, r1 = 0.0f, r2 = 0.0f;
+                const int i = vb * BX + t, i2 = vb2 * BX + t;
+                if (i < A.N) {
                     int x, y, zz;
                     cell_xyz(L0.d, i, x, y, zz);
-                    pcg_init_site<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D, A.r,
-                                     x, y, zz, v);
+                    r1 = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D,
+                                           x, y, zz, v);
                 }
-            }
-            ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
-        });
-        sync();
-        if (ok)
-            scalar(A.part[1], 2, op, A.nbs);
+                if (vb2 < A.nbs && i2 < A.N) {
+                    int x, y, zz;
+                    cell_xyz(L0.d, i2, x, y, zz);
+                    r2 = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D,
+                                           x, y, zz, w);
+                }
+                if (i < A.N)
+                    A.r[i] = r1;
+                if (vb2 < A.nbs && i2 < A.N)
+                    A.r[i2] = r2;
+                ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
+                if (vb2 < A.nbs)
+                    ps_group_partials<2>(w, A.part[1], vb2, A.nbs, gsm);
+            };
+            if (PS_PAIRS)
+                ps_for_vblock_pairs(A.nbs, init_pass);
+            else
+                ps_for_vblocks(A.nbs, [&](int vb, int t) { init_pass(vb, A.nbs, t); });
+        }
+        sync_scalar(A.part[1], 2, op, A.nbs);
     };
 
     start(A.x, 0);
     while (ok && !s.done)
         iteration(A.x);
     if (ok && A.mode == PS_FORWARD) {
-        ps_for(A.N, [&](int i) { pcg_apply_site(i, L0.D, A.x, nullptr, A.pot, A.pot_lo); });
+        ps_apply(A.N, L0.D, A.x, nullptr, A.pot, A.pot_lo);
         sync();
         // refinement: the true residual of the updated potential, once, if the pass iterated
         if (ok && s.refine) {
@@ -416,9 +645,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
             while (ok && !s.done)
                 iteration(A.delta2);
             if (ok)
-                ps_for(A.N, [&](int i) {
-                    pcg_apply_site(i, L0.D, A.delta2, A.x, A.pot, A.pot_lo);
-                });
+                ps_apply(A.N, L0.D, A.delta2, A.x, A.pot, A.pot_lo);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
