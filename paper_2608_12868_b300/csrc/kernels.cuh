@@ -894,4 +894,45 @@ __global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restr
     obs_final_block(partials, nblocks, obs, blockIdx.x);
 }
 
+// The same sums split over NOBS x (OBS_THREADS / 32) one-warp CTAs (FP64 adds are slow on
+// this part, so one CTA per observable is latency-bound): CTA (k, w) forms warp w's sum of
+// obs_final_block's order and the last CTA of observable k to finish adds the warp sums in
+// order. Same bits as k_obs_final. cnt[NOBS] must be zero before the first launch; the last
+// CTA resets it.
+__global__ void __launch_bounds__(32) k_obs_final_split(const double *__restrict__ partials,
+                                                        long long nblocks, double *wsum,
+                                                        unsigned *cnt, double *obs)
+{
+    constexpr int NW = OBS_THREADS / 32;
+    const int k = blockIdx.x / NW, w = blockIdx.x % NW;
+    const double *p = partials + k * nblocks;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long b = 32 * w + threadIdx.x;
+    for (; b + 3 * OBS_THREADS < nblocks; b += 4 * OBS_THREADS) {
+        a0 += p[b];
+        a1 += p[b + OBS_THREADS];
+        a2 += p[b + 2 * OBS_THREADS];
+        a3 += p[b + 3 * OBS_THREADS];
+    }
+    for (; b < nblocks; b += OBS_THREADS)
+        a0 += p[b];
+    double a = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) {
+        wsum[blockIdx.x] = a;
+        __threadfence();
+        if (atomicAdd(&cnt[k], 1u) == (unsigned)(NW - 1)) {
+            __threadfence();
+            double t = 0.0;
+            for (int j = 0; j < NW; j++)
+                t += __ldcg(wsum + k * NW + j);
+            obs[NOBS + k] = obs[k];
+            obs[k] = t;
+            cnt[k] = 0u;
+        }
+    }
+}
+
 }  // namespace lbehd

@@ -55,6 +55,8 @@ struct lbehd_handle {
     uint8_t *info = nullptr, *normal = nullptr;
     int16_t *elec = nullptr;
     double *obs_partials = nullptr, *obs = nullptr;
+    double *obs_wsum = nullptr;    // [NOBS][OBS_THREADS / 32] warp sums of k_obs_final_split
+    unsigned *obs_cnt = nullptr;   // [NOBS] arrival counters of k_obs_final_split
     int *flag = nullptr;
     // Poisson: multigrid hierarchy (level 0 = the lattice) and CG vectors on level 0
     struct Level {
@@ -649,7 +651,8 @@ void collide(lbehd_handle *h, bool with_obs = true)
     });
     if (with_obs)
         launch(h, LBEHD_KC_OBS, 1, [&] {
-            k_obs_final<<<NOBS, OBS_THREADS, 0, h->ls>>>(h->obs_partials, (long long)nblk, h->obs);
+            k_obs_final_split<<<NOBS * (OBS_THREADS / 32), 32, 0, h->ls>>>(
+                h->obs_partials, (long long)nblk, h->obs_wsum, h->obs_cnt, h->obs);
         });
 }
 
@@ -1002,10 +1005,13 @@ int init_impl(lbehd_handle *h)
     }
     h->obs_partials = (double *)dev_alloc(h, NOBS * nblk_max * sizeof(double));
     h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
+    h->obs_wsum = (double *)dev_alloc(h, NOBS * (OBS_THREADS / 32) * sizeof(double));
+    h->obs_cnt = (unsigned *)dev_alloc(h, NOBS * sizeof(unsigned));
     h->flag = (int *)dev_alloc(h, sizeof(int));
     if (!h->u || !h->q || !h->pot || !h->pot_lo || !h->eps || !h->V || !h->info || !h->normal || !h->elec ||
-        !h->obs_partials || !h->obs || !h->flag)
+        !h->obs_partials || !h->obs || !h->flag || !h->obs_wsum || !h->obs_cnt)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (fields)");
+    CK(h, cudaMemsetAsync(h->obs_cnt, 0, NOBS * sizeof(unsigned), h->stream));
     // Poisson: CG vectors, reductions, multigrid hierarchy
     {
         int dev = 0, nsm = 148;
