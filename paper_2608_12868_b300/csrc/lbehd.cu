@@ -1877,6 +1877,8 @@ struct lbehd_batch {
     PopMaps *maps = nullptr;           // device: [2][n] tensor maps, per step parity
     TailLevels *tails = nullptr;       // device: [n] shared-memory tails (b0, x0 set)
     ActiveLists *act = nullptr;        // device: instances active in each mode
+    unsigned *icnt = nullptr;          // device: per-instance arrivals of the split scalar kernel
+    double *wsum = nullptr;            // device: its virtual-warp sums
     int cta_cap = 2368;                // CTAs of a batched Poisson launch (16 per SM)
     int *counters = nullptr;           // device: loop-condition counts [3], then loop passes
                                        //   [3] main CG, [4] refinement CG, [5] refinement blocks
@@ -2226,8 +2228,10 @@ void batch_scalar(lbehd_batch *b, ScalarBatch &S, int mode, int nv, int op, bool
     S.cond_ref = cond_ref;
     S.counters = b->counters;
     S.act = b->act;
+    S.icnt = b->icnt;
+    S.wsum = b->wsum;
     S.eager = b->prof ? 1 : 0;
-    blaunch(b, k_pcg_scalar_batch, S, (int)ids.size(), SCALAR_THREADS, 0, LBEHD_KC_CG);
+    blaunch(b, k_pcg_scalar_batch_split, S, 32 * (int)ids.size(), 32, 0, LBEHD_KC_CG);
 }
 
 // r = b - A (phi + x) and the CG start of every instance active in `mode`.
@@ -2708,7 +2712,8 @@ void batch_release(lbehd_batch *b)
         delete h;
     }
     b->inst.clear();
-    for (void *p : {(void *)b->maps, (void *)b->tails, (void *)b->counters, (void *)b->act}) {
+    for (void *p : {(void *)b->maps, (void *)b->tails, (void *)b->counters, (void *)b->act,
+                    (void *)b->icnt, (void *)b->wsum}) {
         if (!p)
             continue;
         if (b->free)
@@ -2720,6 +2725,8 @@ void batch_release(lbehd_batch *b)
     b->tails = nullptr;
     b->counters = nullptr;
     b->act = nullptr;
+    b->icnt = nullptr;
+    b->wsum = nullptr;
     for (cudaStream_t *sx : {&b->aux, &b->aux2})
         if (*sx) {
             cudaStreamDestroy(*sx);
@@ -3136,7 +3143,9 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
     b->tails = (TailLevels *)balloc((size_t)n * sizeof(TailLevels));
     b->counters = (int *)balloc(8 * sizeof(int));
     b->act = (ActiveLists *)balloc(sizeof(ActiveLists));
-    if (!b->maps || !b->tails || !b->counters || !b->act)
+    b->icnt = (unsigned *)balloc(BATCH_MAX * sizeof(unsigned));
+    b->wsum = (double *)balloc(BATCH_MAX * 2 * 32 * sizeof(double));
+    if (!b->maps || !b->tails || !b->counters || !b->act || !b->icnt || !b->wsum)
         return bail(LBEHD_ERR_OOM, "device allocation of the batch tables failed");
     {
         // shared-memory tails of the instances, with their level's arrays filled in
@@ -3154,6 +3163,7 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
         if (cudaMemcpyAsync(b->tails, T.data(), n * sizeof(TailLevels), cudaMemcpyHostToDevice,
                             b->stream) != cudaSuccess ||
             cudaMemsetAsync(b->counters, 0, 8 * sizeof(int), b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->icnt, 0, BATCH_MAX * sizeof(unsigned), b->stream) != cudaSuccess ||
             cudaMemsetAsync(b->act, 0, sizeof(ActiveLists), b->stream) != cudaSuccess ||
             cudaStreamSynchronize(b->stream) != cudaSuccess)
             return bail(LBEHD_ERR_CUDA, "upload of the batch tables failed");

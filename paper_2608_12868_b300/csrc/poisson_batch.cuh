@@ -33,7 +33,7 @@ __device__ __forceinline__ bool batch_active(int mode, const CgScalars *s)
     return ref != 0 && !done;
 }
 
-// Instances active in modes 1-3 (index 0 unused), rewritten by k_pcg_scalar_batch.
+// Instances active in modes 1-3 (index 0 unused), rewritten by k_pcg_scalar_batch_split.
 struct ActiveLists {
     int count[4];
     int ids[4][BATCH_MAX];
@@ -366,30 +366,16 @@ struct ScalarBatch {
     int *counters;                            // [2] arrivals (zero between launches); [3..5]
                                               // pass counts (ops 3, 5, 4); [6..7] eager
     ActiveLists *act;                         // rewritten after ops 0, 3, 4, 5
+    unsigned *icnt;                           // [BATCH_MAX] arrivals per instance (split form)
+    double *wsum;                             // [BATCH_MAX][2][32] virtual-warp sums
 };
 
-// The CG scalar update of every active instance (one block each). The last block to finish
-// (arrival count) rewrites the active lists, sets the batch's loop conditions from them and
-// zeroes the count for the next launch.
-__global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar_batch(const __grid_constant__ ScalarBatch A)
+// The last block's work after every instance's update: rewrite the active lists, set the
+// batch's loop conditions (or, eager, hand them to the host) and zero the arrival count.
+// Run by one warp.
+__device__ __forceinline__ void batch_scalar_finish(const ScalarBatch &A, int lane)
 {
-    const int k = blockIdx.x;
-    CgScalars *s = A.g.s[k];
-    if (batch_active(A.g.mode, s))   // block-uniform: every thread reads before any update
-        pcg_scalar_block(A.partials[k], A.nblocks[k], A.nv, A.op, s);
-    if (A.loop_mode < 0 && !A.set_ref)
-        return;
-    __shared__ int last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&A.counters[2], 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last || threadIdx.x >= 32)
-        return;
-    __threadfence();
-    // the last block: every instance's flags are final
-    const int lane = threadIdx.x, n = A.g.n;
+    const int n = A.g.n;
     int cnt[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int h = 0; h < BATCH_MAX / 32; h++) {
@@ -427,6 +413,59 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar_batch(const __gri
         cudaGraphSetConditional(A.cond, any_act > 0 ? 1u : 0u);
     if (A.set_ref)
         cudaGraphSetConditional(A.cond_ref, any_ref > 0 ? 1u : 0u);
+}
+
+// The CG scalar update of every active instance, each instance's sums split over 32
+// one-warp CTAs (FP64 adds are slow on this part, so one 1024-thread CTA per instance is
+// latency-bound): CTA (k, w) forms virtual warp w's sums of pcg_scalar_block's order, the
+// last CTA of instance k adds them (the butterfly over 32) and updates its scalars (same bits
+// as pcg_scalar_block), and the last instance to finish does the lists and conditions
+// (batch_scalar_finish). icnt must be zero before the first launch; it is reset as it is used.
+__global__ void __launch_bounds__(32) k_pcg_scalar_batch_split(const __grid_constant__ ScalarBatch A)
+{
+    const int k = blockIdx.x >> 5, w = blockIdx.x & 31, lane = threadIdx.x;
+    const int ninst = (int)gridDim.x >> 5;
+    CgScalars *s = A.g.s[k];
+    const bool act = batch_active(A.g.mode, s);   // read before the instance's update
+    if (act)
+        for (int v = 0; v < A.nv; v++) {
+            const double a = pcg_vwarp_sum(A.partials[k] + v * A.nblocks[k], A.nblocks[k], 32 * w + lane);
+            if (lane == 0)
+                A.wsum[(k * 2 + v) * 32 + w] = a;
+        }
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(&A.icnt[k], 1u) == 31u;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0))
+        return;
+    __threadfence();
+    if (act) {
+        double tot[2] = {0.0, 0.0};
+        for (int v = 0; v < A.nv; v++) {
+            double a = __ldcg(A.wsum + (k * 2 + v) * 32 + lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+            tot[v] = a;
+        }
+        if (lane == 0)
+            pcg_scalar_update(tot, A.op, s);
+    }
+    if (lane == 0)
+        A.icnt[k] = 0u;
+    if (A.loop_mode < 0 && !A.set_ref)
+        return;
+    last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(&A.counters[2], 1) == ninst - 1;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0))
+        return;
+    __threadfence();
+    batch_scalar_finish(A, lane);
 }
 
 static_assert(sizeof(MgBatch) <= 32000 && sizeof(CgBatch) <= 32000 &&
