@@ -463,9 +463,15 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
     // at most TAIL_THREADS cells: thread t owns cell t, whose coordinates, neighbours,
     // coefficients and right-hand side stay in registers across the sweeps (b is fixed while
     // a level is smoothed). Same arithmetic as gs, in offdiag_sum's order.
+    // A level of at most 32 cells is swept by warp 0 alone, with warp barriers.
     auto owned = [&](int l, int nsw, auto color_of) {
         const MgDims d = T.d[l];
         const int n = ncell(l), o = T.off[l];
+        const bool warp_only = n <= 32;
+        if (warp_only && t >= 32) {
+            __syncthreads();
+            return;
+        }
         const bool own = t < n;
         int col = -1, n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0;
         float di = 0.f, bi = 0.f, kxi = 0.f, kxm = 0.f, kyi = 0.f, kym = 0.f, kzi = 0.f, kzm = 0.f;
@@ -503,8 +509,13 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
                 }
                 sx[o + t] = __fdiv_rn(__fadd_rn(bi, s), di);
             }
-            __syncthreads();
+            if (warp_only)
+                __syncwarp();
+            else
+                __syncthreads();
         }
+        if (warp_only)
+            __syncthreads();
     };
     // down: smooth, restrict
 #pragma unroll 1
