@@ -42,6 +42,11 @@ COLLIDE_BYTES = {3: 83 * 4 * 2 + 24 + 8 + 24 + 8 + 4 + 1, 2: 41 * 4 * 2 + 24 + 8
 # Whole-step model of the hot path per site update: populations read + written once
 # (664 B in 3D), macroscopic fields ~92 B, and ~16 B per Poisson sweep.
 STEP_BYTES = {3: (756, 16), 2: (388, 12)}
+# DRAM bytes per launch of the collide kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of 2 launches in one ncu capture; profiles/k_collide_droplet_3d_128x64x64.md), by
+# workload and autotuned variant. Only these are reported as roofline traffic.
+COLLIDE_TRAFFIC = {("droplet_3d_128x64x64", "staged32x4"): 342.35e6,
+                   ("droplet_3d_128x64x64", "staged64x2"): 344.34e6}
 # LBEHD_OPT_COLLIDE values
 COLLIDE_CHOICES = {"auto": 0, "global": 1, "staged": 2, "staged64x2": 3, "staged16x8": 4}
 VARIANT_NAMES = {1: "global", 2: "staged32x4", 3: "staged64x2", 4: "staged16x8"}
@@ -320,7 +325,9 @@ def run_ours(args, world, rank, local):
                 "eager_pass_ms_per_step": prof_ms / args.steps,
             },
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": COLLIDE_TRAFFIC.get(
+                             (w.name, tuned["variant"] if tuned else args.collide)),
                          "kernel": "k_collide (" + (tuned["variant"] if tuned else args.collide)
                                    + ")", "peak_source": peak_kind,
                          "timing": "CUDA events around each k_collide launch over a second "
