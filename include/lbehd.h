@@ -188,6 +188,12 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   shared-memory tail level, even nx on the levels above it); 0 the multi-launch graph
  *   with conditional nodes. Both give the same bits. */
 #define LBEHD_OPT_POISSON_KERNEL 4
+/*   LBEHD_OPT_BARRIER_TEST: test hook for the persistent solve's time-out path. value > 0:
+ *   its grid barriers wait for one CTA more than is launched and give up after `value`
+ *   polls, so every solve times out; each CTA leaves at its next barrier, the kernel ends and
+ *   the next lbehd_observe returns LBEHD_ERR_CUDA ("grid barrier timed out"). The error is
+ *   sticky for the handle. 0 (default): normal barriers. */
+#define LBEHD_OPT_BARRIER_TEST 5
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 /* The value in effect: for LBEHD_OPT_COLLIDE the kernel the automatic choice resolved to,
  * for LBEHD_OPT_POISSON_KERNEL 1 only if the persistent solve is on and this lattice allows

@@ -106,6 +106,8 @@ struct lbehd_handle {
     PsBarrier *ps_bar = nullptr;
     double *ps_part = nullptr;
     unsigned *h_ps_err = nullptr;  // pinned copy of ps_bar->error
+    unsigned ps_spin_limit = PS_SPIN_LIMIT;
+    int ps_extra = 0;              // LBEHD_OPT_BARRIER_TEST
     float mg_scale = 0.6f;
     int cur = 0;                   // population buffer holding the state at time n
     int pcur = 0;                  // phi / rho buffer holding the last step's fields
@@ -366,6 +368,8 @@ template <int D>
 int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float *rhs)
 {
     PsArgs A = h->ps;
+    A.spin_limit = h->ps_spin_limit;
+    A.extra = h->ps_extra;
     A.mode = mode;
     A.x = x;
     A.rho = rho;
@@ -1320,6 +1324,17 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
                 cudaGraphExecDestroy(e);
                 e = nullptr;
             }
+    } else if (option == LBEHD_OPT_BARRIER_TEST) {
+        if (value < 0 || value > (long long)PS_SPIN_LIMIT)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_BARRIER_TEST takes 0 to 2^24");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->ps_extra = value > 0 ? 1 : 0;
+        h->ps_spin_limit = value > 0 ? (unsigned)value : PS_SPIN_LIMIT;
+        for (auto &e : h->adj.solve)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
     } else if (option == LBEHD_OPT_ADJ_TRAJECTORY) {
         if (value < 0 || value > 1)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_ADJ_TRAJECTORY takes 0 or 1");
@@ -1380,12 +1395,12 @@ int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
     out->poisson_resid = h->h_cg->bb > 0.0 ? std::sqrt(h->h_cg->rr / h->h_cg->bb) : 0.0;
     out->status = flag ? LBEHD_ERR_NONFINITE
                        : (h->status ? h->status : (h->h_cg->nonconv ? LBEHD_ERR_POISSON_NOCONV : 0));
-    if (flag)
-        return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
-    if (h->h_ps_err && *h->h_ps_err) {
+    if (h->h_ps_err && *h->h_ps_err) {   // the root cause when both are set
         out->status = LBEHD_ERR_CUDA;
         return fail(h, LBEHD_ERR_CUDA, "persistent Poisson solve: a grid barrier timed out");
     }
+    if (flag)
+        return fail(h, LBEHD_ERR_NONFINITE, "non-finite value in the state");
     return LBEHD_OK;
 }
 

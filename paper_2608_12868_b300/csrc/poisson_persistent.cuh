@@ -79,6 +79,9 @@ struct PsArgs {
     double *wsum;              // [2][32] virtual-warp sums of a split scalar reduction
     CgScalars *s;
     PsBarrier *bar;
+    unsigned spin_limit;       // polls before a barrier wait gives up (PS_SPIN_LIMIT)
+    int extra;                 // arrivals expected beyond the CTAs (0; 1 only to test the
+                               // time-out: every barrier then runs out)
 };
 
 constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
@@ -109,14 +112,15 @@ __device__ __forceinline__ void ps_fence()
 }
 
 // Grid barrier number `epoch` (1, 2, ...). Returns false once any CTA has timed out.
-__device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok_sh)
+__device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok_sh,
+                                        unsigned spin_limit, int extra)
 {
     epoch++;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         ps_fence();
-        const unsigned target = epoch * gridDim.x;
+        const unsigned target = epoch * (gridDim.x + (unsigned)extra);
         const unsigned last = atomicAdd(&bar->count, 1u) + 1u;   // == target: everyone is in
         unsigned spins = 0;
         while (last < target && ps_load_volatile(&bar->count) < target) {
@@ -124,7 +128,7 @@ __device__ __forceinline__ bool ps_sync(PsBarrier *bar, unsigned &epoch, int *ok
                 ok = 0;
                 break;
             }
-            if (++spins > PS_SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 if (atomicExch(&bar->error, 1u) == 0u)
                     bar->where = epoch;
                 ok = 0;
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     bool ok = true;
     auto sync = [&]() {
         if (ok)
-            ok = ps_sync(A.bar, epoch, &ok_sh);
+            ok = ps_sync(A.bar, epoch, &ok_sh, A.spin_limit, A.extra);
     };
     // barrier, then the CG scalar update from the partial arrays, in the fixed order of
     // pcg_scalar_block: small reductions are summed by every CTA; large ones have their 32

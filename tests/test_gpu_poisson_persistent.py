@@ -91,3 +91,24 @@ def test_persistent_solve_in_the_adjoint(gpu):
         grads.append(s.adjoint_backward())
         s.close()
     assert np.array_equal(grads[0], grads[1]), np.abs(grads[0] - grads[1]).max()
+
+
+def test_barrier_time_out_is_reported(gpu):
+    """A grid barrier that waits for an arrival that never comes (LBEHD_OPT_BARRIER_TEST:
+    one CTA more than launched, 2000 polls) gives up: every CTA leaves at its next barrier,
+    the kernel ends, the next observe reports LBEHD_ERR_CUDA, and the CUDA context stays
+    usable (a new handle steps and matches a handle that never timed out)."""
+    w = W.small_3d()
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.step(3)
+    assert sim.observe()["status"] == 0
+    sim.set_option(gpu.OPT_BARRIER_TEST, 2000)
+    sim.step(1)
+    with pytest.raises(gpu.LBEHDError) as err:
+        sim.observe()
+    assert "grid barrier timed out" in str(err.value)
+    sim.close()
+    a, b = pair(gpu, w)
+    a.step(12)
+    b.step(12)
+    assert_same(a, b)
