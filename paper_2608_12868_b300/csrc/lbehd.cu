@@ -325,7 +325,8 @@ int ps_setup(lbehd_handle *h)
     h->ps_part = (double *)dev_alloc(h, 2 * pn * sizeof(double));
     h->ps_bar = (PsBarrier *)dev_alloc(h, sizeof(PsBarrier));
     h->ps.wsum = (double *)dev_alloc(h, 2 * 32 * sizeof(double));
-    if (!h->ps_part || !h->ps_bar || !h->ps.wsum)
+    h->ps.p2 = (float *)dev_alloc(h, h->N * sizeof(float));
+    if (!h->ps_part || !h->ps_bar || !h->ps.wsum || !h->ps.p2)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (persistent Poisson)");
     CK(h, cudaMemsetAsync(h->ps_bar, 0, sizeof(PsBarrier), h->stream));
     CK(h, cudaMallocHost(&h->h_ps_err, sizeof(unsigned)));

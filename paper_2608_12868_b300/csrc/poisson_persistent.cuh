@@ -74,7 +74,7 @@ struct PsArgs {
     float *x, *delta2;
     // adjoint: right-hand side (the solution is in x)
     const float *rhs;
-    float *r, *p, *q;          // r is L[0].b; z is L[0].x
+    float *r, *p, *p2, *q;     // r is L[0].b; z is L[0].x; p and p2 alternate
     double *part[2];           // partial arrays, alternating so a scalar read never races
     double *wsum;              // [2][32] virtual-warp sums of a split scalar reduction
     CgScalars *s;
@@ -89,9 +89,6 @@ constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
 // Reductions of at least PS_SPLIT_MIN partials have their 32 virtual-warp sums computed on
 // separate CTAs (FP64 adds are slow on this part; one CTA summing 8192 partials takes ~10 us).
 constexpr long long PS_SPLIT_MIN = 2048;
-// The defect and Ap phases can handle two of a group's virtual blocks per pass (measured a
-// little slower on 128x64x64: more spilled registers; kept off).
-constexpr bool PS_PAIRS = false;
 
 __device__ __forceinline__ void ps_named_sync(int id)
 {
@@ -225,70 +222,32 @@ __device__ __forceinline__ void ps_apply(int n, const float *Dg, const float *de
     }
 }
 
-// p = z + beta p.
-__device__ __forceinline__ void ps_p(int n, float beta, const float *zv, float *p)
+// Level 0's zero start and first red half sweep at one cell, from its own b (= r) and D:
+// (b + 0) / D on active red cells, 0 elsewhere (the neighbours are all 0).
+__device__ __forceinline__ float ps_first_red(int x, int y, int z, float bi, float di)
 {
-    const int S = gridDim.x * PS_THREADS;
-    for (int i0 = blockIdx.x * PS_THREADS + threadIdx.x; i0 < n; i0 += PS_B * S) {
-        float zz[PS_B], pp[PS_B];
-#pragma unroll
-        for (int j = 0; j < PS_B; j++) {
-            const int i = i0 + j * S;
-            zz[j] = pp[j] = 0.0f;
-            if (i < n) {
-                zz[j] = zv[i];
-                pp[j] = p[i];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < PS_B; j++) {
-            const int i = i0 + j * S;
-            if (i < n)
-                p[i] = beta != 0.0f ? __fmaf_rn(beta, pp[j], zz[j]) : zz[j];
-        }
-    }
+    return ((x + y + z) & 1) == 0 && di > 0.0f ? __fdiv_rn(__fadd_rn(bi, 0.0f), di) : 0.0f;
 }
 
-// r . z over the sites of virtual block b (of nb) for this thread, in site order.
-__device__ __forceinline__ void ps_dot_range(int n, const float *a, const float *b_, int b,
-                                             int nb, int t, float (&v)[1])
-{
-    const int S = nb * BX;
-    for (int i0 = b * BX + t; i0 < n; i0 += PS_B * S) {
-        float x[PS_B], y[PS_B];
-#pragma unroll
-        for (int j = 0; j < PS_B; j++) {
-            const int i = i0 + j * S;
-            x[j] = y[j] = 0.0f;
-            if (i < n) {
-                x[j] = a[i];
-                y[j] = b_[i];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < PS_B; j++)
-            if (i0 + j * S < n)
-                v[0] = __fmaf_rn(x[j], y[j], v[0]);
-    }
-}
-
-// delta += alpha p, r -= alpha q, ||r||^2 over the sites of virtual block b, in site order.
+// delta += alpha p, r -= alpha q, ||r||^2 over the sites of virtual block b, in site order;
+// then level 0's first red half sweep of the next V-cycle at the same sites (from the new r).
 __device__ __forceinline__ void ps_update_range(int n, const float *p, const float *q,
                                                 float *delta, float *r, float a, int b, int nb,
-                                                int t, float (&v)[1])
+                                                int t, float (&v)[1], const PsLevel &L0)
 {
     const int S = nb * BX;
     for (int i0 = b * BX + t; i0 < n; i0 += PS_B * S) {
-        float pp[PS_B], qq[PS_B], dd[PS_B], rr[PS_B];
+        float pp[PS_B], qq[PS_B], dd[PS_B], rr[PS_B], dg[PS_B];
 #pragma unroll
         for (int j = 0; j < PS_B; j++) {
             const int i = i0 + j * S;
-            pp[j] = qq[j] = dd[j] = rr[j] = 0.0f;
+            pp[j] = qq[j] = dd[j] = rr[j] = dg[j] = 0.0f;
             if (i < n) {
                 pp[j] = p[i];
                 qq[j] = q[i];
                 dd[j] = delta[i];
                 rr[j] = r[i];
+                dg[j] = L0.D[i];
             }
         }
 #pragma unroll
@@ -299,19 +258,65 @@ __device__ __forceinline__ void ps_update_range(int n, const float *p, const flo
                 const float ri = __fmaf_rn(-a, qq[j], rr[j]);
                 r[i] = ri;
                 v[0] = __fmaf_rn(ri, ri, v[0]);
+                int x, y, z;
+                cell_xyz(L0.d, i, x, y, z);
+                L0.x[i] = ps_first_red(x, y, z, ri, dg[j]);
             }
         }
     }
 }
 
-// Loop over virtual blocks two at a time (group-uniform): f(vb, vb2, t) with vb2 the group's
-// next block (vb2 >= nvb: none), so that two sites' loads are in flight together.
-template <class F>
-__device__ __forceinline__ void ps_for_vblock_pairs(int nvb, F &&f)
+// Level 0's last red half sweep at the sites of 1D virtual block b (red cells updated from
+// their black neighbours, which this phase does not write), and r . z over the same sites in
+// site order (z = the level's x after the sweep).
+__device__ __forceinline__ void ps_gs0_dot_range(const PsLevel &L0, const float *r, int b,
+                                                 int nb, int t, float (&v)[1])
 {
-    const int g = threadIdx.x / BX, t = threadIdx.x % BX, st = gridDim.x * PS_GROUPS;
-    for (int vb = blockIdx.x * PS_GROUPS + g; vb < nvb; vb += 2 * st)
-        f(vb, vb + st, t);
+    const MgDims &d = L0.d;
+    const int S = nb * BX, n = L0.n;
+    for (int i = b * BX + t; i < n; i += S) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        if (((x + y + z) & 1) == 0)
+            mg_gs_cell(d, L0.D, L0.kx, L0.ky, L0.kz, L0.b, L0.x, x, y, z);
+        v[0] = __fmaf_rn(r[i], L0.x[i], v[0]);
+    }
+}
+
+// q_i = (A p)_i with p = z + beta p_old formed at the site and its neighbours as pcg_p_site
+// forms it (p_i returned for storing); the arithmetic of pcg_Ap_value.
+template <int D>
+__device__ __forceinline__ float ps_Ap_value(const MgDims &d, const float *eps,
+                                             const uint8_t *info, const float *Dg,
+                                             const float *p_old, const float *zv, float beta,
+                                             int x, int y, int z, float &pi_out, float (&v)[1])
+{
+    const int i = cell(d, x, y, z);
+    const Nb6 nb = nb6(d, i, x, y, z);
+    const float Di = Dg[i], ei = eps[i];
+    const float pi = beta != 0.0f ? __fmaf_rn(beta, p_old[i], zv[i]) : zv[i];
+    int pt[2 * D];
+    float ej[2 * D], pj[2 * D];
+#pragma unroll
+    for (int f = 0; f < 2 * D; f++) {
+        const int j = nb.n[f];
+        pt[f] = info[j] & 3;
+        ej[f] = eps[j];
+        pj[f] = beta != 0.0f ? __fmaf_rn(beta, p_old[j], zv[j]) : zv[j];
+    }
+    float qi = 0.0f;
+    if (Di > 0.0f) {
+#pragma unroll
+        for (int f = 0; f < 2 * D; f++) {
+            if (pt[f] == PT_FLUID)
+                qi = __fmaf_rn(__fmul_rn(0.5f, __fadd_rn(ei, ej[f])), __fsub_rn(pi, pj[f]), qi);
+            else if (pt[f] == PT_DIRICHLET)
+                qi = __fmaf_rn(ei, pi, qi);
+        }
+        v[0] = __fmul_rn(pi, qi);
+    }
+    pi_out = pi;
+    return qi;
 }
 
 // One red-black half sweep (colour c) of level L, cells in flat order (nx even).
@@ -503,12 +508,20 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     const PsLevel &L0 = A.L[0];
     float *z = L0.x;
 
-    // one symmetric V-cycle: z ~= A^-1 r
+    // the p buffers alternate: Ap reads the previous direction and writes the new one
+    float *p_old = A.p, *p_new = A.p2;
+
+    // one symmetric V-cycle, z ~= A^-1 r. After an iteration's update, level 0's zero start
+    // and first red half sweep were done by that update (z_ready); the last red half sweep of
+    // level 0 also forms the r . z partials (then the caller's op-1 reduction ends the phase).
+    bool z_ready = false;
     auto vcycle = [&]() {
         for (int l = 0; l < A.nl && ok; l++) {
             const PsLevel &L = A.L[l];
-            ps_gs_first(L);
-            sync();
+            if (l > 0 || !z_ready) {
+                ps_gs_first(L);
+                sync();
+            }
             ps_gs(L, 1);
             sync();
             for (int k = 1; k < A.nu && ok; k++) {
@@ -533,8 +546,16 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
                 else
                     ps_gs(L, 1);
                 sync();
-                ps_gs(L, 0);
-                sync();
+                if (l == 0 && k == A.nu - 1) {
+                    ps_for_vblocks(A.nb1, [&](int vb, int t) {
+                        float v[1] = {0.0f};
+                        ps_gs0_dot_range(L0, A.r, vb, A.nb1, t, v);
+                        ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
+                    });
+                } else {
+                    ps_gs(L, 0);
+                    sync();
+                }
             }
         }
     };
@@ -542,96 +563,59 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     // one preconditioned CG iteration on the increment (or adjoint potential) xv
     auto iteration = [&](float *xv) {
         vcycle();
+        sync_scalar(A.part[0], 1, 1, A.nb1);   // r . z
         if (!ok)
             return;
-        ps_for_vblocks(A.nb1, [&](int vb, int t) {
+        const float beta = pcg_beta(&s);
+        ps_for_vblocks(A.nbs, [&](int vb, int t) {
+            // p = z + beta p and q = A p, p formed on the fly at the site and its neighbours
+            const int i = vb * BX + t;
             float v[1] = {0.0f};
-            ps_dot_range(A.N, A.r, z, vb, A.nb1, t, v);
-            ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
-        });
-        sync_scalar(A.part[0], 1, 1, A.nb1);
-        if (!ok)
-            return;
-        ps_p(A.N, pcg_beta(&s), z, A.p);
-        sync();
-        auto Ap_pass = [&](int vb, int vb2, int t) {
-            // q = A p at one site of each of two virtual blocks, stored after both
-            float v[1] = {0.0f}, w[1] = {0.0f}, q1 = 0.0f, q2 = 0.0f;
-            const int i = vb * BX + t, i2 = vb2 * BX + t;
             if (i < A.N) {
                 int x, y, zz;
                 cell_xyz(L0.d, i, x, y, zz);
-                q1 = pcg_Ap_value<D>(L0.d, A.eps, A.info, L0.D, A.p, x, y, zz, v);
+                float pi;
+                A.q[i] = ps_Ap_value<D>(L0.d, A.eps, A.info, L0.D, p_old, z, beta, x, y, zz, pi,
+                                        v);
+                p_new[i] = pi;
             }
-            if (vb2 < A.nbs && i2 < A.N) {
-                int x, y, zz;
-                cell_xyz(L0.d, i2, x, y, zz);
-                q2 = pcg_Ap_value<D>(L0.d, A.eps, A.info, L0.D, A.p, x, y, zz, w);
-            }
-            if (i < A.N)
-                A.q[i] = q1;
-            if (vb2 < A.nbs && i2 < A.N)
-                A.q[i2] = q2;
             ps_group_partials<1>(v, A.part[1], vb, A.nbs, gsm);
-            if (vb2 < A.nbs)
-                ps_group_partials<1>(w, A.part[1], vb2, A.nbs, gsm);
-        };
-        if (PS_PAIRS)
-            ps_for_vblock_pairs(A.nbs, Ap_pass);
-        else
-            ps_for_vblocks(A.nbs, [&](int vb, int t) { Ap_pass(vb, A.nbs, t); });
-        sync_scalar(A.part[1], 1, 2, A.nbs);
+        });
+        sync_scalar(A.part[1], 1, 2, A.nbs);   // p . Ap
         if (!ok)
             return;
         const float alpha = (float)s.alpha;
         ps_for_vblocks(A.nb1, [&](int vb, int t) {
             float v[1] = {0.0f};
-            ps_update_range(A.N, A.p, A.q, xv, A.r, alpha, vb, A.nb1, t, v);
+            ps_update_range(A.N, p_new, A.q, xv, A.r, alpha, vb, A.nb1, t, v, L0);
             ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
         });
-        sync_scalar(A.part[0], 1, 3, A.nb1);
+        float *tp = p_old;
+        p_old = p_new;
+        p_new = tp;
+        z_ready = true;
+        sync_scalar(A.part[0], 1, 3, A.nb1);   // ||r||^2
     };
 
-    // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4
+    // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4 (most
+    // solves stop here, so this phase does nothing for the V-cycle)
     auto start = [&](float *xv, int op) {
-        if (A.mode == PS_ADJOINT) {
-            ps_for_vblocks(A.nbs, [&](int vb, int t) {
-                const int i = vb * BX + t;
-                float v[2] = {0.0f, 0.0f};
-                if (i < A.N)
+        ps_for_vblocks(A.nbs, [&](int vb, int t) {
+            const int i = vb * BX + t;
+            float v[2] = {0.0f, 0.0f};
+            if (i < A.N) {
+                if (A.mode == PS_ADJOINT) {
                     adj_pcg_init_site<D>(L0.d, A.eps, A.info, L0.D, xv, A.rhs, A.r, i, v);
-                ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
-            });
-        } else {
-            auto init_pass = [&](int vb, int vb2, int t) {
-                // the defect at one site of each of two virtual blocks, stored after both
-                float v[2] = {0.0f, 0.0f}, w[2] = {0.0f, 0.0f}, r1 = 0.0f, r2 = 0.0f;
-                const int i = vb * BX + t, i2 = vb2 * BX + t;
-                if (i < A.N) {
+                } else {
                     int x, y, zz;
                     cell_xyz(L0.d, i, x, y, zz);
-                    r1 = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D,
-                                           x, y, zz, v);
+                    A.r[i] = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info,
+                                               L0.D, x, y, zz, v);
                 }
-                if (vb2 < A.nbs && i2 < A.N) {
-                    int x, y, zz;
-                    cell_xyz(L0.d, i2, x, y, zz);
-                    r2 = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info, L0.D,
-                                           x, y, zz, w);
-                }
-                if (i < A.N)
-                    A.r[i] = r1;
-                if (vb2 < A.nbs && i2 < A.N)
-                    A.r[i2] = r2;
-                ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
-                if (vb2 < A.nbs)
-                    ps_group_partials<2>(w, A.part[1], vb2, A.nbs, gsm);
-            };
-            if (PS_PAIRS)
-                ps_for_vblock_pairs(A.nbs, init_pass);
-            else
-                ps_for_vblocks(A.nbs, [&](int vb, int t) { init_pass(vb, A.nbs, t); });
-        }
+            }
+            ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
+        });
+        z_ready = false;
         sync_scalar(A.part[1], 2, op, A.nbs);
     };
 
