@@ -458,6 +458,8 @@ def run_adjoint(args, dev):
     bwd_ms, g = timed(sa, A.adjoint_backward)
     t_region1 = time.time()
     info = A.adjoint_info()
+    # the backward pass leaves A in the state after its forward run: B's, bit for bit
+    same = all(np.array_equal(A.array(k), B.array(k)) for k in ("g", "fphi", "frho", "pot"))
     A.close()
     B.close()
     return {
@@ -472,6 +474,7 @@ def run_adjoint(args, dev):
         "backward_vs_plain": bwd_ms / plain_ms,
         "plain_poisson_iters_per_step": plain_iters,
         "adjoint_cg_iters_per_step": info["adjoint_cg_iters"] / max(info["steps_reversed"], 1),
+        "same_state_as_plain": same,
         "device_gb": info["device_bytes"] / 1e9,
         "loss": L, "grad_max_abs": float(np.abs(g).max()),
         "timing": "CUDA events on each simulation's stream; same steps for plain and adjoint",

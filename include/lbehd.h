@@ -305,6 +305,21 @@ typedef struct lbehd_adjoint_info {
 } lbehd_adjoint_info;
 int lbehd_adjoint_get_info(lbehd_handle *h, lbehd_adjoint_info *out);
 
+/* ---------------------------------------------------------------- checkpoint / restore
+ * A handle's whole state in one caller-owned device buffer of lbehd_state_bytes(h) bytes
+ * (16-byte aligned): a 1 KiB header (lattice extents, step counter and parities, electrode
+ * potentials, the last two steps' observable sums), then per site the populations,
+ * Phi^{n-1}, rho^{n-1}, u^{n-1}, Q^{n-1}, the potential pair, both warm-start increments
+ * and the permittivity the multigrid preconditioner was last built from (4 Q + Q_s + 13
+ * floats per site). lbehd_load_state into a handle of the same lattice and configuration
+ * continues the saved run bit for bit (the preconditioner is rebuilt from the saved
+ * permittivity). Both synchronise the handle's stream. Errors: LBEHD_ERR_INVALID_ARG (null
+ * or unaligned buffer, batch instance, a buffer that is not a state of this lattice),
+ * LBEHD_ERR_CUDA. The paper's runs are long; this is the restart point of one. */
+size_t lbehd_state_bytes(lbehd_handle *h);
+int lbehd_save_state(lbehd_handle *h, void *dst_device);
+int lbehd_load_state(lbehd_handle *h, const void *src_device);
+
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
 const char *lbehd_last_error(lbehd_handle *h);
 

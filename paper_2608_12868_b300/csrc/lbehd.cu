@@ -72,6 +72,7 @@ struct lbehd_handle {
     // increment of step s-2 (the charge collision with tau_rho ~ 1/2 makes consecutive
     // increments alternate). delta2: correction of a refinement pass.
     float *inc[2] = {}, *delta2 = nullptr;
+    float *eps_mg = nullptr;       // eps the multigrid hierarchy was last built from
     float *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
     double *cg_partials = nullptr;
     CgScalars *cg_s = nullptr;
@@ -535,6 +536,8 @@ void mg_setup(lbehd_handle *h)
                                                              C.kz);
         }
     });
+    // the eps of this build (saved with a state, so that a restore rebuilds this hierarchy)
+    cudaMemcpyAsync(h->eps_mg, h->eps, h->N * sizeof(float), cudaMemcpyDeviceToDevice, h->ls);
     h->mg_valid = true;
 }
 
@@ -1029,6 +1032,9 @@ int init_impl(lbehd_handle *h)
     h->nblocks_site = (N + BX - 1) / BX;
     h->inc[0] = (float *)dev_alloc(h, N * fb);
     h->inc[1] = (float *)dev_alloc(h, N * fb);
+    h->eps_mg = (float *)dev_alloc(h, N * fb);
+    if (!h->eps_mg)
+        return fail(h, LBEHD_ERR_OOM, "device allocation failed (multigrid eps)");
     h->delta2 = (float *)dev_alloc(h, N * fb);
     h->cg_r = (float *)dev_alloc(h, N * fb);
     h->cg_p = (float *)dev_alloc(h, N * fb);
@@ -1408,11 +1414,11 @@ int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
 // ------------------------------------------------------------ discrete adjoint
 
 // Floats per site of a saved state: populations, Phi^{n-1}, rho^{n-1}, u^{n-1}, Q^{n-1},
-// then the potential (hi, lo) and both warm-start increments.
-size_t adj_state_floats(const lbehd_handle *h) { return (size_t)(4 * h->Q + h->QS + 12); }
+// then the potential (hi, lo), both warm-start increments and the multigrid's eps.
+size_t adj_state_floats(const lbehd_handle *h) { return (size_t)(4 * h->Q + h->QS + 13); }
 
 struct StateView {
-    float *g, *fphi, *frho, *phi_prev, *rho_prev, *u, *q, *pot, *pot_lo, *inc0, *inc1;
+    float *g, *fphi, *frho, *phi_prev, *rho_prev, *u, *q, *pot, *pot_lo, *inc0, *inc1, *eps_mg;
 };
 
 StateView state_view(const lbehd_handle *h, float *base)
@@ -1430,6 +1436,7 @@ StateView state_view(const lbehd_handle *h, float *base)
     v.pot_lo = v.pot + N;
     v.inc0 = v.pot_lo + N;
     v.inc1 = v.inc0 + N;
+    v.eps_mg = v.inc1 + N;
     return v;
 }
 
@@ -1473,6 +1480,7 @@ int adj_save(lbehd_handle *h, float *dst, bool with_potential = true)
     CK(h, cp(v.pot_lo, h->pot_lo, N));
     CK(h, cp(v.inc0, h->inc[0], N));
     CK(h, cp(v.inc1, h->inc[1], N));
+    CK(h, cp(v.eps_mg, h->eps_mg, N));
     return LBEHD_OK;
 }
 
@@ -1481,13 +1489,16 @@ lbehd_handle::HostState host_state(const lbehd_handle *h)
     return lbehd_handle::HostState{h->step, h->cur, h->pcur, h->first, h->mg_valid};
 }
 
+// Restore a saved state (with its potential). The multigrid hierarchy is rebuilt from the
+// saved eps of its last build, so the next steps repeat the saved run's iterates exactly.
+template <int D>
 int adj_restore(lbehd_handle *h, const float *src, const lbehd_handle::HostState &hs)
 {
     h->step = hs.step;
     h->cur = hs.cur;
     h->pcur = hs.pcur;
     h->first = hs.first;
-    h->mg_valid = false;   // rebuilt from this state's permittivity at the next step
+    h->mg_valid = false;
     const size_t N = h->N, fb = sizeof(float);
     const StateView v = state_view(h, const_cast<float *>(src));
     auto cp = [&](float *d, const float *s, size_t n) {
@@ -1504,6 +1515,12 @@ int adj_restore(lbehd_handle *h, const float *src, const lbehd_handle::HostState
     CK(h, cp(h->pot_lo, v.pot_lo, N));
     CK(h, cp(h->inc[0], v.inc0, N));
     CK(h, cp(h->inc[1], v.inc1, N));
+    if (hs.mg_valid) {   // eps is formed again by the next step's moments kernel
+        CK(h, cp(h->eps, v.eps_mg, N));
+        h->ls = h->stream;
+        mg_setup<D>(h);
+        CK(h, cudaGetLastError());
+    }
     return LBEHD_OK;
 }
 
@@ -1825,7 +1842,7 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     const int nck = (a.T + a.K - 1) / a.K;
     for (int ck = nck - 1; ck >= 0; ck--) {
         const int t0 = ck * a.K, t1 = std::min(a.T, t0 + a.K);
-        if ((rc = adj_restore(h, a.ckpt[ck], a.ckpt_host[ck])))
+        if ((rc = adj_restore<D>(h, a.ckpt[ck], a.ckpt_host[ck])))
             return rc;
         // replay the interval, keeping every step's input state (and, without a recorded
         // trajectory, its potential)
@@ -1870,11 +1887,74 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     std::copy(g.begin(), g.begin() + (size_t)a.S * a.E, grad);
     (void)SS;
     // leave the handle as the forward run left it
-    if ((rc = adj_restore(h, a.fin, a.fin_host)))
+    if ((rc = adj_restore<D>(h, a.fin, a.fin_host)))
         return rc;
     if ((rc = adj_set_V(h, a.T - 1)))
         return rc;
-    h->mg_valid = false;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEHD_OK;
+}
+
+// A saved state for lbehd_save_state / lbehd_load_state: this header (padded to
+// STATE_HEADER bytes), then the arrays of adj_save.
+constexpr size_t STATE_HEADER = 1024;
+constexpr uint32_t STATE_MAGIC = 0x4C424548u;   // "LBEH"
+struct StateHeader {
+    uint32_t magic, version, dim, nx, ny, nz, Q, QS, n_electrodes;
+    int32_t cur, pcur, first, mg_valid, pad;
+    int64_t step;
+};
+static_assert(sizeof(StateHeader) + (LBEHD_MAX_ELECTRODES + 2 * NOBS) * sizeof(double) <=
+                  STATE_HEADER, "state header too large");
+
+size_t state_bytes(const lbehd_handle *h)
+{
+    return STATE_HEADER + adj_state_floats(h) * h->N * sizeof(float);
+}
+
+int save_state(lbehd_handle *h, void *dst)
+{
+    char *d = (char *)dst;
+    StateHeader H{STATE_MAGIC, 1u, (uint32_t)h->dim, (uint32_t)h->nx, (uint32_t)h->ny,
+                  (uint32_t)h->nz, (uint32_t)h->Q, (uint32_t)h->QS,
+                  (uint32_t)h->cfg.n_electrodes, h->cur, h->pcur, h->first ? 1 : 0,
+                  h->mg_valid ? 1 : 0, 0, h->step};
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(d, &H, sizeof(H), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpyAsync(d + sizeof(H), h->V, LBEHD_MAX_ELECTRODES * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(d + sizeof(H) + LBEHD_MAX_ELECTRODES * sizeof(double), h->obs,
+                          2 * NOBS * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    int rc = adj_save(h, (float *)(d + STATE_HEADER), true);
+    if (rc)
+        return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEHD_OK;
+}
+
+template <int D>
+int load_state(lbehd_handle *h, const void *src)
+{
+    const char *s = (const char *)src;
+    StateHeader H;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&H, s, sizeof(H), cudaMemcpyDeviceToHost));
+    if (H.magic != STATE_MAGIC || H.version != 1u)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "not a saved lbehd state");
+    if (H.dim != (uint32_t)h->dim || H.nx != (uint32_t)h->nx || H.ny != (uint32_t)h->ny ||
+        H.nz != (uint32_t)h->nz || H.Q != (uint32_t)h->Q || H.QS != (uint32_t)h->QS ||
+        H.n_electrodes != (uint32_t)h->cfg.n_electrodes)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "saved state is of another lattice");
+    if ((H.cur & ~1) || (H.pcur & ~1) || H.step < 0)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "saved state header is corrupt");
+    CK(h, cudaMemcpyAsync(h->V, s + sizeof(H), LBEHD_MAX_ELECTRODES * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->obs, s + sizeof(H) + LBEHD_MAX_ELECTRODES * sizeof(double),
+                          2 * NOBS * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    const lbehd_handle::HostState hs{H.step, H.cur, H.pcur, H.first != 0, H.mg_valid != 0};
+    int rc = adj_restore<D>(h, (const float *)(s + STATE_HEADER), hs);
+    if (rc)
+        return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     return LBEHD_OK;
 }
@@ -2967,6 +3047,33 @@ int lbehd_set_option(lbehd_handle *h, int option, long long value)
     if (h->batch_owned)
         return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: use lbehd_batch_set_option");
     return set_option_impl(h, option, value);
+}
+
+size_t lbehd_state_bytes(lbehd_handle *h)
+{
+    return h ? state_bytes(h) : 0;
+}
+
+int lbehd_save_state(lbehd_handle *h, void *dst)
+{
+    if (!h || !dst)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or destination");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: states are saved per handle");
+    if ((uintptr_t)dst % 16)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "state buffer must be 16-byte aligned");
+    return save_state(h, dst);
+}
+
+int lbehd_load_state(lbehd_handle *h, const void *src)
+{
+    if (!h || !src)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "null handle or source");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: states are loaded per handle");
+    if ((uintptr_t)src % 16)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "state buffer must be 16-byte aligned");
+    return h->dim == 2 ? load_state<2>(h, src) : load_state<3>(h, src);
 }
 
 int lbehd_get_option(lbehd_handle *h, int option, long long *value)

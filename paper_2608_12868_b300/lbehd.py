@@ -93,7 +93,8 @@ EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
            "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
            "lbehd_launch_count", "lbehd_set_option", "lbehd_get_option", "lbehd_get_stats", "lbehd_profile_enable",
            "lbehd_profile_read", "lbehd_autotune", "lbehd_adjoint_forward",
-           "lbehd_adjoint_backward", "lbehd_adjoint_get_info", "lbehd_last_error",
+           "lbehd_adjoint_backward", "lbehd_adjoint_get_info", "lbehd_state_bytes",
+           "lbehd_save_state", "lbehd_load_state", "lbehd_last_error",
            "lbehd_destroy",
            "lbehd_batch_init", "lbehd_batch_step", "lbehd_batch_size", "lbehd_batch_instance",
            "lbehd_batch_observe", "lbehd_batch_set_option", "lbehd_batch_autotune",
@@ -138,6 +139,10 @@ def load():
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_adjoint_backward.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_adjoint_get_info.argtypes = [P, ctypes.POINTER(AdjointInfo)]
+    lib.lbehd_state_bytes.argtypes = [P]
+    lib.lbehd_state_bytes.restype = ctypes.c_size_t
+    lib.lbehd_save_state.argtypes = [P, P]
+    lib.lbehd_load_state.argtypes = [P, P]
     lib.lbehd_batch_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(P)]
     lib.lbehd_batch_step.argtypes = [P, ctypes.c_int]
     lib.lbehd_batch_size.argtypes = [P]
@@ -375,6 +380,24 @@ class Simulation(_HandleOps):
         g = np.zeros(self._adj_shape, dtype=np.float64)
         self._check(self._lib.lbehd_adjoint_backward(self._h, _dptr(g, ctypes.c_double)))
         return g
+
+    def save_state(self, out=None):
+        """The handle's whole state (lbehd_save_state) in a uint8 CUDA tensor (allocated here
+        unless `out` is given)."""
+        import torch
+        n = int(self._lib.lbehd_state_bytes(self._h))
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=self.device)
+        if out.numel() * out.element_size() < n or not out.is_cuda:
+            raise ValueError(f"need a CUDA tensor of at least {n} bytes")
+        self._check(self._lib.lbehd_save_state(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def load_state(self, state):
+        """Continue from a state saved by save_state on a handle of the same lattice."""
+        if not state.is_cuda:
+            raise ValueError("the state must be a CUDA tensor")
+        self._check(self._lib.lbehd_load_state(self._h, ctypes.c_void_p(state.data_ptr())))
 
     def adjoint_info(self):
         """The recorded adjoint run: steps, checkpoint spacing and count, whether the
