@@ -98,3 +98,25 @@ def test_poisson_adjoint_solve_matches_finite_differences(oracle_mod, ref):
             args_m = (tm, rho.detach(), V.detach()) if which == "eps" else (eps.detach(), tm, V.detach())
             fd = (f(*args_p) - f(*args_m)) / (2 * h)
             assert abs(fd - float(g[i])) <= 1e-5 * abs(fd) + 1e-12, (which, i, fd, float(g[i]))
+
+
+def test_reference_taylor_remainder_is_second_order(oracle_mod, ref):
+    """Along a random direction d, the Taylor remainder |L(V + h d) - L(V) - h g.d| of the
+    schedule loss falls as h^2 (about 4x per halving of h): the reference gradient g is the
+    derivative of L, not just close to a difference quotient."""
+    w = tiny_3d()
+    _, m = model_for(oracle_mod, ref, w)
+    Vs = torch.tensor([[0.03, 0.05], [0.06, 0.01]], dtype=T, requires_grad=True)
+    L = ref.schedule_loss(m, w.phi_init, Vs, 6)
+    L.backward()
+    d = torch.tensor(np.random.default_rng(5).normal(size=(2, 2)), dtype=T)
+    gd = float((Vs.grad * d).sum())
+    L0 = float(L.detach())
+    # small enough that a gradient error of 1 % would pull the ratios towards 2 (first order),
+    # large enough that the remainders stay far above FP64 rounding of L (~1e-14)
+    hs = [1e-3, 5e-4, 2.5e-4]
+    rem = [abs(float(ref.schedule_loss(m, w.phi_init, Vs.detach() + h * d, 6)) - L0 - h * gd)
+           for h in hs]
+    for a, b in zip(rem, rem[1:]):
+        assert 3.6 < a / b < 4.4, rem
+    assert rem[-1] < 0.1 * abs(hs[-1] * gd), (rem, gd)
