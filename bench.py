@@ -333,6 +333,12 @@ def run_ours(args, world, rank, local):
                          "timing": "CUDA events around each k_collide launch over a second "
                                    "timed region of the same length",
                          "bytes_per_launch": coll_bytes},
+            "step_roofline": {
+                "bytes_per_update": sb + sp * iters_per_step,
+                "model": f"{sb} B per site update (populations read + written, fields) + "
+                         f"{sp} B per CG iteration x {iters_per_step:.3f} iterations per step",
+                "achieved_gbs": step_gbs, "frac_of_measured": step_gbs / peak,
+                "frac_of_nominal_8tbs": step_gbs / 8000.0},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * len(Vh),
                     "d2h_bytes_per_step": 2 * 16 * 8 + 4},
