@@ -134,6 +134,21 @@ def test_droplet_2d_128x64(gpu, oracle_mod):
         compare_obs(sim, orc)
 
 
+def test_droplet_2d_128x64_full_run(gpu, oracle_mod):
+    """The 2D 128x64 workload over its full 2000 steps in the benchmark's launch
+    configuration (step graphs, persistent Gauss-law solve): droplet velocity and electric
+    forces within 0.5 % of the FP64 oracle every 250 steps, centroid within 1e-3 lu, component
+    masses within 1e-5."""
+    w = W.droplet_2d_128x64()
+    sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
+    assert sim.get_option(gpu.OPT_POISSON_KERNEL) == 1
+    for _ in range(8):
+        sim.step(250)
+        orc.step(250)
+        compare_obs(sim, orc)
+    assert sim.observe()["step"] == 1999
+
+
 def test_droplet_3d_128x64x64_full_size(gpu, oracle_mod):
     """The 3D 128x64x64 workload at full size, in the launch configuration the benchmark
     times (graph replay with the device-side Poisson loop): every population after 3 steps."""
@@ -222,14 +237,23 @@ def test_mass_conservation_long_run(gpu):
 
 
 def test_largest_workload_runs(gpu):
-    """384x128x96 long-transport lattice: allocates, steps, stays finite and conserving."""
+    """384x128x96 long-transport lattice (4.7 M sites) in the benchmark's launch
+    configuration: allocates, steps, stays finite and conserving; its persistent Gauss-law
+    solve (four multigrid levels above the tail) gives the multi-launch solve's bits."""
     w = W.transport_3d_384x128x96()
-    sim = gpu.Simulation(w)
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    assert sim.get_option(gpu.OPT_POISSON_KERNEL) == 1
     sim.step(2)
     m0 = sim.observe()["mass"]
     sim.step(20)
     o = sim.observe()
+    assert o["status"] == 0
     assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6
+    ref = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    ref.set_option(gpu.OPT_POISSON_KERNEL, 0)
+    ref.step(22)
+    for name in ("g", "pot", "pot_lo"):
+        assert np.array_equal(sim.array(name), ref.array(name)), name
 
 
 def test_error_paths(gpu):
