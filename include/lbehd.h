@@ -286,7 +286,7 @@ int lbehd_autotune(lbehd_handle *h, int reps, double *ms);
  * same symmetric operator (preconditioned CG), the reverse of the moments and wetting ghosts,
  * and the per-electrode sums. The first step of a fresh handle has no backward differences
  * and contributes none. Afterwards the handle is again in the state after the last step.
- * Memory: (ceil(steps / K) + K + 1) saved states of (4 Q + Q_s + 12) floats per site, plus
+ * Memory: (ceil(steps / K) + K + 1) saved states of (4 Q + Q_s + 13) floats per site, plus
  * 2 floats per site per step for the recorded potential.
  * Synchronise. Errors: LBEHD_ERR_INVALID_ARG (no recorded run, bad sizes, batch instance),
  * LBEHD_ERR_OOM, LBEHD_ERR_CUDA; LBEHD_ERR_POISSON_NOCONV from the forward is reported but
