@@ -54,7 +54,12 @@ struct lbehd_handle {
     double *V = nullptr;           // electrode potentials (device, FP64)
     uint8_t *info = nullptr, *normal = nullptr;
     int16_t *elec = nullptr;
+    // obs_partials: [2][NOBS][obs_stride] block partials, one set per step parity; obs:
+    // [2 NOBS] the last two steps' sums, then [2 NOBS] a copy kept across an adjoint backward
     double *obs_partials = nullptr, *obs = nullptr;
+    size_t obs_stride = 0;
+    long long obs_nblk[2] = {0, 0};   // blocks of the partial set of each parity
+    int obs_pending = 0;              // steps (at most 2 counted) whose sums are not in obs
     double *obs_wsum = nullptr;    // [NOBS][OBS_THREADS / 32] warp sums of k_obs_final_split
     unsigned *obs_cnt = nullptr;   // [NOBS] arrival counters of k_obs_final_split
     int *flag = nullptr;
@@ -598,6 +603,12 @@ int poisson(lbehd_handle *h)
     return LBEHD_OK;
 }
 
+// Block partials of the observables written by the collide kernel of a step of parity `cur`.
+double *obs_buf(const lbehd_handle *h, int cur)
+{
+    return h->obs_partials + (size_t)cur * NOBS * h->obs_stride;
+}
+
 State collide_state(const lbehd_handle *h, int cur, int pcur)
 {
     State S;
@@ -616,7 +627,7 @@ State collide_state(const lbehd_handle *h, int cur, int pcur)
     S.pot = h->pot;
     S.pot_lo = h->pot_lo;
     S.info = h->info;
-    S.obs_partials = h->obs_partials;
+    S.obs_partials = obs_buf(h, cur);
     S.flag = h->flag;
     return S;
 }
@@ -634,15 +645,23 @@ int resolved_variant(const lbehd_handle *h)
 // tile shape index of a staged variant: 2 -> TY 4, 3 -> TY 2, 4 -> TY 8
 int tile_shape(int v) { return v == 3 ? 1 : (v == 4 ? 2 : 0); }
 
+// Blocks of the collide launch in effect (one observable partial per block).
+long long collide_launch_blocks(const lbehd_handle *h)
+{
+    const int v = resolved_variant(h);
+    return v == 1 ? (long long)h->nblocks : (long long)h->nblocks_tile[tile_shape(v)];
+}
+
+// The fused collide + stream kernel of one step. Its block partials of the observables stay
+// in the partial set of the step's parity; obs_finalize sums them when they are read.
 template <int D>
-void collide(lbehd_handle *h, bool with_obs = true)
+void collide(lbehd_handle *h)
 {
     const State S = collide_state(h, h->cur, h->pcur);
     // variants: 1 global loads, 2/3/4 staged tiles with TY = 4 / 2 / 8
     const int v = resolved_variant(h);
     const int shape = tile_shape(v);
     const bool staged = v != 1;
-    const size_t nblk = staged ? h->nblocks_tile[shape] : h->nblocks;
     const int first = h->first ? 1 : 0;
     launch(h, LBEHD_KC_COLLIDE, 1, [&] {
         if (!staged)
@@ -657,11 +676,35 @@ void collide(lbehd_handle *h, bool with_obs = true)
             k_collide_staged<D, 8><<<h->grid_tile[2], h->block, staged_smem_bytes<D, 8>(), h->ls>>>(
                 h->P, S, first, h->maps[2][h->cur]);
     });
-    if (with_obs)
+}
+
+// A step of parity h->cur has left its observable partials (called before cur flips).
+void obs_note_step(lbehd_handle *h)
+{
+    h->obs_nblk[h->cur] = collide_launch_blocks(h);
+    h->obs_pending = std::min(h->obs_pending + 1, 2);
+}
+
+// Sum the partials of the steps not yet reduced into obs: [0, NOBS) the last step's sums,
+// [NOBS, 2 NOBS) the step's before. Each reduction is the fixed-order k_obs_final_split,
+// which moves the previous sums up before writing the new ones, so the sums are the same
+// bits as a reduction after every step.
+int obs_finalize(lbehd_handle *h)
+{
+    if (!h->obs_pending)
+        return LBEHD_OK;
+    const int last = h->cur ^ 1;
+    h->ls = h->stream;
+    for (int k = h->obs_pending; k >= 1; k--) {
+        const int par = k == 2 ? last ^ 1 : last;
         launch(h, LBEHD_KC_OBS, 1, [&] {
             k_obs_final_split<<<NOBS * (OBS_THREADS / 32), 32, 0, h->ls>>>(
-                h->obs_partials, (long long)nblk, h->obs_wsum, h->obs_cnt, h->obs);
+                obs_buf(h, par), h->obs_nblk[par], h->obs_wsum, h->obs_cnt, h->obs);
         });
+    }
+    h->obs_pending = 0;
+    CK(h, cudaGetLastError());
+    return LBEHD_OK;
 }
 
 // Append a conditional node (while or if, on handle `cond`) to the ongoing capture of
@@ -848,6 +891,7 @@ int do_step(lbehd_handle *h)
         CK(h, cudaGraphLaunch(h->gexec[parity][refresh], h->stream));
         h->graph_launches++;
         h->launches += h->graph_static_kernels[parity][refresh];
+        obs_note_step(h);
         h->cur ^= 1;
         h->pcur ^= 1;
         h->step++;
@@ -861,6 +905,7 @@ int do_step(lbehd_handle *h)
         return prc;
     collide<D>(h);
     CK(h, cudaGetLastError());
+    obs_note_step(h);
     h->cur ^= 1;
     h->pcur ^= 1;
     h->first = false;
@@ -1011,8 +1056,9 @@ int init_impl(lbehd_handle *h)
             nblk_max = std::max(nblk_max, h->nblocks_tile[k]);
         }
     }
-    h->obs_partials = (double *)dev_alloc(h, NOBS * nblk_max * sizeof(double));
-    h->obs = (double *)dev_alloc(h, 2 * NOBS * sizeof(double));
+    h->obs_stride = nblk_max;
+    h->obs_partials = (double *)dev_alloc(h, 2 * NOBS * nblk_max * sizeof(double));
+    h->obs = (double *)dev_alloc(h, 4 * NOBS * sizeof(double));
     h->obs_wsum = (double *)dev_alloc(h, NOBS * (OBS_THREADS / 32) * sizeof(double));
     h->obs_cnt = (unsigned *)dev_alloc(h, NOBS * sizeof(unsigned));
     h->flag = (int *)dev_alloc(h, sizeof(int));
@@ -1162,7 +1208,7 @@ int init_impl(lbehd_handle *h)
     CK(h, cudaMemsetAsync(h->pot, 0, N * fb, s));
     CK(h, cudaMemsetAsync(h->pot_lo, 0, N * fb, s));
     CK(h, cudaMemsetAsync(h->eps, 0, N * fb, s));
-    CK(h, cudaMemsetAsync(h->obs, 0, 2 * NOBS * sizeof(double), s));
+    CK(h, cudaMemsetAsync(h->obs, 0, 4 * NOBS * sizeof(double), s));
     CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), s));
     k_init<D><<<h->grid, h->block, 0, s>>>(h->P, h->phi[1], h->g[0], h->fphi[0], h->frho[0], h->info);
     h->launches++;
@@ -1240,6 +1286,8 @@ int autotune_impl(lbehd_handle *h, int reps, double *ms_out)
 {
     reps = std::max(1, std::min(reps, 1000));
     const size_t N = h->N, fb = sizeof(float);
+    if (int rc0 = obs_finalize(h))   // the timed launches overwrite the partial sets
+        return rc0;
     CK(h, cudaStreamSynchronize(h->stream));
     float *save[4] = {h->cg_r, h->cg_p, h->cg_q, h->delta2};
     for (int c = 0; c < 3; c++)
@@ -1263,11 +1311,11 @@ int autotune_impl(lbehd_handle *h, int reps, double *ms_out)
         double ms = -1.0;
         if (v == 1 || h->maps_ok) {
             h->collide_variant = v;
-            collide<D>(h, false);
-            collide<D>(h, false);
+            collide<D>(h);
+            collide<D>(h);
             cudaEventRecord(e0, h->stream);
             for (int r = 0; r < reps; r++)
-                collide<D>(h, false);
+                collide<D>(h);
             cudaEventRecord(e1, h->stream);
             float t = 0.0f;
             cudaError_t e = cudaEventSynchronize(e1);
@@ -1371,6 +1419,8 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
 // the stream is synchronised, fill *out.
 int observe_enqueue(lbehd_handle *h, double *o, int *flag)
 {
+    if (int rc = obs_finalize(h))
+        return rc;
     CK(h, cudaMemcpyAsync(o, h->obs, 2 * NOBS * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(h->h_cg, h->cg_s, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->stream));
@@ -1596,6 +1646,11 @@ int adjoint_forward(lbehd_handle *h, const double *V, int S, int seg, double *lo
             CK(h, cudaMemcpyAsync(pt + N, h->pot_lo, N * fb, cudaMemcpyDeviceToDevice, h->stream));
         }
     }
+    if ((rc0 = obs_finalize(h)))
+        return rc0;
+    // the backward's replays overwrite the sums: keep this run's last two
+    CK(h, cudaMemcpyAsync(h->obs + 2 * NOBS, h->obs, 2 * NOBS * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
     double o[2 * NOBS];
     CK(h, cudaMemcpyAsync(o, h->obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -1886,9 +1941,12 @@ int adjoint_backward(lbehd_handle *h, double *grad)
     a.adj_iters = it1 - it0 - (a.ptraj ? 0 : a.fwd_iters);
     std::copy(g.begin(), g.begin() + (size_t)a.S * a.E, grad);
     (void)SS;
-    // leave the handle as the forward run left it
+    // leave the handle as the forward run left it, observables included
     if ((rc = adj_restore<D>(h, a.fin, a.fin_host)))
         return rc;
+    CK(h, cudaMemcpyAsync(h->obs, h->obs + 2 * NOBS, 2 * NOBS * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
+    h->obs_pending = 0;
     if ((rc = adj_set_V(h, a.T - 1)))
         return rc;
     CK(h, cudaStreamSynchronize(h->stream));
@@ -1919,6 +1977,8 @@ int save_state(lbehd_handle *h, void *dst)
                   (uint32_t)h->nz, (uint32_t)h->Q, (uint32_t)h->QS,
                   (uint32_t)h->cfg.n_electrodes, h->cur, h->pcur, h->first ? 1 : 0,
                   h->mg_valid ? 1 : 0, 0, h->step};
+    if (int rc0 = obs_finalize(h))
+        return rc0;
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaMemcpy(d, &H, sizeof(H), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpyAsync(d + sizeof(H), h->V, LBEHD_MAX_ELECTRODES * sizeof(double),
@@ -1951,6 +2011,7 @@ int load_state(lbehd_handle *h, const void *src)
                           cudaMemcpyDeviceToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->obs, s + sizeof(H) + LBEHD_MAX_ELECTRODES * sizeof(double),
                           2 * NOBS * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    h->obs_pending = 0;
     const lbehd_handle::HostState hs{H.step, H.cur, H.pcur, H.first != 0, H.mg_valid != 0};
     int rc = adj_restore<D>(h, (const float *)(s + STATE_HEADER), hs);
     if (rc)
@@ -2652,7 +2713,7 @@ int batch_collide(lbehd_batch *b, int parity, const std::vector<int> &order, boo
     OA->n = n;
     for (int k = 0; k < n; k++) {
         const lbehd_handle *h = b->inst[k];
-        OA->partials[k] = h->obs_partials;
+        OA->partials[k] = obs_buf(h, parity);
         OA->nblocks[k] = collide_blocks(h, resolved_variant(h));
         OA->obs[k] = h->obs;
     }
@@ -2745,6 +2806,9 @@ int batch_step_one(lbehd_batch *b)
                 worst = rc;
             else if (rc)
                 return bfail(b, rc, "first step: " + h->err);
+            // the batched steps reduce every instance's observables after each step
+            if (const int r2 = obs_finalize(h))
+                return bfail(b, r2, "first step: " + h->err);
         }
         return worst;
     }

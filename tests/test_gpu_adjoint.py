@@ -162,6 +162,21 @@ def test_schedule_loss_autograd_and_state(gpu):
         assert np.abs(sim.array(name) - plain.array(name)).max() <= 1e-6, name
 
 
+def test_observables_after_the_backward_are_the_forward_runs(gpu):
+    """The backward's replays overwrite the observable sums; afterwards the handle reports
+    the sums of the forward run's last two steps again, bit for bit."""
+    w = tiny_3d()
+    V = np.array([[0.03, 0.05], [0.06, 0.01]])
+    sim = gpu.Simulation(w)
+    sim.adjoint_forward(V, 6)
+    before = sim.observe()
+    sim.adjoint_backward()
+    after = sim.observe()
+    for k in ("step", "M1", "centroid", "velocity", "f_ele", "f_ele_total", "f_drag", "mass",
+              "charge"):
+        assert np.array_equal(np.asarray(before[k]), np.asarray(after[k])), k
+
+
 def test_recorded_potential_and_replayed_solve_agree(gpu):
     """Backward replays with the recorded potential trajectory, and replays that solve
     Gauss's law again (LBEHD_OPT_ADJ_TRAJECTORY = 0), give the same gradient bit for bit:
