@@ -624,8 +624,10 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         iteration(A.x);
     if (ok && A.mode == PS_FORWARD) {
         ps_apply(A.N, L0.D, A.x, nullptr, A.pot, A.pot_lo);
-        sync();
         // refinement: the true residual of the updated potential, once, if the pass iterated
+        // (s.refine is the same in every CTA; without it the kernel's end is the barrier)
+        if (ok && s.refine)
+            sync();
         if (ok && s.refine) {
             ps_for(A.N, [&](int i) { A.delta2[i] = 0.0f; });
             sync();
