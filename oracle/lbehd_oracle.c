@@ -158,6 +158,17 @@ void oracle_normals(const oprm_t *p, const olat_t *L, const uint8_t *solid, int3
 /* ------------------------------------------------------------------ Poisson */
 
 /* Face coefficient between fluid node i and neighbour j for the operator of Eq. 13. */
+/* Eq. 11: the coefficients Upsilon_i of the ternary free energy from the pairwise surface
+ * tensions, Upsilon_i = gamma_ij + gamma_ik - gamma_jk ({i, j, k} = {1, 2, 3}), and
+ * Upsilon_T = 3 / sum_i (1 / Upsilon_i). */
+void oracle_upsilon(double g12, double g13, double g23, double Y[3], double *YT)
+{
+    Y[0] = g12 + g13 - g23;
+    Y[1] = g12 + g23 - g13;
+    Y[2] = g13 + g23 - g12;
+    *YT = 3.0 / (1.0 / Y[0] + 1.0 / Y[1] + 1.0 / Y[2]);
+}
+
 static double eps_face(const ost_t *s, long i, long j)
 {
     if (!s->solid[j])
@@ -435,11 +446,8 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
 
     /* 5. Chemical potential (Eq. 10, Upsilons from Eq. 11), capillary force
      *    F_s = sum_i mu_i grad Phi_i, and the AC sharpening flux F_Phi,i (Eq. 18). */
-    double Y1 = p->gamma12 + p->gamma13 - p->gamma23;
-    double Y2 = p->gamma12 + p->gamma23 - p->gamma13;
-    double Y3 = p->gamma13 + p->gamma23 - p->gamma12;
-    double Y[3] = {Y1, Y2, Y3};
-    double YT = 3.0 / (1.0 / Y1 + 1.0 / Y2 + 1.0 / Y3);
+    double Y[3], YT;
+    oracle_upsilon(p->gamma12, p->gamma13, p->gamma23, Y, &YT);
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         for (int a = 0; a < 3; a++)

@@ -185,6 +185,16 @@ def set_threads(n):
     lib().oracle_set_threads(int(n))
 
 
+def upsilon(gamma12, gamma13, gamma23):
+    """Eq. 11: (Upsilon_1, Upsilon_2, Upsilon_3) and Upsilon_T of the ternary free energy
+    from the pairwise surface tensions (the coefficients the oracle's step uses)."""
+    Y = (ctypes.c_double * 3)()
+    YT = ctypes.c_double()
+    lib().oracle_upsilon(ctypes.c_double(gamma12), ctypes.c_double(gamma13),
+                         ctypes.c_double(gamma23), Y, ctypes.byref(YT))
+    return np.array(Y[:]), YT.value
+
+
 def get_threads():
     return int(lib().oracle_get_threads())
 
