@@ -61,12 +61,31 @@ struct CollideBatch {
     const PopMaps *maps;                          // staged: [n] tensor maps in global memory
 };
 
+// The block's instance parameters and state pointers, copied from the parameter table into
+// shared memory by the first threads (the caller synchronises before use). The collide body
+// reads them many times; from the table, every read is an indexed constant load (measured:
+// 89.6 -> 82.4 us per 128x64x64 instance for the staged 64x2 kernel with four instances).
+__device__ __forceinline__ void batch_entry_to_smem(const CollideBatch &A, int k, Params &sP,
+                                                    State &sS)
+{
+    static_assert(sizeof(Params) % 4 == 0 && sizeof(State) % 4 == 0, "word copies");
+    const int t = threadIdx.x;
+    if (t < (int)(sizeof(Params) / 4))
+        reinterpret_cast<int *>(&sP)[t] = reinterpret_cast<const int *>(&A.P[k])[t];
+    if (t < (int)(sizeof(State) / 4))
+        reinterpret_cast<int *>(&sS)[t] = reinterpret_cast<const int *>(&A.S[k])[t];
+}
+
 // Global-load collide over the flattened sites of every instance.
 template <int D>
 __global__ void __launch_bounds__(BX, 4) k_collide_batch(const __grid_constant__ CollideBatch A)
 {
     const int k = batch_instance(A.start, A.n, blockIdx.x);
-    const Params &P = A.P[k];
+    __shared__ __align__(16) Params sP;
+    __shared__ __align__(16) State sS;
+    batch_entry_to_smem(A, k, sP, sS);
+    __syncthreads();
+    const Params &P = sP;
     const int b = blockIdx.x - A.start[k];
     const int i = b * BX + threadIdx.x;
     float ob[NOBS];
@@ -75,9 +94,9 @@ __global__ void __launch_bounds__(BX, 4) k_collide_batch(const __grid_constant__
         ob[m] = 0.0f;
     if (i < (int)P.N) {
         const int r = i / P.nx;
-        collide_global_site<D>(P, A.S[k], A.first, i - r * P.nx, r % P.ny, r / P.ny, ob);
+        collide_global_site<D>(P, sS, A.first, i - r * P.nx, r % P.ny, r / P.ny, ob);
     }
-    block_obs_partials(ob, A.S[k].obs_partials, b, A.start[k + 1] - A.start[k]);
+    block_obs_partials(ob, sS.obs_partials, b, A.start[k + 1] - A.start[k]);
 }
 
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
@@ -98,13 +117,13 @@ __global__ void __launch_bounds__(BX, 4) k_collide_staged_batch(const __grid_con
     const int tx = A.tiles_x[k], ty = A.tiles_y[k];
     const int bx = b % tx, r = b / tx;
     const PopMaps *m = A.maps + k;
-    if (threadIdx.x == 0) {
-        tensormap_acquire(&m->g);
+    if (threadIdx.x == 0)   // the only map the staged tile reads
         tensormap_acquire(&m->fphi);
-        tensormap_acquire(&m->frho);
-    }
-    collide_staged_tile<D, TY>(A.P[k], A.S[k], A.first, m, bx * Halo<D, TY>::TX, (r % ty) * TY,
-                               r / ty, b, A.start[k + 1] - A.start[k]);
+    __shared__ __align__(16) Params sP;
+    __shared__ __align__(16) State sS;
+    batch_entry_to_smem(A, k, sP, sS);   // collide_staged_tile synchronises before reading them
+    collide_staged_tile<D, TY>(sP, sS, A.first, m, bx * Halo<D, TY>::TX, (r % ty) * TY, r / ty,
+                               b, A.start[k + 1] - A.start[k]);
 }
 
 struct ObsBatch {
