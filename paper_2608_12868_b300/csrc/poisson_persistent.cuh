@@ -82,6 +82,8 @@ struct PsArgs {
     unsigned spin_limit;       // polls before a barrier wait gives up (PS_SPIN_LIMIT)
     int extra;                 // arrivals expected beyond the CTAs (0; 1 only to test the
                                // time-out: every barrier then runs out)
+    int pre;                   // forward: r and its partials part[1] were formed by k_pcg_init
+                               // launched just before (the start then only reduces them)
 };
 
 constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
@@ -482,8 +484,9 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     // pcg_scalar_block: small reductions are summed by every CTA; large ones have their 32
     // virtual-warp sums spread over CTAs 0 .. 32 nv - 1, a second barrier, then every CTA
     // finishes the butterfly over the 32 sums and updates its copy of the scalars
-    auto sync_scalar = [&](const double *part, int nv, int op, int nblk) {
-        sync();
+    auto sync_scalar = [&](const double *part, int nv, int op, int nblk, bool first = true) {
+        if (first)   // not for partials written by the kernel before this one
+            sync();
         if (!ok)
             return;
         if ((long long)nv * nblk < PS_SPLIT_MIN || (int)gridDim.x < 32 * nv) {
@@ -628,7 +631,12 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         sync_scalar(A.part[1], 2, op, A.nbs);
     };
 
-    start(A.x, 0);
+    if (A.pre && A.mode == PS_FORWARD) {
+        z_ready = false;
+        sync_scalar(A.part[1], 2, 0, A.nbs, false);
+    } else {
+        start(A.x, 0);
+    }
     while (ok && !s.done)
         iteration(A.x);
     if (ok && A.mode == PS_FORWARD) {
