@@ -382,16 +382,19 @@ int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float
     A.rho = rho;
     A.rhs = rhs;
     CK(h, cudaMemsetAsync(&h->ps_bar->count, 0, sizeof(unsigned), h->ls));
-    // The forward start r = b - A (phi + x) as an ordinary launch: at full occupancy it runs
-    // near bandwidth, where the persistent kernel's 1024-thread CTAs take it in four
-    // latency-bound rounds. Same per-site body and block partition as the start phase.
-    A.pre = mode == PS_FORWARD ? 1 : 0;
-    if (A.pre) {
-        const auto &L0 = h->mg[0];
+    // The start r = b - A (phi + x) (forward) or rhs - A x (adjoint) as an ordinary launch:
+    // at full occupancy it runs near bandwidth, where the persistent kernel's 1024-thread
+    // CTAs take it in four latency-bound rounds. Same per-site body and block partition as
+    // the kernel's own start phase.
+    A.pre = 1;
+    const auto &L0 = h->mg[0];
+    if (mode == PS_FORWARD)
         k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
             L0.d, A.pot, A.pot_lo, x, A.eps, rho, A.info, L0.D, A.r, A.part[1]);
-        h->launches += 1;
-    }
+    else
+        k_adj_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
+            L0.d, A.eps, A.info, L0.D, x, rhs, A.r, A.part[1]);
+    h->launches += 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)h->ps_grid);
     cfg.blockDim = dim3(PS_THREADS);

@@ -82,8 +82,8 @@ struct PsArgs {
     unsigned spin_limit;       // polls before a barrier wait gives up (PS_SPIN_LIMIT)
     int extra;                 // arrivals expected beyond the CTAs (0; 1 only to test the
                                // time-out: every barrier then runs out)
-    int pre;                   // forward: r and its partials part[1] were formed by k_pcg_init
-                               // launched just before (the start then only reduces them)
+    int pre;                   // r and its partials part[1] were formed by k_pcg_init or
+                               // k_adj_pcg_init launched just before (the start only reduces)
 };
 
 constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         sync_scalar(A.part[1], 2, op, A.nbs);
     };
 
-    if (A.pre && A.mode == PS_FORWARD) {
+    if (A.pre) {
         z_ready = false;
         sync_scalar(A.part[1], 2, 0, A.nbs, false);
     } else {
