@@ -888,9 +888,12 @@ __global__ void __launch_bounds__(BX) k_adj_pcg_init(MgDims d, const float *__re
                                                      const float *__restrict__ mu,
                                                      const float *__restrict__ rhs,
                                                      float *__restrict__ r,
-                                                     double *__restrict__ partials)
+                                                     double *__restrict__ partials,
+                                                     unsigned *zero = nullptr)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
+    if (zero && i == 0)   // the grid-barrier counter of the persistent solve that follows
+        *zero = 0u;
     float v[2] = {0.f, 0.f};
     if (i < d.nx * d.ny * d.nz)
         adj_pcg_init_site<D>(d, eps, info, Dg, mu, rhs, r, i, v);

@@ -370,7 +370,7 @@ int ps_setup(lbehd_handle *h)
 bool ps_use(const lbehd_handle *h) { return h->ps_ok && h->ps_on; }
 
 // One persistent solve on h->ls: the forward step's (increment x, this step's charge rho) or
-// the adjoint's (solution x, right-hand side rhs). The barrier counter is reset first.
+// the adjoint's (solution x, right-hand side rhs), after the launch that forms its start.
 template <int D>
 int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float *rhs)
 {
@@ -381,19 +381,18 @@ int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float
     A.x = x;
     A.rho = rho;
     A.rhs = rhs;
-    CK(h, cudaMemsetAsync(&h->ps_bar->count, 0, sizeof(unsigned), h->ls));
     // The start r = b - A (phi + x) (forward) or rhs - A x (adjoint) as an ordinary launch:
     // at full occupancy it runs near bandwidth, where the persistent kernel's 1024-thread
     // CTAs take it in four latency-bound rounds. Same per-site body and block partition as
-    // the kernel's own start phase.
+    // the kernel's own start phase. It also resets the barrier counter.
     A.pre = 1;
     const auto &L0 = h->mg[0];
     if (mode == PS_FORWARD)
         k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
-            L0.d, A.pot, A.pot_lo, x, A.eps, rho, A.info, L0.D, A.r, A.part[1]);
+            L0.d, A.pot, A.pot_lo, x, A.eps, rho, A.info, L0.D, A.r, A.part[1], &h->ps_bar->count);
     else
         k_adj_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
-            L0.d, A.eps, A.info, L0.D, x, rhs, A.r, A.part[1]);
+            L0.d, A.eps, A.info, L0.D, x, rhs, A.r, A.part[1], &h->ps_bar->count);
     h->launches += 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)h->ps_grid);

@@ -677,9 +677,12 @@ __global__ void __launch_bounds__(BX) k_pcg_init(MgDims d, const float *__restri
                                                  const float *__restrict__ rho,
                                                  const uint8_t *__restrict__ info,
                                                  const float *__restrict__ Dg,
-                                                 float *__restrict__ r, double *__restrict__ partials)
+                                                 float *__restrict__ r, double *__restrict__ partials,
+                                                 unsigned *zero = nullptr)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
+    if (zero && i == 0)   // the grid-barrier counter of the persistent solve that follows
+        *zero = 0u;
     float v[2] = {0.f, 0.f};
     if (i < d.nx * d.ny * d.nz) {
         int x, y, z;
