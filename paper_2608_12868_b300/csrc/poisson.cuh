@@ -423,7 +423,9 @@ struct TailLevels {
 // threads stride over the cells of each level. Same arithmetic, cell by cell, as the
 // multi-launch levels above it (and the same for any assignment of cells to threads: a
 // red-black half sweep reads only cells of the other colour).
-__device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
+// ops_loaded: the levels' operators (D, kx, ky, kz) are already in `sm` from an earlier call
+// of the same CTA (a persistent solve keeps them across its V-cycles).
+__device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm, bool ops_loaded = false)
 {
     const int tot = T.total, t = threadIdx.x;
     float *sD = sm, *skx = sm + tot, *sky = sm + 2 * tot, *skz = sm + 3 * tot, *sx = sm + 4 * tot,
@@ -433,10 +435,12 @@ __device__ __forceinline__ void mg_tail_block(const TailLevels &T, float *sm)
     for (int l = 0; l < T.nl; l++) {
         const int n = ncell(l), o = T.off[l];
         for (int c = t; c < n; c += TAIL_THREADS) {
-            sD[o + c] = T.D[l][c];
-            skx[o + c] = T.kx[l][c];
-            sky[o + c] = T.ky[l][c];
-            skz[o + c] = T.kz[l][c];
+            if (!ops_loaded) {
+                sD[o + c] = T.D[l][c];
+                skx[o + c] = T.kx[l][c];
+                sky[o + c] = T.ky[l][c];
+                skz[o + c] = T.kz[l][c];
+            }
             sx[o + c] = 0.0f;
             if (l == 0)
                 sb[c] = T.b0[c];

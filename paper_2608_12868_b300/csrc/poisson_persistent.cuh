@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     // one symmetric V-cycle, z ~= A^-1 r. After an iteration's update, level 0's zero start
     // and first red half sweep were done by that update (z_ready); the last red half sweep of
     // level 0 also forms the r . z partials (then the caller's op-1 reduction ends the phase).
-    bool z_ready = false;
+    bool z_ready = false, tail_ops = false;
     auto vcycle = [&]() {
         for (int l = 0; l < A.nl && ok; l++) {
             const PsLevel &L = A.L[l];
@@ -547,8 +547,10 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         }
         if (!ok)
             return;
-        if (blockIdx.x == 0)
-            mg_tail_block(A.tail, tail_sm);
+        if (blockIdx.x == 0) {   // the tail's operators stay in shared memory after the first
+            mg_tail_block(A.tail, tail_sm, tail_ops);
+            tail_ops = true;
+        }
         sync();
         for (int l = A.nl - 1; l >= 0 && ok; l--) {
             const PsLevel &L = A.L[l];
