@@ -612,18 +612,21 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels T)
 // are close, so their difference is exact in FP32, and r keeps the accuracy an FP64
 // evaluation of b - A phi would have, in FP32 arithmetic.
 // pcg_init_value returns r_i without storing it (so that several sites' loads can be in
-// flight together); pcg_init_site stores it.
+// flight together); pcg_init_site stores it. zero_delta: delta is all zeros (read as such
+// without loading it; same arithmetic).
 template <int D>
 __device__ __forceinline__ float pcg_init_value(const MgDims &d, const float *pot,
                                                 const float *pot_lo, const float *delta,
                                                 const float *eps, const float *rho,
                                                 const uint8_t *info, const float *Dg, int x,
-                                                int y, int z, float (&v)[2])
+                                                int y, int z, float (&v)[2],
+                                                bool zero_delta = false)
 {
     {
         const int i = cell(d, x, y, z);
         const Nb6 nb = nb6(d, i, x, y, z);
-        const float Di = Dg[i], ei = eps[i], hi = pot[i], lo = pot_lo[i], di = delta[i];
+        const float Di = Dg[i], ei = eps[i], hi = pot[i], lo = pot_lo[i];
+        const float di = zero_delta ? 0.0f : delta[i];
         const float rh = rho[i];
         int pt[2 * D];
         float ph[2 * D], pl[2 * D], dl[2 * D], ej[2 * D];
@@ -633,7 +636,7 @@ __device__ __forceinline__ float pcg_init_value(const MgDims &d, const float *po
             pt[f] = info[j] & 3;
             ph[f] = pot[j];
             pl[f] = pot_lo[j];
-            dl[f] = delta[j];
+            dl[f] = zero_delta ? 0.0f : delta[j];
             ej[f] = eps[j];
         }
         float ri = 0.0f;

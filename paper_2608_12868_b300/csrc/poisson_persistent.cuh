@@ -613,7 +613,8 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
 
     // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4 (most
     // solves stop here, so this phase does nothing for the V-cycle)
-    auto start = [&](float *xv, int op) {
+    // zero_x: xv is to start from zero; it is read as zero and zeroed in the same pass
+    auto start = [&](float *xv, int op, bool zero_x = false) {
         ps_for_vblocks(A.nbs, [&](int vb, int t) {
             const int i = vb * BX + t;
             float v[2] = {0.0f, 0.0f};
@@ -624,7 +625,9 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
                     int x, y, zz;
                     cell_xyz(L0.d, i, x, y, zz);
                     A.r[i] = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info,
-                                               L0.D, x, y, zz, v);
+                                               L0.D, x, y, zz, v, zero_x);
+                    if (zero_x)
+                        xv[i] = 0.0f;
                 }
             }
             ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
@@ -648,9 +651,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         if (ok && s.refine)
             sync();
         if (ok && s.refine) {
-            ps_for(A.N, [&](int i) { A.delta2[i] = 0.0f; });
-            sync();
-            start(A.delta2, 4);
+            start(A.delta2, 4, true);   // delta2 = 0: read as zero, zeroed in the same pass
             while (ok && !s.done)
                 iteration(A.delta2);
             if (ok)
