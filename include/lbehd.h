@@ -183,10 +183,10 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   reproduce the same potential bit for bit). */
 #define LBEHD_OPT_ADJ_TRAJECTORY 3
 /*   LBEHD_OPT_POISSON_KERNEL: 1 (default) in LBEHD_POISSON_GRAPH mode each Gauss-law solve
- *   (start, CG iterations with their V-cycles, potential update, refinement pass) is one
- *   persistent cooperative kernel with grid-wide barriers, where the lattice allows it (a
- *   shared-memory tail level, even nx on the levels above it); 0 the multi-launch graph
- *   with conditional nodes. Both give the same bits. */
+ *   is one launch that forms the start residual, then one persistent cooperative kernel with
+ *   grid-wide barriers (CG iterations with their V-cycles, potential update, refinement
+ *   pass), where the lattice allows it (a shared-memory tail level, even nx on the levels
+ *   above it); 0 the multi-launch graph with conditional nodes. Both give the same bits. */
 #define LBEHD_OPT_POISSON_KERNEL 4
 /*   LBEHD_OPT_BARRIER_TEST: test hook for the persistent solve's time-out path. value > 0:
  *   its grid barriers wait for one CTA more than is launched and give up after `value`
