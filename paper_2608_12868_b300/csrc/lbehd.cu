@@ -385,7 +385,6 @@ int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float
     // at full occupancy it runs near bandwidth, where the persistent kernel's 1024-thread
     // CTAs take it in four latency-bound rounds. Same per-site body and block partition as
     // the kernel's own start phase. It also resets the barrier counter.
-    A.pre = 1;
     const auto &L0 = h->mg[0];
     if (mode == PS_FORWARD)
         k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(

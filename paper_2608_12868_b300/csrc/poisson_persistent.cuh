@@ -1,6 +1,7 @@
 // poisson_persistent.cuh -- the Gauss-law solve of one step (Eq. 13) as one persistent
-// kernel: start, every preconditioned-CG iteration (the V-cycle included), the update of the
-// potential and the refinement pass, with grid-wide barriers in place of kernel boundaries.
+// kernel after the launch that forms the start residual: the start's reduction, every
+// preconditioned-CG iteration (the V-cycle included), the update of the potential and the
+// refinement pass, with grid-wide barriers in place of kernel boundaries.
 //
 // One CTA of PS_THREADS = 1024 threads per SM, launched cooperatively (all CTAs resident).
 // The CG loop of the multi-launch form is latency-bound: a V-cycle of ~36 small dependent
@@ -82,8 +83,6 @@ struct PsArgs {
     unsigned spin_limit;       // polls before a barrier wait gives up (PS_SPIN_LIMIT)
     int extra;                 // arrivals expected beyond the CTAs (0; 1 only to test the
                                // time-out: every barrier then runs out)
-    int pre;                   // r and its partials part[1] were formed by k_pcg_init or
-                               // k_adj_pcg_init launched just before (the start only reduces)
 };
 
 constexpr int PS_FORWARD = 0, PS_ADJOINT = 1;
@@ -611,37 +610,30 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         sync_scalar(A.part[0], 1, 3, A.nb1);   // ||r||^2
     };
 
-    // start: r = b - A (phi + xv) (forward) or r = rhs - A xv (adjoint), then op 0 / 4 (most
-    // solves stop here, so this phase does nothing for the V-cycle)
-    // zero_x: xv is to start from zero; it is read as zero and zeroed in the same pass
-    auto start = [&](float *xv, int op, bool zero_x = false) {
+    // the refinement pass's start: r = b - A phi of the updated potential, with its increment
+    // delta2 read as zero and zeroed in the same pass, then op 4 (this phase does nothing for
+    // the V-cycle: most refinement passes stop here)
+    auto refine_start = [&]() {
         ps_for_vblocks(A.nbs, [&](int vb, int t) {
             const int i = vb * BX + t;
             float v[2] = {0.0f, 0.0f};
             if (i < A.N) {
-                if (A.mode == PS_ADJOINT) {
-                    adj_pcg_init_site<D>(L0.d, A.eps, A.info, L0.D, xv, A.rhs, A.r, i, v);
-                } else {
-                    int x, y, zz;
-                    cell_xyz(L0.d, i, x, y, zz);
-                    A.r[i] = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, xv, A.eps, A.rho, A.info,
-                                               L0.D, x, y, zz, v, zero_x);
-                    if (zero_x)
-                        xv[i] = 0.0f;
-                }
+                int x, y, zz;
+                cell_xyz(L0.d, i, x, y, zz);
+                A.r[i] = pcg_init_value<D>(L0.d, A.pot, A.pot_lo, A.delta2, A.eps, A.rho,
+                                           A.info, L0.D, x, y, zz, v, true);
+                A.delta2[i] = 0.0f;
             }
             ps_group_partials<2>(v, A.part[1], vb, A.nbs, gsm);
         });
         z_ready = false;
-        sync_scalar(A.part[1], 2, op, A.nbs);
+        sync_scalar(A.part[1], 2, 4, A.nbs);
     };
 
-    if (A.pre) {
-        z_ready = false;
-        sync_scalar(A.part[1], 2, 0, A.nbs, false);
-    } else {
-        start(A.x, 0);
-    }
+    // the start residual r and its partials part[1] come from the k_pcg_init (forward) or
+    // k_adj_pcg_init (adjoint) launch just before this kernel: only their reduction is left
+    z_ready = false;
+    sync_scalar(A.part[1], 2, 0, A.nbs, false);
     while (ok && !s.done)
         iteration(A.x);
     if (ok && A.mode == PS_FORWARD) {
@@ -651,7 +643,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         if (ok && s.refine)
             sync();
         if (ok && s.refine) {
-            start(A.delta2, 4, true);   // delta2 = 0: read as zero, zeroed in the same pass
+            refine_start();
             while (ok && !s.done)
                 iteration(A.delta2);
             if (ok)
