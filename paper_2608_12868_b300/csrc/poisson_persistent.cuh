@@ -28,13 +28,12 @@
 //    own lane, summed in the restriction's order), and "prolongation, then the first black
 //    half sweep" (neighbours read as prolongation leaves them).
 //
-// Barrier: a monotonic arrival counter (reset by the host before each launch) that barrier
-// k waits to reach k * gridDim.x; thread 0 of each CTA spins with a backoff and an
+// Barrier: a monotonic arrival counter (zeroed by the start launch before each solve) that
+// barrier k waits to reach k * gridDim.x; thread 0 of each CTA spins with a backoff and an
 // iteration limit. On time-out it raises the error word, and every CTA leaves at its next
 // barrier; the host reads the word and reports the step as failed.
 #pragma once
 
-#include "adjoint.cuh"
 #include "poisson.cuh"
 
 namespace lbehd {
