@@ -2266,14 +2266,17 @@ void batch_vcycle(lbehd_batch *b, MgBatch &A, int mode)
     for (int l = 0; l < maxd; l++) {
         const std::vector<int> ids = above(l);
         fill_mg(b, A, ids, at(l));
-        blaunch(b, k_mg_zero_batch, A, fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
+        // zero + the first red half sweep in one pass when every instance sweeps at least once
+        const bool fused = sweeping(ids, 0, nu_of).size() == ids.size();
+        blaunch(b, fused ? k_mg_gs_first_batch : k_mg_zero_batch, A,
+                fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
         auto half = [&b, l](int k) {
             const MgDims &d = b->inst[k]->mg[l].d;
             return ceil_div((long long)(d.nx / 2) * d.ny * d.nz, BX);
         };
         for (int sw = 0; sw < max_nu; sw++) {
             const int hb = fill_grid_set(b, A.g, sweeping(ids, sw, nu_of), mode, half);
-            for (int color = 0; color < 2; color++) {
+            for (int color = (fused && sw == 0) ? 1 : 0; color < 2; color++) {
                 A.color = color;
                 A.sweep = sw;
                 blaunch(b, k_mg_gs_batch, A, hb, BX);

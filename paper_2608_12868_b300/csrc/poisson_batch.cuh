@@ -201,6 +201,26 @@ __global__ void __launch_bounds__(BX) k_mg_gs_batch(const __grid_constant__ MgBa
     });
 }
 
+// x = 0 on this level, then the first red half sweep. Every neighbour is 0, so a red cell
+// with D > 0 gets (b + 0) / D (offdiag_sum of zeros is +0) and every other cell 0: the same
+// bits as k_mg_zero_batch followed by k_mg_gs_batch with colour 0, in one pass.
+__global__ void __launch_bounds__(BX) k_mg_gs_first_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const int i = b * BX + threadIdx.x;
+        if (i >= cells(m.f))
+            return;
+        int x, y, z;
+        cell_xyz(m.f, i, x, y, z);
+        const float di = m.D[i];
+        float v = 0.0f;
+        if (((x + y + z) & 1) == 0 && di > 0.0f)
+            v = __fdiv_rn(__fadd_rn(m.b[i], 0.0f), di);
+        m.x[i] = v;
+    });
+}
+
 __global__ void __launch_bounds__(BX) k_mg_resid_batch(const __grid_constant__ MgBatch A)
 {
     for_work(A.g, [&](int k, int b) {
