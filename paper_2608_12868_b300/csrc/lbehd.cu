@@ -2282,11 +2282,12 @@ void batch_vcycle(lbehd_batch *b, MgBatch &A, int mode)
                 blaunch(b, k_mg_gs_batch, A, hb, BX);
             }
         }
-        auto coarse_cells = [&b, l](int k) {
-            return ceil_div(dims_cells(b->inst[k]->mg[l + 1].d), BX);
+        // residual + restriction in one pass, 8 lanes per coarse cell
+        auto coarse_lanes = [&b, l](int k) {
+            return ceil_div(dims_cells(b->inst[k]->mg[l + 1].d) * 8, BX);
         };
-        blaunch(b, k_mg_resid_batch, A, fill_grid_set(b, A.g, ids, mode, cells_f(l)), BX);
-        blaunch(b, k_mg_restrict_sum_batch, A, fill_grid_set(b, A.g, ids, mode, coarse_cells), BX);
+        blaunch(b, k_mg_resid_restrict_batch, A, fill_grid_set(b, A.g, ids, mode, coarse_lanes),
+                BX);
     }
     // bottom: shared-memory tails, and the coarsest-level sweeps of instances without one
     {

@@ -247,6 +247,51 @@ __global__ void __launch_bounds__(BX) k_mg_restrict_sum_batch(const __grid_const
     });
 }
 
+// The fine level's residual and its restriction in one pass: 8 lanes per coarse cell form
+// the residuals of its children, and the first lane sums them in the child order of
+// mg_restrict_sum_cell (the same bits as k_mg_resid_batch then k_mg_restrict_sum_batch).
+// A work item is BX / 8 coarse cells. Needs even fine x and y extents (every coarsened
+// level has them).
+__global__ void __launch_bounds__(BX) k_mg_resid_restrict_batch(const __grid_constant__ MgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        const MgDims &f = m.f;
+        const int lane = threadIdx.x & 31, ch = threadIdx.x & 7;
+        const int I = b * (BX / 8) + (threadIdx.x >> 3);
+        const bool own = I < cells(m.c);
+        bool z1 = false;
+        float r = 0.0f;
+        if (own) {
+            int X, Y, Z;
+            cell_xyz(m.c, I, X, Y, Z);
+            const int z0 = m.cz2 ? 2 * Z : Z;
+            z1 = m.cz2 && z0 + 1 < f.nz;
+            const int g = ch & 1;
+            if (g == 0 || z1) {
+                const int x = 2 * X + (ch >> 2), y = 2 * Y + ((ch >> 1) & 1), z = z0 + g;
+                const int i = cell(f, x, y, z);
+                const float di = m.D[i], xi = m.x[i], bi = m.b[i];
+                const float Ax =
+                    __fmaf_rn(di, xi, -offdiag_sum(f, i, x, y, z, m.kx, m.ky, m.kz, m.x));
+                r = di > 0.0f ? __fsub_rn(bi, Ax) : 0.0f;
+            }
+        }
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            v[j] = __shfl_sync(0xffffffffu, r, (lane & ~7) + j);
+        if (ch == 0 && own) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if ((j & 1) == 0 || z1)
+                    acc = __fadd_rn(acc, v[j]);
+            m.bc[I] = acc;
+        }
+    });
+}
+
 __global__ void __launch_bounds__(BX) k_mg_prolong_batch(const __grid_constant__ MgBatch A)
 {
     for_work(A.g, [&](int k, int b) {
