@@ -221,35 +221,10 @@ __global__ void __launch_bounds__(BX) k_mg_gs_first_batch(const __grid_constant_
     });
 }
 
-__global__ void __launch_bounds__(BX) k_mg_resid_batch(const __grid_constant__ MgBatch A)
-{
-    for_work(A.g, [&](int k, int b) {
-        const MgInst &m = A.m[k];
-        const int i = b * BX + threadIdx.x;
-        if (i >= cells(m.f))
-            return;
-        int x, y, z;
-        cell_xyz(m.f, i, x, y, z);
-        mg_resid_cell(m.f, m.D, m.kx, m.ky, m.kz, m.b, m.x, m.r, x, y, z);
-    });
-}
-
-__global__ void __launch_bounds__(BX) k_mg_restrict_sum_batch(const __grid_constant__ MgBatch A)
-{
-    for_work(A.g, [&](int k, int b) {
-        const MgInst &m = A.m[k];
-        const int i = b * BX + threadIdx.x;
-        if (i >= cells(m.c))
-            return;
-        int X, Y, Z;
-        cell_xyz(m.c, i, X, Y, Z);
-        mg_restrict_sum_cell(m.f, m.c, m.cz2, m.r, m.bc, X, Y, Z);
-    });
-}
-
 // The fine level's residual and its restriction in one pass: 8 lanes per coarse cell form
 // the residuals of its children, and the first lane sums them in the child order of
-// mg_restrict_sum_cell (the same bits as k_mg_resid_batch then k_mg_restrict_sum_batch).
+// mg_restrict_sum_cell (the same bits as mg_resid_cell on every fine cell, then
+// mg_restrict_sum_cell).
 // A work item is BX / 8 coarse cells. Needs even fine x and y extents (every coarsened
 // level has them).
 __global__ void __launch_bounds__(BX) k_mg_resid_restrict_batch(const __grid_constant__ MgBatch A)
