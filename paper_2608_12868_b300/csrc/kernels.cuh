@@ -10,7 +10,7 @@
 //               push-stream the momentum, three phase-field (Eqs. 15-17) and charge
 //               populations with halfway bounce-back, and block partial sums (FP64) of the
 //               droplet observables;
-//   k_obs_final the deterministic FP64 sum of those partials.
+//   k_obs_final_split  the deterministic FP64 sum of those partials (when they are read).
 //
 // The raw-moment MRT collisions are evaluated in closed form. With every moment of order
 // >= 3 relaxing at rate 1 (and the trace of the momentum flux at s_bulk), M^-1 m* reduces
@@ -66,16 +66,6 @@ struct State {
     double *obs_partials;             // [NOBS][nblocks]
     int *flag;                        // bit 0: non-finite value seen; bit 1: staging timed out
 };
-
-template <class L>
-__device__ __forceinline__ size_t nbr_index(int n, int x, int y, int z, int xp, int xm, int yp,
-                                            int ym, int zp, int zm, int nx, int ny)
-{
-    const int X = L::ex(n) > 0 ? xp : (L::ex(n) < 0 ? xm : x);
-    const int Y = L::ey(n) > 0 ? yp : (L::ey(n) < 0 ? ym : y);
-    const int Z = L::ez(n) > 0 ? zp : (L::ez(n) < 0 ? zm : z);
-    return (size_t)X + (size_t)nx * ((size_t)Y + (size_t)ny * (size_t)Z);
-}
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -891,17 +881,11 @@ __device__ __forceinline__ void obs_final_block(const double *__restrict__ parti
     }
 }
 
-__global__ void __launch_bounds__(OBS_THREADS) k_obs_final(const double *__restrict__ partials,
-                                                          long long nblocks,
-                                                          double *__restrict__ obs)
-{
-    obs_final_block(partials, nblocks, obs, blockIdx.x);
-}
-
 // The same sums split over NOBS x (OBS_THREADS / 32) one-warp CTAs (FP64 adds are slow on
 // this part, so one CTA per observable is latency-bound): CTA (k, w) forms warp w's sum of
 // obs_final_block's order and the last CTA of observable k to finish adds the warp sums in
-// order. Same bits as k_obs_final. cnt[NOBS] must be zero before the first launch; the last
+// order. Same bits as obs_final_block (one CTA per observable, as the batched form sums).
+// cnt[NOBS] must be zero before the first launch; the last
 // CTA resets it.
 __global__ void __launch_bounds__(32) k_obs_final_split(const double *__restrict__ partials,
                                                         long long nblocks, double *wsum,
