@@ -148,16 +148,17 @@ int lbehd_init(const lbehd_config *cfg, lbehd_handle **out);
 
 /* Advance n >= 0 coupled steps: phase moments and wetting ghosts, Poisson solve, forces,
  * fused collide + push-stream of the momentum, three phase-field and charge populations,
- * observable reductions. Returns LBEHD_ERR_POISSON_NOCONV if any solve hit the cap
- * (the steps are still completed). */
+ * block partial sums of the observables. Returns LBEHD_ERR_POISSON_NOCONV if any solve hit
+ * the cap (the steps are still completed). */
 int lbehd_step(lbehd_handle *h, int n);
 
 /* Set the electrode potentials used from the next step on (Dirichlet values of the
  * Gauss law; the programmable switching of the Results). n must equal cfg->n_electrodes. */
 int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n);
 
-/* Synchronise the stream and fill *out with the last step's observables. Returns
- * LBEHD_ERR_NONFINITE if a non-finite value was detected. */
+/* Sum the last two steps' observable partials on the device (fixed order, FP64; the drag
+ * force uses both), synchronise the stream and fill *out with the last step's observables.
+ * Returns LBEHD_ERR_NONFINITE if a non-finite value was detected. */
 int lbehd_observe(lbehd_handle *h, lbehd_obs *out);
 
 /* Copy one array (enum lbehd_array) to host memory dst of at least *bytes; synchronises. */
