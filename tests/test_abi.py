@@ -74,3 +74,24 @@ def test_batch_init_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert b"share dim" in lib.lbehd_last_error(None)
     assert lib.lbehd_batch_size(None) == 0
     assert lib.lbehd_batch_instance(None, 0) is None
+
+
+def test_entry_points_reject_a_null_handle_without_a_gpu(lib):
+    """Every handle-taking call returns LBEHD_ERR_INVALID_ARG for a null handle and leaves a
+    message, before any CUDA call (so this runs without a device)."""
+    from paper_2608_12868_b300 import lbehd
+    P = ctypes.c_void_p
+    v = ctypes.c_longlong()
+    obs = lbehd.Obs()
+    calls = {
+        "lbehd_step": lambda: lib.lbehd_step(None, 1),
+        "lbehd_observe": lambda: lib.lbehd_observe(None, ctypes.byref(obs)),
+        "lbehd_set_option": lambda: lib.lbehd_set_option(None, 1, 0),
+        "lbehd_get_option": lambda: lib.lbehd_get_option(None, 1, ctypes.byref(v)),
+        "lbehd_save_state": lambda: lib.lbehd_save_state(None, P(16)),
+        "lbehd_load_state": lambda: lib.lbehd_load_state(None, P(16)),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+        assert lib.lbehd_last_error(None), name
+    assert lib.lbehd_state_bytes(None) == 0
