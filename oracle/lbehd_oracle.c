@@ -14,7 +14,7 @@
  * Eq. 15 and the momentum/charge collision equations are written: m = M f,
  * m* = (I - S) m + S m_eq + (I - S/2) M C, f* = M^-1 m*.
  *
- * Readings of points the paper leaves open (each is listed in the design notes):
+ * Readings of points the paper leaves open:
  *  - Phase field and momentum use D2Q9 / D3Q19; charge uses D2Q5 / D3Q7.
  *  - Moment basis: raw monomials with the second-order block split into trace and
  *    deviatoric parts; all moments of order >= 3 relax at rate 1.
@@ -58,6 +58,7 @@ typedef struct {
     double cos12, cos13, cos23;   /* wetting angles on substrate solid (class 1) */
     double mobility, W, alpha;
     double body[3];
+    double body1[3];              /* force density on the droplet phase: Phi_1 body1 */
     double s_bulk;
     double poisson_tol;
     int poisson_max_iter;
@@ -157,7 +158,6 @@ void oracle_normals(const oprm_t *p, const olat_t *L, const uint8_t *solid, int3
 
 /* ------------------------------------------------------------------ Poisson */
 
-/* Face coefficient between fluid node i and neighbour j for the operator of Eq. 13. */
 /* Eq. 11: the coefficients Upsilon_i of the ternary free energy from the pairwise surface
  * tensions, Upsilon_i = gamma_ij + gamma_ik - gamma_jk ({i, j, k} = {1, 2, 3}), and
  * Upsilon_T = 3 / sum_i (1 / Upsilon_i). */
@@ -169,6 +169,7 @@ void oracle_upsilon(double g12, double g13, double g23, double Y[3], double *YT)
     *YT = 3.0 / (1.0 / Y[0] + 1.0 / Y[1] + 1.0 / Y[2]);
 }
 
+/* Face coefficient between fluid node i and neighbour j for the operator of Eq. 13. */
 static double eps_face(const ost_t *s, long i, long j)
 {
     if (!s->solid[j])
@@ -492,7 +493,10 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
 
     /* 7. E = -grad phi (isotropic stencil; zero-flux solid neighbours mirror the
      *    node's own value, Dirichlet neighbours hold their value), grad eps from the
-     *    eps field, electric force F_e = rho_e E - |E|^2 grad(eps) / 2 (Eq. 12). */
+     *    eps field, electric force F_e = rho_e E - |E|^2 grad(eps) / 2 (Eq. 12).
+     *    Total force F = F_s + F_e + body + Phi_1 body1: a uniform body force and one
+     *    acting on the droplet phase alone (gravity on a droplet much denser than its
+     *    surroundings, the sliding-droplet validation of the Methods). */
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         for (int a = 0; a < 3; a++)
@@ -514,7 +518,8 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
         for (int a = 0; a < 3; a++) {
             s->E[a * N + i] = -gp[a];
             s->Fe[a * N + i] = s->rho[i] * (-gp[a]) - 0.5 * E2 * ge[a];
-            s->F[a * N + i] = s->Fs[a * N + i] + s->Fe[a * N + i] + p->body[a];
+            s->F[a * N + i] = s->Fs[a * N + i] + s->Fe[a * N + i] + p->body[a] +
+                              s->Phi[i] * p->body1[a];
         }
     }
 

@@ -135,7 +135,8 @@ class _OPrm(ctypes.Structure):
                 ("cos23", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("W", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("body", ctypes.c_double * 3),
-                ("s_bulk", ctypes.c_double), ("poisson_tol", ctypes.c_double),
+                ("body1", ctypes.c_double * 3), ("s_bulk", ctypes.c_double),
+                ("poisson_tol", ctypes.c_double),
                 ("poisson_max_iter", ctypes.c_int), ("n_electrodes", ctypes.c_int),
                 ("V", ctypes.c_double * 64)]
 
@@ -253,6 +254,7 @@ class OracleSim:
         self.post = z(max(Q, QS))
         self.cg = [z(1)[0] for _ in range(4)]
         self.step_count = 0
+        self._drop_prev = self._drop_cur = None   # (M1, sum Phi_1 u) of the last two steps
         self.poisson_iters = 0
         self.poisson_resid = 0.0
         self._prm = self._make_prm()
@@ -283,6 +285,7 @@ class OracleSim:
         s.mobility, s.W, s.alpha = p["mobility"], p["W"], p["alpha"]
         for a in range(3):
             s.body[a] = p.get("body", (0, 0, 0))[a]
+            s.body1[a] = p.get("body_droplet", (0, 0, 0))[a]
         s.s_bulk = p.get("s_bulk", 1.0)
         s.poisson_tol = p.get("oracle_poisson_tol", 1e-12)
         s.poisson_max_iter = p.get("oracle_poisson_max_iter", 200000)
@@ -320,31 +323,63 @@ class OracleSim:
                                    ctypes.byref(self._ls), ctypes.byref(self._st))
             bad += rc != 0
             self.step_count += 1
+            self._drop_prev, self._drop_cur = self._drop_cur, self._droplet_momentum()
             self.poisson_iters = self._st.poisson_iters
             self.poisson_resid = self._st.poisson_resid
         return bad
 
     # ----------------------------------------------------------------- observables
 
+    def _droplet_momentum(self):
+        """(M1, sum Phi_1 u) over fluid nodes, of the fields of the step just taken."""
+        P1 = self.Phi[0] * (self.solid == 0)
+        return P1.sum(), np.array([(P1 * self.u[a]).sum() for a in range(3)])
+
+    def set_body_force(self, body=None, body_droplet=None):
+        """Change the uniform and the droplet-phase body force from the next step on."""
+        if body is not None:
+            self.params["body"] = tuple(body)
+        if body_droplet is not None:
+            self.params["body_droplet"] = tuple(body_droplet)
+        for a in range(3):
+            self._prm.body[a] = self.params.get("body", (0, 0, 0))[a]
+            self._prm.body1[a] = self.params.get("body_droplet", (0, 0, 0))[a]
+
     def observables(self):
         """Droplet observables of the fields computed in the last step (FP64 sums over
         fluid nodes): mass M1 = sum Phi_1, centroid sum Phi_1 x / M1, velocity
-        sum Phi_1 u / M1, electric force on the droplet sum Phi_1 F_e, total electric
-        force sum F_e, per-component mass sum Phi_i and total charge sum rho_e."""
+        V = sum Phi_1 u / M1, electric force on the droplet sum Phi_1 F_e, total electric
+        force sum F_e, per-component mass sum Phi_i and total charge sum rho_e.
+
+        Drag (Results, the force balance of the migrating droplet, Eqs. 1 and 5: the
+        driving force minus the droplet's inertia m dV/dt, which is -m dV/dt when nothing
+        drives it): f_drag = f_ele + M1 (body + body_droplet) - M1 (V^n - V^{n-1}), with
+        unit density so that m = M1, dV/dt the difference of the last two steps'
+        velocities, and the body forces' share on the droplet M1 (body + body_droplet).
+        Zero until two steps have been taken."""
         fluid = (self.solid == 0)
         nz, ny, nx = self.shape
         zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         P1 = self.Phi[0] * fluid
         M1 = P1.sum()
+        inv = 1.0 / M1 if M1 != 0.0 else 0.0
         out = {
             "M1": M1,
-            "centroid": np.array([(P1 * xx).sum(), (P1 * yy).sum(), (P1 * zz).sum()]) / M1,
-            "velocity": np.array([(P1 * self.u[a]).sum() for a in range(3)]) / M1,
+            "centroid": np.array([(P1 * xx).sum(), (P1 * yy).sum(), (P1 * zz).sum()]) * inv,
+            "velocity": np.array([(P1 * self.u[a]).sum() for a in range(3)]) * inv,
             "f_ele": np.array([(P1 * self.Fe[a]).sum() for a in range(3)]),
             "f_ele_total": np.array([(self.Fe[a] * fluid).sum() for a in range(3)]),
             "mass": np.array([(self.Phi[c] * fluid).sum() for c in range(3)]),
             "charge": (self.rho * fluid).sum(),
         }
+        drag = np.zeros(3)
+        if self._drop_prev is not None:
+            M1p, Pp = self._drop_prev
+            Vp = Pp / M1p if M1p != 0.0 else np.zeros(3)
+            push = (np.asarray(self.params.get("body", (0, 0, 0)), dtype=np.float64) +
+                    np.asarray(self.params.get("body_droplet", (0, 0, 0)), dtype=np.float64))
+            drag = out["f_ele"] + M1 * push - M1 * (out["velocity"] - Vp)
+        out["f_drag"] = drag
         return out
 
     def poisson(self):

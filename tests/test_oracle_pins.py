@@ -505,3 +505,100 @@ def test_charge_diffusion_variance(oracle_mod, dim):
     s.step(101)
     t = s.step_count - 1
     assert abs((var(s.rho) - v0) / (2 * 0.05 * t) - 1) < 0.02
+
+
+def _charge_in_uniform_flow(O, dim, U, alpha, steps):
+    """A small charge blob (sigma = 0, so no conduction; amplitude 1e-7, so its own field
+    exerts a negligible force) in a fully periodic box whose fluid moves uniformly at
+    u = (U, 0, 0). A uniform background of opposite charge makes the box neutral, so the
+    Gauss-law problem without Dirichlet nodes is consistent; it is translation invariant and
+    drops out of the blob's moments. Momentum and charge populations start at their
+    equilibria with that velocity. Returns the blob's centroid shift along x and its
+    variance growth along x and along y."""
+    shape = (1, 40, 96) if dim == 2 else (24, 24, 64)
+    zz, yy, xx = _grid(shape)
+    solid, elec = _periodic(shape)
+    one = np.ones(shape)
+    phi = np.stack([0 * one, 0 * one, one])
+    p = W.make_params(V=(), alpha=alpha)
+    p["sig"] = (0.0, 0.0, 0.0)
+    s = _sim(O, dim, shape, solid, elec, phi, p)
+    u = np.array([U, 0.0, 0.0])
+    ef, cs2 = s.Lf.e.astype(float), s.Lf.cs2
+    for n in range(s.Lf.Q):
+        eu = ef[n] @ u
+        s.g[n] = s.Lf.w[n] * (1 + eu / cs2 + eu * eu / (2 * cs2 * cs2) - u @ u / (2 * cs2))
+    x0, yc, zc = 20.0, shape[1] / 2 - 0.5, shape[0] / 2 - 0.5
+    r2 = (xx - x0) ** 2 + (yy - yc) ** 2 + ((zz - zc) ** 2 if dim == 3 else 0)
+    blob = 1e-7 * np.exp(-r2 / 8.0)
+    Q = blob.sum()
+    bg = -Q / blob.size
+    es, cs2s = s.Ls.e.astype(float), s.Ls.cs2
+    for q in range(s.Ls.Q):
+        s.frho[q] = s.Ls.w[q] * (blob + bg) * (1 + (es[q] @ u) / cs2s)
+
+    def stats(b):
+        c = (b * xx).sum() / Q
+        return c, (b * (xx - c) ** 2).sum() / Q, (b * (yy - yc) ** 2).sum() / Q
+
+    c0, vx0, vy0 = stats(blob)
+    s.step(steps)
+    # frho holds the populations after `steps` collide + stream passes
+    b1 = s.frho.sum(0) - bg
+    assert abs(b1.sum() / Q - 1) < 1e-9
+    c1, vx1, vy1 = stats(b1)
+    return c1 - c0, vx1 - vx0, vy1 - vy0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_charge_advection_in_uniform_flow(oracle_mod, dim):
+    """Eq. 14 with u: the rho_e u flux of the charge equation (the e.u / c_s^2 term of the
+    charge equilibrium, Eq. 20b's collision) carries a blob at exactly the fluid velocity,
+    so its centroid moves by U per step; and with the R = w e.d(rho_e u)/dt / c_s^2 term of
+    the charge collision the blob still spreads isotropically, by 2 alpha t along and
+    across the flow. Without R (or with its sign flipped) the scheme's O(dt) error reduces
+    the along-flow diffusivity by about (tau - 1/2) U^2 (twice that): 3 % (6 %) of alpha in
+    2D and 3.4 % (7.4 %) in 3D at U = 0.1, which the 1 % bar catches. A dropped or
+    sign-flipped e.u term fails the centroid check."""
+    U, alpha, steps = (0.1, 0.05, 160) if dim == 2 else (0.1, 0.05, 100)
+    shift, dvx, dvy = _charge_in_uniform_flow(oracle_mod, dim, U, alpha, steps)
+    assert abs(shift / (U * steps) - 1) < 1e-6, shift
+    assert abs(dvy / (2 * alpha * steps) - 1) < 0.02, dvy
+    assert abs(dvx / dvy - 1) < 0.01, (dvx, dvy)
+
+
+@pytest.mark.parametrize("which", ["droplet", "uniform"])
+def test_drag_force_balance_in_a_uniform_mixture(oracle_mod, which):
+    """Drag as the force balance of the Results (driving force minus the droplet's inertia
+    m dV/dt; -m dV/dt with no drive). In a periodic box filled with a uniform mixture
+    Phi_1 = Phi_2 = 1/2 every site accelerates as a whole: u^n = (n + 1/2) F. A uniform
+    body force b moves the droplet phase with everything else, so it meets no drag. A body
+    force b1 on the droplet phase alone (force density Phi_1 b1) drives M1 b1 into the
+    droplet but accelerates only at b1 / 2 per step, because every site carries as much
+    lubricant: the drag is M1 b1 / 2, the force handed to the lubricant. A mistake in the
+    inertia term (a sign, the M1 factor, a lag other than one step) or in the body forces'
+    share changes these values."""
+    shape = (1, 6, 5)
+    one = np.ones(shape)
+    phi = np.stack([0.5 * one, 0.5 * one, 0 * one])
+    b = np.array([3e-6, -2e-6, 0.0])
+    kw = {"body": tuple(b)} if which == "uniform" else {}
+    p = W.make_params(V=(), **kw)
+    if which == "droplet":
+        p["body_droplet"] = tuple(b)
+    s = _sim(oracle_mod, 2, shape, *_periodic(shape), phi, p)
+    s.step(1)
+    assert np.all(s.observables()["f_drag"] == 0.0)   # no V^{n-1} yet
+    s.step(9)
+    o = s.observables()
+    n = s.step_count - 1
+    acc = b if which == "uniform" else 0.5 * b
+    assert np.abs(o["velocity"] - (n + 0.5) * acc).max() < 1e-15
+    assert np.all(o["f_ele"] == 0.0)
+    expect = np.zeros(3) if which == "uniform" else 0.5 * o["M1"] * b
+    assert np.abs(o["f_drag"] - expect).max() < 1e-9 * o["M1"] * np.abs(b).max()
+    # switched off: the mixture coasts, dV/dt = 0 and nothing drives it, so no drag
+    s.set_body_force(body=(0, 0, 0), body_droplet=(0, 0, 0))
+    s.step(3)
+    o = s.observables()
+    assert np.abs(o["f_drag"]).max() < 1e-9 * o["M1"] * np.abs(b).max()
