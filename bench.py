@@ -155,13 +155,18 @@ def max_over_ranks(world, value, device=None):
     return float(t.item())
 
 
-def cpu_oracle_rate(workload, steps, budget_s=None):
-    """Time the FP64 oracle as it stands on the host cores: (MLUPS, steps run, cores)."""
+def cpu_oracle_rate(workload, steps, budget_s=None, warm_steps=0, threads=None):
+    """Time the FP64 oracle as it stands on the host cores: `warm_steps` untimed coupled
+    steps (the first solves start from phi = 0 and take the most CG iterations), then up to
+    `steps` timed ones, stopping early once `budget_s` seconds have been spent.
+    Returns (MLUPS, timed steps, threads used, seconds)."""
     from oracle import oracle as O
-    cores = len(os.sched_getaffinity(0))
+    cores = threads or len(os.sched_getaffinity(0))
     O.set_threads(cores)
     w = workload
     sim = O.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    if warm_steps:
+        sim.step(warm_steps)
     done, t0 = 0, time.perf_counter()
     while done < steps:
         sim.step(1)
@@ -173,26 +178,46 @@ def cpu_oracle_rate(workload, steps, budget_s=None):
 
 
 def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores, on the same workload and metric. One benchmark
+    step of this arm is ONE coupled step of the whole lattice (the oracle needs seconds per
+    step): --warmup untimed steps, then --steps timed ones (fewer if the time budget
+    LBEHD_REF_BUDGET_S runs out first); `steps` and `ms_per_step` report what ran."""
     if rank != 0:
         return
     from paper_2608_12868_b300 import workloads as W
     w = W.WORKLOADS[args.workload]()
-    total = args.steps + args.warmup
     budget = float(os.environ.get("LBEHD_REF_BUDGET_S", "150"))
-    mlups, done, cores, dt = cpu_oracle_rate(w, total, budget_s=budget)
-    sample = (f"{done} coupled steps of the full {'x'.join(map(str, w.shape[::-1]))} lattice "
-              f"(of {total} requested; capped at {budget:.0f} s), FP64, {cores} threads")
+    mlups, done, cores, dt = cpu_oracle_rate(w, args.steps, budget_s=budget,
+                                             warm_steps=args.warmup)
+    sample = (f"{done} timed coupled steps (after {args.warmup} untimed) of the full "
+              f"{'x'.join(map(str, w.shape[::-1]))} lattice (of {args.steps} requested; "
+              f"capped at {budget:.0f} s), FP64, {cores} threads")
     line = {
         "metric": METRIC, "value": mlups, "unit": UNIT, "impl": "reference", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / done * 1e3 * args.lb_steps,
+        "steps": done, "warmup": args.warmup, "ms_per_step": dt / done * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "sites": w.sites, "lb_steps_per_step": args.lb_steps},
+        "config": {"workload": w.name, "sites": w.sites, "lb_steps_per_step": 1},
         "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_oracle_baselines(args):
+    """The CPU baselines of the plan: the FP64 oracle single-threaded and on every host core,
+    on the 2D 128x64 workload (all 2000 steps) and on the 3D 128x64x64 workload (its first
+    steps). One JSON line per measurement."""
+    from paper_2608_12868_b300 import workloads as W
+    cores = len(os.sched_getaffinity(0))
+    plan = [("droplet_2d_128x64", 2000, 0), ("droplet_3d_128x64x64", args.oracle_3d_steps, 0)]
+    for name, steps, warm in plan:
+        w = W.WORKLOADS[name]()
+        for threads in (1, cores):
+            mlups, done, used, dt = cpu_oracle_rate(w, steps, warm_steps=warm, threads=threads)
+            print(json.dumps({"oracle_baseline": name, "steps": done, "threads": used,
+                              "seconds": dt, "value": mlups, "unit": UNIT}), flush=True)
 
 
 def run_ours(args, world, rank, local):
@@ -289,6 +314,10 @@ def run_ours(args, world, rank, local):
     step_gbs = step_bytes / (ms / 1e3 / (L * args.steps)) / 1e9
     share = {k: round(v[0] / prof_ms, 4) for k, v in prof.items()}
 
+    others = {}
+    if args.other_workloads:
+        for name, n in (("droplet_2d_128x64", 2000), ("transport_3d_384x128x96", 4000)):
+            others[name] = run_workload_line(args, dev, name, n, peak, peak_kind)
     batched = None
     if args.batched > 0:
         batched = run_batched(args, dev, value / world, peak, peak_kind, clk)
@@ -296,15 +325,17 @@ def run_ours(args, world, rank, local):
     if args.adjoint_segments > 0 and args.adjoint_seg_steps > 0:
         adjoint = run_adjoint(args, dev)
     clk.stop()
-    for extra in (batched, adjoint):
+    for extra in (batched, adjoint, *others.values()):
         if extra is not None:
             extra["clocks"] = clk.summary(*extra.pop("window"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, done, cores, dt = cpu_oracle_rate(w, args.cpu_steps)
+        mlups, done, cores, dt = cpu_oracle_rate(w, args.cpu_steps, budget_s=args.cpu_seconds,
+                                                 warm_steps=1)
         cpu = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {done} coupled steps of the same lattice, FP64, {dt:.1f} s"}
+               "sample": f"{done} coupled steps of the same lattice after one untimed step, "
+                         f"FP64, {dt:.1f} s"}
 
     if rank == 0:
         clocks = clk.summary(t_region0, t_region1)
@@ -340,17 +371,74 @@ def run_ours(args, world, rank, local):
                 "achieved_gbs": step_gbs, "frac_of_measured": step_gbs / peak,
                 "frac_of_nominal_8tbs": step_gbs / 8000.0},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * len(Vh),
-                    "d2h_bytes_per_step": 2 * 16 * 8 + 4},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": Vh.nbytes,
+                    # lbehd_observe reads back the last two steps' 16 observable sums
+                    # (FP64), the error flag, the CG scalars (104 B) and the barrier error word
+                    "d2h_bytes_per_step": 2 * 16 * 8 + 4 + 104 + 4},
             "gpu_launches": launches,
             "clocks": clocks,
             "autotune": tuned,
             "batched": batched,
             "adjoint": adjoint,
+            "other_workloads": others or None,
             "obs_status": obs["status"],
             "mass_drift": float(np.abs(obs["mass"] / warm_obs["mass"] - 1).max()),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_workload_line(args, dev, name, steps, peak, peak_kind):
+    """Throughput of another configuration in the benchmark's launch configuration (step
+    graphs, persistent Gauss-law solve, autotuned collide kernel): `steps` coupled steps
+    timed with CUDA events after a warm-up, inputs resident. A workload with an electrode
+    schedule switches electrodes at its scheduled steps (the switch synchronises, between
+    timed chunks)."""
+    import torch
+    from paper_2608_12868_b300 import lbehd
+    from paper_2608_12868_b300 import workloads as W
+    w = W.WORKLOADS[name]()
+    stream = torch.cuda.Stream(dev)
+    sim = lbehd.Simulation(w, stream=stream, device=dev.index, poisson_mode=lbehd.POISSON_GRAPH)
+    sim.step(1)
+    variant, _ = sim.autotune(reps=5)
+    sched = sorted(w.schedule) if len(w.schedule) > 1 else []
+    warm = min(args.warmup * 100, 1000)
+    sim.step(warm)
+    torch.cuda.synchronize(dev)
+    t = 1 + warm
+    m0 = sim.observe()["mass"]
+    st0 = sim.stats()
+    # chunks between electrode switches inside the timed window
+    cuts = [k for k, _ in sched if t < k < t + steps]
+    bounds = [t] + cuts + [t + steps]
+    ms = 0.0
+    t_region0 = time.time()
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        for k, V in sched:
+            if k == a:
+                sim.set_electrodes(V)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(b - a)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+    t_region1 = time.time()
+    st1 = sim.stats()
+    o = sim.observe()
+    iters = (st1["poisson_iters"] - st0["poisson_iters"]) / steps
+    sb, sp = STEP_BYTES[w.dim]
+    gbs = w.sites * (sb + sp * iters) / (ms / 1e3 / steps) / 1e9
+    out = {"workload": name, "sites": w.sites, "value": w.sites * steps / (ms / 1e3) / 1e6,
+           "unit": UNIT, "lb_steps_timed": steps, "timed_from_step": t,
+           "electrode_switches_timed": len(cuts), "ms_per_lb_step": ms / steps,
+           "poisson_iters_per_lb_step": iters, "step_gbs_model": gbs,
+           "step_model_frac": gbs / peak, "peak_source": peak_kind,
+           "collide_variant": VARIANT_NAMES.get(variant, str(variant)),
+           "status": o["status"], "mass_drift": float(np.abs(o["mass"] / m0 - 1).max()),
+           "window": (t_region0, t_region1)}
+    sim.close()
+    return out
 
 
 def run_batched(args, dev, plain_mlups, peak, peak_kind, clk):
@@ -573,10 +661,20 @@ def main():
     ap.add_argument("--adjoint-segments", type=int, default=20,
                     help="segments of the differentiable-control schedule (0: skip the adjoint)")
     ap.add_argument("--adjoint-seg-steps", type=int, default=200)
+    ap.add_argument("--other-workloads", type=int, default=1,
+                    help="1: also time the 2D 128x64 run (2000 steps) and the 384x128x96 "
+                         "transport run (4000 steps, electrode switches); 0: skip")
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=8,
+                    help="timed oracle steps of the cpu_baseline (after one untimed step)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="time budget of the cpu_baseline's timed oracle steps")
+    ap.add_argument("--oracle-baselines", action="store_true",
+                    help="only time the FP64 oracle on 1 and on all host cores (2D 128x64, "
+                         "2000 steps; 3D 128x64x64, --oracle-3d-steps steps)")
+    ap.add_argument("--oracle-3d-steps", type=int, default=25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run a profiler window of this many eager steps (for ncu)")
@@ -589,6 +687,9 @@ def main():
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     if args.profile_steps or args.profile_adjoint:
         run_profile_window(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.oracle_baselines:
+        run_oracle_baselines(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBEHD_ABI_VERSION 2
+#define LBEHD_ABI_VERSION 3
 
 #define LBEHD_OK 0
 #define LBEHD_ERR_INVALID_ARG (-1)
@@ -82,6 +82,11 @@ typedef struct lbehd_config {
     double W;                /* interface width (5) */
     double alpha;            /* charge diffusivity of Eq. 14 */
     double body_force[3];    /* uniform body force density added to F */
+    double body_force_droplet[3]; /* force density on the droplet phase alone: F gains
+                                   * Phi_1 * body_force_droplet (gravity on a droplet much
+                                   * denser than its surroundings, the sliding droplet of the
+                                   * Methods' validation; zero for the electrically driven
+                                   * runs) */
     double s_bulk;           /* relaxation rate of the trace of the momentum flux (1) */
     double poisson_tol;      /* relative residual ||b - A phi||_2 / ||b||_2 to stop at */
     int poisson_max_iter;    /* cap on preconditioned-CG iterations per step */
@@ -109,7 +114,11 @@ typedef struct lbehd_obs {
     double velocity[3];      /* sum Phi_1 u / M1 */
     double f_ele[3];         /* electric force on the droplet, sum Phi_1 F_e */
     double f_ele_total[3];   /* sum F_e over the fluid */
-    double f_drag[3];        /* f_ele - M1 (V^n - V^{n-1}): drag from the force balance */
+    double f_drag[3];        /* drag from the force balance (Results, Eqs. 1 and 5): the
+                              * driving force on the droplet minus its inertia,
+                              * f_ele + M1 (body_force + body_force_droplet) - M1 (V^n - V^{n-1})
+                              * (unit density, m = M1), with the body forces in effect when
+                              * lbehd_observe is called; -M1 dV/dt for an undriven droplet */
     double mass[3];          /* sum Phi_i, per component */
     double charge;           /* sum rho_e */
     int poisson_iters;       /* CG iterations of the last step's Poisson solve */
@@ -155,6 +164,14 @@ int lbehd_step(lbehd_handle *h, int n);
 /* Set the electrode potentials used from the next step on (Dirichlet values of the
  * Gauss law; the programmable switching of the Results). n must equal cfg->n_electrodes. */
 int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n);
+
+/* Set the uniform and the droplet-phase body force densities (3 components each, as
+ * cfg->body_force and cfg->body_force_droplet) used from the next step on: the sliding and
+ * deceleration runs switch the drive on and off. Either pointer may be NULL to keep that
+ * force. Synchronises the stream and discards captured step graphs (the next step captures
+ * them again). A recorded adjoint run is dropped (its replays would no longer match).
+ * Errors: LBEHD_ERR_INVALID_ARG (null handle, non-finite value, instance of a batch). */
+int lbehd_set_body_force(lbehd_handle *h, const double *body, const double *body_droplet);
 
 /* Sum the last two steps' observable partials on the device (fixed order, FP64; the drag
  * force uses both), synchronise the stream and fill *out with the last step's observables.

@@ -228,6 +228,7 @@ int oracle_poisson(const oprm_t *p, const olat_t *S, ost_t *s)
     double *b = s->qsrc; /* borrowed as the right-hand side; rewritten later */
     double *diag = s->post;
 
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         if (s->solid[i]) {
             s->pot[i] = is_dirichlet(s, i) ? dirichlet_value(p, s, i) : 0.0;
@@ -248,6 +249,7 @@ int oracle_poisson(const oprm_t *p, const olat_t *S, ost_t *s)
     }
     double bnorm = sqrt(dot_fluid(s, N, b, b));
     if (bnorm == 0.0) {
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < N; i++)
             if (!s->solid[i])
                 s->pot[i] = 0.0;
@@ -256,6 +258,7 @@ int oracle_poisson(const oprm_t *p, const olat_t *S, ost_t *s)
         return 0;
     }
     poisson_apply(p, S, s, s->pot, Ad);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         r[i] = s->solid[i] ? 0.0 : b[i] - Ad[i];
         z[i] = r[i] / diag[i];
@@ -267,6 +270,7 @@ int oracle_poisson(const oprm_t *p, const olat_t *S, ost_t *s)
     while (rn > p->poisson_tol * bnorm && it < p->poisson_max_iter) {
         poisson_apply(p, S, s, d, Ad);
         double alpha = rz / dot_fluid(s, N, d, Ad);
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < N; i++) {
             if (s->solid[i])
                 continue;
@@ -277,6 +281,7 @@ int oracle_poisson(const oprm_t *p, const olat_t *S, ost_t *s)
         double rz_new = dot_fluid(s, N, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < N; i++)
             if (!s->solid[i])
                 d[i] = z[i] + beta * d[i];
@@ -391,6 +396,7 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
 
     /* 2. Wetting ghosts (Eq. 20a) on boundary solid nodes, explicit in the fluid
      *    values at f = s + e_k: Phi_i(s) = Phi_i(f) - |e_k| * RHS_i(Phi(f)). */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         if (!s->solid[i] || s->normal[i] == 0)
             continue;
@@ -413,6 +419,7 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
     }
 
     /* 3. Phase-dependent properties, linear in Phi_i (Table 1 values per phase). */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         double e = 0.0, sg = 0.0;
         for (int c = 0; c < 3; c++) {
@@ -544,6 +551,7 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
 
     /* Backward differences are zero on the first step. */
     if (!s->have_prev) {
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < N; i++) {
             for (int c = 0; c < 3; c++)
                 for (int a = 0; a < 3; a++)
@@ -668,6 +676,7 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
     stream_pull(p, Ls, s, s->post, s->frho);
 
     /* 10. Products kept for the next step's backward differences. */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         for (int c = 0; c < 3; c++)
             for (int a = 0; a < 3; a++)

@@ -179,7 +179,7 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         Fe[a] = rho * E[a] - 0.5f * E2 * geps[a];
-        F[a] = Fs[a] + Fe[a] + P.body[a];
+        F[a] = Fs[a] + Fe[a] + P.body[a] + Pc[0] * P.body1[a];
     }
     float gn[3], lam[3], ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f, FPhi[3][3];
 #pragma unroll
@@ -468,10 +468,12 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
     for (int n = 0; n < Q; n++)
         A.lg_out[(size_t)n * N + i] = gsb[n] + edot<L>(n, ub);
 
-    // ---- forces: F = Fs + Fe + body; Fe = rho E - E2 geps / 2; Fs = sum mu_c gP_c
+    // ---- forces: F = Fs + Fe + body + Phi_1 body1; Fe = rho E - E2 geps / 2;
+    //      Fs = sum mu_c gP_c
     float gPb[3][3], gpotb[3], gepsb[3], Eb[3], E2b = 0.0f, mub[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
+        Pcb[0] += Fb[a] * P.body1[a];
         rhob += Fb[a] * E[a];
         Eb[a] = Fb[a] * rho;
         E2b += -0.5f * Fb[a] * geps[a];

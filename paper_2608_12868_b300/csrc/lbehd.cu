@@ -937,6 +937,7 @@ int set_params(lbehd_handle *h)
         P.eps[k] = (float)c.eps[k];
         P.sig[k] = (float)c.sigma[k];
         P.body[k] = (float)c.body_force[k];
+        P.body1[k] = (float)c.body_force_droplet[k];
     }
     // Eq. 11
     const double Y1 = c.gamma12 + c.gamma13 - c.gamma23;
@@ -1453,7 +1454,9 @@ int observe_fill(lbehd_handle *h, const double *o, int flag, lbehd_obs *out)
         out->f_ele[a] = o[7 + a];
         out->f_ele_total[a] = o[10 + a];
         const double Vp = M1p != 0.0 ? o[NOBS + 4 + a] / M1p : 0.0;
-        out->f_drag[a] = h->step >= 2 ? o[7 + a] - M1 * (out->velocity[a] - Vp) : 0.0;
+        const double drive = h->cfg.body_force[a] + h->cfg.body_force_droplet[a];
+        out->f_drag[a] =
+            h->step >= 2 ? o[7 + a] + M1 * drive - M1 * (out->velocity[a] - Vp) : 0.0;
     }
     out->mass[0] = M1;
     out->mass[1] = o[13];
@@ -3045,6 +3048,34 @@ int lbehd_set_electrodes(lbehd_handle *h, const double *V, int n)
     // pageable source: the copy is staged before this call returns
     CK(h, cudaMemcpyAsync(h->V, V, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    return LBEHD_OK;
+}
+
+int lbehd_set_body_force(lbehd_handle *h, const double *body, const double *body_droplet)
+{
+    if (!h)
+        return fail(nullptr, LBEHD_ERR_INVALID_ARG, "null handle");
+    if (h->batch_owned)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: body forces are set at init");
+    for (int k = 0; k < 3; k++)
+        if ((body && !std::isfinite(body[k])) || (body_droplet && !std::isfinite(body_droplet[k])))
+            return fail(h, LBEHD_ERR_INVALID_ARG, "body force must be finite");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; k++) {
+        if (body)
+            h->cfg.body_force[k] = body[k];
+        if (body_droplet)
+            h->cfg.body_force_droplet[k] = body_droplet[k];
+        h->P.body[k] = (float)h->cfg.body_force[k];
+        h->P.body1[k] = (float)h->cfg.body_force_droplet[k];
+    }
+    for (auto &row : h->gexec)   // captured graphs hold the previous parameters
+        for (auto &e : row)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    h->adj.have = false;
     return LBEHD_OK;
 }
 

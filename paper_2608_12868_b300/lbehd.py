@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
                 ("theta12", ctypes.c_double), ("theta13", ctypes.c_double),
                 ("theta23", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("W", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("body_force", _D3), ("s_bulk", ctypes.c_double),
+                ("body_force", _D3), ("body_force_droplet", _D3), ("s_bulk", ctypes.c_double),
                 ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
                 ("poisson_mode", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
                 ("poisson_fixed_iters", ctypes.c_int), ("mg_nu", ctypes.c_int),
@@ -90,7 +90,8 @@ class LBEHDError(RuntimeError):
 _lib = None
 
 EXPORTS = ("lbehd_abi_version", "lbehd_config_size", "lbehd_init", "lbehd_step",
-           "lbehd_set_electrodes", "lbehd_observe", "lbehd_copy_out", "lbehd_device_ptr",
+           "lbehd_set_electrodes", "lbehd_set_body_force", "lbehd_observe", "lbehd_copy_out",
+           "lbehd_device_ptr",
            "lbehd_launch_count", "lbehd_set_option", "lbehd_get_option", "lbehd_get_stats", "lbehd_profile_enable",
            "lbehd_profile_read", "lbehd_autotune", "lbehd_adjoint_forward",
            "lbehd_adjoint_backward", "lbehd_adjoint_get_info", "lbehd_state_bytes",
@@ -118,6 +119,8 @@ def load():
     lib.lbehd_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(P)]
     lib.lbehd_step.argtypes = [P, ctypes.c_int]
     lib.lbehd_set_electrodes.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.lbehd_set_body_force.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
     lib.lbehd_observe.argtypes = [P, ctypes.POINTER(Obs)]
     lib.lbehd_copy_out.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t]
     lib.lbehd_device_ptr.argtypes = [P, ctypes.c_int, ctypes.POINTER(P),
@@ -197,6 +200,7 @@ def make_config(w, c, *, poisson_mode=POISSON_HOST, poisson_check_every=1, poiss
     for k in range(3):
         c.nu[k], c.eps[k], c.sigma[k] = p["nu"][k], p["eps"][k], p["sig"][k]
         c.body_force[k] = p.get("body", (0.0, 0.0, 0.0))[k]
+        c.body_force_droplet[k] = p.get("body_droplet", (0.0, 0.0, 0.0))[k]
     c.gamma12, c.gamma13, c.gamma23 = p["gamma12"], p["gamma13"], p["gamma23"]
     c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
     c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
@@ -331,6 +335,17 @@ class Simulation(_HandleOps):
     def step(self, n=1):
         """Advance n steps; returns 0 or -3 (a Poisson solve hit its cap)."""
         return self._check(self._lib.lbehd_step(self._h, int(n)), allow=(-3,))
+
+    def set_body_force(self, body=None, body_droplet=None):
+        """Uniform and droplet-phase body force densities from the next step on (None keeps
+        the current one)."""
+        arrs = [None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+                for b in (body, body_droplet)]
+        for a in arrs:
+            if a is not None and a.shape != (3,):
+                raise ValueError("body forces have 3 components")
+        ptrs = [None if a is None else _dptr(a, ctypes.c_double) for a in arrs]
+        self._check(self._lib.lbehd_set_body_force(self._h, *ptrs))
 
     def profile(self, enable=True):
         """Record per-kernel device time with CUDA events on the library's stream."""

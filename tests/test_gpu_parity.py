@@ -5,7 +5,10 @@ Bars (written here, derived from the target tolerances of the method):
 * populations: relative L-infinity max|f_gpu - f_oracle| / max|f_oracle| <= 1e-5 per
   population set after up to 100 steps (FP32 state against FP64);
 * fields Phi_i: absolute L-infinity <= 1e-5 (they are O(1));
-* droplet observables (centroid velocity, electric force, drag): 0.5 % of their magnitude;
+* droplet observables (centroid velocity, electric force): 0.5 % of their magnitude; the
+  drag (force balance: driving force minus M1 dV/dt) 0.5 % of max(|drag|, DRAG_FLOOR |f_ele|):
+  while the droplet still accelerates the drag is a small difference of two large terms, and
+  its FP32 error is set by that of f_ele and of M1 dV/dt, not by its own size;
 * per-component mass: conserved to 1e-6 relative on the GPU.
 """
 import numpy as np
@@ -17,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 POP_TOL = 1e-5
 OBS_TOL = 5e-3
+DRAG_FLOOR = 0.1
 
 
 @pytest.fixture(scope="module")
@@ -65,11 +69,13 @@ def compare_fields(sim, orc, phi_tol=1e-5):
         assert rel_linf(pot[fluid], orc.pot[fluid]) <= 1e-5
 
 
-def compare_obs(sim, orc, keys=("velocity", "f_ele", "f_ele_total"), tol=OBS_TOL):
+def compare_obs(sim, orc, keys=("velocity", "f_ele", "f_ele_total", "f_drag"), tol=OBS_TOL):
     og, oo = sim.observe(), orc.observables()
     for k in keys:
         a, b = np.asarray(og[k]), np.asarray(oo[k])
         scale = np.abs(b).max()
+        if k == "f_drag":
+            scale = max(scale, DRAG_FLOOR * np.abs(oo["f_ele"]).max())
         assert np.abs(a - b).max() <= tol * scale, (k, a, b)
     assert np.abs(og["centroid"] - oo["centroid"]).max() <= 1e-3
     assert np.abs(og["mass"] / oo["mass"] - 1).max() <= 1e-5
@@ -151,15 +157,24 @@ def test_droplet_2d_128x64_full_run(gpu, oracle_mod):
 
 def test_droplet_3d_128x64x64_full_size(gpu, oracle_mod):
     """The 3D 128x64x64 workload at full size, in the launch configuration the benchmark
-    times (graph replay with the device-side Poisson loop): every population after 3 steps."""
+    times (graph replay with the persistent Gauss-law solve, autotuned collide kernel):
+    every population set, the fields and the droplet observables after 3 and after 100
+    steps (the FP64 oracle's first 100 steps of this configuration)."""
     w = W.droplet_3d_128x64x64()
     sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
-    sim.step(3)
+    sim.step(1)
+    sim.autotune(reps=2)
+    sim.step(2)
     orc.step(3)
     assert sim.stats()["graph_launches"] == 2
     compare_populations(sim, orc)
     compare_fields(sim, orc)
-    compare_obs(sim, orc, keys=("f_ele", "f_ele_total"))
+    compare_obs(sim, orc)
+    sim.step(97)
+    orc.step(97)
+    compare_populations(sim, orc)
+    compare_fields(sim, orc)
+    compare_obs(sim, orc)
 
 
 @pytest.mark.parametrize("case", ["small_2d", "small_3d"])
@@ -225,15 +240,31 @@ def test_ragged_and_periodic_edge_cases(gpu, oracle_mod):
 
 
 def test_mass_conservation_long_run(gpu):
-    """Per-component mass over 1000 steps of the 3D 128x64x64 workload, FP32 state."""
+    """Per-component mass over the full 10 000 steps of the 3D 128x64x64 workload (FP32
+    state, the benchmark's launch configuration), checked every 2500 steps."""
     w = W.droplet_3d_128x64x64()
     sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     sim.step(1)
+    sim.autotune(reps=2)
     m0 = sim.observe()["mass"]
-    sim.step(1000)
-    o = sim.observe()
-    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6
-    assert o["status"] == 0
+    for _ in range(4):
+        sim.step(2500)
+        o = sim.observe()
+        assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6, o["mass"] / m0 - 1
+        assert o["status"] == 0
+
+
+def test_mid_3d_observables_long_run(gpu, oracle_mod):
+    """Droplet observables of a 40x24x24 copy of the 3D workload (pillars, film, droplet,
+    electrode) against the oracle every 250 steps over 1000 steps, in the benchmark's launch
+    configuration."""
+    w = W.droplet_3d(40, 24, 24, R=7.0, pillar_h=4, seed=21, name="mid_3d_40x24x24")
+    sim, orc = make_pair(gpu, oracle_mod, w, poisson_mode=gpu.POISSON_GRAPH)
+    for _ in range(4):
+        sim.step(250)
+        orc.step(250)
+        compare_obs(sim, orc)
+    compare_populations(sim, orc)
 
 
 def test_largest_workload_runs(gpu):
@@ -254,6 +285,28 @@ def test_largest_workload_runs(gpu):
     ref.step(22)
     for name in ("g", "pot", "pot_lo"):
         assert np.array_equal(sim.array(name), ref.array(name)), name
+
+
+def test_long_transport_two_switches(gpu):
+    """The 384x128x96 long-transport workload through two electrode switches of its
+    schedule (electrode k live during steps [2000 k, 2000 (k + 1))), 4500 steps: every
+    component's mass within 1e-6 and no error status."""
+    w = W.transport_3d_384x128x96()
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.step(1)
+    sim.autotune(reps=2)
+    m0 = sim.observe()["mass"]
+    done = 1
+    for k, V in sorted(w.schedule)[:3]:
+        if k > done:
+            sim.step(k - done)
+            done = k
+        sim.set_electrodes(V)
+    sim.step(4500 - done)
+    o = sim.observe()
+    assert o["status"] == 0
+    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6, o["mass"] / m0 - 1
+    assert np.isfinite(o["centroid"]).all() and np.isfinite(o["f_drag"]).all()
 
 
 def test_error_paths(gpu):

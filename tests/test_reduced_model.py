@@ -1,0 +1,105 @@
+"""The reduced-order droplet model (Results, Eqs. 1-7) against its closed-form limits.
+
+* constant drive (alpha0 -> 0): S(t) = (A / c) (t - tau (1 - e^{-t/tau})), tau = m / c;
+* free deceleration (A = 0): S(t) = V0 tau (1 - e^{-t/tau}), stopping distance
+  S_max = m V0 / c, so the paper's C_drag,sim = m V0 / (2 R0 mu_bar S_max) recovers C_drag;
+* overdamped limit (m -> 0): dS/dt = A e^{-2 alpha0 (S0 - S)} / c integrates to the first
+  term of Eq. 7, and with inertia Eq. 7's correction 2 alpha0 m S_t / c closes most of the
+  gap while the viscous time m / c stays short (the paper's condition for Eq. 6);
+* the fits recover the coefficients of synthetic data exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2608_12868_b300 import reduced_model as RM
+
+
+def test_constant_drive_closed_form():
+    m, c, A = 2.0, 0.5, 3e-3
+    model = RM.ReducedModel(m=m, c=c, A=A, alpha0=0.0, S0=10.0)
+    t = np.linspace(0.0, 40.0, 41)
+    S, V = model.trajectory(t)
+    tau = m / c
+    assert np.abs(S - A / c * (t - tau * (1 - np.exp(-t / tau)))).max() < 1e-10
+    assert np.abs(V - A / c * (1 - np.exp(-t / tau))).max() < 1e-12
+
+
+def test_free_deceleration_and_drag_coefficient():
+    m, R0, mu_bar, C = 3.0, 2.0, 0.05, 4.0
+    c = C * 2 * R0 * mu_bar
+    model = RM.ReducedModel(m=m, c=c, A=0.0, alpha0=0.1, S0=5.0)
+    V0 = 0.2
+    t = np.linspace(0.0, 60 * m / c, 61)
+    S, V = model.trajectory(t, V_init=V0)
+    tau = m / c
+    assert np.abs(S - V0 * tau * (1 - np.exp(-t / tau))).max() < 1e-8
+    S_max = S[-1] / (1 - math.exp(-t[-1] / tau))
+    assert abs(RM.drag_coefficient_deceleration(m, V0, S_max, R0, mu_bar) / C - 1) < 1e-8
+    assert abs(RM.drag_coefficient(c * 0.3, 0.3, R0, mu_bar) / C - 1) < 1e-12
+
+
+def test_overdamped_limit_is_eq7_first_term():
+    c, A, a0, S0, St = 1.0, 2e-3, 0.05, 30.0, 20.0
+    # closed form of dS/dt = A e^{-2 a0 (S0 - S)} / c
+    exact = c / (2 * a0 * A) * (math.exp(2 * a0 * S0) - math.exp(2 * a0 * (S0 - St)))
+    tiny = RM.ReducedModel(m=1e-9, c=c, A=A, alpha0=a0, S0=S0)
+    assert abs(tiny.transport_time(St) / exact - 1) < 1e-9
+    # a viscous time of 10 against a transit time of ~9e4: the ODE is overdamped
+    light = RM.ReducedModel(m=10.0, c=c, A=A, alpha0=a0, S0=S0)
+    t, _ = light.time_to_reach(St, dt=2.5)
+    assert abs(t / exact - 1) < 1e-3
+
+
+def test_eq7_with_inertia():
+    """With a short viscous time m / c (Eq. 6's condition), Eq. 7 matches the ODE's transit
+    time better than the overdamped term alone."""
+    c, A, a0, S0, St = 1.0, 2e-3, 0.05, 30.0, 20.0
+    m = 30.0
+    model = RM.ReducedModel(m=m, c=c, A=A, alpha0=a0, S0=S0)
+    t_ode, _ = model.time_to_reach(St)
+    overdamped = c / (2 * a0 * A) * (math.exp(2 * a0 * S0) - math.exp(2 * a0 * (S0 - St)))
+    eq7 = model.transport_time(St)
+    assert abs(eq7 - t_ode) < abs(overdamped - t_ode)
+    assert abs(eq7 / t_ode - 1) < 0.02
+
+
+def test_fits_recover_synthetic_coefficients():
+    V = np.linspace(1e-4, 5e-3, 17)
+    c, resid = RM.fit_drag(V, 0.37 * V)
+    assert abs(c - 0.37) < 1e-12 and resid < 1e-12
+    S_e = np.linspace(5.0, 40.0, 23)
+    B, a0, resid = RM.fit_force_law(S_e, 4e-3 * np.exp(-2 * 0.031 * S_e))
+    assert abs(B / 4e-3 - 1) < 1e-10 and abs(a0 - 0.031) < 1e-12 and resid < 1e-10
+    with pytest.raises(ValueError):
+        RM.fit_force_law([1.0, 2.0], [1.0, -1.0])
+
+
+def test_strip_solution_pieces():
+    """Eq. 4: alpha0 from the strip height; C_ele scales with phi0^2; Eq. 2's K_e for a
+    perfectly conducting droplet in an insulator is 2 pi eps R0^3."""
+    a0 = RM.strip_alpha0(3.0, 5.0)
+    assert abs(a0 - math.pi / 16) < 1e-15
+    c1, c2 = RM.strip_C_ele(0.05, 3.0, 5.0), RM.strip_C_ele(0.1, 3.0, 5.0)
+    assert c1 > 0 and abs(c2 / c1 - 4) < 1e-12
+    assert abs(RM.dep_prefactor(10.0, 2.0, 1.0, 0.0) - 2 * math.pi * 10.0 * 8.0) < 1e-12
+    F = RM.electric_force([0.0, 1.0], 2.0, 3.0, 0.25, Lam=0.5)
+    assert abs(F[0] - 3.0) < 1e-15 and abs(F[1] - 3.0 * math.exp(-0.5)) < 1e-15
+    assert abs(RM.effective_viscosity([1.0, 8.0, 0.125]) - 1.0) < 1e-15
+
+
+def test_switching_schedule_carries_state():
+    """Two-stage protocol: the first switch is where Eq. 5 first reaches the switching
+    distance; the second stage starts from the first stage's velocity."""
+    model = RM.ReducedModel(m=5.0, c=1.0, A=2e-3, alpha0=0.05, S0=0.0)
+    times, where = RM.switching_schedule(model, [60.0, 100.0, 140.0], x_start=20.0,
+                                         switch_distance=10.0)
+    assert np.allclose(where, [50.0, 90.0])
+    first = RM.ReducedModel(5.0, 1.0, 2e-3, 0.05, 40.0)
+    t1, v1 = first.time_to_reach(30.0)
+    assert abs(times[0] - t1) < 1e-9
+    second = RM.ReducedModel(5.0, 1.0, 2e-3, 0.05, 50.0)
+    t2, _ = second.time_to_reach(40.0, V_init=v1)
+    assert abs(times[1] - (t1 + t2)) < 1e-9
+    assert times[1] > times[0] > 0
