@@ -260,14 +260,16 @@ int lbehd_profile_read(lbehd_handle *h, double *ms, long long *count);
  * centroid[3] = sum Phi_1 x / M1, velocity[3] = sum Phi_1 u / M1, mass[3] = sum Phi_i,
  * the quantities lbehd_observe reports for the droplet.
  * Scratch: the per-block partial sums live in one file-scope __device__ array of
- * 2048 x 10 doubles (160 KB), which every GPU that loads the library holds until the
+ * 2048 x 9 doubles (144 KB), which every GPU that loads the library holds until the
  * process exits. This caps the lattice at 2048 x 8192 = 16 777 216 sites; larger lattices
- * are rejected with LBEHD_ERR_INVALID_ARG. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. Every call overwrites the partials it reads, so nothing needs
- * clearing, but all calls share the array: calls whose kernels overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.
- * Errors: LBEHD_ERR_INVALID_ARG (bad extents, null pointer, too large), LBEHD_ERR_CUDA;
+ * are rejected with LBEHD_ERR_INVALID_ARG. The first call on a device (and the first after a
+ * device reset, which gives the device a new context) looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture. Every call overwrites the partials it reads, so nothing needs clearing, but all
+ * calls share the array: calls whose kernels overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.
+ * Errors: LBEHD_ERR_INVALID_ARG (bad extents, null pointer, too large), LBEHD_ERR_CUDA (also
+ * when a CUDA error from the caller's earlier work is still pending; it is left in place);
  * the message is in lbehd_last_error(NULL). */
 int lbehd_phase_moments_noalloc(int dim, int nx, int ny, int nz, const float *phi,
                                 const float *u, const uint8_t *solid, double *out, void *stream);

@@ -591,9 +591,11 @@ int poisson(lbehd_handle *h)
         return rc;
     int iters = h->h_cg->iters;
     pcg_apply(h, x, nullptr);
-    // refinement: only after a pass that iterated (with none, the start residual was the
-    // true residual and already within the tolerance)
-    for (int pass = 0; pass < 3 && h->h_cg->iters > 0; pass++) {
+    // refinement: only after a pass of two or more iterations (with none, the start residual
+    // was the true residual and already within the tolerance; after one, the recursive
+    // residual still is, to FP32 rounding of one update far below it)
+    for (int pass = 0; pass < 3 && (pass > 0 || h->h_cg->refine) && h->h_cg->iters > 0;
+         pass++) {
         CK(h, cudaMemsetAsync(h->delta2, 0, h->N * sizeof(float), h->ls));
         pcg_start<D>(h, h->delta2, 4);   // true residual of the updated potential
         rc = pcg_host_loop<D>(h, h->delta2);

@@ -12,6 +12,7 @@
 // It is the same reduction that lbehd_observe reports for the droplet (volume, centroid,
 // velocity, per-component mass), taken from stored fields (Phi_1..3, u) instead of inside
 // the fused collide kernel.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,17 +27,54 @@ void set_global_error(const std::string &msg);   // lbehd.cu: message for lbehd_
 
 namespace {
 
-constexpr int NM_VALS = 10;        // M1, sum Phi1 x (3), sum Phi1 u (3), sum Phi2, sum Phi3, fluid count
+constexpr int NM_VALS = 9;         // M1, sum Phi1 x (3), sum Phi1 u (3), sum Phi2, sum Phi3
 constexpr int NM_THREADS = 256;
 constexpr int NM_MAX_BLOCKS = 2048;
 constexpr long long NM_SITES_PER_BLOCK = 8192;   // each block reduces <= 8192 sites
 
-// Scratch: one FP64 partial per value and block (2048 * 10 * 8 B = 160 KB per device).
+// Scratch: one FP64 partial per value and block (2048 * 9 * 8 B = 144 KB per device).
 static __device__ __align__(256) double g_partials[NM_MAX_BLOCKS * NM_VALS];
 
+// Device address of g_partials, looked up once per device and context: a device reset (or a
+// new primary context) reloads the module, and the array may then sit at another address,
+// so the cached address is kept together with the id of the context it belongs to.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-double *g_scratch_ptr[MAX_DEVICES] = {};   // device address of g_partials, per device
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    double *ptr = nullptr;
+};
+ScratchAddr g_scratch[MAX_DEVICES];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if it cannot be read).
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 __global__ void __launch_bounds__(NM_THREADS) k_moments_partials(int nx, int ny, long long N,
                                                                  const float *__restrict__ phi,
@@ -64,7 +102,6 @@ __global__ void __launch_bounds__(NM_THREADS) k_moments_partials(int nx, int ny,
         acc[6] += (double)p1 * u[2 * N + i];
         acc[7] += phi[N + i];
         acc[8] += phi[2 * N + i];
-        acc[9] += 1.0;
     }
     __shared__ double sm[NM_VALS][NM_THREADS / 32];
 #pragma unroll
@@ -138,26 +175,39 @@ extern "C" int lbehd_phase_moments_noalloc(int dim, int nx, int ny, int nz, cons
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return fail(LBEHD_ERR_CUDA, "lbehd_phase_moments_noalloc: no usable current device");
+    // An error left by the caller's own earlier work is reported as such and left in place
+    // (cudaGetLastError below would otherwise clear it and blame this call's launches).
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return fail(LBEHD_ERR_CUDA, std::string("lbehd_phase_moments_noalloc: an earlier CUDA "
+                                                "error is pending: ") +
+                                        cudaGetErrorString(e));
     double *scratch = nullptr;
     {
-        // once per device, with that device current: the device address of the file-scope
-        // scratch array (its name in host code is only a host-side handle)
+        // once per device and context, with that device current: the device address of the
+        // file-scope scratch array (its name in host code is only a host-side handle)
+        const unsigned long long ctx = current_context_id();
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        ScratchAddr &a = g_scratch[dev];
+        if (!a.ptr || ctx == 0 || a.ctx_id != ctx) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_partials);
             if (e != cudaSuccess || !p)
                 return fail(LBEHD_ERR_CUDA, std::string("lbehd_phase_moments_noalloc: "
                                                         "cudaGetSymbolAddress failed: ") +
                                                 cudaGetErrorString(e));
-            g_scratch_ptr[dev] = (double *)p;
+            a.ptr = (double *)p;
+            a.ctx_id = ctx;
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = a.ptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
     k_moments_partials<<<(unsigned)nblocks, NM_THREADS, 0, s>>>(nx, ny, N, phi, u, solid, scratch);
-    k_moments_final<<<1, 32 * NM_VALS, 0, s>>>(scratch, (int)nblocks, out);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_moments_final<<<1, 32 * NM_VALS, 0, s>>>(scratch, (int)nblocks, out);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess)
         return fail(LBEHD_ERR_CUDA, std::string("lbehd_phase_moments_noalloc: launch failed: ") +
                                         cudaGetErrorString(e));

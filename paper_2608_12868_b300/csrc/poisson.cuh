@@ -858,7 +858,8 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 //   op 4: restart   as op 0 for a refinement pass (keeps the step counter)
 //   op 1: r.z       rz                -> beta = rz / rz_old, rz_old = rz
 //   op 2: p.Ap      pq                -> alpha = rz / pq
-//   op 3: ||r||^2   rr                -> iters++, done / converged, refine = 1
+//   op 3: ||r||^2   rr                -> iters++, done / converged, refine = 1 from the
+//                                        second iteration on
 //   op 5: ||r||^2   as op 3, for a refinement pass (leaves refine alone)
 // (op 0 clears refine.) pcg_scalar_block returns true in thread 0 after updating *s.
 // k_pcg_scalar: with use_cond, ops 0, 4, 3 and 5 also set the graph's while-loop condition
@@ -910,7 +911,12 @@ __device__ __forceinline__ void pcg_scalar_update(const double (&tot)[2], int op
         s->iters += 1;
         s->step_iters += 1;
         s->total_iters += 1;
-        if (op == 3)
+        // A refinement pass re-forms the true residual and corrects the drift of the CG's
+        // recursive one. One iteration from the warm start leaves r0 within a few times the
+        // tolerance, and the FP32 rounding of that single update is ~1e-7 of r0, far below the
+        // tolerance: only a pass of two or more iterations (large increments, the first
+        // solve, an electrode switch) needs the check.
+        if (op == 3 && s->iters >= 2)
             s->refine = 1;
         s->converged = s->rr <= s->tol2 * s->bb || s->rr < 1e-60;
         s->done = s->converged || s->iters >= s->max_iter;
@@ -958,11 +964,11 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
         return;
     if (use_cond && op != 1 && op != 2)
         cudaGraphSetConditional(cond, s->done ? 0u : 1u);
-    // refinement check runs only when the main pass iterated
+    // refinement check runs only when the main pass took two or more iterations
     if (use_ref && op == 0)
         cudaGraphSetConditional(cond_ref, 0u);
     if (use_ref && op == 3)
-        cudaGraphSetConditional(cond_ref, 1u);
+        cudaGraphSetConditional(cond_ref, s->refine ? 1u : 0u);
 }
 
 // phi += delta on active cells, phi kept as the compensated pair hi + lo (two-sum in FP32:
