@@ -681,25 +681,30 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
         atomicOr(S.flag, 1);
 }
 
-// Block partial sums of the observables: FP32 within a warp, FP64 across warps.
+// Block partial sums of the observables: FP32 within the block (warp butterflies, then the
+// block's warps in order), one conversion to FP64 per observable; the sum over blocks is FP64
+// (k_obs_final_split). The FP64 pipe of this part is narrow: converting and adding every
+// warp's sums in FP64 at the end of each block kept it 18 % busy over the whole collide
+// kernel (ncu). A block's FP32 partial carries ~1e-7 relative rounding, which the FP64 sum
+// over thousands of blocks does not accumulate into a bias.
 __device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], double *partials,
                                                    size_t blk, size_t nblk)
 {
-    __shared__ double sm[NOBS][BX / 32];
+    __shared__ float sm[NOBS][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NOBS; k++) {
         const float v = warp_sum(ob[k]);
         if (lane == 0)
-            sm[k][wid] = (double)v;
+            sm[k][wid] = v;
     }
     __syncthreads();
     if (threadIdx.x < NOBS) {
-        double acc = 0.0;
+        float acc = 0.0f;
 #pragma unroll
         for (int w = 0; w < BX / 32; w++)
             acc += sm[threadIdx.x][w];
-        partials[threadIdx.x * nblk + blk] = acc;
+        partials[threadIdx.x * nblk + blk] = (double)acc;
     }
 }
 

@@ -22,11 +22,13 @@
 //    then, after a barrier, every CTA finishes the butterfly (FP64 adds are slow on this
 //    part, and the split spreads them over SMs);
 //  * the shared-memory tail runs in CTA 0 with the 1024-thread k_mg_tail body;
-//  * three fused phases reproduce a pair of launches exactly: "zero, then the first red half
+//  * fused phases reproduce a sequence of launches exactly: "zero, then the first red half
 //    sweep" (every neighbour is 0, so x = (b + 0) / D on red cells and 0 elsewhere),
-//    "residual, then the sum over each coarse cell's children" (each child's residual on its
-//    own lane, summed in the restriction's order), and "prolongation, then the first black
-//    half sweep" (neighbours read as prolongation leaves them).
+//    "residual, then the sum over each coarse cell's children, then the coarse level's zero
+//    start and first red half sweep" (each child's residual on its own lane, summed in the
+//    restriction's order; the red update needs only the cell's own new b), and
+//    "prolongation, then the first black half sweep" (neighbours read as prolongation
+//    leaves them).
 //
 // Barrier: a monotonic arrival counter (zeroed by the start launch before each solve) that
 // barrier k waits to reach k * gridDim.x; thread 0 of each CTA spins with a backoff and an
@@ -388,8 +390,11 @@ __device__ __forceinline__ float ps_resid(const PsLevel &F, int x, int y, int z)
 // b_c = sum over each coarse cell's children of the fine residual, in the order of
 // mg_restrict_sum_cell ((x, y, z) = (2X + a, 2Y + b, z0 + g), a outermost). Eight lanes per
 // coarse cell: lane ch = 4a + 2b + g of the group evaluates one child, the group's first
-// lane gathers the eight by shuffles and sums them in that order.
-__device__ __forceinline__ void ps_resid_restrict(const PsLevel &F, const PsLevel &C)
+// lane gathers the eight by shuffles and sums them in that order. With `start`, the same
+// lane also does the coarse level's zero start and first red half sweep at that cell (the
+// value ps_gs_first writes there, from the b just formed), which saves that phase's grid
+// barrier.
+__device__ __forceinline__ void ps_resid_restrict(const PsLevel &F, const PsLevel &C, bool start)
 {
     const MgDims &f = F.d, &c = C.d;
     const int span = (C.n * 8 + 31) & ~31;   // whole warps: every lane reaches the shuffles
@@ -418,6 +423,11 @@ __device__ __forceinline__ void ps_resid_restrict(const PsLevel &F, const PsLeve
                 if ((j & 1) == 0 || z1)
                     acc = __fadd_rn(acc, v[j]);
             C.b[I] = acc;
+            if (start) {
+                int X, Y, Z;
+                cell_xyz(c, I, X, Y, Z);
+                C.x[I] = ps_first_red(X, Y, Z, acc, C.D[I]);
+            }
         }
     }
 }
@@ -528,7 +538,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     auto vcycle = [&]() {
         for (int l = 0; l < A.nl && ok; l++) {
             const PsLevel &L = A.L[l];
-            if (l > 0 || !z_ready) {
+            if (l == 0 && !z_ready) {   // coarser levels were started by the restriction
                 ps_gs_first(L);
                 sync();
             }
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
                 ps_gs(L, 1);
                 sync();
             }
-            ps_resid_restrict(L, A.L[l + 1]);
+            ps_resid_restrict(L, A.L[l + 1], l + 1 < A.nl);
             sync();
         }
         if (!ok)

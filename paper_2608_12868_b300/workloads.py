@@ -271,6 +271,57 @@ def small_2d(nx=48, ny=32, seed=5, R=8.0, V=0.05):
                     schedule=[(0, [V])])
 
 
+def electrode_above(dim=2, nx=256, ny=24, nz=1, *, l_e=8, x_e=240, w_e=8, V=0.05, wall=True,
+                    droplet=None, pillar_h=0, seed=6, name=None):
+    """The electrode geometry of the paper's Fig. 1: an electrode block held at V above a
+    grounded substrate, every other wall zero-flux (Results, the problem set-up: the pillar
+    surface at zero potential, the electrode at phi0, Neumann elsewhere).
+
+    Vertical axis v (y in 2D, z in 3D) with nv nodes: the substrate floor v = 0 (and any
+    micropillars of height pillar_h, width 4, gap 4) is grounded (solid class 1, id -2); the
+    top wall v = nv - 1 is zero-flux (class 2, id -1); the electrode (class 2, id 0) hangs
+    from the top wall, l_e nodes high (v in [nv - 1 - l_e, nv - 1)), at x in [x_e, x_e + w_e),
+    across all of y. With `wall` a zero-flux column at x = 0 ends the x-periodicity. The
+    potential lives in the strip between the ground nodes (v = 0) and the zero-flux face of
+    the top wall (v = nv - 1.5): height H = nv - 1.5 = h_e + l_e, the electrode-surface
+    distance h_e = H - l_e. `droplet` = (xc, R) puts a droplet resting on the floor (or the
+    pillar tops); without it the box holds the ambient phase alone."""
+    shape = (nz, ny, nx)
+    zz, yy, xx = _coords(shape)
+    vert = yy if dim == 2 else zz
+    nv = ny if dim == 2 else nz
+    solid = np.zeros(shape, dtype=np.uint8)
+    elec = np.full(shape, -1, dtype=np.int16)
+    solid[vert == 0] = 1
+    elec[vert == 0] = -2
+    if pillar_h > 0:
+        in_p = (xx % 8) < 4
+        if dim == 3:
+            in_p &= (yy % 8) < 4
+        m = in_p & (vert >= 1) & (vert <= pillar_h) & (xx >= 8) & (xx < x_e - 8)
+        solid[m] = 1
+        elec[m] = -2
+    solid[vert == nv - 1] = 2
+    m = (xx >= x_e) & (xx < x_e + w_e) & (vert >= nv - 1 - l_e) & (vert < nv - 1)
+    solid[m] = 2
+    elec[m] = 0
+    if wall:
+        solid[xx == 0] = 2
+        elec[(xx == 0) & (vert > 0)] = -1
+    if droplet is not None:
+        xc, R = droplet
+        base = pillar_h + 0.5 if pillar_h > 0 else 0.5
+        center = (xc, base + R - 2) if dim == 2 else (xc, ny / 2.0, base + R - 2)
+        phi = droplet_on_film(dim, shape, solid, center=center, R=R, film_top=base, seed=seed)
+    else:
+        phi = np.zeros((3,) + shape)
+        phi[2] = 1.0
+        phi[:, solid != 0] = 0.0
+    params = make_params(V=(V,), R=droplet[1] if droplet else 8.0, height=nv)
+    return Workload(name or f"electrode_above_{dim}d_{nx}x{ny}x{nz}", dim, shape, solid, elec,
+                    phi, params, steps=1, schedule=[(0, [V])])
+
+
 WORKLOADS = {
     "droplet_2d_128x64": droplet_2d_128x64,
     "droplet_3d_128x64x64": droplet_3d_128x64x64,

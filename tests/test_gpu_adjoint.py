@@ -4,7 +4,11 @@
   differentiable PyTorch) on tiny 3D and 2D lattices: the gradient of the droplet's x
   centroid with respect to a piecewise-constant electrode schedule, within 1e-3 of the
   largest gradient component (FP32 state against FP64).
-* The 24x16x16 copy of the differentiable-control case against the same reference.
+* The 24x16x16 copy of the differentiable-control case against the same reference, and,
+  over a 100-step schedule, component by component: within 1e-3 relative of the FP64
+  discrete adjoint for every component above 2 % of the largest, and within 1e-3 relative of
+  central differences (h = 1e-4) of the FP64 oracle's forward on sampled components (the FP64
+  forward keeps finite differences free of the FP32 rounding that h = 1e-4 would amplify).
 * Against central finite differences of the GPU forward itself: a 40x16x16 lattice (1e-2
   of the largest component), and the full 96x64x64 control case, 4000 steps and 320
   parameters, on 8 sampled parameters (1e-3 of the largest component).
@@ -72,6 +76,50 @@ def test_control_copy_24x16x16_matches_fp64_reference(gpu, oracle_mod):
     g = sim.adjoint_backward()
     assert abs(L - L_ref) <= 1e-6 * abs(L_ref)
     assert np.abs(g - g_ref).max() <= 1e-3 * np.abs(g_ref).max(), (g, g_ref)
+
+
+def _oracle_loss(oracle_mod, w, V, seg):
+    """x centroid of the droplet after the schedule V (segments x electrodes, seg steps each)
+    run by the FP64 oracle: the fields of the last step, as lbehd_adjoint_forward reports."""
+    orc = oracle_mod.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    for k in range(V.shape[0]):
+        orc.set_electrodes(V[k])
+        orc.step(seg)
+    return orc.observables()["centroid"][0]
+
+
+COMPONENT_FLOOR = 0.02   # components below 2 % of the largest are compared in absolute terms
+
+
+def test_control_copy_100_steps_component_by_component(gpu, oracle_mod):
+    """The 24x16x16 copy of the control case over 5 segments of 20 steps (4 electrodes, 20
+    parameters, 100 steps). Every gradient component above COMPONENT_FLOOR of the largest
+    within 1e-3 relative of the FP64 discrete adjoint (the rest within 1e-3 COMPONENT_FLOOR of
+    the largest); on the four largest components, the GPU adjoint within 1e-3 relative of
+    central differences of the FP64 oracle forward at h = 1e-4, and the FP64 adjoint within
+    1e-5 relative of the same differences."""
+    w = W.control_3d_24x16x16(segments=5, seg_steps=20)
+    V = np.array([v for _, v in w.schedule])
+    seg = 20
+    L_ref, g_ref = reference_grad(oracle_mod, w, V, seg)
+    sim = gpu.Simulation(w)
+    L = sim.adjoint_forward(V, seg)
+    g = sim.adjoint_backward()
+    assert abs(L - L_ref) <= 1e-6 * abs(L_ref)
+    scale = np.abs(g_ref).max()
+    big = np.abs(g_ref) >= COMPONENT_FLOOR * scale
+    rel = np.abs(g - g_ref)[big] / np.abs(g_ref)[big]
+    assert rel.max() <= 1e-3, (rel.max(), g, g_ref)
+    assert np.abs(g - g_ref)[~big].max(initial=0.0) <= 1e-3 * COMPONENT_FLOOR * scale
+    h = 1e-4
+    for flat in np.argsort(-np.abs(g_ref).ravel())[:4]:
+        k, e = np.unravel_index(flat, V.shape)
+        Vp, Vm = V.copy(), V.copy()
+        Vp[k, e] += h
+        Vm[k, e] -= h
+        fd = (_oracle_loss(oracle_mod, w, Vp, seg) - _oracle_loss(oracle_mod, w, Vm, seg)) / (2 * h)
+        assert abs(g_ref[k, e] - fd) <= 1e-5 * abs(fd), (k, e, g_ref[k, e], fd)
+        assert abs(g[k, e] - fd) <= 1e-3 * abs(fd), (k, e, g[k, e], fd)
 
 
 def test_control_96x64x64_matches_finite_differences(gpu):

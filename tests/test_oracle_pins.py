@@ -602,3 +602,35 @@ def test_drag_force_balance_in_a_uniform_mixture(oracle_mod, which):
     s.step(3)
     o = s.observables()
     assert np.abs(o["f_drag"]).max() < 1e-9 * o["M1"] * np.abs(b).max()
+
+
+def _strip_far_field(O, ny, l_e):
+    """Potential of the paper's Fig. 1 electrode geometry (2D, no droplet, no charge): the
+    oracle's Gauss-law solution, the strip height H = ny - 1.5 from the grounded floor
+    nodes to the zero-flux face of the top wall, and the row in the middle."""
+    w = W.electrode_above(2, 256, ny, 1, l_e=l_e, x_e=240, w_e=8, V=0.05)
+    s = _sim(O, w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    s.params["oracle_poisson_tol"] = 1e-14
+    s._prm.poisson_tol = 1e-14
+    s.step(1)
+    return s.pot[0], ny - 1.5, ny // 2
+
+
+@pytest.mark.parametrize("ny,l_e", [(24, 8), (34, 12)])
+def test_strip_lowest_mode_far_from_the_electrode(oracle_mod, ny, l_e):
+    """Eqs. 3-4 rest on the lowest mode of Laplace's equation in the strip between the
+    grounded surface and the zero-flux top: phi ~ sin(k v) e^{-alpha S_e}, k = pi / (2 H).
+    For the discrete operator of Eq. 13 that mode is exact, with the x decay rate fixed by
+    cosh(alpha) = 2 - cos(k): far from the electrode every three consecutive values along a
+    row satisfy phi(x - 1) + phi(x + 1) = 2 cosh(alpha) phi(x), and every column is
+    proportional to sin(k v). A Dirichlet face coefficient of eps/2 instead of eps (or a
+    ground held one node off) moves the effective strip height and fails both."""
+    pot, H, v = _strip_far_field(oracle_mod, ny, l_e)
+    k = np.pi / (2 * H)
+    alpha = np.arccosh(2 - np.cos(k))
+    row = pot[v, 30:101]   # 140 or more nodes from the electrode: higher modes < 2e-6
+    est = np.arccosh((row[2:] + row[:-2]) / row[1:-1] / 2)
+    assert np.abs(est / alpha - 1).max() < 1e-4, (est.min(), est.max(), alpha)
+    vv = np.arange(1, pot.shape[0] - 1)
+    col = pot[vv, 120] / pot[v, 120]
+    assert np.abs(col - np.sin(k * vv) / np.sin(k * v)).max() < 1e-5

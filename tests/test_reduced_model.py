@@ -103,3 +103,30 @@ def test_switching_schedule_carries_state():
     t2, _ = second.time_to_reach(40.0, V_init=v1)
     assert abs(times[1] - (t1 + t2)) < 1e-9
     assert times[1] > times[0] > 0
+
+
+@pytest.mark.parametrize("ny,l_e", [(24, 8), (34, 12)])
+def test_eq4_amplitude_against_the_gauss_law_solution(oracle_mod, ny, l_e):
+    """Eq. 4's C_ele, as printed, against the lowest strip mode of the oracle's Gauss-law
+    solution on the Fig. 1 geometry (2D, electrode block of height l_e hanging from the
+    zero-flux top, grounded floor, H = ny - 1.5 = h_e + l_e). With phi ~ a sin(alpha0 v)
+    e^{-alpha0 S_e}, Eq. 3's force K_e d|E|^2/dx gives C_ele = 2 alpha0 (a alpha0)^2: the
+    one-mode approximation of the paper's semi-infinite strip lands within 20 % of the exact
+    amplitude (measured 12-14 % low)."""
+    from paper_2608_12868_b300 import workloads as W
+    w = W.electrode_above(2, 256, ny, 1, l_e=l_e, x_e=240, w_e=8, V=0.05)
+    s = oracle_mod.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    s._prm.poisson_tol = 1e-14
+    s.step(1)
+    pot = s.pot[0]
+    H = ny - 1.5
+    k = math.pi / (2 * H)
+    alpha = math.acosh(2 - math.cos(k))
+    v = ny // 2
+    xs = np.arange(30, 141)
+    X = np.stack([np.exp(alpha * (xs - 240)), np.exp(-alpha * xs)], 1)
+    coef, *_ = np.linalg.lstsq(X, pot[v, xs], rcond=None)
+    a_sim = coef[0] / math.sin(k * v)
+    a0 = RM.strip_alpha0(H - l_e, l_e)
+    a_eq4 = math.sqrt(RM.strip_C_ele(0.05, H - l_e, l_e) / (2 * a0)) / a0
+    assert 0.8 < a_sim / a_eq4 < 1.0, a_sim / a_eq4
