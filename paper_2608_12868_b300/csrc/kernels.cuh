@@ -756,6 +756,11 @@ struct PopMaps {
     CUtensorMap g, fphi, frho;
 };
 
+__device__ __forceinline__ void prefetch_l1(const float *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             int c2, int c3, uint64_t *bar)
 {
@@ -812,6 +817,16 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     const bool active = x < P.nx && y < P.ny;
     const int i = active ? x + P.nx * (y + P.ny * z) : 0;
     const SitePre pre = load_site_pre(S, N, i);   // issued now, used after the staging
+    // The momentum and charge populations are read late, in the collisions; ask L1 for
+    // their lines now so their DRAM latency overlaps the halo loads and the stencils.
+    if (active) {
+#pragma unroll
+        for (int n = 0; n < Q; n++)
+            prefetch_l1(S.g + (size_t)n * N + i);
+#pragma unroll
+        for (int n = 0; n < L::QS; n++)
+            prefetch_l1(S.frho + (size_t)n * N + i);
+    }
     // stencil fields of the tile and its halo, periodic in every direction: every load of
     // this thread is issued before the first shared-memory store
     constexpr int HIT = (HN + BX - 1) / BX;
