@@ -265,11 +265,11 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         const float b0 = post_bar(A.lg_in, 0);   // rest: dp - sum_{n>=1} v_n
         float C0b = 0.0f, Vb[3] = {0.f, 0.f, 0.f}, c_nub = 0.0f;
         float d1b = 0.f, d2b = 0.f, dxyb = 0.f, dxzb = 0.f, dyzb = 0.f, dTb = 0.f, dpb = b0;
-        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) - (u[0] * F[0] - u[1] * F[1]);
-        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) - (u[0] * F[0] - u[2] * F[2]);
-        const float dxy = m2[3] - u[0] * u[1] - 0.5f * (u[0] * F[1] + u[1] * F[0]);
-        const float dxz = m2[4] - u[0] * u[2] - 0.5f * (u[0] * F[2] + u[2] * F[0]);
-        const float dyz = m2[5] - u[1] * u[2] - 0.5f * (u[1] * F[2] + u[2] * F[1]);
+        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) + (u[0] * F[0] - u[1] * F[1]);
+        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) + (u[0] * F[0] - u[2] * F[2]);
+        const float dxy = m2[3] - u[0] * u[1] + 0.5f * (u[0] * F[1] + u[1] * F[0]);
+        const float dxz = m2[4] - u[0] * u[2] + 0.5f * (u[0] * F[2] + u[2] * F[0]);
+        const float dyz = m2[5] - u[1] * u[2] + 0.5f * (u[1] * F[2] + u[2] * F[1]);
 #pragma unroll
         for (int n = 1; n < Q; n++) {
             const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
@@ -326,23 +326,23 @@ __device__ void adj_collide_site(const Params &P, const AdjFwd &Fw, const AdjBuf
         m2b[3] += dxyb;
         m2b[4] += dxzb;
         m2b[5] += dyzb;
-        ub[0] += -d1b * (2.0f * u[0] + F[0]) - d2b * (2.0f * u[0] + F[0]);
-        ub[1] += d1b * (2.0f * u[1] + F[1]);
-        ub[2] += d2b * (2.0f * u[2] + F[2]);
-        Fb[0] += -(d1b + d2b) * u[0];
-        Fb[1] += d1b * u[1];
-        Fb[2] += d2b * u[2];
-        ub[0] += -dxyb * (u[1] + 0.5f * F[1]) - dxzb * (u[2] + 0.5f * F[2]);
-        ub[1] += -dxyb * (u[0] + 0.5f * F[0]) - dyzb * (u[2] + 0.5f * F[2]);
-        ub[2] += -dxzb * (u[0] + 0.5f * F[0]) - dyzb * (u[1] + 0.5f * F[1]);
-        Fb[0] += -0.5f * (dxyb * u[1] + dxzb * u[2]);
-        Fb[1] += -0.5f * (dxyb * u[0] + dyzb * u[2]);
-        Fb[2] += -0.5f * (dxzb * u[0] + dyzb * u[1]);
+        ub[0] += (d1b + d2b) * (F[0] - 2.0f * u[0]);
+        ub[1] += d1b * (2.0f * u[1] - F[1]);
+        ub[2] += d2b * (2.0f * u[2] - F[2]);
+        Fb[0] += (d1b + d2b) * u[0];
+        Fb[1] += -d1b * u[1];
+        Fb[2] += -d2b * u[2];
+        ub[0] += -dxyb * (u[1] - 0.5f * F[1]) - dxzb * (u[2] - 0.5f * F[2]);
+        ub[1] += -dxyb * (u[0] - 0.5f * F[0]) - dyzb * (u[2] - 0.5f * F[2]);
+        ub[2] += -dxzb * (u[0] - 0.5f * F[0]) - dyzb * (u[1] - 0.5f * F[1]);
+        Fb[0] += 0.5f * (dxyb * u[1] + dxzb * u[2]);
+        Fb[1] += 0.5f * (dxyb * u[0] + dyzb * u[2]);
+        Fb[2] += 0.5f * (dxzb * u[0] + dyzb * u[1]);
         dpb += -(float)D * (1.0f / 3.0f) * dTb;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            ub[a] += -dTb * (2.0f * u[a] + F[a]);
-            Fb[a] += -dTb * u[a];
+            ub[a] += dTb * (F[a] - 2.0f * u[a]);
+            Fb[a] += dTb * u[a];
         }
         // c_nu = 1 - 1/(3 nu + 0.5)
         const float nub = c_nub * inv_cs2 / (den * den);

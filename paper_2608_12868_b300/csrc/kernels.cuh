@@ -526,14 +526,16 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
         const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
         const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
         const float c_b = 1.0f - P.s_bulk;
-        // non-equilibrium moments of g - g_eq + R/2 (deviatoric / off-diagonal / trace)
+        // non-equilibrium moments of g - g_eq + R/2 (deviatoric / off-diagonal / trace):
+        // second moments of the populations less those of the equilibrium (c_s^2 p* I + u u)
+        // plus half those of the force term (u F + F u)
         const float uFd[3] = {u[0] * F[0], u[1] * F[1], u[2] * F[2]};
-        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) - (uFd[0] - uFd[1]);
-        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) - (uFd[0] - uFd[2]);
-        const float dxy = m2[3] - u[0] * u[1] - 0.5f * (u[0] * F[1] + u[1] * F[0]);
-        const float dxz = m2[4] - u[0] * u[2] - 0.5f * (u[0] * F[2] + u[2] * F[0]);
-        const float dyz = m2[5] - u[1] * u[2] - 0.5f * (u[1] * F[2] + u[2] * F[1]);
-        const float dT = (m2[0] + m2[1] + m2[2]) - (float)D * (1.0f / 3.0f) * dp - uu - uF;
+        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) + (uFd[0] - uFd[1]);
+        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) + (uFd[0] - uFd[2]);
+        const float dxy = m2[3] - u[0] * u[1] + 0.5f * (u[0] * F[1] + u[1] * F[0]);
+        const float dxz = m2[4] - u[0] * u[2] + 0.5f * (u[0] * F[2] + u[2] * F[0]);
+        const float dyz = m2[5] - u[1] * u[2] + 0.5f * (u[1] * F[2] + u[2] * F[1]);
+        const float dT = (m2[0] + m2[1] + m2[2]) - (float)D * (1.0f / 3.0f) * dp - uu + uF;
         // w_n [C0 + e.V + (e.u)(4.5 e.u + 4.5 e.F)] = g_eq,n - w_n + R_n / 2
         const float C0 = dp - 1.5f * uu - 1.5f * uF;
         const float V[3] = {3.0f * u[0] + 1.5f * F[0], 3.0f * u[1] + 1.5f * F[1],
