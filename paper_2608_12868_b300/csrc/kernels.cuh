@@ -275,7 +275,9 @@ struct GlobalStencil {
 };
 
 // Tiles of the staged collide kernel: TX x TY sites (TX * TY = BX), TY in {2, 4, 8}.
-// Halo tile layout: HX x HY x HZ sites, fields [Phi_1, Phi_2, Phi_3, pot, pot_lo] then info.
+// Halo tile layout: HX x HY x HZ sites, each as a float4 (Phi_1, Phi_2, Phi_3, pot) and a
+// float2 (pot_lo, node class as the bits of a float), so that a neighbour's six fields come
+// in two shared-memory loads.
 template <int D, int TY>
 struct Halo {
     static constexpr int TX = BX / TY;
@@ -285,21 +287,23 @@ struct Halo {
 
 template <int D, int TY>
 struct SmemStencil {
-    const float *f;        // 5 * Halo::N floats
-    const uint8_t *info;   // Halo::N bytes
-    int h;                 // halo index of the site
+    const float4 *a;   // Halo::N of (Phi_1, Phi_2, Phi_3, pot)
+    const float2 *b;   // Halo::N of (pot_lo, info bits)
+    int h;             // halo index of the site
     template <class L>
     __device__ __forceinline__ void at(int n, float (&P)[3], float &ph, float &lo, int &pt) const
     {
         using H = Halo<D, TY>;
-        constexpr int HX = H::HX, HXY = H::HX * H::HY, HN = H::N;
+        constexpr int HX = H::HX, HXY = H::HX * H::HY;
         const int j = h + L::ex(n) + HX * L::ey(n) + HXY * L::ez(n);
-        P[0] = f[j];
-        P[1] = f[HN + j];
-        P[2] = f[2 * HN + j];
-        ph = f[3 * HN + j];
-        lo = f[4 * HN + j];
-        pt = info[j] & 3;
+        const float4 v = a[j];
+        const float2 w = b[j];
+        P[0] = v.x;
+        P[1] = v.y;
+        P[2] = v.z;
+        ph = v.w;
+        lo = w.x;
+        pt = __float_as_int(w.y) & 3;
     }
 };
 
@@ -782,7 +786,7 @@ constexpr int staged_pop_floats()
 template <int D, int TY>
 constexpr size_t staged_smem_bytes()
 {
-    return (size_t)staged_pop_floats<D>() * 4 + (size_t)Halo<D, TY>::N * (5 * 4 + 1);
+    return (size_t)staged_pop_floats<D>() * 4 + (size_t)Halo<D, TY>::N * (16 + 8);
 }
 
 // The step on a TX x TY tile: thread 0 issues a 4D TMA tensor copy of the tile's phase-field
@@ -801,8 +805,8 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     using H = Halo<D, TY>;
     constexpr int Q = L::Q, HN = H::N, HX = H::HX, HY = H::HY, TX = H::TX;
     extern __shared__ __align__(128) float spop[];   // populations, then halo fields
-    float *shal = spop + staged_pop_floats<D>();
-    uint8_t *sinf = reinterpret_cast<uint8_t *>(shal + 5 * HN);
+    float4 *sha = reinterpret_cast<float4 *>(spop + staged_pop_floats<D>());
+    float2 *shb = reinterpret_cast<float2 *>(sha + HN);
     __shared__ __align__(8) uint64_t bar;
     const int t = threadIdx.x, tx = t & (TX - 1), ty = t / TX;
     if (t == 0) {
@@ -856,10 +860,8 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     for (int k = 0; k < HIT; k++) {
         const int e = t + k * BX;
         if (e < HN) {
-#pragma unroll
-            for (int f = 0; f < 5; f++)
-                shal[f * HN + e] = hv[k][f];
-            sinf[e] = hinf[k];
+            sha[e] = make_float4(hv[k][0], hv[k][1], hv[k][2], hv[k][3]);
+            shb[e] = make_float2(hv[k][4], __int_as_float((int)hinf[k]));
         }
     }
     __syncthreads();
@@ -876,9 +878,9 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
         return;
     }
     const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
-    if (active && (sinf[h] & 3) == PT_FLUID) {
+    if (active && (__float_as_int(shb[h].y) & 3) == PT_FLUID) {
         const StagedPops pops{S.g, S.frho, spop, N, (size_t)i, t, Q};
-        const SmemStencil<D, TY> st{shal, sinf, h};
+        const SmemStencil<D, TY> st{sha, shb, h};
         collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
     block_obs_partials(ob, S.obs_partials, blk, nblk);
