@@ -93,7 +93,9 @@ typedef struct lbehd_config {
     int poisson_mode;        /* LBEHD_POISSON_HOST or LBEHD_POISSON_FIXED */
     int poisson_check_every; /* iterations between host convergence checks (HOST mode) */
     int poisson_fixed_iters; /* iterations per step in LBEHD_POISSON_FIXED */
-    int mg_nu;               /* red-black pre/post smoothing sweeps per level (0 -> 2) */
+    int mg_nu;               /* red-black pre/post smoothing sweep pairs per level
+                              * (0 -> 2; with the block-local smoother of
+                              * LBEHD_OPT_MG_SMOOTHER, pairs per block, 0 -> 3) */
     int mg_coarse_sweeps;    /* symmetric sweep pairs on the coarsest level (0 -> 8) */
     int mg_max_levels;       /* multigrid levels (0 -> as many as the extents allow) */
     double mg_scale;         /* scale of the Galerkin coarse operators (0 -> 0.6) */
@@ -212,10 +214,21 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   the next lbehd_observe returns LBEHD_ERR_CUDA ("grid barrier timed out"). The error is
  *   sticky for the handle. 0 (default): normal barriers. */
 #define LBEHD_OPT_BARRIER_TEST 5
+/*   LBEHD_OPT_MG_SMOOTHER: the smoother of the multigrid preconditioner on the levels above
+ *   the shared-memory tail. 1 (default where the lattice has such levels): block-local,
+ *   block-Jacobi between blocks of 16x8x8 (2D: 32x32) cells, red-black Gauss-Seidel sweeps
+ *   within a block against its halo as it was when the pass began (mg_nu pairs per pass,
+ *   default 3); one grid-wide dependency per level and direction of a V-cycle. 0:
+ *   red-black Gauss-Seidel half sweeps over whole levels (mg_nu pairs, default 2). Both are
+ *   symmetric, so CG converges to the same tolerance with either; the solutions differ
+ *   within it. The persistent and the multi-launch solves give the same bits for either
+ *   value. Batched instances run 0 (setting 1 on a batch fails with
+ *   LBEHD_ERR_INVALID_ARG). */
+#define LBEHD_OPT_MG_SMOOTHER 6
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 /* The value in effect: for LBEHD_OPT_COLLIDE the kernel the automatic choice resolved to,
- * for LBEHD_OPT_POISSON_KERNEL 1 only if the persistent solve is on and this lattice allows
- * it. Errors: LBEHD_ERR_INVALID_ARG (unknown option, null output). */
+ * for LBEHD_OPT_POISSON_KERNEL and LBEHD_OPT_MG_SMOOTHER 1 only if the option is on and this
+ * lattice allows it. Errors: LBEHD_ERR_INVALID_ARG (unknown option, null output). */
 int lbehd_get_option(lbehd_handle *h, int option, long long *value);
 
 /* Counters since init (synchronises: reads the device-side iteration counter). */

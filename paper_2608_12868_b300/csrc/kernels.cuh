@@ -327,6 +327,273 @@ __device__ __forceinline__ SitePre load_site_pre(const State &S, size_t N, int i
     return p;
 }
 
+// Push streaming of one site's post-collision populations: f*_n goes to x + e_n, or into the
+// opposite slot at x when x + e_n is solid (halfway bounce-back).
+template <class L>
+struct Pusher {
+    unsigned fluid_nb;   // bit n: x + e_n is fluid
+    int i, N;
+    int oxp, oxm, oyp, oym, ozp, ozm;   // periodic neighbour offsets
+    __device__ __forceinline__ int off(int n) const
+    {
+        return (L::ex(n) > 0 ? oxp : (L::ex(n) < 0 ? oxm : 0)) +
+               (L::ey(n) > 0 ? oyp : (L::ey(n) < 0 ? oym : 0)) +
+               (L::ez(n) > 0 ? ozp : (L::ez(n) < 0 ? ozm : 0));
+    }
+    __device__ __forceinline__ void operator()(float *out, int n, float v) const
+    {
+        const bool fl = (fluid_nb >> n) & 1u;
+        const int slot = fl ? n : opposite(n);
+        const int site = fl ? i + off(n) : i;
+        out[(size_t)slot * N + site] = v;
+    }
+};
+
+template <class L>
+__device__ __forceinline__ Pusher<L> make_pusher(const Params &P, int x, int y, int z, int i,
+                                                 unsigned fluid_nb)
+{
+    const int nx = P.nx, nxy = P.nx * P.ny;
+    return Pusher<L>{fluid_nb, i, (int)P.N,
+                     x + 1 == P.nx ? 1 - P.nx : 1, x == 0 ? P.nx - 1 : -1,
+                     (y + 1 == P.ny ? 1 - P.ny : 1) * nx, (y == 0 ? P.ny - 1 : -1) * nx,
+                     (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, (z == 0 ? P.nz - 1 : -1) * nxy};
+}
+
+// Moments of the (shifted, gs = g - w) momentum populations: dp = sum gs, jm = sum e gs,
+// m2 = (sum ex^2 gs, sum ey^2 gs, sum ez^2 gs, sum ex ey gs, sum ex ez gs, sum ey ez gs).
+template <int D, class Pops>
+__device__ __forceinline__ void momentum_moments(const Pops &pops, float &dp, float (&jm)[3],
+                                                 float (&m2)[6])
+{
+    using L = Lat<D>;
+    dp = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        jm[a] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        m2[k] = 0.0f;
+#pragma unroll
+    for (int n = 0; n < L::Q; n++) {
+        const float v = pops.g(n);
+        dp += v;
+        if (L::ex(n))
+            jm[0] += L::ex(n) > 0 ? v : -v;
+        if (L::ey(n))
+            jm[1] += L::ey(n) > 0 ? v : -v;
+        if (L::ez(n))
+            jm[2] += L::ez(n) > 0 ? v : -v;
+        if (L::ex(n))
+            m2[0] += v;   // sum ex^2 gs
+        if (L::ey(n))
+            m2[1] += v;
+        if (L::ez(n))
+            m2[2] += v;
+        if (L::ex(n) && L::ey(n))
+            m2[3] += L::ex(n) * L::ey(n) > 0 ? v : -v;
+        if (L::ex(n) && L::ez(n))
+            m2[4] += L::ex(n) * L::ez(n) > 0 ? v : -v;
+        if (L::ey(n) && L::ez(n))
+            m2[5] += L::ey(n) * L::ez(n) > 0 ? v : -v;
+    }
+}
+
+// Momentum collision (incompressible equilibrium, Guo forcing, MRT) and its push.
+template <int D, class Push>
+__device__ __forceinline__ void momentum_collide(const Params &P, const State &S, const Push &push,
+                                                 const float (&Pc)[3],
+                                                 float dp, const float (&m2)[6],
+                                                 const float (&u)[3], const float (&F)[3])
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q;
+    constexpr float inv_cs2 = 3.0f;
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
+    const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
+    const float c_b = 1.0f - P.s_bulk;
+    // non-equilibrium moments of g - g_eq + R/2 (deviatoric / off-diagonal / trace):
+    // second moments of the populations less those of the equilibrium (c_s^2 p* I + u u)
+    // plus half those of the force term (u F + F u)
+    const float uFd[3] = {u[0] * F[0], u[1] * F[1], u[2] * F[2]};
+    const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) + (uFd[0] - uFd[1]);
+    const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) + (uFd[0] - uFd[2]);
+    const float dxy = m2[3] - u[0] * u[1] + 0.5f * (u[0] * F[1] + u[1] * F[0]);
+    const float dxz = m2[4] - u[0] * u[2] + 0.5f * (u[0] * F[2] + u[2] * F[0]);
+    const float dyz = m2[5] - u[1] * u[2] + 0.5f * (u[1] * F[2] + u[2] * F[1]);
+    const float dT = (m2[0] + m2[1] + m2[2]) - (float)D * (1.0f / 3.0f) * dp - uu + uF;
+    // w_n [C0 + e.V + (e.u)(4.5 e.u + 4.5 e.F)] = g_eq,n - w_n + R_n / 2
+    const float C0 = dp - 1.5f * uu - 1.5f * uF;
+    const float V[3] = {3.0f * u[0] + 1.5f * F[0], 3.0f * u[1] + 1.5f * F[1],
+                        3.0f * u[2] + 1.5f * F[2]};
+    float sum = 0.0f;
+#pragma unroll
+    for (int n = 1; n < Q; n++) {
+        const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+        const int e2 = cx * cx + cy * cy + cz * cz;
+        const float eu = (cx ? (cx > 0 ? u[0] : -u[0]) : 0.f) + (cy ? (cy > 0 ? u[1] : -u[1]) : 0.f) +
+                         (cz ? (cz > 0 ? u[2] : -u[2]) : 0.f);
+        const float eF = (cx ? (cx > 0 ? F[0] : -F[0]) : 0.f) + (cy ? (cy > 0 ? F[1] : -F[1]) : 0.f) +
+                         (cz ? (cz > 0 ? F[2] : -F[2]) : 0.f);
+        const float eV = (cx ? (cx > 0 ? V[0] : -V[0]) : 0.f) + (cy ? (cy > 0 ? V[1] : -V[1]) : 0.f) +
+                         (cz ? (cz > 0 ? V[2] : -V[2]) : 0.f);
+        float v = L::w(n) * (C0 + eV + eu * (4.5f * eu + 4.5f * eF));
+        float corr = 0.0f, corrT = 0.0f;
+        if (D == 3) {
+            if (e2 == 1) {
+                corr = cx ? (d1 + d2) * (1.0f / 6.0f)
+                          : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
+                                : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
+                corrT = dT * (1.0f / 6.0f);
+            } else {
+                corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
+            }
+        } else {
+            if (e2 == 1) {
+                corr = cx ? 0.25f * d1 : -0.25f * d1;
+                corrT = 0.25f * dT;
+            } else {
+                corr = 0.25f * cx * cy * dxy;
+            }
+        }
+        v += c_nu * corr + c_b * corrT;
+        sum += v;
+        push(S.g_out, n, v);
+    }
+    // rest population: exact remainder of the conserved zeroth moment (the FP32
+    // weights do not sum to 1 exactly, which would otherwise create mass every step).
+    // The shifted populations are small, so the sums' rounding is far below the
+    // phase fields' (whose rest populations use rest_acc).
+    push(S.g_out, 0, dp - sum);
+    if (!isfinite(dp + u[0] + u[1] + u[2]))
+        atomicOr(S.flag, 1);
+}
+
+// Collision of phase field c (Eqs. 15-17) and its push.
+template <int D, class Push, class Pops>
+__device__ __forceinline__ void phase_collide(const Params &P, const State &S, const Push &push,
+                                              const Pops &pops, int c,
+                                              float Pp, float Po, const float (&FP)[3],
+                                              const float (&u)[3], const float (&uo)[3])
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q;
+    constexpr float inv_cs2 = 3.0f;
+    const float c_phi = 1.0f - P.inv_tau_phi;
+    float jf[3] = {0.f, 0.f, 0.f}, fin[Q];
+#pragma unroll
+    for (int n = 1; n < Q; n++) {
+        const float v = pops.phi(c, n);
+        fin[n] = v;
+        if (L::ex(n))
+            jf[0] += L::ex(n) > 0 ? v : -v;
+        if (L::ey(n))
+            jf[1] += L::ey(n) > 0 ? v : -v;
+        if (L::ez(n))
+            jf[2] += L::ez(n) > 0 ? v : -v;
+    }
+    float B[3], del[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float A = L::cs2 * FP[a] + (Pp * u[a] - Po * uo[a]);
+        del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A);
+        B[a] = inv_cs2 * Pp * u[a] + 0.5f * inv_cs2 * A;   // w_n (P + e.B) = f_eq + C/2
+    }
+    float *out = S.fphi_out + (size_t)c * Q * (size_t)P.N;
+    float dsum = 0.0f;
+#pragma unroll
+    for (int n = 1; n < Q; n++) {
+        const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+        const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
+                         (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
+        float v = L::w(n) * (Pp + eB);
+        if (cx * cx + cy * cy + cz * cz == 1)
+            v += (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
+                 (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
+        dsum = rest_acc(dsum, fin[n], v);
+        push(out, n, v);
+    }
+    push(out, 0, __fadd_rn(pops.phi(c, 0), dsum));   // Phi is conserved
+}
+
+// Charge collision (Eq. 20b: advection-diffusion, d(rho u)/dt, conduction) and its push.
+template <int D, class Push, class Pops>
+__device__ __forceinline__ void charge_collide(const Params &P, const State &S, const Push &push,
+                                               const Pops &pops,
+                                               float rho, float rho_o, float qsrc, float q_o,
+                                               const float (&u)[3], const float (&uo)[3])
+{
+    using L = Lat<D>;
+    constexpr int QS = L::QS;
+    constexpr float inv_cs2s = 1.0f / L::cs2s;
+    float jr[3] = {0.f, 0.f, 0.f}, fr[QS];
+#pragma unroll
+    for (int n = 1; n < QS; n++) {
+        const float v = pops.rho(n);
+        fr[n] = v;
+        if (L::ex(n))
+            jr[0] += L::ex(n) > 0 ? v : -v;
+        if (L::ey(n))
+            jr[1] += L::ey(n) > 0 ? v : -v;
+        if (L::ez(n))
+            jr[2] += L::ez(n) > 0 ? v : -v;
+    }
+    const float c_rho = 1.0f - P.inv_tau_rho;
+    const float Qt = qsrc + 0.5f * (qsrc - q_o);
+    float B[3], del[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float Dm = rho * u[a] - rho_o * uo[a];
+        del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm);
+        B[a] = inv_cs2s * (rho * u[a] + 0.5f * Dm);
+    }
+    const float C0 = rho + Qt;
+    float dsum = 0.0f;
+#pragma unroll
+    for (int n = 1; n < QS; n++) {
+        const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+        const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
+                         (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
+        const float ed = (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
+                         (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
+        const float v = L::ws(n) * (C0 + eB) + ed;
+        dsum = rest_acc(dsum, fr[n], v);
+        push(S.frho_out, n, v);
+    }
+    // zeroth moment: rho_e + source
+    push(S.frho_out, 0, __fadd_rn(__fadd_rn(pops.rho(0), Qt), dsum));
+}
+
+// Sharpening flux F_Phi,i of Eq. 18 from the site's Phi_i and their gradients.
+__device__ __forceinline__ void sharpening_flux(float W, const float (&Pc)[3],
+                                                const float (&gP)[3][3], float (&FPhi)[3][3])
+{
+    float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        // n = grad / sqrt(|grad|^2 + 1e-10): continuous where grad Phi vanishes
+        const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
+                               gP[c][2] * gP[c][2] + 1e-10f);
+        const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            ln[c][a] = lam * gP[c][a];
+            J[a] += ln[c][a];
+        }
+        sumsq += Pc[c] * Pc[c];
+    }
+    const float inv_sumsq = 1.0f / sumsq;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float r = Pc[c] * Pc[c] * inv_sumsq;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            FPhi[c][a] = ln[c][a] - r * J[a];
+    }
+}
+
 // Everything the step does at one fluid site after the moments and the Poisson solve:
 // stencils, forces, the three collisions, push streaming, observable contributions.
 // Written for a low instruction count: 32-bit neighbour offsets computed once, the
@@ -341,18 +608,8 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
                                              float (&ob)[NOBS])
 {
     using L = Lat<D>;
-    constexpr int Q = L::Q, QS = L::QS;
+    constexpr int Q = L::Q;
     const int N = (int)P.N;
-    const int nx = P.nx, nxy = P.nx * P.ny;
-    // periodic neighbour offsets
-    const int oxp = x + 1 == P.nx ? 1 - P.nx : 1, oxm = x == 0 ? P.nx - 1 : -1;
-    const int oyp = (y + 1 == P.ny ? 1 - P.ny : 1) * nx, oym = (y == 0 ? P.ny - 1 : -1) * nx;
-    const int ozp = (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, ozm = (z == 0 ? P.nz - 1 : -1) * nxy;
-    auto off = [&](int n) -> int {
-        return (L::ex(n) > 0 ? oxp : (L::ex(n) < 0 ? oxm : 0)) +
-               (L::ey(n) > 0 ? oyp : (L::ey(n) < 0 ? oym : 0)) +
-               (L::ez(n) > 0 ? ozp : (L::ez(n) < 0 ? ozm : 0));
-    };
     // ---- stencils of Phi_i and phi over the flow lattice
     float Pc[3], pot_i, lo_i;
     int pt_i;
@@ -434,60 +691,11 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
 
     // ---- sharpening flux F_Phi,i (Eq. 18)
     float FPhi[3][3];
-    {
-        float ln[3][3], J[3] = {0.f, 0.f, 0.f}, sumsq = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            // n = grad / sqrt(|grad|^2 + 1e-10): continuous where grad Phi vanishes
-            const float gn = sqrtf(gP[c][0] * gP[c][0] + gP[c][1] * gP[c][1] +
-                                   gP[c][2] * gP[c][2] + 1e-10f);
-            const float lam = 4.0f / W * fabsf(Pc[c] * (1.0f - Pc[c])) / gn;
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                ln[c][a] = lam * gP[c][a];
-                J[a] += ln[c][a];
-            }
-            sumsq += Pc[c] * Pc[c];
-        }
-        const float inv_sumsq = 1.0f / sumsq;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const float r = Pc[c] * Pc[c] * inv_sumsq;
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                FPhi[c][a] = ln[c][a] - r * J[a];
-        }
-    }
+    sharpening_flux(P.W, Pc, gP, FPhi);
 
     // ---- momentum moments (shifted populations gs = g - w), velocity
-    float gs[Q];
-    float dp = 0.0f, jm[3] = {0.f, 0.f, 0.f}, m2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int n = 0; n < Q; n++) {
-        const float v = pops.g(n);
-        gs[n] = v;
-        dp += v;
-        constexpr int dummy = 0;
-        (void)dummy;
-        if (L::ex(n))
-            jm[0] += L::ex(n) > 0 ? v : -v;
-        if (L::ey(n))
-            jm[1] += L::ey(n) > 0 ? v : -v;
-        if (L::ez(n))
-            jm[2] += L::ez(n) > 0 ? v : -v;
-        if (L::ex(n))
-            m2[0] += v;   // sum ex^2 gs
-        if (L::ey(n))
-            m2[1] += v;
-        if (L::ez(n))
-            m2[2] += v;
-        if (L::ex(n) && L::ey(n))
-            m2[3] += L::ex(n) * L::ey(n) > 0 ? v : -v;
-        if (L::ex(n) && L::ez(n))
-            m2[4] += L::ex(n) * L::ez(n) > 0 ? v : -v;
-        if (L::ey(n) && L::ez(n))
-            m2[5] += L::ey(n) * L::ez(n) > 0 ? v : -v;
-    }
+    float dp, jm[3], m2[6];
+    momentum_moments<D>(pops, dp, jm, m2);
     float u[3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -515,159 +723,12 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
         S.u[a * (size_t)N + i] = u[a];
     S.q[i] = qsrc;
 
-    // push f*_n to x + e_n, or into the opposite slot at x when x + e_n is solid
-    auto push = [&](float *out, int n, float v) {
-        const bool fl = (fluid_nb >> n) & 1u;
-        const int slot = fl ? n : opposite(n);
-        const int site = fl ? i + off(n) : i;
-        out[(size_t)slot * N + site] = v;
-    };
-
-    // ---- momentum collision (incompressible equilibrium, Guo forcing, MRT)
-    {
-        const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-        const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
-        const float c_nu = 1.0f - 1.0f / (inv_cs2 * nu + 0.5f);
-        const float c_b = 1.0f - P.s_bulk;
-        // non-equilibrium moments of g - g_eq + R/2 (deviatoric / off-diagonal / trace):
-        // second moments of the populations less those of the equilibrium (c_s^2 p* I + u u)
-        // plus half those of the force term (u F + F u)
-        const float uFd[3] = {u[0] * F[0], u[1] * F[1], u[2] * F[2]};
-        const float d1 = (m2[0] - m2[1]) - (u[0] * u[0] - u[1] * u[1]) + (uFd[0] - uFd[1]);
-        const float d2 = (m2[0] - m2[2]) - (u[0] * u[0] - u[2] * u[2]) + (uFd[0] - uFd[2]);
-        const float dxy = m2[3] - u[0] * u[1] + 0.5f * (u[0] * F[1] + u[1] * F[0]);
-        const float dxz = m2[4] - u[0] * u[2] + 0.5f * (u[0] * F[2] + u[2] * F[0]);
-        const float dyz = m2[5] - u[1] * u[2] + 0.5f * (u[1] * F[2] + u[2] * F[1]);
-        const float dT = (m2[0] + m2[1] + m2[2]) - (float)D * (1.0f / 3.0f) * dp - uu + uF;
-        // w_n [C0 + e.V + (e.u)(4.5 e.u + 4.5 e.F)] = g_eq,n - w_n + R_n / 2
-        const float C0 = dp - 1.5f * uu - 1.5f * uF;
-        const float V[3] = {3.0f * u[0] + 1.5f * F[0], 3.0f * u[1] + 1.5f * F[1],
-                            3.0f * u[2] + 1.5f * F[2]};
-        float sum = 0.0f;
+    const Pusher<L> push = make_pusher<L>(P, x, y, z, i, fluid_nb);
+    momentum_collide<D>(P, S, push, Pc, dp, m2, u, F);
 #pragma unroll
-        for (int n = 1; n < Q; n++) {
-            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const int e2 = cx * cx + cy * cy + cz * cz;
-            const float eu = (cx ? (cx > 0 ? u[0] : -u[0]) : 0.f) + (cy ? (cy > 0 ? u[1] : -u[1]) : 0.f) +
-                             (cz ? (cz > 0 ? u[2] : -u[2]) : 0.f);
-            const float eF = (cx ? (cx > 0 ? F[0] : -F[0]) : 0.f) + (cy ? (cy > 0 ? F[1] : -F[1]) : 0.f) +
-                             (cz ? (cz > 0 ? F[2] : -F[2]) : 0.f);
-            const float eV = (cx ? (cx > 0 ? V[0] : -V[0]) : 0.f) + (cy ? (cy > 0 ? V[1] : -V[1]) : 0.f) +
-                             (cz ? (cz > 0 ? V[2] : -V[2]) : 0.f);
-            float v = L::w(n) * (C0 + eV + eu * (4.5f * eu + 4.5f * eF));
-            float corr = 0.0f, corrT = 0.0f;
-            if (D == 3) {
-                if (e2 == 1) {
-                    corr = cx ? (d1 + d2) * (1.0f / 6.0f)
-                              : (cy ? d2 * (1.0f / 6.0f) - d1 * (1.0f / 3.0f)
-                                    : d1 * (1.0f / 6.0f) - d2 * (1.0f / 3.0f));
-                    corrT = dT * (1.0f / 6.0f);
-                } else {
-                    corr = 0.25f * (cx * cy * dxy + cx * cz * dxz + cy * cz * dyz);
-                }
-            } else {
-                if (e2 == 1) {
-                    corr = cx ? 0.25f * d1 : -0.25f * d1;
-                    corrT = 0.25f * dT;
-                } else {
-                    corr = 0.25f * cx * cy * dxy;
-                }
-            }
-            v += c_nu * corr + c_b * corrT;
-            sum += v;
-            push(S.g_out, n, v);
-        }
-        // rest population: exact remainder of the conserved zeroth moment (the FP32
-        // weights do not sum to 1 exactly, which would otherwise create mass every step).
-        // The shifted populations are small, so the sums' rounding is far below the
-        // phase fields' (whose rest populations use rest_acc).
-        push(S.g_out, 0, dp - sum);
-        if (!isfinite(dp + u[0] + u[1] + u[2]))
-            atomicOr(S.flag, 1);
-    }
-
-    // ---- phase-field collisions (Eqs. 15-17)
-    const float c_phi = 1.0f - P.inv_tau_phi;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        float jf[3] = {0.f, 0.f, 0.f}, fin[Q];
-#pragma unroll
-        for (int n = 1; n < Q; n++) {
-            const float v = pops.phi(c, n);
-            fin[n] = v;
-            if (L::ex(n))
-                jf[0] += L::ex(n) > 0 ? v : -v;
-            if (L::ey(n))
-                jf[1] += L::ey(n) > 0 ? v : -v;
-            if (L::ez(n))
-                jf[2] += L::ez(n) > 0 ? v : -v;
-        }
-        const float Pp = Pc[c];
-        float B[3], del[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float A = L::cs2 * FPhi[c][a] + (Pp * u[a] - Po[c] * uo[a]);
-            del[a] = c_phi * 0.5f * (jf[a] - Pp * u[a] + 0.5f * A);
-            B[a] = inv_cs2 * Pp * u[a] + 0.5f * inv_cs2 * A;   // w_n (P + e.B) = f_eq + C/2
-        }
-        float *out = S.fphi_out + (size_t)c * Q * N;
-        float dsum = 0.0f;
-#pragma unroll
-        for (int n = 1; n < Q; n++) {
-            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
-                             (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
-            float v = L::w(n) * (Pp + eB);
-            if (cx * cx + cy * cy + cz * cz == 1)
-                v += (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
-                     (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
-            dsum = rest_acc(dsum, fin[n], v);
-            push(out, n, v);
-        }
-        push(out, 0, __fadd_rn(pops.phi(c, 0), dsum));   // Phi is conserved
-    }
-
-    // ---- charge collision (Eq. 20b): advection-diffusion, d(rho u)/dt, conduction
-    {
-        constexpr float inv_cs2s = 1.0f / L::cs2s;
-        float jr[3] = {0.f, 0.f, 0.f}, fr[QS];
-#pragma unroll
-        for (int n = 1; n < QS; n++) {
-            const float v = pops.rho(n);
-            fr[n] = v;
-            if (L::ex(n))
-                jr[0] += L::ex(n) > 0 ? v : -v;
-            if (L::ey(n))
-                jr[1] += L::ey(n) > 0 ? v : -v;
-            if (L::ez(n))
-                jr[2] += L::ez(n) > 0 ? v : -v;
-        }
-        const float c_rho = 1.0f - P.inv_tau_rho;
-        const float Qt = qsrc + 0.5f * (qsrc - q_o);
-        float B[3], del[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float Dm = rho * u[a] - rho_o * uo[a];
-            del[a] = c_rho * 0.5f * (jr[a] - rho * u[a] + 0.5f * Dm);
-            B[a] = inv_cs2s * (rho * u[a] + 0.5f * Dm);
-        }
-        const float C0 = rho + Qt;
-        float dsum = 0.0f;
-#pragma unroll
-        for (int n = 1; n < QS; n++) {
-            const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
-            const float eB = (cx ? (cx > 0 ? B[0] : -B[0]) : 0.f) + (cy ? (cy > 0 ? B[1] : -B[1]) : 0.f) +
-                             (cz ? (cz > 0 ? B[2] : -B[2]) : 0.f);
-            const float ed = (cx ? (cx > 0 ? del[0] : -del[0]) : 0.f) + (cy ? (cy > 0 ? del[1] : -del[1]) : 0.f) +
-                             (cz ? (cz > 0 ? del[2] : -del[2]) : 0.f);
-            const float v = L::ws(n) * (C0 + eB) + ed;
-            dsum = rest_acc(dsum, fr[n], v);
-            push(S.frho_out, n, v);
-        }
-        // zeroth moment: rho_e + source
-        push(S.frho_out, 0, __fadd_rn(__fadd_rn(pops.rho(0), Qt), dsum));
-    }
+    for (int c = 0; c < 3; c++)
+        phase_collide<D>(P, S, push, pops, c, Pc[c], Po[c], FPhi[c], u, uo);
+    charge_collide<D>(P, S, push, pops, rho, rho_o, qsrc, q_o, u, uo);
 
     // ---- observable contributions
     ob[0] = Pc[0];

@@ -69,8 +69,10 @@ struct lbehd_handle {
         size_t n = 0;
         int cz2 = 0;               // coarsening to the next level halves z too
         float *D = nullptr, *kx = nullptr, *ky = nullptr, *kz = nullptr, *x = nullptr, *b = nullptr;
-        float *r = nullptr;            // residual scratch of the restriction
+        float *r = nullptr;            // residual scratch of the restriction; the
+                                       // block-local smoother's output on the way up
         dim3 grid, grid_half;
+        int nbj = 0;                   // blocks of the block-local smoother
     };
     std::vector<Level> mg;
     // inc[s & 1] holds the potential increment of step s; the warm start of step s is the
@@ -101,6 +103,9 @@ struct lbehd_handle {
     dim3 grid_tile[3];             // TX x TY tiles of the staged collide kernel
     size_t nblocks_tile[3] = {0, 0, 0};
     int mg_nu = 2, mg_coarse = 8;
+    int mg_smoother = 1;           // LBEHD_OPT_MG_SMOOTHER: 1 block-local, 0 whole-level sweeps
+    int bj_nu = 3;                 // sweep pairs per block of the block-local smoother
+    bool bj_ok = false;            // this lattice allows it (a tail level; see mg build)
     int tail_level = -1;           // first level handled by k_mg_tail (-1: none)
     TailLevels tail{};
     size_t tail_smem = 0;
@@ -345,7 +350,7 @@ int ps_setup(lbehd_handle *h)
     A.nb1 = (int)h->nblocks1d;
     for (int l = 0; l <= h->tail_level; l++) {
         const auto &L = h->mg[l];
-        A.L[l] = PsLevel{L.d, L.cz2, (int)L.n, L.D, L.kx, L.ky, L.kz, L.b, L.x};
+        A.L[l] = PsLevel{L.d, L.cz2, (int)L.n, L.D, L.kx, L.ky, L.kz, L.b, L.x, L.nbj, L.r};
     }
     A.tail = h->tail;
     A.tail.b0 = h->mg[h->tail_level].b;
@@ -369,6 +374,8 @@ int ps_setup(lbehd_handle *h)
 
 bool ps_use(const lbehd_handle *h) { return h->ps_ok && h->ps_on; }
 
+bool bj_use(const lbehd_handle *h) { return h->bj_ok && h->mg_smoother == 1; }
+
 // One persistent solve on h->ls: the forward step's (increment x, this step's charge rho) or
 // the adjoint's (solution x, right-hand side rhs), after the launch that forms its start.
 template <int D>
@@ -377,6 +384,8 @@ int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float
     PsArgs A = h->ps;
     A.spin_limit = h->ps_spin_limit;
     A.extra = h->ps_extra;
+    A.bj = bj_use(h) ? 1 : 0;
+    A.nu_bj = h->bj_nu;
     A.mode = mode;
     A.x = x;
     A.rho = rho;
@@ -450,8 +459,38 @@ void vcycle(lbehd_handle *h, size_t l)
     }
 }
 
+// The same V-cycle with the block-local smoother (mg_bj_block): on the way down one smoothing
+// launch from zero per level, then the residual and the restriction; on the way up one
+// launch of prolongation + smoothing per level into the level's r array; level 0's also
+// writes the r . z partials (one per block) into the CG partials. z ends in mg[0].r.
+template <int D>
+void vcycle_bj(lbehd_handle *h, size_t l)
+{
+    const auto &L = h->mg[l];
+    if ((int)l == h->tail_level) {
+        TailLevels T = h->tail;
+        T.b0 = L.b;
+        T.x0 = L.x;
+        k_mg_tail<<<1, TAIL_THREADS, h->tail_smem, h->ls>>>(T);
+        return;
+    }
+    const auto &C = h->mg[l + 1];
+    k_mg_bj<D><<<L.nbj, BJ_THREADS, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, nullptr, L.x,
+                                                h->bj_nu, 0, L.d, 0, nullptr, nullptr, nullptr);
+    k_mg_resid<<<L.grid, h->block, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, L.r);
+    k_mg_restrict_sum<<<C.grid, h->block, 0, h->ls>>>(L.d, C.d, L.cz2, L.r, C.b);
+    vcycle_bj<D>(h, l + 1);
+    const float *xc = (int)l + 1 == h->tail_level ? C.x : C.r;
+    k_mg_bj<D><<<L.nbj, BJ_THREADS, 0, h->ls>>>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, L.r,
+                                                h->bj_nu, 1, C.d, L.cz2, xc,
+                                                l == 0 ? h->cg_r : nullptr,
+                                                l == 0 ? h->cg_partials : nullptr);
+}
+
 int vcycle_launches(const lbehd_handle *h)
 {
+    if (bj_use(h))
+        return 4 * h->tail_level + 1;
     const int levels = (int)h->mg.size();
     if (h->tail_level >= 0)
         return h->tail_level * (4 * h->mg_nu + 3) + 1;   // memsets not counted
@@ -470,11 +509,18 @@ template <int D>
 void pcg_iteration(lbehd_handle *h, float *x)
 {
     auto &L0 = h->mg[0];
-    launch(h, LBEHD_KC_MG, vcycle_launches(h), [&] { vcycle(h, 0); });
-    launch(h, LBEHD_KC_CG, 8, [&] {
-        k_pcg_dot<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_r, L0.x, h->cg_partials);
-        cg_scalar(h, 1, 1, h->nblocks1d);
-        k_pcg_p<<<h->grid1d, h->block, 0, h->ls>>>(h->N, L0.x, h->cg_p, h->cg_s);
+    const bool bj = bj_use(h);
+    launch(h, LBEHD_KC_MG, vcycle_launches(h), [&] {
+        if (bj)
+            vcycle_bj<D>(h, 0);
+        else
+            vcycle(h, 0);
+    });
+    launch(h, LBEHD_KC_CG, bj ? 7 : 8, [&] {
+        if (!bj)
+            k_pcg_dot<<<h->grid1d, h->block, 0, h->ls>>>(h->N, h->cg_r, L0.x, h->cg_partials);
+        cg_scalar(h, 1, 1, bj ? (size_t)L0.nbj : h->nblocks1d);
+        k_pcg_p<<<h->grid1d, h->block, 0, h->ls>>>(h->N, bj ? L0.r : L0.x, h->cg_p, h->cg_s);
         k_pcg_Ap<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(L0.d, h->eps, h->info, L0.D,
                                                                        h->cg_p, h->cg_q,
                                                                        h->cg_partials);
@@ -961,6 +1007,7 @@ int set_params(lbehd_handle *h)
     P.inv_tau_rho = (float)(1.0 / (0.5 + c.alpha / cs2s));
     P.s_bulk = (float)c.s_bulk;
     h->mg_nu = c.mg_nu > 0 ? c.mg_nu : 2;
+    h->bj_nu = c.mg_nu > 0 ? c.mg_nu : 3;
     h->mg_coarse = c.mg_coarse_sweeps > 0 ? c.mg_coarse_sweeps : 8;
     h->mg_scale = c.mg_scale > 0.0 ? (float)c.mg_scale : 0.6f;
     return LBEHD_OK;
@@ -1168,6 +1215,12 @@ int init_impl(lbehd_handle *h)
                 break;
             }
         }
+        // the block-local smoother runs on the levels above a tail, and level 0's r . z
+        // partials (one per block) must fit the CG partial array
+        for (auto &L : h->mg)
+            L.nbj = bj_blocks<D>(L.d);
+        h->bj_ok = h->tail_level > 0 &&
+                   (size_t)h->mg[0].nbj <= std::max(h->nblocks, h->nblocks1d);
     }
     CK(h, cudaMallocHost(&h->h_cg, sizeof(CgScalars)));
     {
@@ -1388,6 +1441,19 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_POISSON_KERNEL takes 0 or 1");
         CK(h, cudaStreamSynchronize(h->stream));
         h->ps_on = value != 0;
+        for (auto &e : h->adj.solve)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    } else if (option == LBEHD_OPT_MG_SMOOTHER) {
+        if (value < 0 || value > 1)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_MG_SMOOTHER takes 0 or 1");
+        if (value == 1 && h->batch_owned)
+            return fail(h, LBEHD_ERR_INVALID_ARG,
+                        "batched instances run the whole-level smoother (LBEHD_OPT_MG_SMOOTHER 0)");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->mg_smoother = (int)value;
         for (auto &e : h->adj.solve)
             if (e) {
                 cudaGraphExecDestroy(e);
@@ -3200,6 +3266,8 @@ int lbehd_get_option(lbehd_handle *h, int option, long long *value)
         *value = h->adj.use_traj ? 1 : 0;
     else if (option == LBEHD_OPT_POISSON_KERNEL)
         *value = ps_use(h) ? 1 : 0;
+    else if (option == LBEHD_OPT_MG_SMOOTHER)
+        *value = bj_use(h) ? 1 : 0;
     else
         return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
     return LBEHD_OK;
@@ -3364,6 +3432,7 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
         if (rc)
             return bail(rc, "instance " + std::to_string(i) + ": " + g_init_error);
         h->batch_owned = true;
+        h->mg_smoother = 0;   // the batched V-cycle sweeps whole levels
         b->inst.push_back(h);
     }
     auto balloc = [&](size_t bytes) -> void * {

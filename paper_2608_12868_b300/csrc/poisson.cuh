@@ -399,6 +399,157 @@ __global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
         mg_prolong_cell(f, c, cz2, Df, xc, xf, x, blockIdx.y, blockIdx.z);
 }
 
+// ---------------------------------------------------------------- block-local smoother
+//
+// The alternative smoother (LBEHD_OPT_MG_SMOOTHER = 1): block-Jacobi between blocks of a level,
+// red-black Gauss-Seidel within each block. A level is tiled into blocks of BjShape cells
+// (1024: one per thread of a 1024-thread CTA; ragged at the high ends). A block copies x on
+// its cells and a one-cell halo (periodic) into shared memory, runs `nu` red-black sweep pairs
+// there with the halo held at its value at the start, and writes its own cells to the output
+// array. Each block's result depends only on the input arrays, so the blocks may run in any
+// order and on any CTA:
+//  * on the way down the level starts from x = 0 (nothing is read) and the pairs run
+//    (red, black); the output is the level's x;
+//  * on the way up every copied cell first takes the coarse correction, x + x_c(parent) on
+//    active cells (the arithmetic of mg_prolong_cell), and the pairs run (black, red), the
+//    transpose of the way down, so the V-cycle stays symmetric; the output goes to a second
+//    array (the level's restriction scratch), since other blocks still read x as their halo.
+// A cell's update has the arithmetic of mg_gs_cell, with its neighbours read from the copy.
+// With r given (level 0 on the way up), the block also forms its partial of r . z over its
+// cells (z = the smoothed x): FP32 within each warp, then FP64 over the warps in order.
+// Against whole-level red-black sweeps, one V-cycle of this smoother costs one grid-wide
+// dependency per level and direction instead of one per half sweep.
+constexpr int BJ_THREADS = 1024;
+
+template <int D>
+struct BjShape;
+template <>
+struct BjShape<3> {
+    static constexpr int X = 16, Y = 8, Z = 8;
+};
+template <>
+struct BjShape<2> {
+    static constexpr int X = 32, Y = 32, Z = 1;
+};
+
+template <int D>
+__host__ __device__ inline int bj_blocks(const MgDims &d)
+{
+    using S = BjShape<D>;
+    return ((d.nx + S::X - 1) / S::X) * ((d.ny + S::Y - 1) / S::Y) * ((d.nz + S::Z - 1) / S::Z);
+}
+
+// v in [-1, n + block extent] folded into [0, n) (a level can be smaller than a block).
+__device__ __forceinline__ int bj_wrap(int v, int n)
+{
+    v = v < 0 ? v + n : v;
+    return v >= n ? v % n : v;
+}
+
+template <int D>
+__device__ __forceinline__ void mg_bj_block(const MgDims &d, const float *Dg, const float *kx,
+                                            const float *ky, const float *kz, const float *b,
+                                            const float *xin, float *xout, int blk, int nu,
+                                            bool up, const MgDims &c, int cz2, const float *xc,
+                                            const float *r, double *partials)
+{
+    using S = BjShape<D>;
+    constexpr int HX = S::X + 2, HY = S::Y + 2, HZ = D == 3 ? S::Z + 2 : 1;
+    constexpr int NH = HX * HY * HZ, SZ = HX * HY;
+    static_assert(S::X * S::Y * S::Z == BJ_THREADS, "one cell per thread");
+    __shared__ float xs[NH];
+    __shared__ double wsm[BJ_THREADS / 32];
+    const int nbx = (d.nx + S::X - 1) / S::X, nby = (d.ny + S::Y - 1) / S::Y;
+    const int bx = blk % nbx, rest = blk / nbx;
+    const int x0 = bx * S::X, y0 = (rest % nby) * S::Y, z0 = (rest / nby) * S::Z;
+    const int t = threadIdx.x;
+    const int lx = t % S::X, ly = (t / S::X) % S::Y, lz = t / (S::X * S::Y);
+    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+    const bool own = x < d.nx && y < d.ny && z < d.nz;
+    const bool zterms = D == 3 && d.nz > 1;
+    float di = 0.0f, bi = 0.0f, ri = 0.0f, k[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int i = 0;
+    if (own) {
+        i = cell(d, x, y, z);
+        const Nb6 nb = nb6(d, i, x, y, z);
+        di = Dg[i];
+        bi = b[i];
+        k[0] = kx[i];
+        k[1] = kx[nb.n[1]];
+        k[2] = ky[i];
+        k[3] = ky[nb.n[3]];
+        if (zterms) {
+            k[4] = kz[i];
+            k[5] = kz[nb.n[5]];
+        }
+        if (r)
+            ri = r[i];
+    }
+    for (int e = t; e < NH; e += BJ_THREADS) {
+        float v = 0.0f;
+        if (up) {
+            const int hx = e % HX, hy = (e / HX) % HY, hz = e / SZ;
+            const int gx = bj_wrap(x0 - 1 + hx, d.nx), gy = bj_wrap(y0 - 1 + hy, d.ny);
+            const int gz = D == 3 ? bj_wrap(z0 - 1 + hz, d.nz) : 0;
+            const int g = cell(d, gx, gy, gz);
+            const float xg = xin[g];
+            v = Dg[g] > 0.0f
+                    ? __fadd_rn(xg, xc[cell(c, gx >> 1, gy >> 1, cz2 ? (gz >> 1) : gz)])
+                    : xg;
+        }
+        xs[e] = v;
+    }
+    __syncthreads();
+    const int h = (lx + 1) + HX * (ly + 1) + (D == 3 ? SZ * (lz + 1) : 0);
+    const int col = (x + y + z) & 1;
+    const bool act = own && di > 0.0f;
+    for (int s = 0; s < nu; s++) {
+        for (int half = 0; half < 2; half++) {
+            if (act && col == (up ? 1 - half : half)) {
+                float sum = __fmul_rn(k[0], xs[h + 1]);
+                sum = __fmaf_rn(k[1], xs[h - 1], sum);
+                sum = __fmaf_rn(k[2], xs[h + HX], sum);
+                sum = __fmaf_rn(k[3], xs[h - HX], sum);
+                if (zterms) {
+                    sum = __fmaf_rn(k[4], xs[h + SZ], sum);
+                    sum = __fmaf_rn(k[5], xs[h - SZ], sum);
+                }
+                xs[h] = __fdiv_rn(__fadd_rn(bi, sum), di);
+            }
+            __syncthreads();
+        }
+    }
+    if (own)
+        xout[i] = xs[h];
+    if (r) {
+        const float v = warp_sum(own ? __fmaf_rn(ri, xs[h], 0.0f) : 0.0f);
+        if ((t & 31) == 0)
+            wsm[t >> 5] = (double)v;
+        __syncthreads();
+        if (t == 0) {
+            double acc = 0.0;
+            for (int w = 0; w < BJ_THREADS / 32; w++)
+                acc += wsm[w];
+            partials[blk] = acc;
+        }
+    }
+    __syncthreads();   // the shared copies are rewritten by this CTA's next block
+}
+
+// One block-local smoothing pass of a level, one CTA per block.
+template <int D>
+__global__ void __launch_bounds__(BJ_THREADS, 1) k_mg_bj(MgDims d, const float *Dg,
+                                                         const float *kx, const float *ky,
+                                                         const float *kz, const float *b,
+                                                         const float *xin, float *xout, int nu,
+                                                         int up, MgDims c, int cz2,
+                                                         const float *xc, const float *r,
+                                                         double *partials)
+{
+    mg_bj_block<D>(d, Dg, kx, ky, kz, b, xin, xout, (int)blockIdx.x, nu, up != 0, c, cz2, xc, r,
+                   partials);
+}
+
 // ---------------------------------------------------------------- small-level tail
 
 constexpr int TAIL_MAX_LEVELS = 8;

@@ -60,12 +60,16 @@ struct PsLevel {
     int cz2, n;
     const float *D, *kx, *ky, *kz;
     float *b, *x;
+    int nbj;       // blocks of the block-local smoother
+    float *xo;     // its output on the way up (the level's restriction scratch)
 };
 
 struct PsArgs {
     int mode;                  // PS_FORWARD or PS_ADJOINT
     int nl;                    // levels smoothed by grid phases: 0 .. nl - 1
     int nu;                    // red-black sweeps before and after the coarse correction
+    int bj;                    // 1: block-local smoother (mg_bj_block), 0: whole-level sweeps
+    int nu_bj;                 // its sweep pairs per block
     int N, nbs, nb1;           // sites, BX-site blocks, 1D blocks (the partial partitions)
     PsLevel L[PS_MAX_LEVELS];  // 0 .. nl (level nl is the tail's finest)
     TailLevels tail;           // b0 = L[nl].b, x0 = L[nl].x
@@ -241,10 +245,12 @@ __device__ __forceinline__ float ps_first_red(int x, int y, int z, float bi, flo
 }
 
 // delta += alpha p, r -= alpha q, ||r||^2 over the sites of virtual block b, in site order;
-// then level 0's first red half sweep of the next V-cycle at the same sites (from the new r).
+// then, with first_red, level 0's first red half sweep of the next V-cycle at the same sites
+// (from the new r; the block-local smoother starts from zero by itself).
 __device__ __forceinline__ void ps_update_range(int n, const float *p, const float *q,
                                                 float *delta, float *r, float a, int b, int nb,
-                                                int t, float (&v)[1], const PsLevel &L0)
+                                                int t, float (&v)[1], const PsLevel &L0,
+                                                bool first_red)
 {
     const int S = nb * BX;
     for (int i0 = b * BX + t; i0 < n; i0 += PS_B * S) {
@@ -269,9 +275,11 @@ __device__ __forceinline__ void ps_update_range(int n, const float *p, const flo
                 const float ri = __fmaf_rn(-a, qq[j], rr[j]);
                 r[i] = ri;
                 v[0] = __fmaf_rn(ri, ri, v[0]);
-                int x, y, z;
-                cell_xyz(L0.d, i, x, y, z);
-                L0.x[i] = ps_first_red(x, y, z, ri, dg[j]);
+                if (first_red) {
+                    int x, y, z;
+                    cell_xyz(L0.d, i, x, y, z);
+                    L0.x[i] = ps_first_red(x, y, z, ri, dg[j]);
+                }
             }
         }
     }
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         __syncthreads();
     };
     const PsLevel &L0 = A.L[0];
-    float *z = L0.x;
+    float *z = A.bj ? L0.xo : L0.x;
 
     // the p buffers alternate: Ap reads the previous direction and writes the new one
     float *p_old = A.p, *p_new = A.p2;
@@ -582,10 +590,45 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         }
     };
 
+    // the same V-cycle with the block-local smoother: per level on the way down one
+    // smoothing phase from zero and the residual + restriction phase, on the way up one
+    // phase of prolongation + smoothing (into the level's xo); level 0's last phase also
+    // forms the r . z partials, one per block
+    auto vcycle_bj = [&]() {
+        for (int l = 0; l < A.nl && ok; l++) {
+            const PsLevel &L = A.L[l];
+            for (int blk = blockIdx.x; blk < L.nbj; blk += gridDim.x)
+                mg_bj_block<D>(L.d, L.D, L.kx, L.ky, L.kz, L.b, nullptr, L.x, blk, A.nu_bj, false,
+                               L.d, 0, nullptr, nullptr, nullptr);
+            sync();
+            ps_resid_restrict(L, A.L[l + 1], false);
+            sync();
+        }
+        if (!ok)
+            return;
+        if (blockIdx.x == 0) {
+            mg_tail_block(A.tail, tail_sm, tail_ops);
+            tail_ops = true;
+        }
+        sync();
+        for (int l = A.nl - 1; l >= 0 && ok; l--) {
+            const PsLevel &L = A.L[l], &C = A.L[l + 1];
+            const float *xc = l + 1 == A.nl ? C.x : C.xo;
+            for (int blk = blockIdx.x; blk < L.nbj; blk += gridDim.x)
+                mg_bj_block<D>(L.d, L.D, L.kx, L.ky, L.kz, L.b, L.x, L.xo, blk, A.nu_bj, true,
+                               C.d, L.cz2, xc, l == 0 ? A.r : nullptr, A.part[0]);
+            if (l > 0)
+                sync();
+        }
+    };
+
     // one preconditioned CG iteration on the increment (or adjoint potential) xv
     auto iteration = [&](float *xv) {
-        vcycle();
-        sync_scalar(A.part[0], 1, 1, A.nb1);   // r . z
+        if (A.bj)
+            vcycle_bj();
+        else
+            vcycle();
+        sync_scalar(A.part[0], 1, 1, A.bj ? L0.nbj : A.nb1);   // r . z
         if (!ok)
             return;
         const float beta = pcg_beta(&s);
@@ -609,7 +652,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
         const float alpha = (float)s.alpha;
         ps_for_vblocks(A.nb1, [&](int vb, int t) {
             float v[1] = {0.0f};
-            ps_update_range(A.N, p_new, A.q, xv, A.r, alpha, vb, A.nb1, t, v, L0);
+            ps_update_range(A.N, p_new, A.q, xv, A.r, alpha, vb, A.nb1, t, v, L0, !A.bj);
             ps_group_partials<1>(v, A.part[0], vb, A.nb1, gsm);
         });
         float *tp = p_old;

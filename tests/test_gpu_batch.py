@@ -2,7 +2,8 @@
 
 Every instance of a batch must compute what the same instance computes alone: the state
 arrays (populations, fields, potential) are compared bit for bit with single-instance
-runs in graph mode using the same collide kernel, after enough steps to include a
+runs in graph mode using the same collide kernel and the batched form's multigrid smoother
+(whole-level red-black sweeps, LBEHD_OPT_MG_SMOOTHER = 0), after enough steps to include a
 multigrid rebuild (every 16 steps). One instance is also compared with the FP64 oracle
 at the parity bars of the single-instance tests. The collide-kernel autotuner must leave
 the state untouched.
@@ -42,8 +43,16 @@ def uneven_3d():
     ]
 
 
-def single_run(gpu, w, variant, steps):
+def plain(gpu, w):
+    """A single handle with the batched form's smoother (whole-level sweeps), the runs a
+    batch instance reproduces bit for bit."""
     sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.set_option(gpu.OPT_MG_SMOOTHER, 0)
+    return sim
+
+
+def single_run(gpu, w, variant, steps):
+    sim = plain(gpu, w)
     sim.set_option(gpu.OPT_COLLIDE, variant)
     sim.step(steps)
     return sim
@@ -120,7 +129,7 @@ def test_batch_autotune_mixed_groups(gpu):
             assert np.array_equal(before[i][n], batch[i].array(n)), (i, n)
     batch.step(17)
     for i, w in enumerate(ws):
-        sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+        sim = plain(gpu, w)
         sim.step(3)
         sim.set_option(gpu.OPT_COLLIDE, variants[i])
         sim.step(17)
@@ -129,8 +138,8 @@ def test_batch_autotune_mixed_groups(gpu):
 
 def test_single_autotune_keeps_state(gpu):
     w = W.small_3d()
-    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
-    ref = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim = plain(gpu, w)
+    ref = plain(gpu, w)
     sim.step(5)
     ref.step(5)
     o0 = sim.observe()
@@ -178,7 +187,7 @@ def test_batched_sweep_64_instances(gpu):
         assert obs[i]["status"] == 0
         assert np.abs(obs[i]["mass"] / m0[i] - 1).max() <= 1e-6, i
     for i, w in enumerate(ws):
-        sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+        sim = plain(gpu, w)
         sim.set_option(gpu.OPT_COLLIDE, variants[i])
         sim.step(20)
         for name in ("g", "fphi", "frho", "pot"):
