@@ -754,17 +754,40 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
 // warp's sums in FP64 at the end of each block kept it 18 % busy over the whole collide
 // kernel (ncu). A block's FP32 partial carries ~1e-7 relative rounding, which the FP64 sum
 // over thousands of blocks does not accumulate into a bias.
+// Warp sums of the 16 observables, transposed: afterwards lane l holds the sum of
+// observable (l >> 1) & 15. Each round halves what a lane carries: it keeps the half its lane
+// bit selects, sends the other half to its partner and adds the partner's. The partners and
+// the operands of every addition are those of warp_sum's butterfly (offsets 16, 8, 4, 2, 1),
+// so each sum has warp_sum's bits; 16 shuffles and 16 adds instead of 80 and 80.
+__device__ __forceinline__ float warp_sum16_transposed(const float (&ob)[16])
+{
+    const int lane = threadIdx.x & 31;
+    float a8[8], a4[4], a2[2];
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        a8[j] = (b16 ? ob[j + 8] : ob[j]) +
+                __shfl_xor_sync(0xffffffffu, b16 ? ob[j] : ob[j + 8], 16);
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        a4[j] = (b8 ? a8[j + 4] : a8[j]) + __shfl_xor_sync(0xffffffffu, b8 ? a8[j] : a8[j + 4], 8);
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+        a2[j] = (b4 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, b4 ? a4[j] : a4[j + 2], 4);
+    float a = (b2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? a2[0] : a2[1], 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    return a;
+}
+
 __device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], double *partials,
                                                    size_t blk, size_t nblk)
 {
+    static_assert(NOBS == 16, "the transposed warp sum carries 16 observables");
     __shared__ float sm[NOBS][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NOBS; k++) {
-        const float v = warp_sum(ob[k]);
-        if (lane == 0)
-            sm[k][wid] = v;
-    }
+    const float v = warp_sum16_transposed(ob);
+    if ((lane & 1) == 0)
+        sm[(lane >> 1) & 15][wid] = v;
     __syncthreads();
     if (threadIdx.x < NOBS) {
         float acc = 0.0f;
