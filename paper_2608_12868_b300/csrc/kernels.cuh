@@ -222,12 +222,16 @@ __global__ void __launch_bounds__(BX) k_fields(Params P, FieldPtrs F)
 
 // Population sources for collide_site: straight from global memory, or from a
 // shared-memory tile staged by bulk copies.
+// Indices n N + i are 32-bit (19 N < 2^31 is checked at init); the 3 Q phase-field arrays
+// need 64 bits.
 struct GlobalPops {
     const float *__restrict__ gp, *__restrict__ fp, *__restrict__ rp;
-    size_t N, i;
-    int Q;
+    int N, i, Q;
     __device__ __forceinline__ float g(int n) const { return gp[n * N + i]; }
-    __device__ __forceinline__ float phi(int c, int n) const { return fp[(c * Q + n) * N + i]; }
+    __device__ __forceinline__ float phi(int c, int n) const
+    {
+        return fp[(size_t)(c * Q + n) * N + i];
+    }
     __device__ __forceinline__ float rho(int n) const { return rp[n * N + i]; }
 };
 
@@ -238,7 +242,7 @@ struct GlobalPops {
 struct StagedPops {
     const float *__restrict__ gp, *__restrict__ rp;
     const float *s;   // [phase array][tile site], stride BX
-    size_t N, i;
+    int N, i;
     int t, Q;
     __device__ __forceinline__ float g(int n) const { return gp[n * N + i]; }
     __device__ __forceinline__ float phi(int c, int n) const { return s[(c * Q + n) * BX + t]; }
@@ -343,9 +347,7 @@ struct Pusher {
     __device__ __forceinline__ void operator()(float *out, int n, float v) const
     {
         const bool fl = (fluid_nb >> n) & 1u;
-        const int slot = fl ? n : opposite(n);
-        const int site = fl ? i + off(n) : i;
-        out[(size_t)slot * N + site] = v;
+        out[fl ? n * N + (i + off(n)) : opposite(n) * N + i] = v;   // < 19 N < 2^31
     }
 };
 
@@ -805,7 +807,7 @@ __device__ __forceinline__ void collide_global_site(const Params &P, const State
 {
     const int i = x + P.nx * (y + P.ny * z);
     if (x < P.nx && (S.info[i] & 3) == PT_FLUID) {
-        const GlobalPops pops{S.g, S.fphi, S.frho, (size_t)P.N, (size_t)i, Lat<D>::Q};
+        const GlobalPops pops{S.g, S.fphi, S.frho, (int)P.N, i, Lat<D>::Q};
         const int nx = P.nx, nxy = P.nx * P.ny;
         const GlobalStencil st{S.phi, S.phi + P.N, S.phi + 2 * P.N, S.pot, S.pot_lo, S.info, i,
                                x + 1 == P.nx ? 1 - P.nx : 1, x == 0 ? P.nx - 1 : -1,
@@ -920,6 +922,7 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     // stencil fields of the tile and its halo, periodic in every direction: every load of
     // this thread is issued before the first shared-memory store
     constexpr int HIT = (HN + BX - 1) / BX;
+    const float *phi0 = S.phi, *phi1 = S.phi + N, *phi2 = S.phi + 2 * N;
     float hv[HIT][5];
     uint8_t hinf[HIT];
 #pragma unroll
@@ -931,10 +934,10 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
             gx += gx < 0 ? P.nx : (gx >= P.nx ? -P.nx : 0);
             gy += gy < 0 ? P.ny : (gy >= P.ny ? -P.ny : 0);
             gz += gz < 0 ? P.nz : (gz >= P.nz ? -P.nz : 0);
-            const size_t g = gx + (size_t)P.nx * (gy + (size_t)P.ny * gz);
-            hv[k][0] = S.phi[g];
-            hv[k][1] = S.phi[N + g];
-            hv[k][2] = S.phi[2 * N + g];
+            const int g = gx + P.nx * (gy + P.ny * gz);
+            hv[k][0] = phi0[g];
+            hv[k][1] = phi1[g];
+            hv[k][2] = phi2[g];
             hv[k][3] = S.pot[g];
             hv[k][4] = S.pot_lo[g];
             hinf[k] = S.info[g];
@@ -963,7 +966,7 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     }
     const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
     if (active && (__float_as_int(shb[h].y) & 3) == PT_FLUID) {
-        const StagedPops pops{S.g, S.frho, spop, N, (size_t)i, t, Q};
+        const StagedPops pops{S.g, S.frho, spop, (int)N, i, t, Q};
         const SmemStencil<D, TY> st{sha, shb, h};
         collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
