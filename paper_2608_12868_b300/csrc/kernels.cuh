@@ -146,16 +146,18 @@ __device__ __forceinline__ void fields_site(const Params &P, const FieldPtrs &F,
     const uint8_t *__restrict__ normal = F.normal;
     const int16_t *__restrict__ elec = F.elec;
     const double *__restrict__ V = F.V;
-    const size_t N = P.N, i = x + (size_t)P.nx * (y + (size_t)P.ny * z);
+    // 32-bit indices below 19 N < 2^31 (checked at init), from one base pointer per set
+    const int N = (int)P.N, i = x + P.nx * (y + P.ny * z);
     const uint8_t inf = info[i];
     float Ph[3] = {0.0f, 0.0f, 0.0f};
     if ((inf & 3) == PT_FLUID) {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
+            const float *fc = fphi + (size_t)c * Q * N;
             float acc = 0.0f;
 #pragma unroll
             for (int n = 0; n < Q; n++)
-                acc += fphi[(c * Q + n) * N + i];
+                acc += fc[n * N + i];
             Ph[c] = acc;
         }
         float r = 0.0f;
@@ -171,14 +173,15 @@ __device__ __forceinline__ void fields_site(const Params &P, const FieldPtrs &F,
             const int kx = L::ex(k), ky = L::ey(k), kz = L::ez(k);
             const int X = (x + kx + P.nx) % P.nx, Y = (y + ky + P.ny) % P.ny,
                       Z = (z + kz + P.nz) % P.nz;
-            const size_t f = X + (size_t)P.nx * (Y + (size_t)P.ny * Z);
+            const int f = X + P.nx * (Y + P.ny * Z);
             float Pf[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
+                const float *fc = fphi + (size_t)c * Q * N;
                 float acc = 0.0f;
 #pragma unroll
                 for (int n = 0; n < Q; n++)
-                    acc += fphi[(c * Q + n) * N + f];
+                    acc += fc[n * N + f];
                 Pf[c] = acc;
             }
             float c12 = 0.0f, c13 = 0.0f, c23 = 0.0f;
