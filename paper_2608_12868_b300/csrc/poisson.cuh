@@ -492,10 +492,11 @@ __device__ __forceinline__ void mg_bj_block(const MgDims &d, const float *Dg, co
             const int gx = bj_wrap(x0 - 1 + hx, d.nx), gy = bj_wrap(y0 - 1 + hy, d.ny);
             const int gz = D == 3 ? bj_wrap(z0 - 1 + hz, d.nz) : 0;
             const int g = cell(d, gx, gy, gz);
-            const float xg = xin[g];
-            v = Dg[g] > 0.0f
-                    ? __fadd_rn(xg, xc[cell(c, gx >> 1, gy >> 1, cz2 ? (gz >> 1) : gz)])
-                    : xg;
+            // the parent's value is read whether or not the cell is active, so that the three
+            // loads are independent
+            const float xg = xin[g], dg = Dg[g];
+            const float xp = xc[cell(c, gx >> 1, gy >> 1, cz2 ? (gz >> 1) : gz)];
+            v = dg > 0.0f ? __fadd_rn(xg, xp) : xg;
         }
         xs[e] = v;
     }
