@@ -221,9 +221,10 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   default 3); one grid-wide dependency per level and direction of a V-cycle. 0:
  *   red-black Gauss-Seidel half sweeps over whole levels (mg_nu pairs, default 2). Both are
  *   symmetric, so CG converges to the same tolerance with either; the solutions differ
- *   within it. The persistent and the multi-launch solves give the same bits for either
- *   value. Batched instances run 0 (setting 1 on a batch fails with
- *   LBEHD_ERR_INVALID_ARG). */
+ *   within it. The persistent, the multi-launch and the batched solves give the same bits
+ *   for either value: a batch instance with the same setting as a single handle steps bit
+ *   for bit like it. A batch starts with 0 (lbehd_batch_set_option changes it for every
+ *   instance). */
 #define LBEHD_OPT_MG_SMOOTHER 6
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 /* The value in effect: for LBEHD_OPT_COLLIDE the kernel the automatic choice resolved to,

@@ -137,6 +137,11 @@ struct MgInst {
     const uint8_t *info;
     float *D, *kx, *ky, *kz, *b, *x, *r;      // this level (r: residual scratch)
     float *Dc, *kxc, *kyc, *kzc, *bc, *xc;    // the coarser level
+    // block-local smoother (k_mg_bj_batch): the coarse correction's source on the way up
+    // (the coarser level's way-up output, or the tail's x), and on level 0 the CG residual
+    // and the r . z partials the way-up pass writes (null on other levels)
+    const float *xcu, *rdot;
+    double *pdot;
 };
 
 struct MgBatch {
@@ -264,6 +269,20 @@ __global__ void __launch_bounds__(BX) k_mg_resid_restrict_batch(const __grid_con
                     acc = __fadd_rn(acc, v[j]);
             m.bc[I] = acc;
         }
+    });
+}
+
+// The block-local smoother's pass (mg_bj_block) on every listed instance, one work item per
+// block, reps sweep pairs per block; A.color = 1 on the way up (prolongation, output in r),
+// 0 on the way down (zero start, output in x).
+template <int D>
+__global__ void __launch_bounds__(BJ_THREADS, 1) k_mg_bj_batch(const __grid_constant__ MgBatch A)
+{
+    const bool up = A.color != 0;
+    for_work(A.g, [&](int k, int b) {
+        const MgInst &m = A.m[k];
+        mg_bj_block<D>(m.f, m.D, m.kx, m.ky, m.kz, m.b, up ? m.x : nullptr, up ? m.r : m.x, b,
+                       m.reps, up, m.c, m.cz2, m.xcu, up ? m.rdot : nullptr, m.pdot);
     });
 }
 

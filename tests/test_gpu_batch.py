@@ -2,8 +2,9 @@
 
 Every instance of a batch must compute what the same instance computes alone: the state
 arrays (populations, fields, potential) are compared bit for bit with single-instance
-runs in graph mode using the same collide kernel and the batched form's multigrid smoother
-(whole-level red-black sweeps, LBEHD_OPT_MG_SMOOTHER = 0), after enough steps to include a
+runs in graph mode using the same collide kernel and the same multigrid smoother (a batch's
+default, whole-level red-black sweeps, and once the block-local smoother), after enough
+steps to include a
 multigrid rebuild (every 16 steps). One instance is also compared with the FP64 oracle
 at the parity bars of the single-instance tests. The collide-kernel autotuner must leave
 the state untouched.
@@ -43,11 +44,11 @@ def uneven_3d():
     ]
 
 
-def plain(gpu, w):
-    """A single handle with the batched form's smoother (whole-level sweeps), the runs a
-    batch instance reproduces bit for bit."""
+def plain(gpu, w, smoother=0):
+    """A single handle in graph mode with the given multigrid smoother (0: a batch's
+    default)."""
     sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
-    sim.set_option(gpu.OPT_MG_SMOOTHER, 0)
+    sim.set_option(gpu.OPT_MG_SMOOTHER, smoother)
     return sim
 
 
@@ -86,6 +87,43 @@ def test_batch_bitwise_equals_single_instances(gpu, variant):
             scale = np.abs(o[k]).max()
             assert np.abs(obs[i][k] - o[k]).max() <= rtol * scale, (i, k, obs[i][k], o[k])
         assert obs[i]["status"] == 0 and obs[i]["step"] == o["step"]
+        sim.close()
+    batch.close()
+
+
+def test_batch_block_smoother_bitwise_equals_single_instances(gpu):
+    """The same comparison with the block-local smoother (LBEHD_OPT_MG_SMOOTHER = 1) on both
+    sides."""
+    ws = uneven_3d()
+    batch = gpu.Batch(ws)
+    batch.set_option(gpu.OPT_MG_SMOOTHER, 1)
+    steps = 20
+    batch.step(steps)
+    for i, w in enumerate(ws):
+        sim = plain(gpu, w, 1)
+        sim.step(steps)
+        assert_same_state(batch[i], sim, f"instance {i}")
+        sim.close()
+    batch.close()
+
+
+def test_batch_mixing_the_two_smoothers(gpu):
+    """A 44^3 lattice coarsens once (22 is not a multiple of 4) to 22^3 = 10648 cells, too many
+    for the shared-memory tail, so it has no tail and keeps whole-level sweeps with the
+    block-local option set, while the other instances smooth block by block: one batched
+    V-cycle runs both on level 0. Every instance equals its single-handle run bit for bit."""
+    ws = uneven_3d()[:2] + [W.droplet_3d(44, 44, 44, R=8.0, pillar_h=4,
+                                         electrodes=[(28, 36, 16, 28)], V=[0.05], seed=25)]
+    batch = gpu.Batch(ws)
+    batch.set_option(gpu.OPT_MG_SMOOTHER, 1)
+    steps = 20
+    batch.step(steps)
+    for i, w in enumerate(ws):
+        sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+        assert sim.get_option(gpu.OPT_MG_SMOOTHER) == (0 if i == 2 else 1)
+        sim.step(steps)
+        assert_same_state(batch[i], sim, f"instance {i}")
+        assert batch.observe()[i]["status"] == 0
         sim.close()
     batch.close()
 

@@ -128,34 +128,3 @@ def test_block_smoother_against_whole_level_sweeps(gpu, case):
     assert tot_b <= 1.25 * tot_w + 3, (tot_b, tot_w)
     scale = np.abs(pot_w).max()
     assert np.abs(pot_b - pot_w).max() <= 1e-5 * scale, np.abs(pot_b - pot_w).max() / scale
-
-
-def test_block_smoother_refused_on_a_batch(gpu):
-    batch = gpu.Batch([W.small_3d(), W.small_3d(seed=9)])
-    with pytest.raises(gpu.LBEHDError):
-        batch.set_option(gpu.OPT_MG_SMOOTHER, 1)
-    batch.set_option(gpu.OPT_MG_SMOOTHER, 0)
-    batch.step(2)
-    assert batch.observe()[0]["status"] == 0
-    batch.close()
-
-
-def test_barrier_time_out_is_reported(gpu):
-    """A grid barrier that waits for an arrival that never comes (LBEHD_OPT_BARRIER_TEST:
-    one CTA more than launched, 2000 polls) gives up: every CTA leaves at its next barrier,
-    the kernel ends, the next observe reports LBEHD_ERR_CUDA, and the CUDA context stays
-    usable (a new handle steps and matches a handle that never timed out)."""
-    w = W.small_3d()
-    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
-    sim.step(3)
-    assert sim.observe()["status"] == 0
-    sim.set_option(gpu.OPT_BARRIER_TEST, 2000)
-    sim.step(1)
-    with pytest.raises(gpu.LBEHDError) as err:
-        sim.observe()
-    assert "grid barrier timed out" in str(err.value)
-    sim.close()
-    a, b = pair(gpu, w)
-    a.step(12)
-    b.step(12)
-    assert_same(a, b)
