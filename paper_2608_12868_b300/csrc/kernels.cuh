@@ -239,17 +239,21 @@ struct GlobalPops {
 };
 
 // The staged kernel's populations: the phase-field sets (57 / 27 arrays) from the tile staged
-// in shared memory, the momentum and charge sets (one coalesced read per array and site)
-// straight from global memory. Measured on 128x64x64: 82.0 us per launch (64x2 tiles)
-// against 85.9 us with all 83 arrays staged.
+// in shared memory; the momentum and charge sets (one coalesced read per array and site) read
+// into registers at the start of the tile, so that their latency overlaps the halo loads.
+// Measured on 128x64x64: 82.0 us per launch (64x2 tiles) against 85.9 us with all 83 arrays
+// staged.
+template <int D>
 struct StagedPops {
-    const float *__restrict__ gp, *__restrict__ rp;
+    float gr[Lat<D>::Q], rr[Lat<D>::QS];
     const float *s;   // [phase array][tile site], stride BX
-    int N, i;
-    int t, Q;
-    __device__ __forceinline__ float g(int n) const { return gp[n * N + i]; }
-    __device__ __forceinline__ float phi(int c, int n) const { return s[(c * Q + n) * BX + t]; }
-    __device__ __forceinline__ float rho(int n) const { return rp[n * N + i]; }
+    int t;
+    __device__ __forceinline__ float g(int n) const { return gr[n]; }
+    __device__ __forceinline__ float phi(int c, int n) const
+    {
+        return s[(c * Lat<D>::Q + n) * BX + t];
+    }
+    __device__ __forceinline__ float rho(int n) const { return rr[n]; }
 };
 
 // Stencil-field sources for collide_site: Phi_1..3, the compensated potential and the node
@@ -615,6 +619,11 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     using L = Lat<D>;
     constexpr int Q = L::Q;
     const int N = (int)P.N;
+    // ---- momentum moments (shifted populations gs = g - w), first: the site's momentum
+    // populations are then dead before the stencils, and ten moments stay live instead
+    float dp, jm[3], m2[6];
+    momentum_moments<D>(pops, dp, jm, m2);
+
     // ---- stencils of Phi_i and phi over the flow lattice
     float Pc[3], pot_i, lo_i;
     int pt_i;
@@ -698,9 +707,7 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     float FPhi[3][3];
     sharpening_flux(P.W, Pc, gP, FPhi);
 
-    // ---- momentum moments (shifted populations gs = g - w), velocity
-    float dp, jm[3], m2[6];
-    momentum_moments<D>(pops, dp, jm, m2);
+    // ---- velocity from the momentum moments (formed above) and the force
     float u[3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -851,11 +858,6 @@ struct PopMaps {
     CUtensorMap g, fphi, frho;
 };
 
-__device__ __forceinline__ void prefetch_l1(const float *p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             int c2, int c3, uint64_t *bar)
 {
@@ -912,16 +914,15 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     const bool active = x < P.nx && y < P.ny;
     const int i = active ? x + P.nx * (y + P.ny * z) : 0;
     const SitePre pre = load_site_pre(S, N, i);   // issued now, used after the staging
-    // The momentum and charge populations are read late, in the collisions; ask L1 for
-    // their lines now so their DRAM latency overlaps the halo loads and the stencils.
-    if (active) {
+    // the momentum and charge populations, issued now into registers (their DRAM latency
+    // overlaps the halo loads; the momentum ones become ten moments first thing)
+    StagedPops<D> pops;
 #pragma unroll
-        for (int n = 0; n < Q; n++)
-            prefetch_l1(S.g + (size_t)n * N + i);
+    for (int n = 0; n < Q; n++)
+        pops.gr[n] = S.g[n * (int)N + i];
 #pragma unroll
-        for (int n = 0; n < L::QS; n++)
-            prefetch_l1(S.frho + (size_t)n * N + i);
-    }
+    for (int n = 0; n < L::QS; n++)
+        pops.rr[n] = S.frho[n * (int)N + i];
     // stencil fields of the tile and its halo, periodic in every direction: every load of
     // this thread is issued before the first shared-memory store
     constexpr int HIT = (HN + BX - 1) / BX;
@@ -969,7 +970,8 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
     }
     const int h = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? 1 : 0));
     if (active && (__float_as_int(shb[h].y) & 3) == PT_FLUID) {
-        const StagedPops pops{S.g, S.frho, spop, (int)N, i, t, Q};
+        pops.s = spop;
+        pops.t = t;
         const SmemStencil<D, TY> st{sha, shb, h};
         collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
     }
