@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(BX) k_mg_prolong(MgDims f, MgDims c, int cz2,
 //    array (the level's restriction scratch), since other blocks still read x as their halo.
 // A cell's update has the arithmetic of mg_gs_cell, with its neighbours read from the copy.
 // With r given (level 0 on the way up), the block also forms its partial of r . z over its
-// cells (z = the smoothed x): FP32 within each warp, then FP64 over the warps in order.
+// cells (z = the smoothed x): FP32 within each warp, then FP64 over the warps by a butterfly.
 // Against whole-level red-black sweeps, one V-cycle of this smoother costs one grid-wide
 // dependency per level and direction instead of one per half sweep.
 constexpr int BJ_THREADS = 1024;
@@ -485,20 +485,30 @@ __device__ __forceinline__ void mg_bj_block(const MgDims &d, const float *Dg, co
         if (r)
             ri = r[i];
     }
-    for (int e = t; e < NH; e += BJ_THREADS) {
-        float v = 0.0f;
-        if (up) {
+    // the copy of x: every load of this thread issued before the first shared store (the
+    // parent's value is read whether or not the cell is active, so that the loads are
+    // independent)
+    constexpr int HIT = (NH + BJ_THREADS - 1) / BJ_THREADS;
+    float hxg[HIT], hdg[HIT], hxp[HIT];
+#pragma unroll
+    for (int k = 0; k < HIT; k++) {
+        const int e = t + k * BJ_THREADS;
+        hxg[k] = hdg[k] = hxp[k] = 0.0f;
+        if (up && e < NH) {
             const int hx = e % HX, hy = (e / HX) % HY, hz = e / SZ;
             const int gx = bj_wrap(x0 - 1 + hx, d.nx), gy = bj_wrap(y0 - 1 + hy, d.ny);
             const int gz = D == 3 ? bj_wrap(z0 - 1 + hz, d.nz) : 0;
             const int g = cell(d, gx, gy, gz);
-            // the parent's value is read whether or not the cell is active, so that the three
-            // loads are independent
-            const float xg = xin[g], dg = Dg[g];
-            const float xp = xc[cell(c, gx >> 1, gy >> 1, cz2 ? (gz >> 1) : gz)];
-            v = dg > 0.0f ? __fadd_rn(xg, xp) : xg;
+            hxg[k] = xin[g];
+            hdg[k] = Dg[g];
+            hxp[k] = xc[cell(c, gx >> 1, gy >> 1, cz2 ? (gz >> 1) : gz)];
         }
-        xs[e] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < HIT; k++) {
+        const int e = t + k * BJ_THREADS;
+        if (e < NH)
+            xs[e] = up ? (hdg[k] > 0.0f ? __fadd_rn(hxg[k], hxp[k]) : hxg[k]) : 0.0f;
     }
     __syncthreads();
     const int h = (lx + 1) + HX * (ly + 1) + (D == 3 ? SZ * (lz + 1) : 0);
@@ -527,11 +537,13 @@ __device__ __forceinline__ void mg_bj_block(const MgDims &d, const float *Dg, co
         if ((t & 31) == 0)
             wsm[t >> 5] = (double)v;
         __syncthreads();
-        if (t == 0) {
-            double acc = 0.0;
-            for (int w = 0; w < BJ_THREADS / 32; w++)
-                acc += wsm[w];
-            partials[blk] = acc;
+        if (t < 32) {   // FP64 over the 32 warp sums by a butterfly (FP64 adds are slow here)
+            double acc = wsm[t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (t == 0)
+                partials[blk] = acc;
         }
     }
     __syncthreads();   // the shared copies are rewritten by this CTA's next block
