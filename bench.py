@@ -46,7 +46,8 @@ STEP_BYTES = {3: (756, 16), 2: (388, 12)}
 # mean of 2 launches in one ncu capture of the current kernel, summarised under profiles/),
 # by workload and autotuned variant. Only these are reported as roofline traffic; a variant
 # without a capture of the current kernel reports null.
-COLLIDE_TRAFFIC = {("droplet_3d_128x64x64", "staged32x4"): 341.24e6}
+COLLIDE_TRAFFIC = {("droplet_3d_128x64x64", "staged32x4"): 341.23e6,
+                   ("droplet_3d_128x64x64", "staged64x2"): 342.37e6}
 # LBEHD_OPT_COLLIDE values
 COLLIDE_CHOICES = {"auto": 0, "global": 1, "staged": 2, "staged64x2": 3, "staged16x8": 4}
 VARIANT_NAMES = {1: "global", 2: "staged32x4", 3: "staged64x2", 4: "staged16x8"}
