@@ -30,6 +30,14 @@
  *    at every other solid face; solved to the fixed point by Jacobi-preconditioned CG.
  *  - Charge (Eq. 14): conduction source Q = div(sigma grad phi) with the same
  *    face discretisation and zero flux at every solid face.
+ *  - Large density ratios (Table 1's densities; Eq. 9 with a variable rho), when
+ *    var_density is set: the momentum populations carry the pressure and rho u,
+ *    g_eq,n = w_n p/c_s^2 + rho s_n(u) (n > 0), g_eq,0 = (w_0 - 1) p/c_s^2 + rho s_0(u),
+ *    s_n(u) = w_n [e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u^2/(2 c_s^2)], with rho = sum_i
+ *    Phi_i rho_i; the force term G_n = (e_n - u).[Gamma_n F + s_n c_s^2 grad rho]/c_s^2,
+ *    Gamma_n = w_n + s_n, carries the body forces and the density gradient; rho u =
+ *    sum e g + F/2 and p = c_s^2/(1 - w_0) [sum_{n>0} g_n + u.grad(rho)/2 + rho s_0(u)];
+ *    one relaxation time, tau = 1/2 + nu/c_s^2, for every moment (BGK).
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,6 +72,8 @@ typedef struct {
     int poisson_max_iter;
     int n_electrodes;
     double V[64];
+    int var_density;              /* 1: the pressure-based variable-density momentum scheme */
+    double rhoph[3];              /* phase densities rho_i (var_density) */
 } oprm_t;
 
 /* State and per-step fields. Every array is owned by the caller. */
@@ -530,15 +540,20 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
         }
     }
 
-    /* 8. Velocity u = j + F/2 (unit reference density), and the conduction source
-     *    Q = div(sigma grad phi) of Eq. 14 with zero flux through every solid face. */
+    /* 8. Velocity u = j + F/2 (unit reference density; with var_density,
+     *    u = (j + F/2) / rho), and the conduction source Q = div(sigma grad phi) of
+     *    Eq. 14 with zero flux through every solid face. */
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         s->qsrc[i] = 0.0;
         if (s->solid[i])
             continue;
+        double dens = 1.0;
+        if (p->var_density)
+            dens = s->Phi[i] * p->rhoph[0] + s->Phi[N + i] * p->rhoph[1] +
+                   s->Phi[2 * N + i] * p->rhoph[2];
         for (int a = 0; a < 3; a++)
-            s->u[a * N + i] += 0.5 * s->F[a * N + i];
+            s->u[a * N + i] = (s->u[a * N + i] + 0.5 * s->F[a * N + i]) / dens;
         double q = 0.0;
         for (int n = 1; n < QS; n++) {
             long j = site_nbr(p, i, Ls->e[n]);
@@ -564,9 +579,55 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
     }
 
     /* 9a. Momentum populations: incompressible equilibrium, Guo-type force term
-     *     R_g, raw-moment MRT (second momentum-collision equation of the Methods). */
+     *     R_g, raw-moment MRT (second momentum-collision equation of the Methods); or,
+     *     with var_density, the pressure-based scheme (header) with one relaxation time. */
     double tau_phi = 0.5 + p->mobility / cs2;
     double tau_rho = 0.5 + p->alpha / cs2s;
+    if (p->var_density) {
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < N; i++) {
+            if (s->solid[i]) {
+                for (int n = 0; n < Q; n++)
+                    s->post[n * N + i] = 0.0;
+                continue;
+            }
+            double u[3] = {s->u[i], s->u[N + i], s->u[2 * N + i]};
+            double F[3] = {s->F[i], s->F[N + i], s->F[2 * N + i]};
+            double dens = 0.0, nu = 0.0, gr[3] = {0, 0, 0};
+            for (int c = 0; c < 3; c++) {
+                dens += s->Phi[c * N + i] * p->rhoph[c];
+                nu += s->Phi[c * N + i] * p->nu[c];
+                for (int a = 0; a < 3; a++)
+                    gr[a] += p->rhoph[c] * s->gradPhi[(c * 3 + a) * N + i];
+            }
+            double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            double sn[QMAX];
+            for (int n = 0; n < Q; n++) {
+                const int *e = Lf->e[n];
+                double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+                sn[n] = Lf->w[n] * (eu / cs2 + eu * eu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+            }
+            double gsum = 0.0;
+            for (int n = 1; n < Q; n++)
+                gsum += s->g[n * N + i];
+            double ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+            double pr = cs2 / (1.0 - Lf->w[0]) * (gsum + 0.5 * ugr + dens * sn[0]);
+            s->pstar[i] = pr;
+            double tau = 0.5 + nu / cs2;
+            for (int n = 0; n < Q; n++) {
+                const int *e = Lf->e[n];
+                double geq = (n == 0 ? Lf->w[0] - 1.0 : Lf->w[n]) * pr / cs2 + dens * sn[n];
+                double G = 0.0;
+                for (int a = 0; a < 3; a++)
+                    G += (e[a] - u[a]) * ((Lf->w[n] + sn[n]) * F[a] + sn[n] * cs2 * gr[a]);
+                G /= cs2;
+                double gn = s->g[n * N + i];
+                s->post[n * N + i] = gn - (gn - geq) / tau + (1.0 - 0.5 / tau) * G;
+            }
+        }
+        stream_pull(p, Lf, s, s->post, s->g);
+    }
+    if (!p->var_density) {
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         if (s->solid[i]) {
@@ -602,6 +663,7 @@ int oracle_step(const oprm_t *p, const olat_t *Lf, const olat_t *Ls, ost_t *s)
     }
     /* Streaming writes into the population array itself (post is a copy). */
     stream_pull(p, Lf, s, s->post, s->g);
+    }
 
     /* 9b. Phase-field populations (Eqs. 15-17) for the three components. */
     for (int c = 0; c < 3; c++) {

@@ -138,7 +138,8 @@ class _OPrm(ctypes.Structure):
                 ("body1", ctypes.c_double * 3), ("s_bulk", ctypes.c_double),
                 ("poisson_tol", ctypes.c_double),
                 ("poisson_max_iter", ctypes.c_int), ("n_electrodes", ctypes.c_int),
-                ("V", ctypes.c_double * 64)]
+                ("V", ctypes.c_double * 64),
+                ("var_density", ctypes.c_int), ("rhoph", ctypes.c_double * 3)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -261,12 +262,14 @@ class OracleSim:
         self._lf, self._ls = _olat(self.Lf), _olat(self.Ls)
         lib().oracle_normals(ctypes.byref(self._prm), ctypes.byref(self._lf),
                              _ptr(self.solid, ctypes.c_uint8), _ptr(self.normal, ctypes.c_int32))
-        # Initial populations at equilibrium with u = 0, p* = 1, rho_e = 0 (Eq. 16 and
-        # the incompressible momentum equilibrium).
+        # Initial populations at equilibrium with u = 0, rho_e = 0 (Eq. 16) and p* = 1
+        # (the incompressible momentum equilibrium) or, with the variable-density scheme,
+        # the gauge pressure p = 0 (every momentum population 0).
         fluid = (self.solid == 0)
         phi0 = np.asarray(phi_init, dtype=np.float64).reshape((3,) + self.shape) * fluid
+        g0 = 0.0 if self._prm.var_density else 1.0
         for n in range(Q):
-            self.g[n] = self.Lf.w[n] * fluid
+            self.g[n] = g0 * self.Lf.w[n] * fluid
             for c in range(3):
                 self.fphi[c, n] = phi0[c] * self.Lf.w[n]
         self._st = self._make_state()
@@ -293,6 +296,9 @@ class OracleSim:
         s.n_electrodes = len(V)
         for k, v in enumerate(V):
             s.V[k] = v
+        s.var_density = 1 if p.get("density_model", 0) == 1 else 0
+        for c in range(3):
+            s.rhoph[c] = p.get("rho_phase", (1.0, 1.0, 1.0))[c]
         return s
 
     def _make_state(self):
