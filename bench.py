@@ -317,7 +317,8 @@ def run_ours(args, world, rank, local):
 
     others = {}
     if args.other_workloads:
-        for name, n in (("droplet_2d_128x64", 2000), ("transport_3d_384x128x96", 4000)):
+        for name, n in (("droplet_2d_128x64", 2000), ("transport_3d_384x128x96", 4000),
+                        ("droplet_3d_128x64x64_table1_densities", 2000)):
             others[name] = run_workload_line(args, dev, name, n, peak, peak_kind)
     batched = None
     if args.batched > 0:
@@ -663,8 +664,9 @@ def main():
                     help="segments of the differentiable-control schedule (0: skip the adjoint)")
     ap.add_argument("--adjoint-seg-steps", type=int, default=200)
     ap.add_argument("--other-workloads", type=int, default=1,
-                    help="1: also time the 2D 128x64 run (2000 steps) and the 384x128x96 "
-                         "transport run (4000 steps, electrode switches); 0: skip")
+                    help="1: also time the 2D 128x64 run (2000 steps), the 384x128x96 "
+                         "transport run (4000 steps, electrode switches) and the 128x64x64 "
+                         "droplet with Table 1's densities (2000 steps); 0: skip")
     ap.add_argument("--poisson", choices=["graph", "host", "fixed"], default="graph")
     ap.add_argument("--fixed-iters", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=1)

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBEHD_ABI_VERSION 3
+#define LBEHD_ABI_VERSION 4
 
 #define LBEHD_OK 0
 #define LBEHD_ERR_INVALID_ARG (-1)
@@ -88,6 +88,21 @@ typedef struct lbehd_config {
                                    * Methods' validation; zero for the electrically driven
                                    * runs) */
     double s_bulk;           /* relaxation rate of the trace of the momentum flux (1) */
+    int density_model;       /* 0: equal densities (the incompressible momentum scheme with the
+                              * raw-moment MRT collision); 1: phase densities rho_phase (Table
+                              * 1's water / oil / air, Eq. 9 with a variable rho): the momentum
+                              * populations carry the gauge pressure p and rho u,
+                              * g_eq,n = w_n p/c_s^2 + rho s_n(u) (n > 0),
+                              * g_eq,0 = (w_0 - 1) p/c_s^2 + rho s_0(u),
+                              * s_n(u) = w_n [e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u^2/(2 c_s^2)],
+                              * the force term (e_n - u).[(w_n + s_n) F + s_n c_s^2 grad rho]
+                              * / c_s^2, rho = sum Phi_i rho_i, rho u = sum e g + F/2,
+                              * p = c_s^2/(1 - w_0) [sum_{n>0} g_n + u.grad(rho)/2 +
+                              * rho s_0(u)], one relaxation time tau = 1/2 + nu/c_s^2 (nu is
+                              * kinematic). The momentum populations are then stored as g
+                              * itself and start at 0 (p = 0, u = 0). Not with the batched
+                              * form or the adjoint (LBEHD_ERR_INVALID_ARG). */
+    double rho_phase[3];     /* phase densities rho_i (density_model 1; all > 0) */
     double poisson_tol;      /* relative residual ||b - A phi||_2 / ||b||_2 to stop at */
     int poisson_max_iter;    /* cap on preconditioned-CG iterations per step */
     int poisson_mode;        /* LBEHD_POISSON_HOST or LBEHD_POISSON_FIXED */

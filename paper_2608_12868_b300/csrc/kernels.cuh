@@ -54,6 +54,8 @@ struct Params {
     float s_bulk;
     float body[3];
     float body1[3];   // force density on the droplet phase alone: Phi_1 body1
+    int var_density;  // 1: the variable-density momentum scheme (phase densities rho_ph)
+    float rho_ph[3];
 };
 
 struct State {
@@ -480,6 +482,52 @@ __device__ __forceinline__ void momentum_collide(const Params &P, const State &S
         atomicOr(S.flag, 1);
 }
 
+// Momentum collision of the variable-density scheme (Table 1's densities in Eq. 9): the
+// populations carry the gauge pressure and rho u (g_eq,n = w_n p/c_s^2 + rho s_n(u), n > 0;
+// g_eq,0 = (w_0 - 1) p/c_s^2 + rho s_0(u); s_n(u) = w_n [e.u/c_s^2 + (e.u)^2/(2 c_s^4) -
+// u^2/(2 c_s^2)]), the force term G_n = (e_n - u).[(w_n + s_n) F + s_n c_s^2 grad rho]/c_s^2
+// carries the force density and the density gradient, p = c_s^2/(1 - w_0) [sum_{n>0} g_n +
+// u.grad(rho)/2 + rho s_0(u)], and every moment relaxes with tau = 1/2 + nu/c_s^2. The
+// populations are stored as g itself. gsum = sum_n g_n, g0 = g_0.
+template <int D, class Push, class Pops>
+__device__ __forceinline__ void momentum_collide_vd(const Params &P, const State &S,
+                                                    const Push &push, const Pops &pops,
+                                                    const float (&Pc)[3], float gsum,
+                                                    float dens, const float (&gr)[3],
+                                                    const float (&u)[3], const float (&F)[3])
+{
+    using L = Lat<D>;
+    constexpr int Q = L::Q;
+    constexpr float inv_cs2 = 3.0f;
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const float ug = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+    const float nu = Pc[0] * P.nu[0] + Pc[1] * P.nu[1] + Pc[2] * P.nu[2];
+    const float itau = 1.0f / (inv_cs2 * nu + 0.5f);
+    const float cf = 1.0f - 0.5f * itau;
+    const float s0 = L::w(0) * (-1.5f * uu);
+    const float pc = ((gsum - pops.g(0)) + 0.5f * ug + dens * s0) *
+                     (1.0f / (1.0f - L::w(0)));   // p / c_s^2
+#pragma unroll
+    for (int n = 0; n < Q; n++) {
+        const int cx = L::ex(n), cy = L::ey(n), cz = L::ez(n);
+        const float eu = (cx ? (cx > 0 ? u[0] : -u[0]) : 0.f) + (cy ? (cy > 0 ? u[1] : -u[1]) : 0.f) +
+                         (cz ? (cz > 0 ? u[2] : -u[2]) : 0.f);
+        const float eF = (cx ? (cx > 0 ? F[0] : -F[0]) : 0.f) + (cy ? (cy > 0 ? F[1] : -F[1]) : 0.f) +
+                         (cz ? (cz > 0 ? F[2] : -F[2]) : 0.f);
+        const float eg = (cx ? (cx > 0 ? gr[0] : -gr[0]) : 0.f) +
+                         (cy ? (cy > 0 ? gr[1] : -gr[1]) : 0.f) +
+                         (cz ? (cz > 0 ? gr[2] : -gr[2]) : 0.f);
+        const float sn = L::w(n) * (inv_cs2 * eu + 4.5f * eu * eu - 1.5f * uu);
+        const float geq = (n == 0 ? L::w(0) - 1.0f : L::w(n)) * pc + dens * sn;
+        const float G = inv_cs2 * (L::w(n) + sn) * (eF - uF) + sn * (eg - ug);
+        const float g = pops.g(n);
+        push(S.g_out, n, g - (g - geq) * itau + cf * G);
+    }
+    if (!isfinite(pc + u[0] + u[1] + u[2]))
+        atomicOr(S.flag, 1);
+}
+
 // Collision of phase field c (Eqs. 15-17) and its push.
 template <int D, class Push, class Pops>
 __device__ __forceinline__ void phase_collide(const Params &P, const State &S, const Push &push,
@@ -610,7 +658,7 @@ __device__ __forceinline__ void sharpening_flux(float W, const float (&Pc)[3],
 // (f*_n = w_n (C + e_n . B) + ...), and the non-equilibrium second moments of the momentum
 // populations formed from their raw moments and the closed-form moments of g_eq and R:
 //   Pi(g_eq) = c_s^2 p* I + u u,   Pi(R) = u F + F u.
-template <int D, class Pops, class Stencil>
+template <int D, class Pops, class Stencil, bool VD = false>
 __device__ __forceinline__ void collide_site(const Params &P, const State &S, int x, int y, int z,
                                              int i, int first, const Pops &pops,
                                              const Stencil &st, const SitePre &pre,
@@ -707,11 +755,18 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     float FPhi[3][3];
     sharpening_flux(P.W, Pc, gP, FPhi);
 
-    // ---- velocity from the momentum moments (formed above) and the force
-    float u[3];
+    // ---- velocity from the momentum moments (formed above) and the force; with variable
+    // density, rho u = j + F/2 with rho = sum Phi_i rho_i
+    float u[3], dens = 1.0f, gr[3] = {0.f, 0.f, 0.f};
+    if (VD) {
+        dens = Pc[0] * P.rho_ph[0] + Pc[1] * P.rho_ph[1] + Pc[2] * P.rho_ph[2];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            gr[a] = P.rho_ph[0] * gP[0][a] + P.rho_ph[1] * gP[1][a] + P.rho_ph[2] * gP[2][a];
+    }
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        u[a] = jm[a] + 0.5f * F[a];
+        u[a] = VD ? (jm[a] + 0.5f * F[a]) / dens : jm[a] + 0.5f * F[a];
     float uo[3], Po[3], rho_o, q_o;
     if (first) {
 #pragma unroll
@@ -736,7 +791,10 @@ __device__ __forceinline__ void collide_site(const Params &P, const State &S, in
     S.q[i] = qsrc;
 
     const Pusher<L> push = make_pusher<L>(P, x, y, z, i, fluid_nb);
-    momentum_collide<D>(P, S, push, Pc, dp, m2, u, F);
+    if (VD)
+        momentum_collide_vd<D>(P, S, push, pops, Pc, dp, dens, gr, u, F);
+    else
+        momentum_collide<D>(P, S, push, Pc, dp, m2, u, F);
 #pragma unroll
     for (int c = 0; c < 3; c++)
         phase_collide<D>(P, S, push, pops, c, Pc[c], Po[c], FPhi[c], u, uo);
@@ -811,7 +869,7 @@ __device__ __forceinline__ void block_obs_partials(const float (&ob)[NOBS], doub
 }
 
 // One site of the global-load variant (no-op for x >= nx or a non-fluid site).
-template <int D>
+template <int D, bool VD = false>
 __device__ __forceinline__ void collide_global_site(const Params &P, const State &S, int first,
                                                     int x, int y, int z, float (&ob)[NOBS])
 {
@@ -824,7 +882,8 @@ __device__ __forceinline__ void collide_global_site(const Params &P, const State
                                (y + 1 == P.ny ? 1 - P.ny : 1) * nx, (y == 0 ? P.ny - 1 : -1) * nx,
                                (z + 1 == P.nz ? 1 - P.nz : 1) * nxy, (z == 0 ? P.nz - 1 : -1) * nxy};
         const SitePre pre = load_site_pre(S, (size_t)P.N, i);
-        collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
+        collide_site<D, GlobalPops, GlobalStencil, VD>(P, S, x, y, z, i, first, pops, st, pre,
+                                                       ob);
     }
 }
 
@@ -840,15 +899,15 @@ __device__ __forceinline__ size_t grid_block_count()
 
 // 4 resident blocks per SM (128 registers per thread; a few bytes of L1-cached spill):
 // the kernel is memory-latency bound and needs the warps.
-template <int D>
+template <int D, bool VD = false>
 __global__ void __launch_bounds__(BX, 4) k_collide(Params P, State S, int first)
 {
     float ob[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; k++)
         ob[k] = 0.0f;
-    collide_global_site<D>(P, S, first, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
-                           blockIdx.z, ob);
+    collide_global_site<D, VD>(P, S, first, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
+                               blockIdx.z, ob);
     block_obs_partials(ob, S.obs_partials, grid_block_index(), grid_block_count());
 }
 
@@ -887,7 +946,7 @@ constexpr size_t staged_smem_bytes()
 // maps). A barrier wait that never completes sets flag bit 1, waits once more for the copies
 // in flight and leaves the block (its partials zeroed).
 constexpr int STAGE_MAX_POLLS = 1 << 22;
-template <int D, int TY>
+template <int D, int TY, bool VD = false>
 __device__ __forceinline__ void collide_staged_tile(const Params &P, const State &S, int first,
                                                     const PopMaps *maps, int x0, int y0, int z,
                                                     size_t blk, size_t nblk)
@@ -973,17 +1032,19 @@ __device__ __forceinline__ void collide_staged_tile(const Params &P, const State
         pops.s = spop;
         pops.t = t;
         const SmemStencil<D, TY> st{sha, shb, h};
-        collide_site<D>(P, S, x, y, z, i, first, pops, st, pre, ob);
+        collide_site<D, StagedPops<D>, SmemStencil<D, TY>, VD>(P, S, x, y, z, i, first, pops, st,
+                                                               pre, ob);
     }
     block_obs_partials(ob, S.obs_partials, blk, nblk);
 }
 
-template <int D, int TY>
+template <int D, int TY, bool VD = false>
 __global__ void __launch_bounds__(BX, 4) k_collide_staged(Params P, State S, int first,
                                                           const __grid_constant__ PopMaps maps)
 {
-    collide_staged_tile<D, TY>(P, S, first, &maps, blockIdx.x * Halo<D, TY>::TX, blockIdx.y * TY,
-                               blockIdx.z, grid_block_index(), grid_block_count());
+    collide_staged_tile<D, TY, VD>(P, S, first, &maps, blockIdx.x * Halo<D, TY>::TX,
+                                   blockIdx.y * TY, blockIdx.z, grid_block_index(),
+                                   grid_block_count());
 }
 
 // Fixed-order FP64 sum of the observable partials: block k reduces observable k.

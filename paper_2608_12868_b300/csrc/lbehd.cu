@@ -698,6 +698,8 @@ int resolved_variant(const lbehd_handle *h)
     const int v = h->collide_variant;
     if (v == 1 || !h->maps_ok)
         return 1;
+    if (h->P.var_density)   // the variable-density scheme has the 32x4 staged kernel only
+        return 2;
     return v == 0 ? 2 : v;
 }
 
@@ -723,7 +725,14 @@ void collide(lbehd_handle *h)
     const bool staged = v != 1;
     const int first = h->first ? 1 : 0;
     launch(h, LBEHD_KC_COLLIDE, 1, [&] {
-        if (!staged)
+        if (h->P.var_density) {
+            if (!staged)
+                k_collide<D, true><<<h->grid, h->block, 0, h->ls>>>(h->P, S, first);
+            else
+                k_collide_staged<D, 4, true>
+                    <<<h->grid_tile[0], h->block, staged_smem_bytes<D, 4>(), h->ls>>>(
+                        h->P, S, first, h->maps[0][h->cur]);
+        } else if (!staged)
             k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, first);
         else if (shape == 0)
             k_collide_staged<D, 4><<<h->grid_tile[0], h->block, staged_smem_bytes<D, 4>(), h->ls>>>(
@@ -1006,6 +1015,14 @@ int set_params(lbehd_handle *h)
     P.inv_tau_phi = (float)(1.0 / (0.5 + c.mobility / cs2));
     P.inv_tau_rho = (float)(1.0 / (0.5 + c.alpha / cs2s));
     P.s_bulk = (float)c.s_bulk;
+    if (c.density_model != 0 && c.density_model != 1)
+        return fail(h, LBEHD_ERR_INVALID_ARG, "density_model takes 0 or 1");
+    P.var_density = c.density_model;
+    for (int k = 0; k < 3; k++) {
+        if (c.density_model == 1 && !(c.rho_phase[k] > 0.0))
+            return fail(h, LBEHD_ERR_INVALID_ARG, "rho_phase must be > 0 with density_model 1");
+        P.rho_ph[k] = c.density_model == 1 ? (float)c.rho_phase[k] : 1.0f;
+    }
     h->mg_nu = c.mg_nu > 0 ? c.mg_nu : 2;
     h->bj_nu = c.mg_nu > 0 ? c.mg_nu : 3;
     h->mg_coarse = c.mg_coarse_sweeps > 0 ? c.mg_coarse_sweeps : 8;
@@ -1235,6 +1252,9 @@ int init_impl(lbehd_handle *h)
         if (rc)
             return rc;
         CK(h, cudaFuncSetAttribute(k_collide_staged<D, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem_bytes<D, 4>()));
+        CK(h, cudaFuncSetAttribute(k_collide_staged<D, 4, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)staged_smem_bytes<D, 4>()));
         CK(h, cudaFuncSetAttribute(k_collide_staged<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)staged_smem_bytes<D, 2>()));
@@ -3317,6 +3337,9 @@ int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int 
         return fail(h, LBEHD_ERR_INVALID_ARG, "null handle, schedule or loss");
     if (h->batch_owned)
         return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: the adjoint is per handle");
+    if (h->P.var_density)
+        return fail(h, LBEHD_ERR_INVALID_ARG,
+                    "the adjoint runs equal densities (density_model 0)");
     if (n_segments < 1 || seg_steps < 1 || (long long)n_segments * seg_steps > (1 << 24))
         return fail(h, LBEHD_ERR_INVALID_ARG, "need n_segments >= 1, seg_steps >= 1");
     if (h->prof)
@@ -3461,6 +3484,10 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
     if ((b->dim == 2 ? batch_kernel_attributes<2>() : batch_kernel_attributes<3>()) != LBEHD_OK)
         return bail(LBEHD_ERR_CUDA, "cudaFuncSetAttribute failed for the batched kernels");
     for (int i = 0; i < n; i++) {
+        if (cfgs[i].density_model != 0)
+            return bail(LBEHD_ERR_INVALID_ARG,
+                        "instance " + std::to_string(i) +
+                            ": the batched form runs equal densities (density_model 0)");
         lbehd_config c = cfgs[i];
         c.stream = b->stream;
         c.poisson_mode = LBEHD_POISSON_GRAPH;

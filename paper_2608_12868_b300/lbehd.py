@@ -53,6 +53,7 @@ class Config(ctypes.Structure):
                 ("theta23", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("W", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("body_force", _D3), ("body_force_droplet", _D3), ("s_bulk", ctypes.c_double),
+                ("density_model", ctypes.c_int), ("rho_phase", _D3),
                 ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
                 ("poisson_mode", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
                 ("poisson_fixed_iters", ctypes.c_int), ("mg_nu", ctypes.c_int),
@@ -206,6 +207,9 @@ def make_config(w, c, *, poisson_mode=POISSON_HOST, poisson_check_every=1, poiss
     c.theta12, c.theta13, c.theta23 = p["theta12"], p["theta13"], p["theta23"]
     c.mobility, c.W, c.alpha = p["mobility"], p["W"], p["alpha"]
     c.s_bulk = p.get("s_bulk", 1.0)
+    c.density_model = int(p.get("density_model", 0))
+    for k in range(3):
+        c.rho_phase[k] = p.get("rho_phase", (1.0, 1.0, 1.0))[k]
     c.poisson_tol = p.get("poisson_tol", 1e-7)
     c.poisson_max_iter = int(p.get("poisson_max_iter", 100))
     c.poisson_check_every = int(poisson_check_every)
@@ -274,8 +278,12 @@ class _HandleOps:
         return self.array(POT).astype(np.float64) + self.array(POT_LO).astype(np.float64)
 
     def populations_g(self):
-        """Momentum populations g_n in float64 (the library stores g_n - w_n)."""
-        return self.array(G).astype(np.float64) + STORAGE_SHIFT[self.dim].reshape((-1, 1, 1, 1))
+        """Momentum populations g_n in float64 (the library stores g_n - w_n; with the
+        variable-density scheme, density_model 1, g_n itself)."""
+        g = self.array(G).astype(np.float64)
+        if self.workload.params.get("density_model", 0) == 1:
+            return g
+        return g + STORAGE_SHIFT[self.dim].reshape((-1, 1, 1, 1))
 
     def tensor(self, which):
         """Zero-copy torch view of one device array (valid until the next step)."""

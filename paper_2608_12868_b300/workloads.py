@@ -78,6 +78,28 @@ def make_params(*, visc_ratio=1.0, theta12=120.0, V=(0.05,), R=16.0, height=64, 
     }
 
 
+# Table 1 (Results): densities 998 (water, the droplet), 970 (silicone oil, the
+# lubricant) and 1.2 kg/m^3 (air); dynamic viscosities 1, 0.5-5 and 0.0179 cP. In lattice
+# units the water density is 1 and its kinematic viscosity NU_DROPLET.
+RHO_TABLE1 = (1.0, 970.0 / 998.0, 1.2 / 998.0)
+
+
+def table1_viscosities(visc_ratio=1.0):
+    """Kinematic viscosities of Table 1 (nu_i = mu_i / rho_i) scaled to nu_water =
+    NU_DROPLET; visc_ratio = mu_oil / mu_water."""
+    return (NU_DROPLET, NU_DROPLET * visc_ratio * 998.0 / 970.0,
+            NU_DROPLET * 0.0179 * 998.0 / 1.2)
+
+
+def with_table1_densities(w, visc_ratio=1.0):
+    """The same workload with Table 1's densities and viscosities (the variable-density
+    momentum scheme, density_model 1)."""
+    params = dict(w.params, density_model=1, rho_phase=RHO_TABLE1,
+                  nu=table1_viscosities(visc_ratio))
+    return Workload(w.name + "_table1_densities", w.dim, w.shape, w.solid, w.elec, w.phi_init,
+                    params, steps=w.steps, schedule=list(w.schedule))
+
+
 def _coords(shape):
     nz, ny, nx = shape
     return np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
@@ -322,9 +344,16 @@ def electrode_above(dim=2, nx=256, ny=24, nz=1, *, l_e=8, x_e=240, w_e=8, V=0.05
                     phi, params, steps=1, schedule=[(0, [V])])
 
 
+def droplet_3d_128x64x64_table1_densities(seed=1):
+    """The 128x64x64 droplet workload with Table 1's densities (water : oil : air =
+    998 : 970 : 1.2) and viscosities, run by the variable-density momentum scheme."""
+    return with_table1_densities(droplet_3d_128x64x64(seed))
+
+
 WORKLOADS = {
     "droplet_2d_128x64": droplet_2d_128x64,
     "droplet_3d_128x64x64": droplet_3d_128x64x64,
+    "droplet_3d_128x64x64_table1_densities": droplet_3d_128x64x64_table1_densities,
     "transport_3d_384x128x96": transport_3d_384x128x96,
     "control_3d_96x64x64": control_3d_96x64x64,
 }

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_binding_layout_matches_library(lib):
     from paper_2608_12868_b300 import lbehd
-    assert lib.lbehd_abi_version() == 3
+    assert lib.lbehd_abi_version() == 4
     assert lib.lbehd_config_size() == ctypes.sizeof(lbehd.Config)
     assert set(lbehd.EXPORTS) <= set(_declared())
 

@@ -1,0 +1,126 @@
+"""The variable-density momentum scheme (Table 1's densities and viscosities,
+density_model 1) on the GPU against the FP64 oracle, plus what the GPU alone can check.
+
+Bars: phase-field and charge populations, Phi_i and the potential as in the
+equal-density parity tests (1e-5); the momentum populations carry the gauge pressure and
+rho u, which are small, so they are compared relative to their largest magnitude at
+G_TOL; the velocity at U_TOL of its largest magnitude (it is largest in the air, where a
+small force moves a light fluid); droplet observables at 0.5 %; component mass conserved to
+1e-6 over 2000 steps. For a drop at rest the velocity is only the spurious current
+(~3e-5): in the air, rho u = sum e g + F/2 is ~1e-3 of the populations it is summed from
+and is then divided by rho = 0.0012, so FP32 rounding (6e-8) of ~20 terms reaches a few
+1e-4 of max|u| there; that case's velocity bar is U_TOL_REST. The batched form and the
+adjoint refuse the scheme.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_12868_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+G_TOL = 1e-4
+U_TOL = 1e-4
+U_TOL_REST = 5e-4
+OBS_TOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_12868_b300 import build, lbehd
+    build.build()
+    return lbehd
+
+
+def rel_linf(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    "small_3d": lambda: W.with_table1_densities(W.small_3d()),
+    "small_2d": lambda: W.with_table1_densities(W.small_2d()),
+    "droplet_3d_48x32x24": lambda: W.with_table1_densities(
+        W.droplet_3d(48, 32, 24, R=7.0, pillar_h=4, electrodes=[(30, 38, 10, 22)], V=[0.05],
+                     seed=11, name="droplet_3d_48x32x24")),
+}
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("case", list(CASES))
+def test_parity_with_the_oracle(gpu, oracle_mod, case, variant):
+    w = CASES[case]()
+    sim = gpu.Simulation(w)
+    sim.set_option(gpu.OPT_COLLIDE, variant)
+    orc = oracle_mod.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    steps = 40
+    sim.step(steps)
+    orc.step(steps)
+    fl = orc.solid == 0
+    errs = {
+        "g": rel_linf(sim.populations_g()[:, fl], orc.g[:, fl]),
+        "fphi": rel_linf(sim.array("fphi")[:, :, fl], orc.fphi[:, :, fl]),
+        "frho": rel_linf(sim.array("frho")[:, fl], orc.frho[:, fl]),
+        "u": rel_linf(sim.array("u")[:, fl], orc.u[:, fl]),
+        "phi": float(np.abs(sim.array("phi")[:, fl] - orc.Phi[:, fl]).max()),
+    }
+    print(case, variant, errs)
+    assert errs["g"] <= G_TOL and errs["u"] <= U_TOL, errs
+    assert errs["fphi"] <= POP_TOL and errs["frho"] <= POP_TOL and errs["phi"] <= POP_TOL, errs
+    og, oo = sim.observe(), orc.observables()
+    assert og["status"] == 0
+    for k in ("velocity", "f_ele"):
+        scale = np.abs(oo[k]).max()
+        assert np.abs(og[k] - oo[k]).max() <= OBS_TOL * scale, (k, og[k], oo[k])
+    sim.close()
+
+
+def test_static_drop_at_the_water_air_ratio(gpu, oracle_mod):
+    """A water drop at rest in air (2D, ratio 830, no electrodes): 400 steps against the
+    oracle, the case its Young-Laplace pin checks."""
+    n, R = 48, 12.0
+    shape = (1, n, n)
+    yy, xx = np.mgrid[0:n, 0:n]
+    c = (n - 1) / 2
+    pd = (0.5 * (1 - np.tanh(2 * (np.sqrt((xx - c) ** 2 + (yy - c) ** 2) - R) / 5)))[None]
+    phi = np.zeros((3,) + shape)
+    phi[0], phi[2] = pd, 1 - pd
+    params = dict(W.make_params(V=()), density_model=1, rho_phase=W.RHO_TABLE1,
+                  nu=W.table1_viscosities())
+    w = W.Workload("drop_2d_48_table1", 2, shape, np.zeros(shape, np.uint8),
+                   np.full(shape, -1, np.int16), phi, params)
+    sim = gpu.Simulation(w)
+    orc = oracle_mod.OracleSim(2, shape, w.solid, w.elec, phi, params)
+    sim.step(400)
+    orc.step(400)
+    assert rel_linf(sim.populations_g(), orc.g) <= G_TOL
+    assert rel_linf(sim.array("u"), orc.u) <= U_TOL_REST
+    assert np.abs(sim.array("phi") - orc.Phi).max() <= POP_TOL
+    sim.close()
+
+
+def test_mass_and_stability_over_2000_steps(gpu):
+    w = CASES["droplet_3d_48x32x24"]()
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.step(1)
+    m0 = sim.observe()["mass"]
+    sim.step(1999)
+    o = sim.observe()
+    assert o["status"] == 0
+    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6, o["mass"] / m0
+    assert np.isfinite(sim.array("u")).all()
+    sim.close()
+
+
+def test_batched_form_and_adjoint_refuse_it(gpu):
+    w = CASES["small_3d"]()
+    with pytest.raises(gpu.LBEHDError):
+        gpu.Batch([w, W.small_3d()])
+    sim = gpu.Simulation(w)
+    V = np.full((2, 1), 0.05)
+    with pytest.raises(gpu.LBEHDError):
+        sim.adjoint_forward(V, 5)
+    sim.close()
