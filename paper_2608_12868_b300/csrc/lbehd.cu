@@ -41,6 +41,8 @@ struct lbehd_handle {
     size_t N = 0;
     int Q = 0, QS = 0;
     Params P{};
+    ParamsVD PV{};                 // the variable-density kernels' extra parameters (rho_ph)
+    bool var_density = false;      // config density_model 1
     cudaStream_t stream = nullptr;
     cudaStream_t ls = nullptr;     // stream the launch helpers enqueue on (stream, or aux
     cudaStream_t aux = nullptr;    //   while a conditional-node body is being captured)
@@ -698,7 +700,7 @@ int resolved_variant(const lbehd_handle *h)
     const int v = h->collide_variant;
     if (v == 1 || !h->maps_ok)
         return 1;
-    if (h->P.var_density)   // the variable-density scheme has the 32x4 staged kernel only
+    if (h->var_density)   // the variable-density scheme has the 32x4 staged kernel only
         return 2;
     return v == 0 ? 2 : v;
 }
@@ -725,13 +727,15 @@ void collide(lbehd_handle *h)
     const bool staged = v != 1;
     const int first = h->first ? 1 : 0;
     launch(h, LBEHD_KC_COLLIDE, 1, [&] {
-        if (h->P.var_density) {
+        if (h->var_density) {
+            ParamsVD PV = h->PV;
+            static_cast<Params &>(PV) = h->P;
             if (!staged)
-                k_collide<D, true><<<h->grid, h->block, 0, h->ls>>>(h->P, S, first);
+                k_collide<D, true><<<h->grid, h->block, 0, h->ls>>>(PV, S, first);
             else
                 k_collide_staged<D, 4, true>
                     <<<h->grid_tile[0], h->block, staged_smem_bytes<D, 4>(), h->ls>>>(
-                        h->P, S, first, h->maps[0][h->cur]);
+                        PV, S, first, h->maps[0][h->cur]);
         } else if (!staged)
             k_collide<D><<<h->grid, h->block, 0, h->ls>>>(h->P, S, first);
         else if (shape == 0)
@@ -1017,11 +1021,11 @@ int set_params(lbehd_handle *h)
     P.s_bulk = (float)c.s_bulk;
     if (c.density_model != 0 && c.density_model != 1)
         return fail(h, LBEHD_ERR_INVALID_ARG, "density_model takes 0 or 1");
-    P.var_density = c.density_model;
+    h->var_density = c.density_model == 1;
     for (int k = 0; k < 3; k++) {
         if (c.density_model == 1 && !(c.rho_phase[k] > 0.0))
             return fail(h, LBEHD_ERR_INVALID_ARG, "rho_phase must be > 0 with density_model 1");
-        P.rho_ph[k] = c.density_model == 1 ? (float)c.rho_phase[k] : 1.0f;
+        h->PV.rho_ph[k] = (float)c.rho_phase[k];
     }
     h->mg_nu = c.mg_nu > 0 ? c.mg_nu : 2;
     h->bj_nu = c.mg_nu > 0 ? c.mg_nu : 3;
@@ -3337,7 +3341,7 @@ int lbehd_adjoint_forward(lbehd_handle *h, const double *V, int n_segments, int 
         return fail(h, LBEHD_ERR_INVALID_ARG, "null handle, schedule or loss");
     if (h->batch_owned)
         return fail(h, LBEHD_ERR_INVALID_ARG, "instance of a batch: the adjoint is per handle");
-    if (h->P.var_density)
+    if (h->var_density)
         return fail(h, LBEHD_ERR_INVALID_ARG,
                     "the adjoint runs equal densities (density_model 0)");
     if (n_segments < 1 || seg_steps < 1 || (long long)n_segments * seg_steps > (1 << 24))
