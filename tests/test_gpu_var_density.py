@@ -78,6 +78,30 @@ def test_parity_with_the_oracle(gpu, oracle_mod, case, variant):
     sim.close()
 
 
+def test_full_size_in_the_benchmark_configuration(gpu, oracle_mod):
+    """The 128x64x64 droplet with Table 1's densities at full size, in the launch
+    configuration the benchmark times (step graphs, persistent Gauss-law solve, autotuned
+    collide kernel), against the oracle after 3 and after 30 steps."""
+    w = W.droplet_3d_128x64x64_table1_densities()
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    orc = oracle_mod.OracleSim(w.dim, w.shape, w.solid, w.elec, w.phi_init, w.params)
+    sim.step(1)
+    sim.autotune(reps=2)
+    sim.step(2)
+    orc.step(3)
+    fl = orc.solid == 0
+    for steps in (0, 27):
+        sim.step(steps)
+        orc.step(steps)
+        assert rel_linf(sim.populations_g()[:, fl], orc.g[:, fl]) <= G_TOL
+        assert rel_linf(sim.array("u")[:, fl], orc.u[:, fl]) <= U_TOL
+        assert rel_linf(sim.array("fphi")[:, :, fl], orc.fphi[:, :, fl]) <= POP_TOL
+        assert rel_linf(sim.array("frho")[:, fl], orc.frho[:, fl]) <= POP_TOL
+        assert np.abs(sim.array("phi")[:, fl] - orc.Phi[:, fl]).max() <= POP_TOL
+    assert sim.observe()["status"] == 0
+    sim.close()
+
+
 def test_static_drop_at_the_water_air_ratio(gpu, oracle_mod):
     """A water drop at rest in air (2D, ratio 830, no electrodes): 400 steps against the
     oracle, the case its Young-Laplace pin checks."""
