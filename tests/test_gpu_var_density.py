@@ -139,6 +139,22 @@ def test_mass_and_stability_over_2000_steps(gpu):
     sim.close()
 
 
+def test_full_size_10000_steps(gpu):
+    """The 128x64x64 droplet with Table 1's densities for 10 000 steps (the configuration's
+    run length): finite, every solve converged, component mass conserved to 1e-6."""
+    w = W.droplet_3d_128x64x64_table1_densities()
+    sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+    sim.step(1)
+    sim.autotune(reps=2)
+    m0 = sim.observe()["mass"]
+    sim.step(9999)
+    o = sim.observe()
+    assert o["status"] == 0
+    assert np.abs(o["mass"] / m0 - 1).max() <= 1e-6, o["mass"] / m0
+    assert np.isfinite(sim.array("u")).all() and np.isfinite(sim.populations_g()).all()
+    sim.close()
+
+
 def test_batched_form_and_adjoint_refuse_it(gpu):
     w = CASES["small_3d"]()
     with pytest.raises(gpu.LBEHDError):
