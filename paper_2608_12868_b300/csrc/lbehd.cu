@@ -77,14 +77,20 @@ struct lbehd_handle {
         int nbj = 0;                   // blocks of the block-local smoother
     };
     std::vector<Level> mg;
-    // inc[s & 1] holds the potential increment of step s; the warm start of step s is the
-    // increment of step s-2 (the charge collision with tau_rho ~ 1/2 makes consecutive
-    // increments alternate). delta2: correction of a refinement pass.
+    // inc[s & 1] holds the potential increment of step s; the warm start of step s is formed
+    // from the increments of steps s-1 and s-2 (LBEHD_OPT_WARM_START), in place in inc[s & 1]
+    // (the charge collision with tau_rho ~ 1/2 makes consecutive increments alternate).
+    // delta2: correction of a refinement pass.
     float *inc[2] = {}, *delta2 = nullptr;
     float *eps_mg = nullptr;       // eps the multigrid hierarchy was last built from
     float *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
     double *cg_partials = nullptr;
     CgScalars *cg_s = nullptr;
+    // LBEHD_OPT_WARM_START: 1 starts each forward solve from the combination of the last two
+    // increments with the least residual (k_pcg_init_mr), 0 from the increment of step s - 2
+    int warm_mode = 1;
+    double *mr_alpha = nullptr;    // multi-launch form: (a1, a2, a . c) of the current start
+    float *mr_part = nullptr;      // MR_NV x nblocks_site FP32 block sums of k_pcg_init_mr
     CgScalars *h_cg = nullptr;     // pinned copy for the host convergence check
     dim3 grid1d;
     size_t nblocks1d = 0;
@@ -376,6 +382,14 @@ int ps_setup(lbehd_handle *h)
 
 bool ps_use(const lbehd_handle *h) { return h->ps_ok && h->ps_on; }
 
+bool mr_use(const lbehd_handle *h) { return h->warm_mode == 1; }
+
+// The other increment buffer: d1 (the last step's increment) when x holds d2.
+const float *mr_other(const lbehd_handle *h, const float *x)
+{
+    return x == h->inc[0] ? h->inc[1] : h->inc[0];
+}
+
 bool bj_use(const lbehd_handle *h) { return h->bj_ok && h->mg_smoother == 1; }
 
 // One persistent solve on h->ls: the forward step's (increment x, this step's charge rho) or
@@ -397,7 +411,19 @@ int ps_launch(lbehd_handle *h, int mode, float *x, const float *rho, const float
     // CTAs take it in four latency-bound rounds. Same per-site body and block partition as
     // the kernel's own start phase. It also resets the barrier counter.
     const auto &L0 = h->mg[0];
-    if (mode == PS_FORWARD)
+    A.mr = mode == PS_FORWARD && mr_use(h) ? 1 : 0;
+    if (A.mr) {
+        // minimal-residual start: r0, q1 = A d1 (into q), q2 = A d2 (into p: the first
+        // iteration does not read the old direction) and the block sums; the kernel sums the
+        // coefficients and forms x0 (and r, if it iterates)
+        A.mr_part = h->mr_part;
+        A.mr_d1 = mr_other(h, x);
+        A.mr_q1 = h->cg_q;
+        A.mr_q2 = h->cg_p;
+        k_pcg_init_mr<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
+            L0.d, A.pot, A.pot_lo, A.mr_d1, x, A.eps, rho, A.info, L0.D, A.r, h->cg_q, h->cg_p,
+            A.part[1], h->mr_part, &h->ps_bar->count);
+    } else if (mode == PS_FORWARD)
         k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
             L0.d, A.pot, A.pot_lo, x, A.eps, rho, A.info, L0.D, A.r, A.part[1], &h->ps_bar->count);
     else
@@ -499,10 +525,11 @@ int vcycle_launches(const lbehd_handle *h)
     return (levels - 1) * (4 * h->mg_nu + 3) + 4 * h->mg_coarse;
 }
 
-void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk)
+void cg_scalar(lbehd_handle *h, int nv, int op, size_t nblk, const double *mr = nullptr)
 {
     k_pcg_scalar<<<1, SCALAR_THREADS, 0, h->ls>>>(h->cg_partials, (long long)nblk, nv, op, h->cg_s,
-                                                   h->cond, h->use_cond, h->cond_ref, h->use_ref);
+                                                   h->cond, h->use_cond, h->cond_ref, h->use_ref,
+                                                   mr);
 }
 
 // One preconditioned CG iteration on level 0 (z = V-cycle(r) lives in mg[0].x), updating
@@ -541,10 +568,29 @@ int read_cg(lbehd_handle *h)
 }
 
 // r = b - A (phi + x) in FP64 and the CG start (op 0: first pass of a step, 4: refinement).
+// The first pass of a step with the minimal-residual start (x holds d2, the other increment
+// buffer d1) replaces x by x0 = a1 d1 + a2 d2 and forms r = b - A (phi + x0) from r0, q1, q2.
 template <int D>
-void pcg_start(lbehd_handle *h, const float *x, int op = 0)
+void pcg_start(lbehd_handle *h, float *x, int op = 0)
 {
     auto &L0 = h->mg[0];
+    if (op == 0 && mr_use(h)) {
+        // the persistent kernel's order: coefficients, x0 and r (here always formed: the same
+        // x0 as the persistent solve forms in its update when the start meets the tolerance),
+        // then the test of the least residual
+        launch(h, LBEHD_KC_CG, 4, [&] {
+            const float *d1 = mr_other(h, x);
+            k_pcg_init_mr<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
+                L0.d, h->pot, h->pot_lo, d1, x, h->eps, h->rho[h->pcur], h->info, L0.D,
+                h->cg_r, h->cg_q, h->cg_p, h->cg_partials, h->mr_part);
+            k_mr_alpha<<<1, SCALAR_THREADS, 0, h->ls>>>(h->mr_part, (int)h->nblocks_site,
+                                                         h->mr_alpha);
+            k_pcg_start_mr<<<h->grid1d, h->block, 0, h->ls>>>((int)h->N, h->mr_alpha, d1, x,
+                                                              h->cg_r, h->cg_q, h->cg_p);
+            cg_scalar(h, 2, op, h->nblocks_site, h->mr_alpha);
+        });
+        return;
+    }
     launch(h, LBEHD_KC_CG, 2, [&] {
         k_pcg_init<D><<<(unsigned)h->nblocks_site, h->block, 0, h->ls>>>(
             L0.d, h->pot, h->pot_lo, x, h->eps, h->rho[h->pcur], h->info, L0.D, h->cg_r,
@@ -1169,7 +1215,10 @@ int init_impl(lbehd_handle *h)
     h->cg_q = (float *)dev_alloc(h, N * fb);
     h->cg_partials = (double *)dev_alloc(h, 2 * std::max(h->nblocks, h->nblocks1d) * sizeof(double));
     h->cg_s = (CgScalars *)dev_alloc(h, sizeof(CgScalars));
-    if (!h->inc[0] || !h->inc[1] || !h->delta2 || !h->cg_r || !h->cg_p || !h->cg_q || !h->cg_partials || !h->cg_s)
+    h->mr_alpha = (double *)dev_alloc(h, 3 * sizeof(double));
+    h->mr_part = (float *)dev_alloc(h, MR_NV * h->nblocks_site * sizeof(float));
+    if (!h->inc[0] || !h->inc[1] || !h->delta2 || !h->cg_r || !h->cg_p || !h->cg_q ||
+        !h->cg_partials || !h->cg_s || !h->mr_alpha || !h->mr_part)
         return fail(h, LBEHD_ERR_OOM, "device allocation failed (Poisson)");
     {
         MgDims d = mg_dims(h->nx, h->ny, h->nz);
@@ -1470,6 +1519,14 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
                 cudaGraphExecDestroy(e);
                 e = nullptr;
             }
+    } else if (option == LBEHD_OPT_WARM_START) {
+        if (value < 0 || value > 1)
+            return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_WARM_START takes 0 or 1");
+        if (value == 1 && h->batch_owned)
+            return fail(h, LBEHD_ERR_INVALID_ARG,
+                        "LBEHD_OPT_WARM_START 1: the batched solve starts from step s - 2's increment");
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->warm_mode = (int)value;
     } else if (option == LBEHD_OPT_MG_SMOOTHER) {
         if (value < 0 || value > 1)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_MG_SMOOTHER takes 0 or 1");
@@ -3329,6 +3386,8 @@ int lbehd_get_option(lbehd_handle *h, int option, long long *value)
         *value = ps_use(h) ? 1 : 0;
     else if (option == LBEHD_OPT_MG_SMOOTHER)
         *value = bj_use(h) ? 1 : 0;
+    else if (option == LBEHD_OPT_WARM_START)
+        *value = h->warm_mode;
     else
         return fail(h, LBEHD_ERR_INVALID_ARG, "unknown option");
     return LBEHD_OK;
@@ -3504,6 +3563,8 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
         // iterations than the block-local smoother (0.86 against 1.04 per instance-step) and
         // run faster as full-occupancy launches over all instances (2786 against 2465 MLUPS)
         h->mg_smoother = 0;
+        // the batched solve starts from the increment of step s - 2 (LBEHD_OPT_WARM_START 0)
+        h->warm_mode = 0;
         b->inst.push_back(h);
     }
     auto balloc = [&](size_t bytes) -> void * {

@@ -7,9 +7,10 @@
 // terms. The potential is stored as a compensated pair of floats (hi + lo); r0 is formed
 // from compensated differences of it, so the FP32 iteration on the small increment is not
 // limited by the rounding of phi itself, and differences of phi (E, the conduction source
-// of Eq. 14) keep ~FP64 accuracy. The warm
-// start is the increment of two steps back (consecutive increments alternate in sign
-// because the charge collision relaxes its first moments with 1 - 1/tau_rho ~ -1).
+// of Eq. 14) keep ~FP64 accuracy. The warm start is the combination of the last two
+// steps' increments with the least residual (k_pcg_init_mr), or the increment of two steps
+// back alone (consecutive increments alternate in sign because the charge collision relaxes
+// its first moments with 1 - 1/tau_rho ~ -1).
 //
 // Preconditioner: one symmetric V-cycle of cell-centred geometric multigrid. Coarse cells
 // aggregate 2x2(x2) fine cells; coarse face coefficients are the sums of the fine faces
@@ -956,6 +957,179 @@ __global__ void __launch_bounds__(BX) k_pcg_Ap(MgDims d, const float *__restrict
     block_partials<1>(v, partials);
 }
 
+// ---------------------------------------------------------------- minimal-residual start
+//
+// The forward solve may start from x0 = a1 d1 + a2 d2, the increments of the last two steps
+// (d1 the last one's, d2 the one before), with (a1, a2) minimising ||b - A (phi + x0)||_2 over
+// their span. With r0 = b - A phi and q_k = A d_k (Dirichlet values held, so A acts on the
+// increments alone) that is the 2 x 2 normal system G a = c, G_kl = q_k . q_l, c_k = q_k . r0,
+// and the least residual is ||r0||^2 - a . c. The sums only choose the start and estimate its
+// residual for the convergence test; they are FP32 block sums (the FP64 pipe of this part is
+// narrow), summed in a fixed order by one 1024-thread block. ||r0||^2 and ||b||^2 are the FP64
+// partials of every other residual. A step whose start meets the tolerance applies x0 and
+// stops; one that does not forms x0 and r = r0 - a1 q1 - a2 q2 site by site and iterates.
+// A singular or nearly singular system (the first solve: d1 = d2 = 0) falls back to one
+// increment or to none.
+constexpr int MR_NV = 5;   // q1.r0, q2.r0, q1.q1, q1.q2, q2.q2
+
+// Threads of the one-block scalar reductions (the CG scalars, the start's coefficients).
+constexpr int SCALAR_THREADS = 1024;
+
+// out = (a1, a2, a . c) from the totals (c1, c2, G11, G12, G22).
+__device__ __forceinline__ void mr_solve(const float (&m)[MR_NV], double *out)
+{
+    const double c1 = m[0], c2 = m[1], g11 = m[2], g12 = m[3], g22 = m[4];
+    const double det = g11 * g22 - g12 * g12;
+    double a1 = 0.0, a2 = 0.0;
+    if (g11 > 0.0 && g22 > 0.0 && det > 1e-6 * g11 * g22) {
+        a1 = (c1 * g22 - c2 * g12) / det;
+        a2 = (c2 * g11 - c1 * g12) / det;
+    } else if (g22 > 0.0) {
+        a2 = c2 / g22;
+    } else if (g11 > 0.0) {
+        a1 = c1 / g11;
+    }
+    out[0] = a1;
+    out[1] = a2;
+    out[2] = a1 * c1 + a2 * c2;
+}
+
+// The coefficients from the first pass's block sums mr_part[k * nblk + b], by one block of
+// SCALAR_THREADS threads in a fixed order: thread t adds blocks t, t + SCALAR_THREADS, ... in
+// order (the MR_NV loads of a block issued together), then the warps' butterflies and the
+// warps in order. Every thread of the block gets out (shared or global memory, written by
+// thread 0, visible after the block barrier this ends with).
+__device__ __forceinline__ void mr_alpha_block(const float *part, int nblk, double *out)
+{
+    constexpr int NW = SCALAR_THREADS / 32;
+    __shared__ float sm[MR_NV][NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float acc[MR_NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = threadIdx.x; j < nblk; j += SCALAR_THREADS) {
+        float v[MR_NV];
+#pragma unroll
+        for (int k = 0; k < MR_NV; k++)
+            v[k] = __ldcg(part + (size_t)k * nblk + j);
+#pragma unroll
+        for (int k = 0; k < MR_NV; k++)
+            acc[k] = __fadd_rn(acc[k], v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < MR_NV; k++) {
+        const float sv = warp_sum(acc[k]);
+        if (lane == 0)
+            sm[k][wid] = sv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot[MR_NV];
+#pragma unroll
+        for (int k = 0; k < MR_NV; k++) {
+            tot[k] = 0.0f;
+            for (int w = 0; w < NW; w++)
+                tot[k] = __fadd_rn(tot[k], sm[k][w]);
+        }
+        mr_solve(tot, out);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SCALAR_THREADS) k_mr_alpha(const float *__restrict__ part,
+                                                             int nblk, double *__restrict__ out)
+{
+    mr_alpha_block(part, nblk, out);
+}
+
+// First pass: r0 = b - A phi (k_pcg_init's start residual with a zero increment, and its FP64
+// block partials of ||r0||^2 and ||b||^2) into r, q1 = A d1 and q2 = A d2, and FP32 block sums
+// of the five products into mr_part[k * nblk + block].
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init_mr(MgDims d, const float *__restrict__ pot,
+                                                    const float *__restrict__ pot_lo,
+                                                    const float *__restrict__ d1,
+                                                    const float *__restrict__ d2,
+                                                    const float *__restrict__ eps,
+                                                    const float *__restrict__ rho,
+                                                    const uint8_t *__restrict__ info,
+                                                    const float *__restrict__ Dg,
+                                                    float *__restrict__ r, float *__restrict__ q1,
+                                                    float *__restrict__ q2,
+                                                    double *__restrict__ partials,
+                                                    float *__restrict__ mr_part,
+                                                    unsigned *zero = nullptr)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int nblk = (int)gridDim.x;
+    if (zero && i == 0)   // the grid-barrier counter of the persistent solve that follows
+        *zero = 0u;
+    float v[2] = {0.f, 0.f}, m[MR_NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < d.nx * d.ny * d.nz) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        const float r0 = pcg_init_value<D>(d, pot, pot_lo, nullptr, eps, rho, info, Dg, x, y, z,
+                                           v, true);
+        float w[1] = {0.f};
+        const float a = pcg_Ap_value<D>(d, eps, info, Dg, d1, x, y, z, w);
+        const float b = pcg_Ap_value<D>(d, eps, info, Dg, d2, x, y, z, w);
+        r[i] = r0;
+        q1[i] = a;
+        q2[i] = b;
+        m[0] = __fmul_rn(a, r0);
+        m[1] = __fmul_rn(b, r0);
+        m[2] = __fmul_rn(a, a);
+        m[3] = __fmul_rn(a, b);
+        m[4] = __fmul_rn(b, b);
+    }
+    block_partials<2>(v, partials, blockIdx.x, nblk);
+    __shared__ float sm[MR_NV][BX / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < MR_NV; k++) {
+        const float s = warp_sum(m[k]);
+        if (lane == 0)
+            sm[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < MR_NV) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int w = 0; w < BX / 32; w++)
+            acc = __fadd_rn(acc, sm[threadIdx.x][w]);
+        mr_part[threadIdx.x * nblk + blockIdx.x] = acc;
+    }
+}
+
+// At one site: x0 = a1 d1 + a2 d2 written over d2 (x holds d2 on entry); returns x0.
+__device__ __forceinline__ float mr_x0_site(int i, float a1, float a2, const float *d1,
+                                            float *x)
+{
+    const float x0 = __fmaf_rn(a2, x[i], __fmul_rn(a1, d1[i]));
+    x[i] = x0;
+    return x0;
+}
+
+// At one site: x0 as mr_x0_site and r = r0 - a1 q1 - a2 q2 over r0.
+__device__ __forceinline__ void mr_start_site(int i, float a1, float a2, const float *d1,
+                                              float *x, float *r, const float *q1,
+                                              const float *q2)
+{
+    mr_x0_site(i, a1, a2, d1, x);
+    r[i] = __fmaf_rn(-a2, q2[i], __fmaf_rn(-a1, q1[i], r[i]));
+}
+
+// x0 and r for every site (grid-stride).
+__global__ void __launch_bounds__(BX) k_pcg_start_mr(int n, const double *__restrict__ alpha,
+                                                     const float *__restrict__ d1,
+                                                     float *__restrict__ x, float *__restrict__ r,
+                                                     const float *__restrict__ q1,
+                                                     const float *__restrict__ q2)
+{
+    const float a1 = (float)alpha[0], a2 = (float)alpha[1];
+    for (int i = blockIdx.x * BX + threadIdx.x; i < n; i += gridDim.x * BX)
+        mr_start_site(i, a1, a2, d1, x, r, q1, q2);
+}
+
 // delta += alpha p, r -= alpha q, partials of ||r||^2.
 __device__ __forceinline__ void pcg_update_range_t(int n, const float *p,
                                                    const float *q,
@@ -1028,7 +1202,6 @@ __global__ void __launch_bounds__(BX) k_pcg_dot(size_t n, const float *__restric
 // (op 0 clears refine.) pcg_scalar_block returns true in thread 0 after updating *s.
 // k_pcg_scalar: with use_cond, ops 0, 4, 3 and 5 also set the graph's while-loop condition
 // to !done; with use_ref, op 0 clears and op 3 sets the condition of the refinement block.
-constexpr int SCALAR_THREADS = 1024;
 
 // The fixed summation order, in two pieces that may run on different SMs: the sum of
 // virtual warp w (lanes = threads 32 w .. 32 w + 31 of the 1024-thread order: each lane's
@@ -1051,10 +1224,13 @@ __device__ __forceinline__ double pcg_vwarp_sum(const double *p, long long nbloc
 }
 
 // CG scalar update (thread 0) from the totals of the op's partial arrays.
-__device__ __forceinline__ void pcg_scalar_update(const double (&tot)[2], int op, CgScalars *s)
+// rr_sub (op 0 only): subtracted from the reduced ||r||^2 (the minimal-residual start's a . c,
+// so that rr is its least residual's norm).
+__device__ __forceinline__ void pcg_scalar_update(const double (&tot)[2], int op, CgScalars *s,
+                                                  double rr_sub = 0.0)
 {
     if (op == 0 || op == 4) {
-        s->rr = tot[0];
+        s->rr = op == 0 && rr_sub != 0.0 ? fmax(tot[0] - rr_sub, 0.0) : tot[0];
         s->bb = tot[1];
         s->iters = 0;
         if (op == 0) {
@@ -1091,7 +1267,7 @@ __device__ __forceinline__ void pcg_scalar_update(const double (&tot)[2], int op
 
 __device__ __forceinline__ bool pcg_scalar_block(const double *partials,
                                                  long long nblocks, int nv, int op,
-                                                 CgScalars *s)
+                                                 CgScalars *s, double rr_sub = 0.0)
 {
     __shared__ double sm[2][SCALAR_THREADS / 32];
     double tot[2] = {0.0, 0.0};
@@ -1112,7 +1288,7 @@ __device__ __forceinline__ bool pcg_scalar_block(const double *partials,
     }
     if (threadIdx.x != 0)
         return false;
-    pcg_scalar_update(tot, op, s);
+    pcg_scalar_update(tot, op, s, rr_sub);
     return true;
 }
 
@@ -1122,9 +1298,11 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_pcg_scalar(const double *__r
                                                                cudaGraphConditionalHandle cond,
                                                                int use_cond,
                                                                cudaGraphConditionalHandle cond_ref,
-                                                               int use_ref)
+                                                               int use_ref,
+                                                               const double *__restrict__ mr = nullptr)
 {
-    if (!pcg_scalar_block(partials, nblocks, nv, op, s))
+    // mr: the minimal-residual start's (a1, a2, a . c); op 0 then tests its least residual
+    if (!pcg_scalar_block(partials, nblocks, nv, op, s, mr ? mr[2] : 0.0))
         return;
     if (use_cond && op != 1 && op != 2)
         cudaGraphSetConditional(cond, s->done ? 0u : 1u);

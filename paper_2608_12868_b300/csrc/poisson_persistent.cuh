@@ -78,6 +78,12 @@ struct PsArgs {
     const float *eps, *rho;
     const uint8_t *info;
     float *x, *delta2;
+    // forward with the minimal-residual start (mr = 1): k_pcg_init_mr's block sums, the last
+    // step's increment d1 and the products q1 = A d1, q2 = A d2 (x holds d2 and r holds
+    // b - A phi on entry, part[1] the partials of their norms)
+    int mr;
+    const float *mr_part;
+    const float *mr_d1, *mr_q1, *mr_q2;
     // adjoint: right-hand side (the solution is in x)
     const float *rhs;
     float *r, *p, *p2, *q;     // r is L[0].b; z is L[0].x; p and p2 alternate
@@ -202,17 +208,20 @@ __device__ __forceinline__ void ps_for_vblocks(int nvb, F &&f)
 // are those of the range bodies in poisson.cuh.
 constexpr int PS_B = 4;
 
-// phi += delta (compensated pair), acc += delta, on active cells.
-__device__ __forceinline__ void ps_apply(int n, const float *Dg, const float *delta, float *acc,
-                                         float *pot, float *pot_lo)
+// phi += delta (compensated pair), acc += delta, on active cells. With d1 (the
+// minimal-residual start, delta holding d2): delta = a1 d1 + a2 d2 first, at every site
+// (mr_x0_site's arithmetic), then the update.
+__device__ __forceinline__ void ps_apply(int n, const float *Dg, float *delta, float *acc,
+                                         float *pot, float *pot_lo, float a1 = 0.0f,
+                                         float a2 = 0.0f, const float *d1 = nullptr)
 {
     const int S = gridDim.x * PS_THREADS;
     for (int i0 = blockIdx.x * PS_THREADS + threadIdx.x; i0 < n; i0 += PS_B * S) {
-        float dg[PS_B], d[PS_B], hi[PS_B], lo[PS_B], ac[PS_B];
+        float dg[PS_B], d[PS_B], hi[PS_B], lo[PS_B], ac[PS_B], e[PS_B];
 #pragma unroll
         for (int j = 0; j < PS_B; j++) {
             const int i = i0 + j * S;
-            dg[j] = d[j] = hi[j] = lo[j] = ac[j] = 0.0f;
+            dg[j] = d[j] = hi[j] = lo[j] = ac[j] = e[j] = 0.0f;
             if (i < n) {
                 dg[j] = Dg[i];
                 d[j] = delta[i];
@@ -220,6 +229,18 @@ __device__ __forceinline__ void ps_apply(int n, const float *Dg, const float *de
                 lo[j] = pot_lo[i];
                 if (acc)
                     ac[j] = acc[i];
+                if (d1)
+                    e[j] = d1[i];
+            }
+        }
+        if (d1) {
+#pragma unroll
+            for (int j = 0; j < PS_B; j++) {
+                const int i = i0 + j * S;
+                if (i < n) {
+                    d[j] = __fmaf_rn(a2, d[j], __fmul_rn(a1, e[j]));
+                    delta[i] = d[j];
+                }
             }
         }
 #pragma unroll
@@ -500,13 +521,14 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     // pcg_scalar_block: small reductions are summed by every CTA; large ones have their 32
     // virtual-warp sums spread over CTAs 0 .. 32 nv - 1, a second barrier, then every CTA
     // finishes the butterfly over the 32 sums and updates its copy of the scalars
-    auto sync_scalar = [&](const double *part, int nv, int op, int nblk, bool first = true) {
+    auto sync_scalar = [&](const double *part, int nv, int op, int nblk, bool first = true,
+                           double rr_sub = 0.0) {
         if (first)   // not for partials written by the kernel before this one
             sync();
         if (!ok)
             return;
         if ((long long)nv * nblk < PS_SPLIT_MIN || (int)gridDim.x < 32 * nv) {
-            pcg_scalar_block(part, nblk, nv, op, &s);
+            pcg_scalar_block(part, nblk, nv, op, &s, rr_sub);
             __syncthreads();
             return;
         }
@@ -529,7 +551,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
                 tot[k] = a;
             }
             if (threadIdx.x == 0)
-                pcg_scalar_update(tot, op, &s);
+                pcg_scalar_update(tot, op, &s, rr_sub);
         }
         __syncthreads();
     };
@@ -683,13 +705,31 @@ __global__ void __launch_bounds__(PS_THREADS, 1) k_poisson_solve(const __grid_co
     };
 
     // the start residual r and its partials part[1] come from the k_pcg_init (forward) or
-    // k_adj_pcg_init (adjoint) launch just before this kernel: only their reduction is left
+    // k_adj_pcg_init (adjoint) launch just before this kernel: only their reduction is left.
+    // The minimal-residual start (k_pcg_init_mr before this kernel) first sums its coefficients
+    // in every CTA, in k_mr_alpha's order, and tests its least residual; if that meets the
+    // tolerance, the potential update forms x0 as it goes, else a phase forms x0 and r.
     z_ready = false;
-    sync_scalar(A.part[1], 2, 0, A.nbs, false);
+    const bool mr = A.mode == PS_FORWARD && A.mr;
+    __shared__ double mra[3];
+    if (mr)
+        mr_alpha_block(A.mr_part, A.nbs, mra);
+    sync_scalar(A.part[1], 2, 0, A.nbs, false, mr ? mra[2] : 0.0);
+    bool x0_formed = !mr;
+    if (ok && mr && !s.done) {
+        const float a1 = (float)mra[0], a2 = (float)mra[1];
+        ps_for(A.N, [&](int i) { mr_start_site(i, a1, a2, A.mr_d1, A.x, A.r, A.mr_q1, A.mr_q2); });
+        x0_formed = true;
+        sync();
+    }
     while (ok && !s.done)
         iteration(A.x);
     if (ok && A.mode == PS_FORWARD) {
-        ps_apply(A.N, L0.D, A.x, nullptr, A.pot, A.pot_lo);
+        if (x0_formed)
+            ps_apply(A.N, L0.D, A.x, nullptr, A.pot, A.pot_lo);
+        else
+            ps_apply(A.N, L0.D, A.x, nullptr, A.pot, A.pot_lo, (float)mra[0], (float)mra[1],
+                     A.mr_d1);
         // refinement: the true residual of the updated potential, once, if the pass iterated
         // (s.refine is the same in every CTA; without it the kernel's end is the barrier)
         if (ok && s.refine)

@@ -22,6 +22,7 @@ ARRAY_NAMES = {"g": G, "fphi": FPHI, "frho": FRHO, "phi": PHI, "rho": RHO, "pot"
 POISSON_HOST, POISSON_FIXED, POISSON_GRAPH = 0, 1, 2
 OPT_COLLIDE, OPT_MG_REFRESH, OPT_ADJ_TRAJECTORY, OPT_POISSON_KERNEL, OPT_BARRIER_TEST = 1, 2, 3, 4, 5
 OPT_MG_SMOOTHER = 6
+OPT_WARM_START = 7
 COLLIDE_AUTO, COLLIDE_GLOBAL, COLLIDE_STAGED = 0, 1, 2
 COLLIDE_STAGED_64x2, COLLIDE_STAGED_16x8 = 3, 4
 

@@ -46,9 +46,10 @@ def uneven_3d():
 
 def plain(gpu, w, smoother=0):
     """A single handle in graph mode with the given multigrid smoother (0: a batch's
-    default)."""
+    default) and a batch's warm start (the increment of step s - 2)."""
     sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     sim.set_option(gpu.OPT_MG_SMOOTHER, smoother)
+    sim.set_option(gpu.OPT_WARM_START, 0)
     return sim
 
 
@@ -120,6 +121,7 @@ def test_batch_mixing_the_two_smoothers(gpu):
     batch.step(steps)
     for i, w in enumerate(ws):
         sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
+        sim.set_option(gpu.OPT_WARM_START, 0)
         assert sim.get_option(gpu.OPT_MG_SMOOTHER) == (0 if i == 2 else 1)
         sim.step(steps)
         assert_same_state(batch[i], sim, f"instance {i}")

@@ -30,7 +30,7 @@ def gpu():
     return lbehd
 
 
-def pair(gpu, w, smoother=1):
+def pair(gpu, w, smoother=1, warm=1):
     a = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     b = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     b.set_option(gpu.OPT_POISSON_KERNEL, 0)
@@ -39,6 +39,8 @@ def pair(gpu, w, smoother=1):
     for s in (a, b):
         s.set_option(gpu.OPT_MG_SMOOTHER, smoother)
         assert s.get_option(gpu.OPT_MG_SMOOTHER) == smoother
+        s.set_option(gpu.OPT_WARM_START, warm)
+        assert s.get_option(gpu.OPT_WARM_START) == warm
     return a, b
 
 
@@ -67,6 +69,18 @@ CASES = {
 def test_persistent_solve_is_the_multi_launch_solve(gpu, case, smoother):
     w = CASES[case]()
     a, b = pair(gpu, w, smoother)
+    steps = 40 if case != "control_3d_96x64x64" else 24
+    a.step(steps)
+    b.step(steps)
+    assert_same(a, b)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_persistent_solve_is_the_multi_launch_solve_step_s2_start(gpu, case):
+    """The same with each solve started from the increment of step s - 2 alone
+    (LBEHD_OPT_WARM_START = 0, a batch's start)."""
+    w = CASES[case]()
+    a, b = pair(gpu, w, 1, warm=0)
     steps = 40 if case != "control_3d_96x64x64" else 24
     a.step(steps)
     b.step(steps)
