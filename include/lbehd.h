@@ -241,16 +241,18 @@ int lbehd_device_ptr(lbehd_handle *h, int which, void **ptr, size_t *bytes);
  *   for bit like it. A batch starts with 0 (lbehd_batch_set_option changes it for every
  *   instance). */
 #define LBEHD_OPT_MG_SMOOTHER 6
-/*   LBEHD_OPT_WARM_START: the start of each step's Gauss-law solve (Eq. 13). 1 (default for
- *   a handle): x0 = a1 d1 + a2 d2 from the increments of the last two steps, with (a1, a2)
+/*   LBEHD_OPT_WARM_START: the start of each step's Gauss-law solve (Eq. 13). 1 (a handle's
+ *   default): x0 = a1 d1 + a2 d2 from the increments of the last two steps, with (a1, a2)
  *   minimising the residual ||b - A (phi + x0)||_2 over their span (a 2 x 2 least-squares
  *   system from one extra pass over the lattice: A d1, A d2 and five dot products). 0: x0 =
  *   d2, the increment of two steps back (the increments of consecutive steps alternate in
  *   sign). Both stop at the same tolerance; the solutions differ within it. On the 128x64x64
- *   droplet in steady state, 88 % of the steps then converge on their start alone against
- *   74 %. The persistent and the multi-launch solves give the same bits for either value.
- *   Batch instances run 0 (the batched solve has no minimal-residual start); setting 1 on
- *   one is rejected with LBEHD_ERR_INVALID_ARG. */
+ *   droplet in steady state, 86 % of the steps then converge on their start alone against
+ *   74 %. The persistent, the multi-launch and the batched solves give the same bits for
+ *   either value. A batch starts with 0 (on the 64-instance sweep 1 lowers the CG
+ *   iterations per instance-step from 0.31 to 0.25 but runs at 3186 against 3594 MLUPS: the
+ *   batched CG loop runs while any instance iterates, and the start's extra passes cover
+ *   all of them); lbehd_batch_set_option changes it for every instance. */
 #define LBEHD_OPT_WARM_START 7
 int lbehd_set_option(lbehd_handle *h, int option, long long value);
 /* The value in effect: for LBEHD_OPT_COLLIDE the kernel the automatic choice resolved to,

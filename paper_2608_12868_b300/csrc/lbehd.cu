@@ -1522,9 +1522,6 @@ int set_option_impl(lbehd_handle *h, int option, long long value)
     } else if (option == LBEHD_OPT_WARM_START) {
         if (value < 0 || value > 1)
             return fail(h, LBEHD_ERR_INVALID_ARG, "LBEHD_OPT_WARM_START takes 0 or 1");
-        if (value == 1 && h->batch_owned)
-            return fail(h, LBEHD_ERR_INVALID_ARG,
-                        "LBEHD_OPT_WARM_START 1: the batched solve starts from step s - 2's increment");
         CK(h, cudaStreamSynchronize(h->stream));
         h->warm_mode = (int)value;
     } else if (option == LBEHD_OPT_MG_SMOOTHER) {
@@ -2544,6 +2541,9 @@ void fill_cg(lbehd_batch *b, CgBatch &C, int parity, XF xsel, AF accsel)
         c.x = xsel(h);
         c.acc = accsel(h);
         c.partials = h->cg_partials;
+        c.d1 = c.x == h->inc[parity] ? h->inc[parity ^ 1] : nullptr;
+        c.mr_part = h->mr_part;
+        c.mr_alpha = h->mr_alpha;
     }
 }
 
@@ -2563,7 +2563,7 @@ int part1d(const lbehd_handle *h) { return (int)h->nblocks1d; }
 // it, else the 1D grid stride).
 void batch_scalar(lbehd_batch *b, ScalarBatch &S, int mode, int nv, int op, int part,
                   int loop_mode, cudaGraphConditionalHandle cond, bool set_ref,
-                  cudaGraphConditionalHandle cond_ref)
+                  cudaGraphConditionalHandle cond_ref, bool mr = false)
 {
     std::memset(&S, 0, sizeof(S));
     const std::vector<int> ids = all_ids(b);
@@ -2574,6 +2574,7 @@ void batch_scalar(lbehd_batch *b, ScalarBatch &S, int mode, int nv, int op, int 
         S.nblocks[k] = part == 1 ? part3d(h)
                        : part == 2 && bj_use(h) ? h->mg[0].nbj
                                                 : part1d(h);
+        S.mr[k] = mr && mr_use(h) ? h->mr_alpha : nullptr;
     }
     S.nv = nv;
     S.op = op;
@@ -2596,9 +2597,26 @@ void batch_pcg_start(lbehd_batch *b, CgBatch &C, ScalarBatch &S, int mode, int o
                      cudaGraphConditionalHandle cond_ref)
 {
     const std::vector<int> ids = all_ids(b);
-    const int blocks = fill_grid_set(b, C.g, ids, mode, [&b](int k) { return part3d(b->inst[k]); });
-    blaunch(b, k_pcg_init_batch<D>, C, blocks, BX, 0, LBEHD_KC_CG);
-    batch_scalar(b, S, mode, 2, op, 1, loop_mode, cond, set_ref, cond_ref);
+    // a step's first pass: the least-residual start on the instances that use it (the
+    // multi-launch form's order: start pass, coefficients, x0 and r, then the test)
+    std::vector<int> plain_ids, mr_ids;
+    for (int k : ids)
+        (op == 0 && mr_use(b->inst[k]) ? mr_ids : plain_ids).push_back(k);
+    const int blocks = fill_grid_set(b, C.g, plain_ids, mode,
+                                     [&b](int k) { return part3d(b->inst[k]); });
+    if (blocks > 0)
+        blaunch(b, k_pcg_init_batch<D>, C, blocks, BX, 0, LBEHD_KC_CG);
+    if (!mr_ids.empty()) {
+        const int b3 = fill_grid_set(b, C.g, mr_ids, mode,
+                                     [&b](int k) { return part3d(b->inst[k]); });
+        blaunch(b, k_pcg_init_mr_batch<D>, C, b3, BX, 0, LBEHD_KC_CG);
+        const int ba = fill_grid_set(b, C.g, mr_ids, mode, [](int) { return 1; });
+        blaunch(b, k_mr_alpha_batch, C, ba, SCALAR_THREADS, 0, LBEHD_KC_CG);
+        const int b1 = fill_grid_set(b, C.g, mr_ids, mode,
+                                     [&b](int k) { return part1d(b->inst[k]); });
+        blaunch(b, k_pcg_start_mr_batch, C, b1, BX, 0, LBEHD_KC_CG);
+    }
+    batch_scalar(b, S, mode, 2, op, 1, loop_mode, cond, set_ref, cond_ref, op == 0);
 }
 
 // One preconditioned CG iteration of every instance active in `mode`.
@@ -3563,7 +3581,10 @@ int lbehd_batch_init(const lbehd_config *cfgs, int n, lbehd_batch **out)
         // iterations than the block-local smoother (0.86 against 1.04 per instance-step) and
         // run faster as full-occupancy launches over all instances (2786 against 2465 MLUPS)
         h->mg_smoother = 0;
-        // the batched solve starts from the increment of step s - 2 (LBEHD_OPT_WARM_START 0)
+        // and the start from the increment of step s - 2: on the 64-instance sweep the
+        // least-residual start lowers the CG iterations per instance-step from 0.31 to 0.25,
+        // but every pass of the batched loop still runs while any instance iterates, and the
+        // start's two extra passes over all instances cost more (3186 against 3594 MLUPS)
         h->warm_mode = 0;
         b->inst.push_back(h);
     }

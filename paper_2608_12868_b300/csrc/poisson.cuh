@@ -1041,28 +1041,19 @@ __global__ void __launch_bounds__(SCALAR_THREADS) k_mr_alpha(const float *__rest
     mr_alpha_block(part, nblk, out);
 }
 
-// First pass: r0 = b - A phi (k_pcg_init's start residual with a zero increment, and its FP64
-// block partials of ||r0||^2 and ||b||^2) into r, q1 = A d1 and q2 = A d2, and FP32 block sums
-// of the five products into mr_part[k * nblk + block].
+// First pass, one block `blk` of nblk BX-site blocks: r0 = b - A phi (k_pcg_init's start
+// residual with a zero increment, and its FP64 block partials of ||r0||^2 and ||b||^2) into r,
+// q1 = A d1 and q2 = A d2, and FP32 block sums of the five products into
+// mr_part[k * nblk + blk]. The shared scratch is free again on return.
 template <int D>
-__global__ void __launch_bounds__(BX) k_pcg_init_mr(MgDims d, const float *__restrict__ pot,
-                                                    const float *__restrict__ pot_lo,
-                                                    const float *__restrict__ d1,
-                                                    const float *__restrict__ d2,
-                                                    const float *__restrict__ eps,
-                                                    const float *__restrict__ rho,
-                                                    const uint8_t *__restrict__ info,
-                                                    const float *__restrict__ Dg,
-                                                    float *__restrict__ r, float *__restrict__ q1,
-                                                    float *__restrict__ q2,
-                                                    double *__restrict__ partials,
-                                                    float *__restrict__ mr_part,
-                                                    unsigned *zero = nullptr)
+__device__ __forceinline__ void mr_init_block(const MgDims &d, const float *pot,
+                                              const float *pot_lo, const float *d1,
+                                              const float *d2, const float *eps,
+                                              const float *rho, const uint8_t *info,
+                                              const float *Dg, float *r, float *q1, float *q2,
+                                              double *partials, float *mr_part, int blk, int nblk)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int nblk = (int)gridDim.x;
-    if (zero && i == 0)   // the grid-barrier counter of the persistent solve that follows
-        *zero = 0u;
+    const int i = blk * BX + threadIdx.x;
     float v[2] = {0.f, 0.f}, m[MR_NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (i < d.nx * d.ny * d.nz) {
         int x, y, z;
@@ -1081,7 +1072,7 @@ __global__ void __launch_bounds__(BX) k_pcg_init_mr(MgDims d, const float *__res
         m[3] = __fmul_rn(a, b);
         m[4] = __fmul_rn(b, b);
     }
-    block_partials<2>(v, partials, blockIdx.x, nblk);
+    block_partials<2>(v, partials, (size_t)blk, (size_t)nblk);
     __shared__ float sm[MR_NV][BX / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -1096,8 +1087,30 @@ __global__ void __launch_bounds__(BX) k_pcg_init_mr(MgDims d, const float *__res
 #pragma unroll
         for (int w = 0; w < BX / 32; w++)
             acc = __fadd_rn(acc, sm[threadIdx.x][w]);
-        mr_part[threadIdx.x * nblk + blockIdx.x] = acc;
+        mr_part[threadIdx.x * nblk + blk] = acc;
     }
+    __syncthreads();
+}
+
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init_mr(MgDims d, const float *__restrict__ pot,
+                                                    const float *__restrict__ pot_lo,
+                                                    const float *__restrict__ d1,
+                                                    const float *__restrict__ d2,
+                                                    const float *__restrict__ eps,
+                                                    const float *__restrict__ rho,
+                                                    const uint8_t *__restrict__ info,
+                                                    const float *__restrict__ Dg,
+                                                    float *__restrict__ r, float *__restrict__ q1,
+                                                    float *__restrict__ q2,
+                                                    double *__restrict__ partials,
+                                                    float *__restrict__ mr_part,
+                                                    unsigned *zero = nullptr)
+{
+    if (zero && blockIdx.x == 0 && threadIdx.x == 0)   // the persistent solve's barrier counter
+        *zero = 0u;
+    mr_init_block<D>(d, pot, pot_lo, d1, d2, eps, rho, info, Dg, r, q1, q2, partials, mr_part,
+                     (int)blockIdx.x, (int)gridDim.x);
 }
 
 // At one site: x0 = a1 d1 + a2 d2 written over d2 (x holds d2 on entry); returns x0.

@@ -335,6 +335,11 @@ struct CgInst {
     float *r, *p, *q, *z;      // z: the level-0 V-cycle output
     float *x, *acc;            // the increment solved for; where apply accumulates it (or null)
     double *partials;
+    // the least-residual start (LBEHD_OPT_WARM_START 1): the last step's increment (x holds
+    // the one before), the start pass's block sums and the coefficients (a1, a2, a . c)
+    const float *d1;
+    float *mr_part;
+    double *mr_alpha;
 };
 
 struct CgBatch {
@@ -356,6 +361,39 @@ __global__ void __launch_bounds__(BX) k_pcg_init_batch(const __grid_constant__ C
                              v);
         }
         block_partials_loop<2>(v, c.partials, b, c.nbs);
+    });
+}
+
+// The least-residual start of every instance in the set: the first pass (mr_init_block over
+// the instance's BX-site blocks, r0 into r, A d1 into q, A d2 into p), the coefficients (one
+// SCALAR_THREADS block per instance, k_mr_alpha's order), then x0 and r (k_pcg_start_mr's
+// per-site arithmetic).
+template <int D>
+__global__ void __launch_bounds__(BX) k_pcg_init_mr_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        mr_init_block<D>(c.d, c.pot, c.pot_lo, c.d1, c.x, c.eps, c.rho, c.info, c.Dg, c.r, c.q,
+                         c.p, c.partials, c.mr_part, b, c.nbs);
+    });
+}
+
+__global__ void __launch_bounds__(SCALAR_THREADS) k_mr_alpha_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int) {
+        const CgInst &c = A.c[k];
+        mr_alpha_block(c.mr_part, c.nbs, c.mr_alpha);
+    });
+}
+
+__global__ void __launch_bounds__(BX) k_pcg_start_mr_batch(const __grid_constant__ CgBatch A)
+{
+    for_work(A.g, [&](int k, int b) {
+        const CgInst &c = A.c[k];
+        const float a1 = (float)c.mr_alpha[0], a2 = (float)c.mr_alpha[1];
+        const int n = cells(c.d);
+        for (int i = b * BX + threadIdx.x; i < n; i += c.nb1d * BX)
+            mr_start_site(i, a1, a2, c.d1, c.x, c.r, c.q, c.p);
     });
 }
 
@@ -427,6 +465,8 @@ struct ScalarBatch {
     ActiveLists *act;                         // rewritten after ops 0, 3, 4, 5
     unsigned *icnt;                           // [BATCH_MAX] arrivals per instance (split form)
     double *wsum;                             // [BATCH_MAX][2][32] virtual-warp sums
+    const double *mr[BATCH_MAX];              // op 0: the instance's least-residual start
+                                              // coefficients (a1, a2, a . c), or null
 };
 
 // The last block's work after every instance's update: rewrite the active lists, set the
@@ -510,7 +550,7 @@ __global__ void __launch_bounds__(32) k_pcg_scalar_batch_split(const __grid_cons
             tot[v] = a;
         }
         if (lane == 0)
-            pcg_scalar_update(tot, A.op, s);
+            pcg_scalar_update(tot, A.op, s, A.op == 0 && A.mr[k] ? A.mr[k][2] : 0.0);
     }
     if (lane == 0)
         A.icnt[k] = 0u;

@@ -44,12 +44,12 @@ def uneven_3d():
     ]
 
 
-def plain(gpu, w, smoother=0):
-    """A single handle in graph mode with the given multigrid smoother (0: a batch's
-    default) and a batch's warm start (the increment of step s - 2)."""
+def plain(gpu, w, smoother=0, warm=0):
+    """A single handle in graph mode with the given multigrid smoother and warm start (0 for
+    both: a batch's defaults)."""
     sim = gpu.Simulation(w, poisson_mode=gpu.POISSON_GRAPH)
     sim.set_option(gpu.OPT_MG_SMOOTHER, smoother)
-    sim.set_option(gpu.OPT_WARM_START, 0)
+    sim.set_option(gpu.OPT_WARM_START, warm)
     return sim
 
 
@@ -88,6 +88,23 @@ def test_batch_bitwise_equals_single_instances(gpu, variant):
             scale = np.abs(o[k]).max()
             assert np.abs(obs[i][k] - o[k]).max() <= rtol * scale, (i, k, obs[i][k], o[k])
         assert obs[i]["status"] == 0 and obs[i]["step"] == o["step"]
+        sim.close()
+    batch.close()
+
+
+def test_batch_least_residual_start_bitwise_equals_single_instances(gpu):
+    """The same comparison with every solve started from the least-residual combination of
+    the last two increments (LBEHD_OPT_WARM_START = 1, a handle's default) on both sides."""
+    ws = uneven_3d()
+    batch = gpu.Batch(ws)
+    batch.set_option(gpu.OPT_WARM_START, 1)
+    steps = 20
+    batch.step(steps)
+    for i, w in enumerate(ws):
+        sim = plain(gpu, w, warm=1)
+        sim.step(steps)
+        assert_same_state(batch[i], sim, f"instance {i}")
+        assert batch.observe()[i]["status"] == 0
         sim.close()
     batch.close()
 

@@ -1,10 +1,11 @@
 """The start of each step's Gauss-law solve (Eq. 13), LBEHD_OPT_WARM_START: 1 (a handle's
 default) starts from the combination of the last two increments with the least residual
-(k_pcg_init_mr), 0 from the increment of step s - 2 alone (a batch's start).
+(k_pcg_init_mr), 0 (a batch's default) from the increment of step s - 2 alone.
 
 Both stop at the same tolerance, so they step the same physics within it; the minimal-residual
 start converges without a CG iteration on more steps. The persistent and the multi-launch
-solves give the same bits with either start (tests/test_gpu_poisson_persistent.py).
+solves give the same bits with either start (tests/test_gpu_poisson_persistent.py), and so
+does a batch instance against a single handle (tests/test_gpu_batch.py).
 """
 import numpy as np
 import pytest
@@ -35,9 +36,10 @@ def test_option_values(gpu):
         sim.set_option(gpu.OPT_WARM_START, 2)
     sim.close()
     batch = gpu.Batch([W.small_3d(), W.small_3d(seed=9)])
-    batch.set_option(gpu.OPT_WARM_START, 0)   # a batch's start
+    batch.set_option(gpu.OPT_WARM_START, 0)
+    batch.set_option(gpu.OPT_WARM_START, 1)
     with pytest.raises(gpu.LBEHDError):
-        batch.set_option(gpu.OPT_WARM_START, 1)
+        batch.set_option(gpu.OPT_WARM_START, 2)
     batch.close()
 
 
