@@ -975,23 +975,26 @@ constexpr int MR_NV = 5;   // q1.r0, q2.r0, q1.q1, q1.q2, q2.q2
 // Threads of the one-block scalar reductions (the CG scalars, the start's coefficients).
 constexpr int SCALAR_THREADS = 1024;
 
-// out = (a1, a2, a . c) from the totals (c1, c2, G11, G12, G22).
+// out = (a1, a2, a . c) from the totals (c1, c2, G11, G12, G22). Written with the rounding
+// intrinsics, so that every kernel that inlines it (the persistent solve, k_mr_alpha,
+// k_mr_alpha_batch) gets the same bits.
 __device__ __forceinline__ void mr_solve(const float (&m)[MR_NV], double *out)
 {
     const double c1 = m[0], c2 = m[1], g11 = m[2], g12 = m[3], g22 = m[4];
-    const double det = g11 * g22 - g12 * g12;
+    const double gg = __dmul_rn(g11, g22);
+    const double det = __dsub_rn(gg, __dmul_rn(g12, g12));
     double a1 = 0.0, a2 = 0.0;
-    if (g11 > 0.0 && g22 > 0.0 && det > 1e-6 * g11 * g22) {
-        a1 = (c1 * g22 - c2 * g12) / det;
-        a2 = (c2 * g11 - c1 * g12) / det;
+    if (g11 > 0.0 && g22 > 0.0 && det > __dmul_rn(1e-6, gg)) {
+        a1 = __ddiv_rn(__dsub_rn(__dmul_rn(c1, g22), __dmul_rn(c2, g12)), det);
+        a2 = __ddiv_rn(__dsub_rn(__dmul_rn(c2, g11), __dmul_rn(c1, g12)), det);
     } else if (g22 > 0.0) {
-        a2 = c2 / g22;
+        a2 = __ddiv_rn(c2, g22);
     } else if (g11 > 0.0) {
-        a1 = c1 / g11;
+        a1 = __ddiv_rn(c1, g11);
     }
     out[0] = a1;
     out[1] = a2;
-    out[2] = a1 * c1 + a2 * c2;
+    out[2] = __dadd_rn(__dmul_rn(a1, c1), __dmul_rn(a2, c2));
 }
 
 // The coefficients from the first pass's block sums mr_part[k * nblk + b], by one block of
